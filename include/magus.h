@@ -1,0 +1,260 @@
+/*
+ * magus.h - C ABI of libmagus: batched replay of the MAGUS uncore-frequency control step
+ * (arXiv 2502.03796) on one B300 GPU.
+ *
+ * One "round" per monitored interval (dt seconds) of one trace under one policy:
+ *   1. monitor (Sec. 3): counter delta (in bytes_per_count units) -> memory throughput
+ *      x = bytes_per_count * delta / (dt * 1e9) GB/s;
+ *   2. Phase 1 (Sec. 3.1, Algorithm 1): x joins a FIFO of W+1 throughputs; once full,
+ *      derivative = (newest - oldest) / W; > inc -> +1, < dec -> -1, else 0 (a temporary
+ *      decision); 0 while the FIFO fills;
+ *   3. Phase 2 (Sec. 3.2, Algorithm 2): a flag (prediction != 0) joins a zero-filled
+ *      FIFO of L flags; high-frequency state iff sum / L >= high_freq_threshold;
+ *   4. decision (Sec. 3.2, Sec. 6.1): high-frequency -> top of the ladder; else +1 ->
+ *      top, -1 -> bottom (decreases go directly to the lower bound), 0 -> hold.  The
+ *      level chosen after interval t governs interval t+1; the first interval runs at the
+ *      bottom of the ladder (Sec. 4: idle nodes sit at the minimum uncore frequency);
+ *   5. energy model (not from the paper): interval t at level f lasts
+ *      dt * max(1, x_t / C(f)) with C(f) = bw_ref * f / f_ref and draws
+ *      P(f) = p_static + p_dyn * (f / f_ref)^2; E = sum P * duration, T = sum duration,
+ *      EDP = E * T (Sec. 5.4 names the energy-delay product as a metric).
+ *
+ * Conventions
+ *   - Every function returns int status: MAGUS_OK (0) or a negative MAGUS_E* code, and
+ *     never throws.  magus_last_error() gives a message for the calling thread.
+ *   - The caller owns every input and output buffer; the library owns handles and their
+ *     device workspace (allocated lazily, within the handle's memory budget).
+ *   - "device" pointers are CUDA device memory of the handle's device; "host" pointers
+ *     are ordinary (pageable or pinned) host memory.
+ *   - Per-pair outputs are pair-major: pair p = trace * n_configs + config.
+ *   - magus_replay_run / _plain / _detail are asynchronous on the given stream
+ *     (a cudaStream_t passed as void*, NULL = legacy default stream).  Device-side input
+ *     errors detected by a kernel are reported by the next magus_replay_status().
+ *
+ * Packed trace layout (device or host): traces are stored back to back; trace i starts at
+ * element offset off_i with off_0 = 0 and off_{i+1} = off_i + round_up(n_i, 4), so every
+ * trace starts on a 16-byte boundary; the buffer holds magus_packed_size() elements
+ * (padding elements are read but ignored).  Deltas are uint32 counts of bytes_per_count
+ * bytes per interval.
+ */
+#ifndef MAGUS_H
+#define MAGUS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MAGUS_OK 0
+#define MAGUS_EINVAL (-1)    /* invalid argument */
+#define MAGUS_ENOMEM (-2)    /* allocation failed or memory budget exceeded */
+#define MAGUS_EBUSY (-3)     /* serving: admission refused (no slot / memory) */
+#define MAGUS_EAGAIN (-4)    /* serving: result not ready yet */
+#define MAGUS_ETIMEDOUT (-5) /* a bounded device-side wait gave up */
+#define MAGUS_ECUDA (-6)     /* CUDA runtime error */
+#define MAGUS_ENOTFOUND (-7) /* serving: unknown request id */
+
+#define MAGUS_MAX_WINDOW 64  /* upper bound of direv_length (W) and tune_window (L) */
+#define MAGUS_MAX_LEVELS 32  /* upper bound of the ladder length */
+
+/* Policy parameters (Algorithm 1 and Algorithm 2 arguments). */
+typedef struct {
+    double inc_threshold;       /* Alg. 1 inc_threshold, GB/s per interval */
+    double dec_threshold;       /* Alg. 1 dec_threshold, GB/s per interval */
+    int32_t direv_length;       /* Alg. 1 direv_length W, 1..64 */
+    int32_t tune_window;        /* Alg. 2 len(uncore_tune_ls) L, 1..64 */
+    double high_freq_threshold; /* Alg. 2 high_freq_threshold (paper: 0.6) */
+    int32_t step_mode;          /* 0: jump to the ladder bounds (Sec. 6.1); 1: one rung per
+                                   decision (only magus_replay_plain / _detail) */
+    int32_t reserved;           /* must be 0 */
+} magus_policy_t;
+
+/* Ladder and energy model. */
+typedef struct {
+    double dt_s;                /* monitoring interval, s (1e-9 .. 1e6) */
+    int32_t n_levels;           /* K, 2..32 */
+    int32_t bytes_per_count;    /* bytes per counter unit (64-byte lines), 1..2^20 */
+    const double *f_ghz;        /* host, K strictly ascending frequencies */
+    double p_static_w, p_dyn_w; /* P(f) = p_static + p_dyn (f / f_ref)^2 */
+    double f_ref_ghz;           /* reference frequency (top of the ladder) */
+    double bw_ref_gbs;          /* capacity at f_ref, GB/s */
+} magus_model_t;
+
+/* Carried per-pair state for split replay: feeding a trace in pieces with the same state
+ * reproduces the whole-trace logs exactly and energies additively.  All pairs of one trace
+ * in a call must carry states of the same earlier pieces (the delta history is read from
+ * the state of the trace's first policy). */
+typedef struct {
+    uint64_t n_seen;            /* intervals consumed so far (0 for a fresh trace) */
+    uint64_t flags;             /* bit q = flag of interval n_seen - 64 + q (bit 63 newest) */
+    uint32_t level;             /* ladder index governing the next interval (0 or K-1 in
+                                   jump mode) */
+    uint32_t reserved;
+    uint32_t hist[MAGUS_MAX_WINDOW]; /* deltas of intervals n_seen-64 .. n_seen-1 */
+} magus_state_t;
+
+/* Frequency-change log.  Entry = ((t + 1) << 5) | level: from interval t+1 on (global
+ * interval index, counting n_seen) the uncore runs at ladder index `level`.  Entries of a
+ * pair are in time order at entries[pair * capacity ...]; entries beyond capacity are
+ * counted and hashed but not stored.  change_hash = sum over entries of
+ * SplitMix64-mix(((t + 1) << 8) | level) mod 2^64 (order-free, additive over splits). */
+typedef struct {
+    uint32_t *entries;          /* device [pairs * capacity] or NULL */
+    uint64_t capacity;          /* entries per pair (ignored when entries == NULL) */
+    uint64_t *n_changes;        /* device [pairs] or NULL */
+    uint64_t *change_hash;      /* device [pairs] or NULL */
+    uint64_t *n_hf;             /* device [pairs] or NULL: rounds in the high-frequency state */
+} magus_freq_log_t;
+
+typedef struct magus_replay magus_replay_t;
+
+/* ---------------------------------------------------------------------------------------
+ * Replay handles
+ * ------------------------------------------------------------------------------------- */
+
+/* Create a replay handle on CUDA device `device`.  mem_budget bounds the handle's own
+ * device workspace in bytes (0 = 1 GiB).  The model is copied.  Errors: EINVAL (bad model:
+ * K out of range, ladder not strictly ascending, non-positive dt / capacities), ECUDA. */
+int magus_replay_open(magus_replay_t **h, const magus_model_t *model, int device, size_t mem_budget);
+
+/* Replay n_traces x n_configs (trace, policy) pairs (rounds above) with the time-parallel
+ * batched kernel; every policy must have step_mode 0.
+ *   traces     device, packed layout; base address 16-byte aligned
+ *   lengths    host [n_traces] intervals per trace (0 allowed)
+ *   configs    host [n_configs], 1 <= n_configs <= 4096
+ *   log        optional (NULL): change log / counts / hash / hf counts (device arrays)
+ *   out_energy device [pairs] J, out_edp device [pairs] J*s (both required);
+ *   out_time   device [pairs] s or NULL
+ *   io_state   device [pairs] or NULL: read at the start and written at the end of each pair
+ * Asynchronous on `stream`.  Errors: EINVAL (argument checks), ENOMEM (budget), ECUDA. */
+int magus_replay_run(magus_replay_t *h, const uint32_t *traces, const uint64_t *lengths,
+                     int32_t n_traces, const magus_policy_t *configs, int32_t n_configs,
+                     const magus_freq_log_t *log, double *out_energy, double *out_edp,
+                     double *out_time, magus_state_t *io_state, void *stream);
+
+/* Same computation through host memory: traces (packed layout), outputs and log arrays are
+ * HOST pointers.  The library streams the traces to the device in batches, overlapping the
+ * copies with the replay, and returns when every output is back on the host. */
+int magus_replay_run_host(magus_replay_t *h, const uint32_t *traces, const uint64_t *lengths,
+                          int32_t n_traces, const magus_policy_t *configs, int32_t n_configs,
+                          const magus_freq_log_t *log, double *out_energy, double *out_edp,
+                          double *out_time);
+
+/* The plain form: one kernel launch per trace, one thread per policy, literal FP64
+ * arithmetic in the order of the rounds above, global-memory loads.  Same arguments and
+ * outputs as magus_replay_run (no io_state); supports step_mode 1. */
+int magus_replay_plain(magus_replay_t *h, const uint32_t *traces, const uint64_t *lengths,
+                       int32_t n_traces, const magus_policy_t *configs, int32_t n_configs,
+                       const magus_freq_log_t *log, double *out_energy, double *out_edp,
+                       double *out_time, void *stream);
+
+/* One trace, one policy, per-interval detail (plain kernel): out_level[t] = ladder index
+ * governing interval t, out_derivative[t] = Algorithm 1 derivative of round t (NaN while
+ * the FIFO fills).  trace, out_level (uint8 [n]), out_derivative (double [n]) and the
+ * log / totals are device pointers; out_level / out_derivative may be NULL. */
+int magus_replay_detail(magus_replay_t *h, const uint32_t *trace, uint64_t n,
+                        const magus_policy_t *config, uint8_t *out_level, double *out_derivative,
+                        const magus_freq_log_t *log, double *out_energy, double *out_edp,
+                        double *out_time, void *stream);
+
+/* Wait for `stream` and report device-side input errors seen since the last call (EINVAL
+ * for a carried level that is neither 0 nor K-1 in jump mode; ETIMEDOUT for a bounded
+ * device wait that gave up), then clear them. */
+int magus_replay_status(magus_replay_t *h, void *stream);
+
+/* Device time of the most recent batched-kernel launch of this handle (CUDA events recorded
+ * on the launching stream right before and after the kernel); waits for that launch. */
+int magus_replay_kernel_ms(magus_replay_t *h, float *ms);
+
+/* Tile shape of the batched kernel: warps per policy that split a trace chunk in time
+ * (time_groups) x policies per CTA (policy_slots); time_groups * policy_slots = 8.
+ * (0, 0) restores the automatic choice.  EINVAL for unsupported shapes. */
+int magus_replay_set_tile(magus_replay_t *h, int32_t time_groups, int32_t policy_slots);
+
+/* Autotuner: time every supported tile shape on the given (device, packed) workload and
+ * keep the fastest for later calls with the same policy count.  out_best (host, 2 ints,
+ * optional) receives {time_groups, policy_slots}; out_ms (host, optional) the best time.
+ * Outputs go to the handle's workspace only.  Synchronous. */
+int magus_replay_autotune(magus_replay_t *h, const uint32_t *traces, const uint64_t *lengths,
+                          int32_t n_traces, const magus_policy_t *configs, int32_t n_configs,
+                          int32_t *out_best, float *out_ms, void *stream);
+
+int magus_replay_close(magus_replay_t *h);
+
+/* ---------------------------------------------------------------------------------------
+ * Helpers (host only, no device needed)
+ * ------------------------------------------------------------------------------------- */
+
+/* Packed layout: offsets[i] (host, may be NULL) and the total element count. */
+int magus_packed_size(const uint64_t *lengths, int32_t n_traces, uint64_t *offsets, uint64_t *total);
+
+/* Integer decision bounds the batched kernel derives for one policy (diagnostics and
+ * tests).  out[0] = m_up, out[1] = m_dn, out[2] = k_min, out[3] = band half-width b:
+ * with m = delta_t - delta_{t-W}, Algorithm 1 returns +1 for m > m_up + b and never for
+ * m <= m_up - b (likewise -1 for m < m_dn - b and never for m >= m_dn + b); rounds inside
+ * a band are decided by exact FP64.  k_min = smallest flag count c with
+ * c / L >= high_freq_threshold (L + 1 if none). */
+int magus_policy_bounds(const magus_policy_t *policy, const magus_model_t *model, int64_t out[4]);
+
+const char *magus_last_error(void);
+const char *magus_version(void);
+
+/* ---------------------------------------------------------------------------------------
+ * Serving: an online controller over many node streams with device-resident state.
+ * Requests carry new deltas of one stream; requests that arrive while others run are
+ * batched into the next launch (continuous batching); each stream's state stays on the
+ * device between requests.
+ * ------------------------------------------------------------------------------------- */
+
+typedef struct magus_serve magus_serve_t;
+
+typedef struct {
+    uint64_t n_seen;            /* stream intervals consumed after this request */
+    uint32_t level;             /* level governing the stream's next interval */
+    uint32_t n_changes;         /* change-log entries produced by this request */
+    uint64_t change_hash;       /* hash of those entries (same definition as the replay log) */
+    uint32_t n_hf;              /* high-frequency rounds in this request */
+    uint32_t reserved;
+    double energy_j, time_s;    /* energy and duration charged for this request's intervals */
+    double latency_s;           /* submit -> result available on the host */
+} magus_result_t;
+
+typedef struct {
+    uint64_t submitted, completed, rejected, launches;
+    uint64_t samples;           /* intervals processed */
+    double p50_s, p99_s, p999_s, max_s; /* latency of completed requests */
+} magus_serve_stats_t;
+
+/* Open a serving runtime: n_streams device-resident stream states (all fresh), one policy
+ * (step_mode 0).  mem_budget bounds the bytes of request payload admitted but not yet
+ * completed (0 = 8 GiB); max_batch_requests / max_batch_samples cap one launch (0 =
+ * defaults).  A background thread forms batches, launches them and completes requests. */
+int magus_serve_open(magus_serve_t **s, const magus_model_t *model, const magus_policy_t *policy,
+                     int32_t n_streams, size_t mem_budget, int device,
+                     int32_t max_batch_requests, int64_t max_batch_samples);
+
+/* Submit n (1..65536) new deltas (host memory, copied) of stream_id.  Requests of one stream
+ * are applied in submission order.  EBUSY when the memory budget is exhausted. */
+int magus_serve_submit(magus_serve_t *s, uint32_t stream_id, const uint32_t *deltas, uint32_t n,
+                       uint64_t *req_id);
+
+/* Result of a request: EAGAIN until it is done, ENOTFOUND for unknown / already-polled ids.
+ * A successful poll releases the request. */
+int magus_serve_poll(magus_serve_t *s, uint64_t req_id, magus_result_t *out);
+
+/* Block until every submitted request is complete. */
+int magus_serve_drain(magus_serve_t *s);
+
+int magus_serve_stats(magus_serve_t *s, magus_serve_stats_t *out);
+
+/* Export all stream states (host, n_streams entries) for checkpointing. */
+int magus_serve_export(magus_serve_t *s, magus_state_t *out_states);
+
+int magus_serve_close(magus_serve_t *s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MAGUS_H */

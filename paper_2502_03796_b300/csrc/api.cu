@@ -1,0 +1,696 @@
+// api.cu - C ABI of libmagus: replay handles, argument checks, planning, workspace.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <new>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "magus_internal.h"
+
+using namespace magus;
+
+struct magus_replay {
+    int device = 0;
+    int sms = 0;
+    std::vector<double> f;
+    magus_model_t model{};
+    DevModel dm{};
+    size_t budget = 0;
+    // device memory owned by the handle
+    int *status = nullptr;            // device status word
+    unsigned int *queue = nullptr;    // work counter
+    void *ws = nullptr;               // plan workspace (policies, items, offsets, lengths)
+    size_t ws_size = 0;
+    cudaEvent_t ws_ev = nullptr;      // last use of the workspace
+    bool ws_ev_pending = false;
+    // pinned staging ring for plan uploads
+    void *pin[2] = {nullptr, nullptr};
+    size_t pin_size[2] = {0, 0};
+    cudaEvent_t pin_ev[2] = {nullptr, nullptr};
+    bool pin_pending[2] = {false, false};
+    int pin_next = 0;
+    // scratch for autotuning and host-memory runs
+    void *scratch = nullptr;
+    size_t scratch_size = 0;
+    // host-memory runs: copy / compute streams, per-slot events
+    cudaStream_t hs_copy = nullptr, hs_comp = nullptr;
+    cudaEvent_t hs_ready[2] = {nullptr, nullptr}, hs_done[2] = {nullptr, nullptr};
+    cudaEvent_t k_ev[2] = {nullptr, nullptr};  // around the last batched-kernel launch
+    bool k_timed = false;
+    int tile_tg = 0, tile_cw = 0;     // 0: automatic
+    std::map<int, std::pair<int, int>> tuned;
+};
+
+namespace {
+
+const char *kVersion = "magus-b300 0.1 (sm_103a)";
+
+int cuda_fail(cudaError_t e, const char *what) {
+    set_error(std::string(what) + ": " + cudaGetErrorString(e));
+    return MAGUS_ECUDA;
+}
+
+#define CK(call, what)                                  \
+    do {                                                \
+        cudaError_t e_ = (call);                        \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+    } while (0)
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// Device-memory growth inside the handle budget.  Waits for the previous user first.
+int ensure_ws(magus_replay *h, void **buf, size_t *size, size_t need) {
+    if (need <= *size) return MAGUS_OK;
+    size_t want = std::max(need, *size * 2);
+    size_t other = (buf == &h->ws ? h->scratch_size : h->ws_size);
+    if (want + other > h->budget) want = need;
+    if (want + other > h->budget) {
+        set_error("device workspace of " + std::to_string(need) + " bytes exceeds the handle's memory budget");
+        return MAGUS_ENOMEM;
+    }
+    if (h->ws_ev_pending) CK(cudaEventSynchronize(h->ws_ev), "cudaEventSynchronize");
+    if (*buf) CK(cudaFree(*buf), "cudaFree");
+    *buf = nullptr;
+    *size = 0;
+    cudaError_t e = cudaMalloc(buf, want);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        set_error("cudaMalloc of the workspace failed");
+        return MAGUS_ENOMEM;
+    }
+    *size = want;
+    return MAGUS_OK;
+}
+
+int ensure_pin(magus_replay *h, int slot, size_t need) {
+    if (h->pin_pending[slot]) {
+        CK(cudaEventSynchronize(h->pin_ev[slot]), "cudaEventSynchronize");
+        h->pin_pending[slot] = false;
+    }
+    if (need <= h->pin_size[slot]) return MAGUS_OK;
+    if (h->pin[slot]) CK(cudaFreeHost(h->pin[slot]), "cudaFreeHost");
+    h->pin[slot] = nullptr;
+    h->pin_size[slot] = 0;
+    size_t want = std::max(need, (size_t)1 << 16);
+    cudaError_t e = cudaMallocHost(&h->pin[slot], want);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        set_error("pinned staging allocation failed");
+        return MAGUS_ENOMEM;
+    }
+    h->pin_size[slot] = want;
+    return MAGUS_OK;
+}
+
+int check_policies(magus_replay *h, const magus_policy_t *configs, int32_t n_configs,
+                   std::vector<DevPolicy> *out, bool jump_only) {
+    if (!configs || n_configs < 1 || n_configs > 4096) {
+        set_error("configs must be non-NULL with 1 <= n_configs <= 4096");
+        return MAGUS_EINVAL;
+    }
+    out->resize(n_configs);
+    for (int c = 0; c < n_configs; c++) {
+        std::string err;
+        int rc = derive_policy(configs[c], h->model, &(*out)[c], &err);
+        if (rc) {
+            set_error("policy " + std::to_string(c) + ": " + err);
+            return rc;
+        }
+        if (jump_only && configs[c].step_mode != 0) {
+            set_error("the batched kernel supports step_mode 0 only (use magus_replay_plain)");
+            return MAGUS_EINVAL;
+        }
+    }
+    return MAGUS_OK;
+}
+
+struct Plan {
+    std::vector<DevPolicy> pols;
+    std::vector<WorkItem> items;
+    std::vector<uint64_t> offsets, lengths;
+    int tg = 8, cw = 1;
+};
+
+void choose_tile(magus_replay *h, int n_configs, int *tg, int *cw) {
+    if (h->tile_tg) {
+        *tg = h->tile_tg;
+        *cw = h->tile_cw;
+        return;
+    }
+    auto it = h->tuned.find(n_configs);
+    if (it != h->tuned.end()) {
+        *tg = it->second.first;
+        *cw = it->second.second;
+        return;
+    }
+    int c = 1;
+    while (c * 2 <= std::min(8, n_configs)) c *= 2;
+    *cw = c;
+    *tg = 8 / c;
+}
+
+int build_plan(magus_replay *h, const uint64_t *lengths, int32_t n_traces, const magus_policy_t *configs,
+               int32_t n_configs, int tg, int cw, Plan *pl) {
+    int rc = check_policies(h, configs, n_configs, &pl->pols, true);
+    if (rc) return rc;
+    pl->tg = tg;
+    pl->cw = cw;
+    pl->offsets.resize(n_traces);
+    pl->lengths.assign(lengths, lengths + n_traces);
+    uint64_t off = 0;
+    for (int i = 0; i < n_traces; i++) {
+        pl->offsets[i] = off;
+        off += (lengths[i] + 3) / 4 * 4;
+    }
+    // longest traces first: the persistent CTAs take items in this order
+    std::vector<int> order(n_traces);
+    for (int i = 0; i < n_traces; i++) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return lengths[a] > lengths[b]; });
+    const int blocks = (n_configs + cw - 1) / cw;
+    pl->items.clear();
+    pl->items.reserve((size_t)n_traces * blocks);
+    for (int i : order)
+        for (int b = 0; b < blocks; b++) pl->items.push_back(WorkItem{(uint32_t)i, (uint32_t)(b * cw)});
+    return MAGUS_OK;
+}
+
+struct Outs {
+    double *energy, *edp, *time;
+    uint32_t *log_entries;
+    uint64_t log_cap;
+    uint64_t *n_changes, *change_hash, *n_hf;
+    magus_state_t *state;
+};
+
+// Upload the plan through pinned staging and launch the batched kernel on `stream`.
+int launch_plan(magus_replay *h, const Plan &pl, const uint32_t *traces, const Outs &o, cudaStream_t stream,
+                float *ms_out = nullptr) {
+    const size_t n_items = pl.items.size();
+    const size_t sz_pol = align_up(pl.pols.size() * sizeof(DevPolicy), 256);
+    const size_t sz_items = align_up(std::max<size_t>(n_items, 1) * sizeof(WorkItem), 256);
+    const size_t sz_off = align_up(std::max<size_t>(pl.offsets.size(), 1) * 8, 256);
+    const size_t total = sz_pol + sz_items + 2 * sz_off;
+    int rc = ensure_ws(h, &h->ws, &h->ws_size, total);
+    if (rc) return rc;
+    const int slot = h->pin_next;
+    h->pin_next ^= 1;
+    rc = ensure_pin(h, slot, total);
+    if (rc) return rc;
+    char *pin = (char *)h->pin[slot];
+    memcpy(pin, pl.pols.data(), pl.pols.size() * sizeof(DevPolicy));
+    if (n_items) memcpy(pin + sz_pol, pl.items.data(), n_items * sizeof(WorkItem));
+    if (!pl.offsets.empty()) {
+        memcpy(pin + sz_pol + sz_items, pl.offsets.data(), pl.offsets.size() * 8);
+        memcpy(pin + sz_pol + sz_items + sz_off, pl.lengths.data(), pl.lengths.size() * 8);
+    }
+    if (h->ws_ev_pending) CK(cudaStreamWaitEvent(stream, h->ws_ev, 0), "cudaStreamWaitEvent");
+    char *ws = (char *)h->ws;
+    CK(cudaMemcpyAsync(ws, pin, total, cudaMemcpyHostToDevice, stream), "cudaMemcpyAsync(plan)");
+    CK(cudaEventRecord(h->pin_ev[slot], stream), "cudaEventRecord");
+    h->pin_pending[slot] = true;
+    CK(cudaMemsetAsync(h->queue, 0, sizeof(unsigned int), stream), "cudaMemsetAsync");
+
+    TpParams p;
+    memset(&p, 0, sizeof(p));
+    p.traces = traces;
+    p.pols = (const DevPolicy *)ws;
+    p.n_pols = (int32_t)pl.pols.size();
+    p.items = (const WorkItem *)(ws + sz_pol);
+    p.offsets = (const uint64_t *)(ws + sz_pol + sz_items);
+    p.lengths = (const uint64_t *)(ws + sz_pol + sz_items + sz_off);
+    p.n_items = (int32_t)n_items;
+    p.queue = h->queue;
+    p.status = h->status;
+    p.model = h->dm;
+    p.energy = o.energy;
+    p.edp = o.edp;
+    p.time = o.time;
+    p.log_entries = o.log_entries;
+    p.log_cap = o.log_cap;
+    p.n_changes = o.n_changes;
+    p.change_hash = o.change_hash;
+    p.n_hf = o.n_hf;
+    p.state = o.state;
+    int smem = 0;
+    const int per_sm = tp_max_ctas_per_sm(pl.tg, pl.cw, &smem);
+    if (per_sm <= 0) {
+        set_error("tile shape does not fit on this device");
+        return MAGUS_ECUDA;
+    }
+    const int grid = (int)std::max<size_t>(1, std::min<size_t>(n_items, (size_t)h->sms * per_sm));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (ms_out) {
+        CK(cudaEventCreate(&e0), "cudaEventCreate");
+        CK(cudaEventCreate(&e1), "cudaEventCreate");
+        CK(cudaEventRecord(e0, stream), "cudaEventRecord");
+    }
+    if (n_items) {
+        CK(cudaEventRecord(h->k_ev[0], stream), "cudaEventRecord");
+        CK(launch_replay_tp(pl.tg, pl.cw, p, grid, stream), "replay kernel launch");
+        CK(cudaEventRecord(h->k_ev[1], stream), "cudaEventRecord");
+        h->k_timed = true;
+    }
+    if (ms_out) {
+        CK(cudaEventRecord(e1, stream), "cudaEventRecord");
+        CK(cudaEventSynchronize(e1), "cudaEventSynchronize");
+        CK(cudaEventElapsedTime(ms_out, e0, e1), "cudaEventElapsedTime");
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+    }
+    CK(cudaEventRecord(h->ws_ev, stream), "cudaEventRecord");
+    h->ws_ev_pending = true;
+    return MAGUS_OK;
+}
+
+int check_run_args(magus_replay *h, const uint32_t *traces, const uint64_t *lengths, int32_t n_traces,
+                   const magus_freq_log_t *log, const double *e, const double *edp) {
+    if (!h) { set_error("NULL handle"); return MAGUS_EINVAL; }
+    if (n_traces < 0) { set_error("n_traces must be >= 0"); return MAGUS_EINVAL; }
+    if (n_traces > 0 && (!lengths || !traces)) { set_error("traces and lengths are required"); return MAGUS_EINVAL; }
+    if (((uintptr_t)traces & 15u) != 0) { set_error("traces must be 16-byte aligned"); return MAGUS_EINVAL; }
+    if (!e || !edp) { set_error("out_energy and out_edp are required"); return MAGUS_EINVAL; }
+    if (log && log->entries && log->capacity == 0) { set_error("log capacity must be >= 1"); return MAGUS_EINVAL; }
+    for (int i = 0; i < n_traces; i++) {
+        if (lengths[i] >= (1ull << 40)) { set_error("trace length too large"); return MAGUS_EINVAL; }
+        if (log && log->entries && lengths[i] >= (1ull << 27) - 1) {
+            set_error("change-log entries hold interval indices below 2^27");
+            return MAGUS_EINVAL;
+        }
+    }
+    return MAGUS_OK;
+}
+
+Outs outs_of(const magus_freq_log_t *log, double *e, double *edp, double *t, magus_state_t *st) {
+    Outs o;
+    memset(&o, 0, sizeof(o));
+    o.energy = e;
+    o.edp = edp;
+    o.time = t;
+    o.state = st;
+    if (log) {
+        o.log_entries = log->entries;
+        o.log_cap = log->entries ? log->capacity : 0;
+        o.n_changes = log->n_changes;
+        o.change_hash = log->change_hash;
+        o.n_hf = log->n_hf;
+    }
+    return o;
+}
+
+
+// Plain kernel: one launch per trace (optionally with per-interval logs for one trace).
+int plain_impl(magus_replay *h, const uint32_t *traces, const uint64_t *lengths, int32_t n_traces,
+               const magus_policy_t *configs, int32_t n_configs, const magus_freq_log_t *log, double *out_energy,
+               double *out_edp, double *out_time, uint8_t *level_log, double *deriv_log, cudaStream_t s) {
+    try {
+        CK(cudaSetDevice(h->device), "cudaSetDevice");
+        std::vector<DevPolicy> pols;
+        int rc = check_policies(h, configs, n_configs, &pols, false);
+        if (rc) return rc;
+        const size_t sz = pols.size() * sizeof(DevPolicy);
+        rc = ensure_ws(h, &h->ws, &h->ws_size, sz);
+        if (rc) return rc;
+        const int slot = h->pin_next;
+        h->pin_next ^= 1;
+        rc = ensure_pin(h, slot, sz);
+        if (rc) return rc;
+        memcpy(h->pin[slot], pols.data(), sz);
+        if (h->ws_ev_pending) CK(cudaStreamWaitEvent(s, h->ws_ev, 0), "cudaStreamWaitEvent");
+        CK(cudaMemcpyAsync(h->ws, h->pin[slot], sz, cudaMemcpyHostToDevice, s), "cudaMemcpyAsync");
+        CK(cudaEventRecord(h->pin_ev[slot], s), "cudaEventRecord");
+        h->pin_pending[slot] = true;
+        Outs o = outs_of(log, out_energy, out_edp, out_time, nullptr);
+        uint64_t off = 0;
+        for (int i = 0; i < n_traces; i++) {
+            PlainParams p;
+            memset(&p, 0, sizeof(p));
+            p.trace = traces + off;
+            p.n = lengths[i];
+            p.pols = (const DevPolicy *)h->ws;
+            p.n_pols = n_configs;
+            p.pair_base = (int64_t)i * n_configs;
+            p.model = h->dm;
+            p.energy = o.energy;
+            p.edp = o.edp;
+            p.time = o.time;
+            p.log_entries = o.log_entries;
+            p.log_cap = o.log_cap;
+            p.n_changes = o.n_changes;
+            p.change_hash = o.change_hash;
+            p.n_hf = o.n_hf;
+            p.level_log = level_log;
+            p.deriv_log = deriv_log;
+            CK(launch_replay_plain(p, s), "plain kernel launch");
+            off += (lengths[i] + 3) / 4 * 4;
+        }
+        CK(cudaEventRecord(h->ws_ev, s), "cudaEventRecord");
+        h->ws_ev_pending = true;
+        return MAGUS_OK;
+    } catch (const std::bad_alloc &) {
+        set_error("out of host memory");
+        return MAGUS_ENOMEM;
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *magus_last_error(void) { return last_error_cstr(); }
+const char *magus_version(void) { return kVersion; }
+
+int magus_packed_size(const uint64_t *lengths, int32_t n_traces, uint64_t *offsets, uint64_t *total) {
+    if (n_traces < 0 || (n_traces > 0 && !lengths) || !total) {
+        set_error("invalid arguments");
+        return MAGUS_EINVAL;
+    }
+    uint64_t off = 0;
+    for (int i = 0; i < n_traces; i++) {
+        if (offsets) offsets[i] = off;
+        off += (lengths[i] + 3) / 4 * 4;
+    }
+    *total = off;
+    return MAGUS_OK;
+}
+
+int magus_policy_bounds(const magus_policy_t *policy, const magus_model_t *model, int64_t out[4]) {
+    if (!policy || !model || !out) { set_error("NULL argument"); return MAGUS_EINVAL; }
+    std::string err;
+    DevModel dm;
+    int rc = derive_model(*model, &dm, &err);
+    if (rc) { set_error(err); return rc; }
+    DevPolicy dp;
+    rc = derive_policy(*policy, *model, &dp, &err);
+    if (rc) { set_error(err); return rc; }
+    out[0] = dp.up_mid;
+    out[1] = dp.dn_mid;
+    out[2] = dp.kmin;
+    out[3] = 3;
+    return MAGUS_OK;
+}
+
+int magus_replay_open(magus_replay_t **out, const magus_model_t *model, int device, size_t mem_budget) {
+    if (!out || !model) { set_error("NULL argument"); return MAGUS_EINVAL; }
+    *out = nullptr;
+    std::string err;
+    DevModel dm;
+    int rc = derive_model(*model, &dm, &err);
+    if (rc) { set_error(err); return rc; }
+    magus_replay *h = new (std::nothrow) magus_replay();
+    if (!h) { set_error("out of host memory"); return MAGUS_ENOMEM; }
+    h->f.assign(model->f_ghz, model->f_ghz + model->n_levels);
+    h->model = *model;
+    h->model.f_ghz = h->f.data();
+    h->dm = dm;
+    h->device = device;
+    h->budget = mem_budget ? mem_budget : ((size_t)1 << 30);
+    cudaError_t e = cudaSetDevice(device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, device);
+    if (e == cudaSuccess) e = cudaMalloc(&h->status, 256);
+    if (e == cudaSuccess) h->queue = (unsigned int *)((char *)h->status + 128);
+    if (e == cudaSuccess) e = cudaMemset(h->status, 0, 256);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ws_ev, cudaEventDisableTiming);
+    for (int s = 0; s < 2 && e == cudaSuccess; s++) e = cudaEventCreateWithFlags(&h->pin_ev[s], cudaEventDisableTiming);
+    for (int s = 0; s < 2 && e == cudaSuccess; s++) e = cudaEventCreate(&h->k_ev[s]);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        magus_replay_close(h);
+        return cuda_fail(e, "magus_replay_open");
+    }
+    *out = h;
+    return MAGUS_OK;
+}
+
+int magus_replay_close(magus_replay_t *h) {
+    if (!h) return MAGUS_OK;
+    cudaSetDevice(h->device);
+    if (h->ws_ev_pending) cudaEventSynchronize(h->ws_ev);
+    for (int s = 0; s < 2; s++) {
+        if (h->pin_pending[s]) cudaEventSynchronize(h->pin_ev[s]);
+        if (h->pin[s]) cudaFreeHost(h->pin[s]);
+        if (h->pin_ev[s]) cudaEventDestroy(h->pin_ev[s]);
+    }
+    for (int s = 0; s < 2; s++) {
+        if (h->hs_ready[s]) cudaEventDestroy(h->hs_ready[s]);
+        if (h->hs_done[s]) cudaEventDestroy(h->hs_done[s]);
+        if (h->k_ev[s]) cudaEventDestroy(h->k_ev[s]);
+    }
+    if (h->hs_copy) cudaStreamDestroy(h->hs_copy);
+    if (h->hs_comp) cudaStreamDestroy(h->hs_comp);
+    if (h->ws) cudaFree(h->ws);
+    if (h->scratch) cudaFree(h->scratch);
+    if (h->status) cudaFree(h->status);
+    if (h->ws_ev) cudaEventDestroy(h->ws_ev);
+    delete h;
+    return MAGUS_OK;
+}
+
+int magus_replay_set_tile(magus_replay_t *h, int32_t tg, int32_t cw) {
+    if (!h) { set_error("NULL handle"); return MAGUS_EINVAL; }
+    if (tg == 0 && cw == 0) {
+        h->tile_tg = h->tile_cw = 0;
+        return MAGUS_OK;
+    }
+    if (!((tg == 8 && cw == 1) || (tg == 4 && cw == 2) || (tg == 2 && cw == 4) || (tg == 1 && cw == 8))) {
+        set_error("supported tiles: (8,1) (4,2) (2,4) (1,8)");
+        return MAGUS_EINVAL;
+    }
+    h->tile_tg = tg;
+    h->tile_cw = cw;
+    return MAGUS_OK;
+}
+
+int magus_replay_run(magus_replay_t *h, const uint32_t *traces, const uint64_t *lengths, int32_t n_traces,
+                     const magus_policy_t *configs, int32_t n_configs, const magus_freq_log_t *log,
+                     double *out_energy, double *out_edp, double *out_time, magus_state_t *io_state,
+                     void *stream) {
+    try {
+        int rc = check_run_args(h, traces, lengths, n_traces, log, out_energy, out_edp);
+        if (rc) return rc;
+        CK(cudaSetDevice(h->device), "cudaSetDevice");
+        int tg, cw;
+        choose_tile(h, n_configs, &tg, &cw);
+        Plan pl;
+        rc = build_plan(h, lengths, n_traces, configs, n_configs, tg, cw, &pl);
+        if (rc) return rc;
+        return launch_plan(h, pl, traces, outs_of(log, out_energy, out_edp, out_time, io_state),
+                           (cudaStream_t)stream);
+    } catch (const std::bad_alloc &) {
+        set_error("out of host memory");
+        return MAGUS_ENOMEM;
+    }
+}
+
+int magus_replay_kernel_ms(magus_replay_t *h, float *ms) {
+    if (!h || !ms) { set_error("NULL argument"); return MAGUS_EINVAL; }
+    if (!h->k_timed) { set_error("no batched kernel launched yet"); return MAGUS_EINVAL; }
+    CK(cudaSetDevice(h->device), "cudaSetDevice");
+    CK(cudaEventSynchronize(h->k_ev[1]), "cudaEventSynchronize");
+    CK(cudaEventElapsedTime(ms, h->k_ev[0], h->k_ev[1]), "cudaEventElapsedTime");
+    return MAGUS_OK;
+}
+
+int magus_replay_status(magus_replay_t *h, void *stream) {
+    if (!h) { set_error("NULL handle"); return MAGUS_EINVAL; }
+    CK(cudaSetDevice(h->device), "cudaSetDevice");
+    CK(cudaStreamSynchronize((cudaStream_t)stream), "cudaStreamSynchronize");
+    int st = 0;
+    CK(cudaMemcpy(&st, h->status, sizeof(int), cudaMemcpyDeviceToHost), "cudaMemcpy(status)");
+    if (st) {
+        CK(cudaMemset(h->status, 0, sizeof(int)), "cudaMemset");
+        set_error(st == MAGUS_ETIMEDOUT ? "a bounded device wait gave up"
+                                        : "a carried level was neither 0 nor K-1");
+    }
+    return st;
+}
+
+int magus_replay_autotune(magus_replay_t *h, const uint32_t *traces, const uint64_t *lengths, int32_t n_traces,
+                          const magus_policy_t *configs, int32_t n_configs, int32_t *out_best, float *out_ms,
+                          void *stream) {
+    try {
+        double *dummy = (double *)16;  // validated as non-NULL; real buffers come from scratch
+        int rc = check_run_args(h, traces, lengths, n_traces, nullptr, dummy, dummy);
+        if (rc) return rc;
+        CK(cudaSetDevice(h->device), "cudaSetDevice");
+        const size_t pairs = (size_t)std::max(n_traces, 1) * n_configs;
+        rc = ensure_ws(h, &h->scratch, &h->scratch_size, pairs * 16);
+        if (rc) return rc;
+        Outs o;
+        memset(&o, 0, sizeof(o));
+        o.energy = (double *)h->scratch;
+        o.edp = o.energy + pairs;
+        static const int shapes[4][2] = {{8, 1}, {4, 2}, {2, 4}, {1, 8}};
+        float best = 1e30f;
+        int bt = 8, bc = 1;
+        for (auto &sh : shapes) {
+            if (sh[1] > 1 && sh[1] / 2 >= n_configs) continue;  // more policy slots than policies
+            Plan pl;
+            rc = build_plan(h, lengths, n_traces, configs, n_configs, sh[0], sh[1], &pl);
+            if (rc) return rc;
+            float ms = 0, mn = 1e30f;
+            for (int rep = 0; rep < 3; rep++) {
+                rc = launch_plan(h, pl, traces, o, (cudaStream_t)stream, &ms);
+                if (rc) return rc;
+                if (rep) mn = std::min(mn, ms);
+            }
+            if (mn < best) {
+                best = mn;
+                bt = sh[0];
+                bc = sh[1];
+            }
+        }
+        h->tuned[n_configs] = {bt, bc};
+        if (out_best) {
+            out_best[0] = bt;
+            out_best[1] = bc;
+        }
+        if (out_ms) *out_ms = best;
+        return MAGUS_OK;
+    } catch (const std::bad_alloc &) {
+        set_error("out of host memory");
+        return MAGUS_ENOMEM;
+    }
+}
+
+int magus_replay_plain(magus_replay_t *h, const uint32_t *traces, const uint64_t *lengths, int32_t n_traces,
+                       const magus_policy_t *configs, int32_t n_configs, const magus_freq_log_t *log,
+                       double *out_energy, double *out_edp, double *out_time, void *stream) {
+    int rc = check_run_args(h, traces, lengths, n_traces, log, out_energy, out_edp);
+    if (rc) return rc;
+    return plain_impl(h, traces, lengths, n_traces, configs, n_configs, log, out_energy, out_edp, out_time,
+                      nullptr, nullptr, (cudaStream_t)stream);
+}
+
+int magus_replay_detail(magus_replay_t *h, const uint32_t *trace, uint64_t n, const magus_policy_t *config,
+                        uint8_t *out_level, double *out_derivative, const magus_freq_log_t *log,
+                        double *out_energy, double *out_edp, double *out_time, void *stream) {
+    if (!h) { set_error("NULL handle"); return MAGUS_EINVAL; }
+    if (n > 0 && !trace) { set_error("trace is required"); return MAGUS_EINVAL; }
+    if (!out_energy || !out_edp) { set_error("out_energy and out_edp are required"); return MAGUS_EINVAL; }
+    if (log && log->entries && log->capacity == 0) { set_error("log capacity must be >= 1"); return MAGUS_EINVAL; }
+    if (n >= (1ull << 27) - 1 && log && log->entries) {
+        set_error("change-log entries hold interval indices below 2^27");
+        return MAGUS_EINVAL;
+    }
+    uint64_t len = n;
+    return plain_impl(h, trace, &len, 1, config, 1, log, out_energy, out_edp, out_time, out_level,
+                      out_derivative, (cudaStream_t)stream);
+}
+
+int magus_replay_run_host(magus_replay_t *h, const uint32_t *traces, const uint64_t *lengths, int32_t n_traces,
+                          const magus_policy_t *configs, int32_t n_configs, const magus_freq_log_t *log,
+                          double *out_energy, double *out_edp, double *out_time) {
+    try {
+        if (n_traces > 0 && !traces) {
+            set_error("traces and lengths are required");
+            return MAGUS_EINVAL;
+        }
+        // host traces need no alignment: they are copied into an aligned device buffer
+        int rc = check_run_args(h, (const uint32_t *)16, lengths, n_traces, log, out_energy, out_edp);
+        if (rc) return rc;
+        CK(cudaSetDevice(h->device), "cudaSetDevice");
+        if (!h->hs_comp) {
+            CK(cudaStreamCreateWithFlags(&h->hs_comp, cudaStreamNonBlocking), "cudaStreamCreate");
+            CK(cudaStreamCreateWithFlags(&h->hs_copy, cudaStreamNonBlocking), "cudaStreamCreate");
+            for (int s = 0; s < 2; s++) {
+                CK(cudaEventCreateWithFlags(&h->hs_ready[s], cudaEventDisableTiming), "cudaEventCreate");
+                CK(cudaEventCreateWithFlags(&h->hs_done[s], cudaEventDisableTiming), "cudaEventCreate");
+            }
+        }
+        int tg, cw;
+        choose_tile(h, n_configs, &tg, &cw);
+        const bool has_log = log != nullptr;
+        const uint64_t cap = (has_log && log->entries) ? log->capacity : 0;
+        const size_t per_pair = 16 + (out_time ? 8 : 0) +
+                                (has_log ? 8 * ((log->n_changes ? 1 : 0) + (log->change_hash ? 1 : 0) +
+                                                (log->n_hf ? 1 : 0)) : 0) + (size_t)cap * 4;
+        // two buffer slots, each holding one batch of traces and its outputs
+        const size_t slot_bytes = std::min<size_t>(h->budget / 2 > (64u << 20) ? h->budget / 2 - (32u << 20)
+                                                                              : (16u << 20),
+                                                   (size_t)512 << 20);
+        std::vector<std::pair<int, int>> batches;
+        for (int i = 0; i < n_traces;) {
+            size_t bytes = 0;
+            int j = i;
+            while (j < n_traces) {
+                size_t add = align_up((lengths[j] + 3) / 4 * 4 * 4, 256) + align_up(per_pair * n_configs, 256) + 2048;
+                if (j > i && bytes + add > slot_bytes) break;
+                bytes += add;
+                j++;
+            }
+            if (bytes > slot_bytes) {
+                set_error("one trace with its outputs exceeds half the memory budget");
+                return MAGUS_ENOMEM;
+            }
+            batches.push_back({i, j});
+            i = j;
+        }
+        rc = ensure_ws(h, &h->scratch, &h->scratch_size, 2 * slot_bytes);
+        if (rc) return rc;
+        std::vector<uint64_t> first_off(batches.size());
+        {
+            uint64_t off = 0;
+            size_t b = 0;
+            for (int i = 0; i < n_traces; i++) {
+                if (b < batches.size() && batches[b].first == i) first_off[b++] = off;
+                off += (lengths[i] + 3) / 4 * 4;
+            }
+        }
+        for (size_t b = 0; b < batches.size(); b++) {
+            const int slot = (int)(b & 1);
+            const int i0 = batches[b].first, i1 = batches[b].second, nt = i1 - i0;
+            char *base = (char *)h->scratch + slot * slot_bytes;
+            uint64_t words = 0;
+            for (int i = i0; i < i1; i++) words += (lengths[i] + 3) / 4 * 4;
+            uint32_t *d_tr = (uint32_t *)base;
+            char *p = base + align_up(words * 4, 256);
+            const size_t np = (size_t)nt * n_configs;
+            double *d_e = (double *)p; p += align_up(np * 8, 256);
+            double *d_edp = (double *)p; p += align_up(np * 8, 256);
+            double *d_t = nullptr;
+            if (out_time) { d_t = (double *)p; p += align_up(np * 8, 256); }
+            magus_freq_log_t dl;
+            memset(&dl, 0, sizeof(dl));
+            if (has_log) {
+                if (log->n_changes) { dl.n_changes = (uint64_t *)p; p += align_up(np * 8, 256); }
+                if (log->change_hash) { dl.change_hash = (uint64_t *)p; p += align_up(np * 8, 256); }
+                if (log->n_hf) { dl.n_hf = (uint64_t *)p; p += align_up(np * 8, 256); }
+                if (cap) { dl.entries = (uint32_t *)p; dl.capacity = cap; p += align_up(np * cap * 4, 256); }
+            }
+            // the copy into this slot waits until the slot's previous batch is finished
+            if (b >= 2) CK(cudaStreamWaitEvent(h->hs_copy, h->hs_done[slot], 0), "cudaStreamWaitEvent");
+            if (words) CK(cudaMemcpyAsync(d_tr, traces + first_off[b], words * 4, cudaMemcpyHostToDevice, h->hs_copy),
+                          "cudaMemcpyAsync(traces)");
+            CK(cudaEventRecord(h->hs_ready[slot], h->hs_copy), "cudaEventRecord");
+            CK(cudaStreamWaitEvent(h->hs_comp, h->hs_ready[slot], 0), "cudaStreamWaitEvent");
+            Plan pl;
+            rc = build_plan(h, lengths + i0, nt, configs, n_configs, tg, cw, &pl);
+            if (rc) return rc;
+            rc = launch_plan(h, pl, d_tr, outs_of(has_log ? &dl : nullptr, d_e, d_edp, d_t, nullptr), h->hs_comp);
+            if (rc) return rc;
+            const size_t po = (size_t)i0 * n_configs;
+            CK(cudaMemcpyAsync(out_energy + po, d_e, np * 8, cudaMemcpyDeviceToHost, h->hs_comp), "cudaMemcpyAsync");
+            CK(cudaMemcpyAsync(out_edp + po, d_edp, np * 8, cudaMemcpyDeviceToHost, h->hs_comp), "cudaMemcpyAsync");
+            if (out_time) CK(cudaMemcpyAsync(out_time + po, d_t, np * 8, cudaMemcpyDeviceToHost, h->hs_comp), "cudaMemcpyAsync");
+            if (has_log) {
+                if (log->n_changes) CK(cudaMemcpyAsync(log->n_changes + po, dl.n_changes, np * 8, cudaMemcpyDeviceToHost, h->hs_comp), "cudaMemcpyAsync");
+                if (log->change_hash) CK(cudaMemcpyAsync(log->change_hash + po, dl.change_hash, np * 8, cudaMemcpyDeviceToHost, h->hs_comp), "cudaMemcpyAsync");
+                if (log->n_hf) CK(cudaMemcpyAsync(log->n_hf + po, dl.n_hf, np * 8, cudaMemcpyDeviceToHost, h->hs_comp), "cudaMemcpyAsync");
+                if (cap) CK(cudaMemcpyAsync(log->entries + po * cap, dl.entries, np * cap * 4, cudaMemcpyDeviceToHost, h->hs_comp), "cudaMemcpyAsync");
+            }
+            CK(cudaEventRecord(h->hs_done[slot], h->hs_comp), "cudaEventRecord");
+        }
+        CK(cudaStreamSynchronize(h->hs_comp), "cudaStreamSynchronize");
+        return magus_replay_status(h, h->hs_comp);
+    } catch (const std::bad_alloc &) {
+        set_error("out of host memory");
+        return MAGUS_ENOMEM;
+    }
+}
+}  // extern "C"

@@ -1,0 +1,93 @@
+// magus_internal.h - structures shared by the replay kernels and their host launchers.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "magus.h"
+
+namespace magus {
+
+// Per-policy parameters as the kernels use them (derived on the host, plan.cu).
+// Algorithm 1's "derivative > inc" is decided on the integer m = a - b
+// (a = delta_t, b = delta_{t-W}) outside a narrow band around the crossover, and by the
+// exact FP64 evaluation inside it.
+struct alignas(16) DevPolicy {
+    int64_t up_mid;        // outside the band: +1 iff m > up_mid
+    int64_t dn_mid;        // outside the band: -1 iff m < dn_mid
+    uint32_t up_lo, up_w;  // band test on the low word: (uint32)(m - up_lo) <= up_w
+    uint32_t dn_lo, dn_w;
+    double inc, dec;       // Alg. 1 thresholds for the exact path
+    int32_t W, L;          // Alg. 1 window, Alg. 2 list length
+    int32_t kmin;          // smallest flag count c with c / L >= high_freq_threshold
+    int32_t step_mode;
+    double th;             // Alg. 2 threshold (the plain kernel evaluates it literally)
+    int32_t pad[2];
+};
+
+// Ladder / energy model as the kernels use it.
+struct DevModel {
+    double q;              // dt * 1e9 (throughput divisor)
+    double bpc;            // bytes per counter unit
+    double dt;
+    int32_t K;
+    uint32_t thr0, thrM;   // delta > thr -> interval stretched at level 0 / K-1 (0xffffffff: never)
+    int32_t pad;
+    double a0, aM;         // seconds per stretched delta unit at level 0 / K-1
+    double P0, PM;         // power at level 0 / K-1
+    double cap[MAGUS_MAX_LEVELS];  // capacity per level, GB/s (plain kernel)
+    double pw[MAGUS_MAX_LEVELS];   // power per level, W (plain kernel)
+};
+
+struct WorkItem {
+    uint32_t trace;
+    uint32_t cfg0;         // first policy of the block
+};
+
+struct TpParams {
+    const uint32_t *traces;
+    const uint64_t *offsets;
+    const uint64_t *lengths;
+    const DevPolicy *pols;
+    int32_t n_pols;
+    int32_t n_items;
+    const WorkItem *items;
+    unsigned int *queue;   // work counter (zeroed before launch)
+    int *status;           // device status word (0 ok, else MAGUS_E*)
+    DevModel model;
+    double *energy, *edp, *time;
+    uint32_t *log_entries;
+    uint64_t log_cap;
+    uint64_t *n_changes, *change_hash, *n_hf;
+    magus_state_t *state;
+};
+
+cudaError_t launch_replay_tp(int time_groups, int policy_slots, const TpParams &p, int grid,
+                             cudaStream_t stream);
+int tp_max_ctas_per_sm(int time_groups, int policy_slots, int *smem_bytes);
+
+struct PlainParams {
+    const uint32_t *trace;
+    uint64_t n;
+    const DevPolicy *pols;
+    int32_t n_pols;
+    int64_t pair_base;     // output index of policy 0 of this trace
+    DevModel model;
+    double *energy, *edp, *time;
+    uint32_t *log_entries;
+    uint64_t log_cap;
+    uint64_t *n_changes, *change_hash, *n_hf;
+    uint8_t *level_log;
+    double *deriv_log;
+};
+cudaError_t launch_replay_plain(const PlainParams &p, cudaStream_t stream);
+
+// Host planning (plan.cu).
+int derive_policy(const magus_policy_t &in, const magus_model_t &m, DevPolicy *out, std::string *err);
+int derive_model(const magus_model_t &m, DevModel *out, std::string *err);
+
+void set_error(const std::string &msg);
+const char *last_error_cstr();
+
+}  // namespace magus

@@ -1,0 +1,110 @@
+// plan.cu - host-side derivation of kernel parameters from a policy and a model.
+//
+// Algorithm 1 (Sec. 3.1) compares derivative = (x_t - x_{t-W}) / W with inc / dec, where
+// x = RN(bpc * delta / q) and every operation rounds to nearest in FP64.  Let
+// m = delta_t - delta_{t-W} (an integer) and r(m) = bpc * m / (q * W) the exact real value.
+// Each of the three roundings moves the result by at most half an ulp of quantities no
+// larger than bpc * 2^32 / q, so |derivative - r(m)| <= 6 * bpc * 2^32 * 2^-53 / (q * W),
+// while consecutive integers m differ by bpc / (q * W) in r(m): the rounding error is below
+// 2^-18 of one integer step.  Hence with c = inc * q * W / bpc:
+//     m >= floor(c) + 4  ->  derivative > inc          (r(m) >= inc + 3 steps)
+//     m <= floor(c) - 3  ->  derivative <= inc         (r(m) <= inc - 3 steps)
+// and only the six integers floor(c) - 2 .. floor(c) + 3 need the FP64 evaluation.  The same
+// holds for dec.  c itself is computed in long double (relative error ~2^-63, so floor(c)
+// is off by at most one for |c| < 2^33, absorbed by the margins above).
+#include <cmath>
+#include <cstring>
+#include <string>
+
+#include "magus_internal.h"
+
+namespace magus {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string &msg) { g_last_error = msg; }
+const char *last_error_cstr() { return g_last_error.c_str(); }
+
+static const long double kReach = 8589934592.0L;  // 2^33 > any |m| = |a - b| < 2^32
+
+int derive_model(const magus_model_t &m, DevModel *out, std::string *err) {
+    if (m.n_levels < 2 || m.n_levels > MAGUS_MAX_LEVELS) { *err = "n_levels must be 2..32"; return MAGUS_EINVAL; }
+    if (!m.f_ghz) { *err = "f_ghz is NULL"; return MAGUS_EINVAL; }
+    if (!(m.dt_s >= 1e-9 && m.dt_s <= 1e6)) { *err = "dt_s must be in [1e-9, 1e6]"; return MAGUS_EINVAL; }
+    if (m.bytes_per_count < 1 || m.bytes_per_count > (1 << 20)) { *err = "bytes_per_count must be 1..2^20"; return MAGUS_EINVAL; }
+    if (!(m.f_ref_ghz > 0) || !std::isfinite(m.f_ref_ghz)) { *err = "f_ref_ghz must be positive"; return MAGUS_EINVAL; }
+    if (!(m.bw_ref_gbs > 0) || !std::isfinite(m.bw_ref_gbs)) { *err = "bw_ref_gbs must be positive"; return MAGUS_EINVAL; }
+    if (!std::isfinite(m.p_static_w) || !std::isfinite(m.p_dyn_w)) { *err = "powers must be finite"; return MAGUS_EINVAL; }
+    for (int k = 0; k < m.n_levels; k++) {
+        if (!(m.f_ghz[k] > 0) || !std::isfinite(m.f_ghz[k])) { *err = "frequencies must be positive"; return MAGUS_EINVAL; }
+        if (k && !(m.f_ghz[k] > m.f_ghz[k - 1])) { *err = "ladder must be strictly ascending"; return MAGUS_EINVAL; }
+    }
+    DevModel d;
+    memset(&d, 0, sizeof(d));
+    d.q = m.dt_s * 1e9;
+    d.bpc = (double)m.bytes_per_count;
+    d.dt = m.dt_s;
+    d.K = m.n_levels;
+    for (int k = 0; k < m.n_levels; k++) {
+        double fr = m.f_ghz[k] / m.f_ref_ghz;
+        d.cap[k] = m.bw_ref_gbs * fr;
+        d.pw[k] = m.p_static_w + m.p_dyn_w * (fr * fr);
+    }
+    auto thr = [&](double cap) -> uint32_t {
+        // x > C  <=>  delta > C q / bpc; the boundary interval itself has x / C within
+        // one rounding of 1, where max(1, x / C) is 1 either way up to an ulp.
+        double v = std::floor(cap * d.q / d.bpc);
+        if (v >= 4294967295.0) return 0xffffffffu;
+        if (v < 0) return 0;
+        return (uint32_t)v;
+    };
+    const int top = m.n_levels - 1;
+    d.thr0 = thr(d.cap[0]);
+    d.thrM = thr(d.cap[top]);
+    d.a0 = d.dt * d.bpc / (d.q * d.cap[0]);
+    d.aM = d.dt * d.bpc / (d.q * d.cap[top]);
+    d.P0 = d.pw[0];
+    d.PM = d.pw[top];
+    *out = d;
+    return MAGUS_OK;
+}
+
+int derive_policy(const magus_policy_t &p, const magus_model_t &m, DevPolicy *out, std::string *err) {
+    if (p.direv_length < 1 || p.direv_length > MAGUS_MAX_WINDOW) { *err = "direv_length must be 1..64"; return MAGUS_EINVAL; }
+    if (p.tune_window < 1 || p.tune_window > MAGUS_MAX_WINDOW) { *err = "tune_window must be 1..64"; return MAGUS_EINVAL; }
+    if (std::isnan(p.inc_threshold) || std::isnan(p.dec_threshold) || std::isnan(p.high_freq_threshold)) {
+        *err = "thresholds must not be NaN"; return MAGUS_EINVAL;
+    }
+    if (p.step_mode != 0 && p.step_mode != 1) { *err = "step_mode must be 0 or 1"; return MAGUS_EINVAL; }
+    if (p.reserved != 0) { *err = "reserved must be 0"; return MAGUS_EINVAL; }
+    DevPolicy d;
+    memset(&d, 0, sizeof(d));
+    d.W = p.direv_length;
+    d.L = p.tune_window;
+    d.inc = p.inc_threshold;
+    d.dec = p.dec_threshold;
+    d.th = p.high_freq_threshold;
+    d.step_mode = p.step_mode;
+    // q is the FP64 product dt * 1e9 that both the oracle and the kernels divide by
+    const long double qd = (long double)(m.dt_s * 1e9);
+    auto crossing = [&](double thr, int64_t *mid, uint32_t *lo, uint32_t *w) {
+        long double c = (long double)thr * qd * (long double)p.direv_length / (long double)m.bytes_per_count;
+        if (c >= kReach) { *mid = (int64_t)kReach; *lo = 0x7fffffffu; *w = 0; return; }
+        if (c <= -kReach) { *mid = -(int64_t)kReach; *lo = 0x7fffffffu; *w = 0; return; }
+        int64_t f = (int64_t)floorl(c);
+        *mid = f;
+        *lo = (uint32_t)(uint64_t)(f - 2);
+        *w = 5;
+    };
+    crossing(p.inc_threshold, &d.up_mid, &d.up_lo, &d.up_w);
+    crossing(p.dec_threshold, &d.dn_mid, &d.dn_lo, &d.dn_w);
+    // Alg. 2: freq = sum / len >= threshold, sum in 0..L
+    d.kmin = d.L + 1;
+    for (int c = 0; c <= d.L; c++) {
+        if ((double)c / (double)d.L >= p.high_freq_threshold) { d.kmin = c; break; }
+    }
+    *out = d;
+    return MAGUS_OK;
+}
+
+}  // namespace magus

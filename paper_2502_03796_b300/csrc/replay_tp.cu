@@ -1,0 +1,541 @@
+// replay_tp.cu - time-parallel batched replay of the MAGUS control step (jump mode).
+//
+// The per-round recurrence (Sec. 3.1 Alg. 1, Sec. 3.2 Alg. 2, Sec. 6.1) splits into
+//   * stencils over the trace: the prediction of round t needs delta_t and delta_{t-W};
+//     the high-frequency state of round t needs the flags of rounds t-L+1 .. t;
+//   * a two-valued latch: after round t the level is the top of the ladder if the round
+//     is high-frequency or predicts +1, the bottom if it predicts -1 (and is not
+//     high-frequency), and unchanged otherwise; "last event wins" is associative.
+// So a trace is cut into 32-round rows: lane j of a warp owns rows of 32 consecutive
+// rounds, builds bit masks of its rounds' predictions, and resolves the latch of its row
+// with one 33-bit addition (carries run from a set-to-top bit until the next
+// set-to-bottom bit).  Rows are chained by a ballot scan inside the warp, warps of a
+// chunk by a short exchange through shared memory, chunks by a carried level.
+//
+// Data path: the CTA streams one trace through a two-stage shared-memory ring with 1-D
+// bulk copies (cp.async.bulk + mbarrier complete_tx); each stage keeps the 64 deltas that
+// precede it so the window W <= 64 never reaches outside shared memory.  One staged chunk
+// feeds every policy the CTA holds (policy_slots groups of time_groups warps).
+//
+// Energy: per level the kernel counts unstretched intervals and sums the deltas of
+// stretched ones (integers, exact); the FP64 totals are formed once per pair.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "magus_internal.h"
+
+namespace magus {
+namespace {
+
+constexpr int HALO = 64;            // deltas kept before each stage (>= max W)
+constexpr int SB = 1024;            // rounds per warp sub-block: 32 rows x 32
+constexpr uint32_t FULL = 0xffffffffu;
+constexpr unsigned long long kWaitNs = 2000000000ull;  // bounded waits: 2 s
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ unsigned long long globaltimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// Wait for `parity` of `bar` with a time limit; false on timeout.
+__device__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = globaltimer();
+    while (true) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (globaltimer() - t0 > kWaitNs) return false;
+    }
+}
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ void group_sync(int id, int nthreads) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+__device__ __forceinline__ uint32_t rotl(uint32_t x, int s) { return __funnelshift_l(x, x, s); }
+__device__ __forceinline__ uint32_t rotr(uint32_t x, int s) { return __funnelshift_r(x, x, s); }
+
+// SplitMix64 output function (Steele, Lea, Flood 2014): hashes change-log entries.
+__device__ __forceinline__ uint64_t mix64(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+    return z ^ (z >> 31);
+}
+__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v) {
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(FULL, v, d);
+    return v;
+}
+
+// Alg. 2 over one row: bit p of the result = high-frequency state of round p.
+// H: flags of the 64 rounds before the row (bit q = round q - 64); FL: flags of the row.
+__device__ __forceinline__ uint32_t hf_row(uint64_t H, uint32_t FL, int L, int kmin) {
+    // window ending just before the row: rounds -L .. -1
+    int cnt = __popcll(H >> (64 - L));
+    // most flags any window ending inside the row can hold
+    const int reach = (L > 1 ? __popcll(H >> (65 - L)) : 0) + __popc(FL);
+    if (reach < kmin) return 0u;
+    // bit p of LV = flag of round p - L (leaving the window at round p)
+    const int s = 64 - L;
+    const uint32_t LV = s == 0 ? (uint32_t)H : (uint32_t)((H >> s) | ((uint64_t)FL << (64 - s)));
+    uint32_t HF = 0;
+#pragma unroll
+    for (int p = 0; p < 32; p++) {
+        cnt += (int)((FL >> p) & 1u) - (int)((LV >> p) & 1u);
+        HF |= (uint32_t)(cnt >= kmin) << p;
+    }
+    return HF;
+}
+
+// Latch over one row: SETM = rounds that leave the level at the top, SET0 = at the bottom
+// (disjoint), cin = level before the row (1 = top).  Returns Lm: bit p = level after
+// round p.  Adding SETM to ~SET0 carries from every set-to-top bit through the following
+// hold bits and stops at the next set-to-bottom bit.
+__device__ __forceinline__ uint32_t latch_row(uint32_t SETM, uint32_t SET0, uint32_t cin) {
+    const uint32_t A = ~SET0;
+    const uint64_t sum = (uint64_t)A + (uint64_t)SETM + (uint64_t)cin;
+    const uint32_t carry_in = (uint32_t)sum ^ A ^ SETM;  // carry into each bit position
+    return (carry_in | SETM) & ~SET0;
+}
+
+struct GroupCarry {
+    uint64_t hist;      // flags of the 64 rounds before the chunk
+    uint64_t count;     // change-log entries emitted so far for the pair
+    uint32_t level;     // level (0 bottom / 1 top) governing the chunk's first round
+    uint32_t pad;
+};
+
+template <int TG, int CW>
+struct Shared {
+    uint64_t bar[2];
+    uint64_t xf[CW][TG];              // flags of the last 64 rounds of each sub-block
+    uint32_t xs[CW][TG];              // sub-block summary: has | exit<<1 | first<<2 | nch<<3
+    GroupCarry carry[CW][2];          // per policy slot, double-buffered by chunk parity
+    unsigned long long red_s0[TG * CW], red_sm[TG * CW], red_hash[TG * CW];
+    uint32_t red_n0[TG * CW], red_nm[TG * CW], red_hf[TG * CW];
+    int item;
+    int abort;
+};
+
+template <int TG, int CW>
+__host__ __device__ constexpr size_t stage_offset() {
+    return (sizeof(Shared<TG, CW>) + 127) / 128 * 128;
+}
+template <int TG, int CW>
+__host__ __device__ constexpr size_t smem_bytes() {
+    return stage_offset<TG, CW>() + 2 * (size_t)(HALO + TG * SB) * sizeof(uint32_t);
+}
+
+template <int TG, int CW>
+__global__ void __launch_bounds__(TG * CW * 32) replay_tp_kernel(const TpParams p) {
+    constexpr int CH = TG * SB;              // rounds per chunk
+    constexpr int STAGE = HALO + CH;         // words per stage
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    Shared<TG, CW> &sh = *reinterpret_cast<Shared<TG, CW> *>(smem_raw);
+    uint32_t *stages = reinterpret_cast<uint32_t *>(smem_raw + stage_offset<TG, CW>());
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int cw = warp / TG, g = warp % TG;
+    const DevModel &M = p.model;
+    const uint32_t topK = (uint32_t)(M.K - 1);
+    const uint32_t lanemask_lt = (1u << lane) - 1u;
+
+    if (tid == 0) {
+        mbar_init(&sh.bar[0], 1);
+        mbar_init(&sh.bar[1], 1);
+        fence_mbar_init();
+        sh.abort = 0;
+    }
+    __syncthreads();
+
+    uint32_t seq = 0;         // chunks loaded by this CTA so far (selects stage and parity)
+    int pend[2] = {-1, -1};   // thread 0: parity of an outstanding bulk copy per stage
+
+    while (true) {
+        if (tid == 0) sh.item = (int)atomicAdd(p.queue, 1u);
+        __syncthreads();
+        const int item = sh.item;
+        if (item >= p.n_items || sh.abort) break;
+        const WorkItem wi = p.items[item];
+        const int cfg = (int)wi.cfg0 + cw;
+        const bool active = cfg < p.n_pols;
+        const uint64_t n = p.lengths[wi.trace];
+        const uint32_t *src = p.traces + p.offsets[wi.trace];
+        const int64_t pair = (int64_t)wi.trace * p.n_pols + (active ? cfg : (int)wi.cfg0);
+        const int64_t pair0 = (int64_t)wi.trace * p.n_pols + (int64_t)wi.cfg0;
+
+        const DevPolicy P = p.pols[active ? cfg : (int)wi.cfg0];
+        uint64_t n_seen0 = 0;
+        if (p.state) n_seen0 = p.state[pair].n_seen;
+
+        // Carried per-pair state: level, flag history, log count.
+        if (g == 0 && lane == 0) {
+            uint32_t lv = 0;
+            uint64_t fl = 0;
+            if (p.state && active) {
+                lv = p.state[pair].level;
+                fl = p.state[pair].flags;
+                if (lv != 0 && lv != topK) {
+                    atomicCAS(p.status, 0, MAGUS_EINVAL);
+                    lv = 0;
+                }
+            }
+            GroupCarry c0;
+            c0.hist = fl;
+            c0.count = 0;
+            c0.level = lv ? 1u : 0u;
+            c0.pad = 0;
+            sh.carry[cw][0] = c0;
+        }
+        // Deltas before the first chunk (the first policy's carried history).
+        uint32_t *st_first = stages + (seq & 1) * STAGE;
+        if (warp == 0) {
+            for (int k = lane; k < HALO; k += 32) st_first[k] = p.state ? p.state[pair0].hist[k] : 0u;
+        }
+        __syncthreads();
+
+        const uint32_t nchunks = (uint32_t)((n + CH - 1) / CH);
+        auto issue = [&](uint32_t c, uint32_t sq) {
+            const uint64_t t0 = (uint64_t)c * CH;
+            const uint64_t left = n - t0;
+            const uint32_t words = (uint32_t)(left < (uint64_t)CH ? left : (uint64_t)CH);
+            const uint32_t bytes = ((words + 3u) & ~3u) * 4u;
+            uint32_t *dst = stages + (sq & 1) * STAGE + HALO;
+            mbar_expect_tx(&sh.bar[sq & 1], bytes);
+            bulk_g2s(dst, src + t0, bytes, &sh.bar[sq & 1]);
+            pend[sq & 1] = (int)((sq >> 1) & 1);
+        };
+        if (tid == 0 && nchunks > 0) issue(0, seq);
+
+        uint32_t acc_n0 = 0, acc_nm = 0, acc_hf = 0;
+        unsigned long long acc_s0 = 0, acc_sm = 0, acc_hash = 0;
+
+        for (uint32_t c = 0; c < nchunks; c++) {
+            const uint32_t sq = seq + c;
+            const int s = (int)(sq & 1);
+            uint32_t *st = stages + s * STAGE;
+            if (tid == 0) {
+                if (!mbar_wait_bounded(&sh.bar[s], (sq >> 1) & 1)) {
+                    atomicCAS(p.status, 0, MAGUS_ETIMEDOUT);
+                    sh.abort = 1;
+                } else {
+                    pend[s] = -1;
+                }
+            }
+            __syncthreads();
+            if (sh.abort) break;
+            // every thread observes the completed phase (acquire of the bulk-copy data)
+            if (tid != 0) (void)mbar_wait_bounded(&sh.bar[s], (sq >> 1) & 1);
+            if (c > 0 && warp == 0) {
+                const uint32_t *prev = stages + (s ^ 1) * STAGE + HALO + CH - HALO;
+                for (int k = lane; k < HALO; k += 32) st[k] = prev[k];
+            }
+            __syncthreads();
+            if (tid == 0 && c + 1 < nchunks) issue(c + 1, sq + 1);
+            if (!active) continue;
+
+            // ---------------------------------------------------------------- phase A
+            // predictions (Alg. 1) and stretch bits of this lane's row, read in rotated
+            // order k = (i + lane) & 31 so the 32 lanes hit 32 different banks.
+            const uint32_t *row = st + HALO + g * SB + 32 * lane;
+            const int64_t r0 = (int64_t)c * CH + g * SB + 32 * lane;  // row start (local)
+            const int64_t left = (int64_t)n - r0;
+            const uint32_t vmask = left >= 32 ? FULL : (left <= 0 ? 0u : ((1u << left) - 1u));
+            uint32_t pmask = vmask;  // rounds whose FIFO holds W+1 samples
+            {
+                const uint64_t gstart = n_seen0 + (uint64_t)r0;
+                if (gstart < (uint64_t)P.W) {
+                    const uint32_t wm = (uint32_t)((uint64_t)P.W - gstart);
+                    pmask &= wm >= 32 ? 0u : (FULL << wm);
+                }
+            }
+            uint32_t UPr = 0, DNr = 0, S0r = 0, SMr = 0, BDr = 0;
+#pragma unroll
+            for (int i = 0; i < 32; i++) {
+                const int k = (i + lane) & 31;
+                const uint32_t a = row[k];
+                const uint32_t b = row[k - P.W];
+                const long long m = (long long)a - (long long)b;
+                UPr |= (uint32_t)(m > P.up_mid) << i;
+                DNr |= (uint32_t)(m < P.dn_mid) << i;
+                const uint32_t m32 = a - b;
+                BDr |= (uint32_t)(((m32 - P.up_lo) <= P.up_w) | ((m32 - P.dn_lo) <= P.dn_w)) << i;
+                S0r |= (uint32_t)(a > M.thr0) << i;
+                SMr |= (uint32_t)(a > M.thrM) << i;
+            }
+            // rounds near a decision boundary: exact FP64 evaluation of Alg. 1
+            {
+                uint32_t todo = BDr & rotr(pmask, lane);
+                if (__any_sync(FULL, todo != 0)) {
+                    while (todo) {
+                        const int i = __ffs(todo) - 1;
+                        todo &= todo - 1;
+                        const int k = (i + lane) & 31;
+                        const uint32_t a = row[k], b = row[k - P.W];
+                        const double xa = __ddiv_rn(__dmul_rn(M.bpc, (double)a), M.q);
+                        const double xb = __ddiv_rn(__dmul_rn(M.bpc, (double)b), M.q);
+                        const double der = __ddiv_rn(__dsub_rn(xa, xb), (double)P.W);
+                        const uint32_t bit = 1u << i;
+                        UPr = (der > P.inc) ? (UPr | bit) : (UPr & ~bit);
+                        DNr = (der < P.dec) ? (DNr | bit) : (DNr & ~bit);
+                    }
+                }
+            }
+            const uint32_t UP = rotl(UPr, lane) & pmask;
+            const uint32_t DN = rotl(DNr, lane) & pmask;
+            const uint32_t S0 = rotl(S0r, lane) & vmask;
+            const uint32_t SM = rotl(SMr, lane) & vmask;
+            const uint32_t FL = UP | DN;   // uncore_tune_ls entries of the row
+            {
+                const uint32_t f30 = __shfl_sync(FULL, FL, 30), f31 = __shfl_sync(FULL, FL, 31);
+                if (lane == 0) sh.xf[cw][g] = (uint64_t)f30 | ((uint64_t)f31 << 32);
+            }
+            if (TG > 1) group_sync(1 + cw, TG * 32); else __syncwarp();
+
+            // ---------------------------------------------------------------- phase B
+            const GroupCarry cr = sh.carry[cw][c & 1];
+            const uint64_t tailH = (g == 0) ? cr.hist : sh.xf[cw][g > 0 ? g - 1 : 0];
+            const uint32_t p1 = __shfl_up_sync(FULL, FL, 1), p2 = __shfl_up_sync(FULL, FL, 2);
+            const uint64_t H = lane >= 2 ? ((uint64_t)p2 | ((uint64_t)p1 << 32))
+                             : lane == 1 ? ((tailH >> 32) | ((uint64_t)p1 << 32))
+                                         : tailH;
+            const uint32_t HF = hf_row(H, FL, P.L, P.kmin) & vmask;
+            const uint32_t SETM = HF | UP;
+            const uint32_t SET0 = DN & ~HF;
+            const uint32_t EV = SETM | SET0;
+            const bool has = EV != 0;
+            const uint32_t exitv = has ? (SETM >> (31 - __clz(EV))) & 1u : 0u;
+            const uint32_t firstv = has ? (SETM >> (__ffs(EV) - 1)) & 1u : 0u;
+            const uint32_t bev = __ballot_sync(FULL, has), bex = __ballot_sync(FULL, exitv);
+            const uint32_t prior = bev & lanemask_lt;
+            const uint32_t cin_prior = prior ? (bex >> (31 - __clz(prior))) & 1u : 0u;
+            {
+                // changes that do not depend on the level entering the sub-block: rows after
+                // the first event row are fixed; the first event row is counted as if it
+                // entered at its own first event's level (no change at that event)
+                uint32_t det = 0;
+                if (prior || has) {
+                    const uint32_t ca = prior ? cin_prior : firstv;
+                    const uint32_t lm = latch_row(SETM, SET0, ca);
+                    det = __popc((lm ^ ((lm << 1) | ca)) & vmask);
+                }
+                const uint32_t wdet = __reduce_add_sync(FULL, det);
+                const int fl_lane = bev ? __ffs(bev) - 1 : 0;
+                const uint32_t wfirst = __shfl_sync(FULL, firstv, fl_lane);
+                if (lane == 0) {
+                    const uint32_t whas = bev != 0;
+                    const uint32_t wexit = whas ? (bex >> (31 - __clz(bev))) & 1u : 0u;
+                    sh.xs[cw][g] = whas | (wexit << 1) | (wfirst << 2) | (wdet << 3);
+                }
+            }
+            if (TG > 1) group_sync(1 + cw, TG * 32); else __syncwarp();
+
+            // ---------------------------------------------------------------- phase C
+            uint32_t wcin = cr.level;
+            uint64_t before = 0;   // changes of earlier sub-blocks of this chunk
+            for (int gg = 0; gg < g; gg++) {
+                const uint32_t sv = sh.xs[cw][gg];
+                if (sv & 1u) {
+                    before += (sv >> 3) + ((((sv >> 2) & 1u) != wcin) ? 1u : 0u);
+                    wcin = (sv >> 1) & 1u;
+                }
+            }
+            const uint32_t cin = prior ? cin_prior : wcin;
+            const uint32_t Lm = latch_row(SETM, SET0, cin);  // level after each round
+            const uint32_t Flev = (Lm << 1) | cin;            // level during each round
+            const uint32_t CHG = (Lm ^ Flev) & vmask;
+
+            acc_n0 += __popc(~Flev & ~S0 & vmask);
+            acc_nm += __popc(Flev & ~SM & vmask);
+            acc_hf += __popc(HF);
+            {
+                const uint32_t M0 = ~Flev & S0 & vmask;
+                if (__any_sync(FULL, M0 != 0)) {
+                    const uint32_t Mr = rotr(M0, lane);
+#pragma unroll
+                    for (int i = 0; i < 32; i++) {
+                        const uint32_t a = row[(i + lane) & 31];
+                        acc_s0 += ((Mr >> i) & 1u) ? a : 0u;
+                    }
+                }
+                const uint32_t MM = Flev & SM & vmask;
+                if (__any_sync(FULL, MM != 0)) {
+                    const uint32_t Mr = rotr(MM, lane);
+#pragma unroll
+                    for (int i = 0; i < 32; i++) {
+                        const uint32_t a = row[(i + lane) & 31];
+                        acc_sm += ((Mr >> i) & 1u) ? a : 0u;
+                    }
+                }
+            }
+            // frequency-change log
+            if (__any_sync(FULL, CHG != 0)) {
+                const uint32_t nch = __popc(CHG);
+                uint32_t incl = nch;
+#pragma unroll
+                for (int d = 1; d < 32; d <<= 1) {
+                    const uint32_t t = __shfl_up_sync(FULL, incl, d);
+                    if (lane >= d) incl += t;
+                }
+                uint64_t off = cr.count + before + (incl - nch);
+                uint32_t bits = CHG;
+                while (bits) {
+                    const int q = __ffs(bits) - 1;
+                    bits &= bits - 1;
+                    const uint64_t when = n_seen0 + (uint64_t)r0 + (uint64_t)q + 1;
+                    const uint32_t lv = ((Lm >> q) & 1u) ? topK : 0u;
+                    if (p.log_entries && off < p.log_cap)
+                        p.log_entries[(uint64_t)pair * p.log_cap + off] = (uint32_t)(when << 5) | lv;
+                    acc_hash += mix64((when << 8) | lv);
+                    off++;
+                }
+            }
+            // carry into the next chunk
+            if (g == TG - 1 && lane == 0) {
+                uint32_t lv = wcin;
+                uint64_t cnt = before;
+                const uint32_t sv = sh.xs[cw][g];
+                if (sv & 1u) {
+                    cnt += (sv >> 3) + ((((sv >> 2) & 1u) != lv) ? 1u : 0u);
+                    lv = (sv >> 1) & 1u;
+                }
+                GroupCarry nx;
+                nx.hist = sh.xf[cw][g];
+                nx.count = cr.count + cnt;
+                nx.level = lv;
+                nx.pad = 0;
+                sh.carry[cw][(c + 1) & 1] = nx;
+            }
+            // state after the last round of the trace
+            if (p.state && left >= 1 && left <= 32) {
+                const int pl = (int)left - 1;
+                magus_state_t &so = p.state[pair];
+                so.n_seen = n_seen0 + n;
+                so.level = ((Lm >> pl) & 1u) ? topK : 0u;
+                so.flags = (H >> (pl + 1)) | ((uint64_t)FL << (63 - pl));
+                for (int k = 0; k < 64; k++) so.hist[k] = row[pl - 63 + k];
+            }
+        }
+        if (sh.abort) break;
+        seq += nchunks;
+
+        // ------------------------------------------------------------------ totals
+        {
+            const uint32_t n0 = __reduce_add_sync(FULL, acc_n0);
+            const uint32_t nm = __reduce_add_sync(FULL, acc_nm);
+            const uint32_t hf = __reduce_add_sync(FULL, acc_hf);
+            const unsigned long long s0 = warp_sum_u64(acc_s0);
+            const unsigned long long smv = warp_sum_u64(acc_sm);
+            const unsigned long long hs = warp_sum_u64(acc_hash);
+            if (lane == 0) {
+                sh.red_n0[warp] = n0;
+                sh.red_nm[warp] = nm;
+                sh.red_hf[warp] = hf;
+                sh.red_s0[warp] = s0;
+                sh.red_sm[warp] = smv;
+                sh.red_hash[warp] = hs;
+            }
+        }
+        __syncthreads();
+        if (g == 0 && lane == 0 && active) {
+            uint64_t N0 = 0, NM = 0, NH = 0;
+            unsigned long long S0 = 0, SMs = 0, HS = 0;
+            for (int w = cw * TG; w < cw * TG + TG; w++) {
+                N0 += sh.red_n0[w];
+                NM += sh.red_nm[w];
+                NH += sh.red_hf[w];
+                S0 += sh.red_s0[w];
+                SMs += sh.red_sm[w];
+                HS += sh.red_hash[w];
+            }
+            const double t0 = M.dt * (double)N0 + M.a0 * (double)S0;   // seconds at the bottom
+            const double tM = M.dt * (double)NM + M.aM * (double)SMs;  // seconds at the top
+            const double T = t0 + tM;
+            const double E = M.P0 * t0 + M.PM * tM;
+            p.energy[pair] = E;
+            p.edp[pair] = E * T;
+            if (p.time) p.time[pair] = T;
+            if (p.n_changes) p.n_changes[pair] = sh.carry[cw][nchunks & 1].count;
+            if (p.change_hash) p.change_hash[pair] = HS;
+            if (p.n_hf) p.n_hf[pair] = NH;
+        }
+        __syncthreads();
+    }
+    // On abort, let outstanding bulk copies land before the CTA's shared memory goes away.
+    if (tid == 0) {
+        for (int s = 0; s < 2; s++)
+            if (pend[s] >= 0) (void)mbar_wait_bounded(&sh.bar[s], (uint32_t)pend[s]);
+    }
+}
+
+template <int TG, int CW>
+cudaError_t launch_t(const TpParams &p, int grid, cudaStream_t stream) {
+    const size_t smem = smem_bytes<TG, CW>();
+    cudaError_t e = cudaFuncSetAttribute(replay_tp_kernel<TG, CW>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    replay_tp_kernel<TG, CW><<<grid, TG * CW * 32, smem, stream>>>(p);
+    return cudaGetLastError();
+}
+
+template <int TG, int CW>
+int occ_t(int *smem_out) {
+    const size_t smem = smem_bytes<TG, CW>();
+    if (smem_out) *smem_out = (int)smem;
+    if (cudaFuncSetAttribute(replay_tp_kernel<TG, CW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem) != cudaSuccess)
+        return 0;
+    int blocks = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, replay_tp_kernel<TG, CW>, TG * CW * 32,
+                                                      smem) != cudaSuccess)
+        return 0;
+    return blocks;
+}
+
+}  // namespace
+
+cudaError_t launch_replay_tp(int tg, int cw, const TpParams &p, int grid, cudaStream_t stream) {
+    if (tg == 8 && cw == 1) return launch_t<8, 1>(p, grid, stream);
+    if (tg == 4 && cw == 2) return launch_t<4, 2>(p, grid, stream);
+    if (tg == 2 && cw == 4) return launch_t<2, 4>(p, grid, stream);
+    if (tg == 1 && cw == 8) return launch_t<1, 8>(p, grid, stream);
+    return cudaErrorInvalidValue;
+}
+
+int tp_max_ctas_per_sm(int tg, int cw, int *smem) {
+    if (tg == 8 && cw == 1) return occ_t<8, 1>(smem);
+    if (tg == 4 && cw == 2) return occ_t<4, 2>(smem);
+    if (tg == 2 && cw == 4) return occ_t<2, 4>(smem);
+    if (tg == 1 && cw == 8) return occ_t<1, 8>(smem);
+    return 0;
+}
+
+}  // namespace magus

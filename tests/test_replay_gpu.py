@@ -1,0 +1,266 @@
+"""GPU parity: the CUDA replay path (through the C ABI) against the CPU oracle.
+
+Decision logs, change counts, change hashes and high-frequency counts must match
+bit-exactly; energy / time / EDP within 1e-9 relative.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import tracegen
+from gpu_util import REL_TOL, assert_pair, oracle_pairs, to_device, to_numpy
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TILES = [(8, 1), (4, 2), (2, 4), (1, 8)]
+
+
+@pytest.fixture(scope="module")
+def mg():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2502_03796_b300 import magus
+    magus.lib()
+    return magus
+
+
+@pytest.fixture(scope="module")
+def rp(mg, ):
+    r = mg.Replay(tracegen.default_model())
+    yield r
+    r.close()
+
+
+def edge_policies():
+    base = tracegen.default_policy()
+    return [
+        base,
+        dict(base, direv_length=1, tune_window=1, high_freq_threshold=1.0),     # hf <=> flag
+        dict(base, direv_length=64, tune_window=64, inc_threshold=0.5, dec_threshold=-0.5),
+        dict(base, direv_length=2, inc_threshold=2.0, dec_threshold=-2.0, high_freq_threshold=0.4),
+        dict(base, high_freq_threshold=0.0),                                     # always hf
+        dict(base, high_freq_threshold=1.5, direv_length=12),                    # never hf
+        dict(base, inc_threshold=float("inf"), dec_threshold=float("-inf")),     # static
+        dict(base, direv_length=7, tune_window=33, inc_threshold=3.3, dec_threshold=-1.25,
+             high_freq_threshold=0.3),
+        dict(base, inc_threshold=-1.0, dec_threshold=-2.0),                      # negative inc
+    ]
+
+
+RAGGED = [0, 1, 3, 4, 5, 31, 32, 33, 63, 64, 65, 1023, 1024, 1025, 2047, 4097, 8191, 8192, 8193,
+          16385, 20000, 24577, 33000]
+
+
+def ragged_set(seed=3):
+    return tracegen.make_traces(np.array(RAGGED, dtype=np.uint64), seed=seed, mean_phase=12.0)
+
+
+def test_single_trace_detail_matches_oracle(rp):
+    ts = tracegen.single_trace()
+    model, pol = tracegen.default_model(), tracegen.default_policy()
+    d = to_device(ts)
+    n = int(ts.lengths[0])
+    out = rp.detail(d, n, pol, log_capacity=n)
+    torch.cuda.synchronize()
+    ref = oracle.replay(ts.trace(0), pol, model, detail=True)
+    o = to_numpy(out)
+    assert np.array_equal(o["level_log"][:n], ref["level_log"])
+    assert np.array_equal(o["deriv_log"][:n].view(np.uint64), ref["deriv_log"].view(np.uint64))
+    assert_pair(o, 0, ref, cap=n, tag="detail")
+
+
+@pytest.mark.parametrize("tile", TILES)
+def test_ragged_batch_all_tiles(rp, tile):
+    ts = ragged_set()
+    model = tracegen.default_model()
+    pols = edge_policies()
+    cap = 40_000
+    rp.set_tile(*tile)
+    try:
+        out = to_numpy(rp.run(to_device(ts), ts.lengths, pols, log_capacity=cap))
+    finally:
+        rp.set_tile(0, 0)
+    assert rp.status() == 0
+    ref = oracle_pairs(ts, pols, model)
+    for p, r in ref.items():
+        assert_pair(out, p, r, cap=cap, tag=f"tile{tile}")
+
+
+def test_plain_kernel_matches_oracle(rp):
+    ts = tracegen.make_traces(np.array([0, 1, 7, 100, 5000, 20000], dtype=np.uint64), seed=11)
+    pols = edge_policies() + [dict(tracegen.default_policy(), step_mode=1, high_freq_threshold=0.9)]
+    cap = 20_000
+    out = to_numpy(rp.plain(to_device(ts), ts.lengths, pols, log_capacity=cap))
+    ref = oracle_pairs(ts, pols, tracegen.default_model())
+    for p, r in ref.items():
+        assert_pair(out, p, r, cap=cap, tag="plain")
+
+
+def band_trace(W, ms, bases):
+    """Blocks [b]*W + [b+m]*W: rounds in the second block see delta_t - delta_{t-W} = m, the
+    next block's rounds see -m."""
+    parts = []
+    for b in bases:
+        for m in ms:
+            a = b + m
+            if 0 <= a <= 0xFFFFFFFF and 0 <= b <= 0xFFFFFFFF:
+                parts += [b] * W + [a] * W
+    return np.array(parts, dtype=np.uint64).astype(np.uint32)
+
+
+@pytest.mark.parametrize("model_kind", ["default", "odd"])
+def test_decision_band_exhaustive(rp, mg, model_kind):
+    """Every integer difference within 8 of each decision crossover, at small, large and
+    > 2^31 base values: exact FP64 agreement of Alg. 1 on both sides."""
+    model = tracegen.default_model()
+    if model_kind == "odd":
+        model = dict(model, dt_s=0.037, bytes_per_count=3)
+    handle = rp if model_kind == "default" else mg.Replay(model)
+    base = tracegen.default_policy()
+    pols = [dict(base, direv_length=5), dict(base, direv_length=7, inc_threshold=3.3, dec_threshold=-0.7),
+            dict(base, direv_length=3, inc_threshold=1e-7, dec_threshold=-2.5e-3)]
+    bases = [0, 7, 1_000_000, 123_456_789, 2**31 - 50, 2**31 + 3, 2**32 - 2**20]
+    traces, lengths = [], []
+    for pol in pols:
+        b = mg.policy_bounds(pol, model)
+        ms = sorted(set(int(x) for c in (b[0], b[1]) for x in range(c - 8, c + 9)))
+        for flagpol in (dict(pol, tune_window=1, high_freq_threshold=1.0),
+                        dict(pol, tune_window=1, high_freq_threshold=2.0)):
+            tr = band_trace(pol["direv_length"], ms, bases)
+            traces.append((tr, flagpol))
+    for tr, pol in traces:
+        ts = tracegen.TraceSet(lengths=np.array([len(tr)], dtype=np.uint64),
+                               offsets=np.zeros(1, dtype=np.uint64),
+                               data=np.concatenate([tr, np.zeros(4, dtype=np.uint32)]))
+        out = to_numpy(handle.run(to_device(ts), ts.lengths, [pol], log_capacity=len(tr)))
+        ref = oracle.replay(tr, pol, model)
+        assert_pair(out, 0, ref, cap=len(tr), tag=f"band {pol}")
+    if handle is not rp:
+        handle.close()
+
+
+def test_split_replay_with_state(rp, mg):
+    """Feeding a trace in pieces with carried state reproduces the whole-trace log and
+    additive energies (against the oracle's whole-trace replay)."""
+    model = tracegen.default_model()
+    ts_all = tracegen.make_traces(np.array([30_000], dtype=np.uint64), seed=5, mean_phase=9.0)
+    full = ts_all.trace(0)
+    pols = [tracegen.default_policy(), dict(tracegen.default_policy(), direv_length=40, tune_window=50,
+                                            high_freq_threshold=0.1)]
+    cuts = [0, 3, 4, 37, 64, 65, 1100, 8192, 8200, 20000, 30_000]
+    state = torch.zeros(len(pols) * mg.STATE_BYTES, dtype=torch.uint8, device="cuda")
+    E = np.zeros(len(pols))
+    T = np.zeros(len(pols))
+    logs = [[] for _ in pols]
+    nhf = np.zeros(len(pols), dtype=np.int64)
+    hsh = [0] * len(pols)
+    for a, b in zip(cuts[:-1], cuts[1:]):
+        piece = full[a:b]
+        ts = tracegen.TraceSet(lengths=np.array([len(piece)], dtype=np.uint64), offsets=np.zeros(1, dtype=np.uint64),
+                               data=np.concatenate([piece, np.zeros(4, dtype=np.uint32)]))
+        cap = max(len(piece), 1)
+        out = to_numpy(rp.run(to_device(ts), ts.lengths, pols, log_capacity=cap, state=state))
+        for c in range(len(pols)):
+            E[c] += out["energy_j"][c]
+            T[c] += out["time_s"][c]
+            nhf[c] += int(out["n_hf"][c])
+            hsh[c] = (hsh[c] + int(out["change_hash"][c])) % 2**64
+            k = int(out["n_changes"][c])
+            logs[c].append(out["log"][c * cap:c * cap + k])
+    assert rp.status() == 0
+    for c, pol in enumerate(pols):
+        ref = oracle.replay(full, pol, model)
+        ent = np.concatenate(logs[c]).astype(np.uint32)
+        assert np.array_equal((ent >> 5).astype(np.uint64), ref["log_t"])
+        assert np.array_equal((ent & 31).astype(np.uint8), ref["log_level"])
+        assert nhf[c] == ref["n_hf"] and hsh[c] == ref["change_hash"]
+        assert abs(E[c] - ref["energy_j"]) <= REL_TOL * ref["energy_j"]
+        assert abs(T[c] - ref["time_s"]) <= REL_TOL * ref["time_s"]
+    st = state.cpu().numpy().view(np.uint64)
+    assert int(st[0]) == 30_000
+
+
+def test_invalid_carried_level_reports_einval(rp, mg):
+    ts = tracegen.make_traces(np.array([100], dtype=np.uint64), seed=1)
+    state = torch.zeros(mg.STATE_BYTES, dtype=torch.uint8, device="cuda")
+    state.view(torch.int32)[4] = 3   # level field (offset 16): neither 0 nor K-1
+    rp.run(to_device(ts), ts.lengths, [tracegen.default_policy()], state=state)
+    assert rp.status() == mg.EINVAL
+    assert rp.status() == 0
+
+
+def test_argument_errors(rp, mg):
+    ts = tracegen.make_traces(np.array([100], dtype=np.uint64), seed=1)
+    d = to_device(ts)
+    with pytest.raises(mg.MagusError) as e:
+        rp.run(d, ts.lengths, [dict(tracegen.default_policy(), direv_length=65)])
+    assert e.value.code == mg.EINVAL
+    with pytest.raises(mg.MagusError):
+        rp.run(d, ts.lengths, [dict(tracegen.default_policy(), step_mode=1)])
+    with pytest.raises(mg.MagusError):
+        rp.run(d[1:], ts.lengths, [tracegen.default_policy()])   # misaligned base
+    with pytest.raises(mg.MagusError):
+        rp.run(d, ts.lengths, [dict(tracegen.default_policy(), inc_threshold=float("nan"))])
+
+
+def test_empty_inputs(rp):
+    ts = tracegen.make_traces(np.array([0, 0], dtype=np.uint64), seed=1)
+    out = to_numpy(rp.run(to_device(ts) if ts.data.size else torch.zeros(4, dtype=torch.int32, device="cuda"),
+                          ts.lengths, [tracegen.default_policy()]))
+    assert np.all(out["energy_j"] == 0) and np.all(out["n_changes"] == 0)
+    out = rp.run(torch.zeros(4, dtype=torch.int32, device="cuda"), np.zeros(0, dtype=np.uint64),
+                 [tracegen.default_policy()])
+    assert out["energy_j"].numel() == 0
+
+
+def test_run_host_matches_device(rp):
+    ts = tracegen.batched(64, 10_000, seed=2)
+    pols = tracegen.sweep_policies()[:5]
+    dev = to_numpy(rp.run(to_device(ts), ts.lengths, pols, log_capacity=2000))
+    host = rp.run_host(ts.data, ts.lengths, pols, log_capacity=2000)
+    for k in ("energy_j", "edp_js", "time_s", "n_changes", "change_hash", "n_hf", "log"):
+        assert np.array_equal(np.asarray(host[k]).view(dev[k].dtype), dev[k]), k
+
+
+def test_sweep_grid_scaled(rp):
+    ts = tracegen.sweep(n_traces=6, n=40_000, seed=0)
+    pols = tracegen.sweep_policies()
+    out = to_numpy(rp.run(to_device(ts), ts.lengths, pols, log_capacity=16_000))
+    ref, _ = oracle.replay_batch(ts.data, ts.offsets, ts.lengths, pols, tracegen.default_model())
+    assert np.array_equal(out["n_changes"], ref["n_changes"].astype(np.uint64))
+    assert np.array_equal(out["change_hash"], ref["change_hash"].astype(np.uint64))
+    assert np.array_equal(out["n_hf"], ref["n_hf"].astype(np.uint64))
+    np.testing.assert_allclose(out["energy_j"], ref["energy_j"], rtol=REL_TOL)
+    np.testing.assert_allclose(out["edp_js"], ref["edp_js"], rtol=REL_TOL)
+    sample = oracle_pairs(ts, pols, tracegen.default_model(), pairs=range(0, 6 * 256, 37))
+    for p, r in sample.items():
+        assert_pair(out, p, r, cap=16_000)
+
+
+def test_uneven_lengths_scaled(rp):
+    ts = tracegen.uneven(n_traces=96, lo=1e2, hi=6e4, seed=4)
+    pols = tracegen.sweep_policies()[:16]
+    out = to_numpy(rp.run(to_device(ts), ts.lengths, pols))
+    ref, _ = oracle.replay_batch(ts.data, ts.offsets, ts.lengths, pols, tracegen.default_model())
+    assert np.array_equal(out["n_changes"], ref["n_changes"].astype(np.uint64))
+    assert np.array_equal(out["change_hash"], ref["change_hash"].astype(np.uint64))
+    assert np.array_equal(out["n_hf"], ref["n_hf"].astype(np.uint64))
+    np.testing.assert_allclose(out["energy_j"], ref["energy_j"], rtol=REL_TOL)
+
+
+def test_full_size_batched_workload(rp):
+    """4,096 traces x 100,000 intervals, one policy, the launch the benchmark times: every
+    pair's counts / hash / energy against the oracle, full logs of sampled pairs."""
+    ts = tracegen.batched()
+    pol = [tracegen.default_policy()]
+    cap = 8192
+    out = to_numpy(rp.run(to_device(ts), ts.lengths, pol, log_capacity=cap))
+    ref, _ = oracle.replay_batch(ts.data, ts.offsets, ts.lengths, pol, tracegen.default_model())
+    assert np.array_equal(out["n_changes"], ref["n_changes"].astype(np.uint64))
+    assert np.array_equal(out["change_hash"], ref["change_hash"].astype(np.uint64))
+    assert np.array_equal(out["n_hf"], ref["n_hf"].astype(np.uint64))
+    np.testing.assert_allclose(out["energy_j"], ref["energy_j"], rtol=REL_TOL)
+    np.testing.assert_allclose(out["time_s"], ref["time_s"], rtol=REL_TOL)
+    for p, r in oracle_pairs(ts, pol, tracegen.default_model(), pairs=[0, 1, 777, 2048, 4095]).items():
+        assert_pair(out, p, r, cap=cap)
