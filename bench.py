@@ -1,0 +1,345 @@
+#!/usr/bin/env python
+"""Benchmark of the MAGUS policy-step replay on one node of B300 GPUs.
+
+One step = one replay of the batched workload: 4,096 synthetic traces x 100,000 intervals
+(uint32 counter deltas, 1.64 GB) under one policy, every pair through Algorithm 1,
+Algorithm 2, the jump-to-bound decision, the energy/EDP charge and the full change log,
+in one persistent launch of the time-parallel kernel.  Inputs are resident in HBM when
+the timed region starts (1.64 GB, larger than the 126 MB L2, so no flush is needed).
+
+With torchrun (N > 1) every rank replays its own 4,096 traces (weak scaling, no data-path
+collective; a barrier and a max-reduction of the elapsed time only).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl magus|reference]
+
+`--impl reference` times the CPU oracle (plain sequential C, OpenMP over pairs) on a
+bounded sample of the same workload: the only reference this paper has.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import tracegen  # noqa: E402
+
+METRIC = "policy-step samples/s & % HBM roofline vs plain launch; serve p50/p99 latency"
+N_TRACES, N_INTERVALS = 4096, 100_000
+LOG_CAP = 8192
+WORKLOAD = "batched replay: 4096 traces x 100000 intervals (phase mean 40), 1 policy (W=5, inc=5, dec=-5, L=10, th=0.6)"
+KERNEL_SOURCES = ["paper_2502_03796_b300/csrc/replay_tp.cu", "paper_2502_03796_b300/csrc/replay_core.cuh",
+                  "paper_2502_03796_b300/csrc/magus_internal.h"]
+
+
+def kernel_sha() -> str:
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks() -> dict:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return dict(hbm_gbs=float(d["hbm_gbs"]), source="measured")
+    return dict(hbm_gbs=6400.0, source="fallback")
+
+
+def ncu_traffic() -> float | None:
+    """Per-launch DRAM bytes of the batched kernel from the committed ncu summary, if it was
+    taken on the current kernel source."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    e = d.get("replay_tp_batched")
+    if not e or e.get("kernel_sha") != kernel_sha():
+        return None
+    return float(e["dram_bytes_per_launch"])
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return dict(sm_mhz=None, sm_max_mhz=None, reasons=["nvidia-smi unavailable"])
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return dict(sm_mhz=float(np.median(sm)) if sm else None, sm_max_mhz=mx, reasons=sorted(reasons),
+                    samples=len(sm))
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        import torch
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(world, v: float, device) -> float:
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def rank_traces(rank: int, n_traces: int = N_TRACES, n: int = N_INTERVALS) -> tracegen.TraceSet:
+    # weak scaling: each rank owns a disjoint block of trace ids
+    return tracegen.batched(n_traces=n_traces, n=n, seed=0, first_id=rank * n_traces)
+
+
+def cpu_oracle_sample(ts: tracegen.TraceSet, policy, model, target_s: float = 6.0):
+    """Time the CPU oracle on a bounded prefix of the workload's traces (~target_s wall on
+    all host cores).  Returns (samples/s, threads, sample description)."""
+    import oracle
+    k = min(64, ts.n_traces)
+    t0 = time.perf_counter()
+    _, used = oracle.replay_batch(ts.data, ts.offsets[:k], ts.lengths[:k], [policy], model)
+    dt = time.perf_counter() - t0
+    rate = k / max(dt, 1e-9)
+    k2 = int(min(ts.n_traces, max(k, rate * target_s)))
+    t0 = time.perf_counter()
+    _, used = oracle.replay_batch(ts.data, ts.offsets[:k2], ts.lengths[:k2], [policy], model)
+    dt = time.perf_counter() - t0
+    samples = int(ts.lengths[:k2].sum())
+    return samples / dt, used, f"first {k2} of {ts.n_traces} traces x {N_INTERVALS} intervals, 1 policy ({dt:.1f} s wall)"
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return 0
+    model, policy = tracegen.default_model(), tracegen.default_policy()
+    ts = rank_traces(0)
+    import oracle
+    # bounded per-step sample sized from a probe so K + W steps end within a few minutes
+    k = 64
+    t0 = time.perf_counter()
+    oracle.replay_batch(ts.data, ts.offsets[:k], ts.lengths[:k], [policy], model)
+    per_trace = (time.perf_counter() - t0) / k
+    budget = 120.0 / max(args.steps + args.warmup, 1)
+    k = int(min(ts.n_traces, max(16, budget / max(per_trace, 1e-9))))
+    for _ in range(args.warmup):
+        oracle.replay_batch(ts.data, ts.offsets[:k], ts.lengths[:k], [policy], model)
+    t0 = time.perf_counter()
+    used = 1
+    for _ in range(args.steps):
+        _, used = oracle.replay_batch(ts.data, ts.offsets[:k], ts.lengths[:k], [policy], model)
+    dt = time.perf_counter() - t0
+    samples = int(ts.lengths[:k].sum()) * args.steps
+    value = samples / dt
+    line = dict(metric=METRIC, value=value, unit="samples/s", n_gpus=args.gpus, steps=args.steps,
+                warmup=args.warmup, ms_per_step=dt / args.steps * 1e3, higher_is_better=True, scaling="weak",
+                vs_baseline=None, dtype="f64", data="synthetic", impl="reference",
+                config=dict(workload=WORKLOAD, sample_traces=k),
+                cpu_baseline=dict(value=value, unit="samples/s", cores=used, kind="oracle",
+                                  sample=f"first {k} of {ts.n_traces} traces per step"),
+                e2e=dict(value=value, unit="samples/s", h2d_bytes_per_step=0, d2h_bytes_per_step=0))
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main() -> int:
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="magus", choices=["magus", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--tile", default="", help="time_groups,policy_slots (default: automatic)")
+    ap.add_argument("--traces", type=int, default=N_TRACES, help="traces per GPU (profiling runs use fewer)")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        return run_reference(args, world, rank)
+
+    import torch
+    from paper_2502_03796_b300 import magus
+
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    model, policy = tracegen.default_model(), tracegen.default_policy()
+    ts = rank_traces(rank, n_traces=args.traces)
+    samples_per_step = ts.n_samples
+    d_tr = torch.from_numpy(ts.data.view(np.int32)).to(dev)
+    rp = magus.Replay(model, device=local, mem_budget=2 << 30)
+    if args.tile:
+        rp.set_tile(*[int(x) for x in args.tile.split(",")])
+    outs = rp.alloc(ts.n_traces, log_capacity=LOG_CAP)
+    stream = torch.cuda.current_stream(dev)
+
+    for _ in range(args.warmup):
+        rp.run(d_tr, ts.lengths, [policy], stream=stream, out=outs)
+    torch.cuda.synchronize(dev)
+    rp.kernel_time()
+    rp.status()
+
+    clocks = ClockSampler(local)
+    barrier(world)
+    torch.cuda.synchronize(dev)
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        rp.run(d_tr, ts.lengths, [policy], stream=stream, out=outs)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier(world)
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    ms = max_over_ranks(world, ms, dev)
+    k_ms, k_n = rp.kernel_time()
+    if rp.status() != 0:
+        raise RuntimeError("device-side status error during the timed region")
+    value = samples_per_step * world * args.steps / (ms * 1e-3)
+
+    # algorithmic bytes of one launch: every delta read once, per-pair totals written once,
+    # every change-log entry written once
+    out_np = outs[0]
+    n_changes = int(out_np["n_changes"].sum().item())
+    alg_bytes = 4 * samples_per_step + 48 * ts.n_traces + 4 * min(n_changes, LOG_CAP * ts.n_traces)
+    k_avg_ms = k_ms / max(k_n, 1)
+    peaks = measured_peaks()
+    achieved = alg_bytes / (k_avg_ms * 1e-3) / 1e9
+    traffic = ncu_traffic()
+    roofline = dict(bound="hbm", achieved=achieved, peak=peaks["hbm_gbs"], unit="GB/s",
+                    frac=achieved / peaks["hbm_gbs"], traffic=traffic,
+                    peak_source=f"{peaks['source']} (MEASURED_PEAKS.json hbm_gbs)" if peaks["source"] == "measured"
+                    else "fallback 6.4 TB/s", kernel="replay_tp_kernel<8,1>", kernel_ms=k_avg_ms,
+                    alg_bytes_per_launch=alg_bytes, frac_of_nominal_8tbs=achieved / 8000.0)
+
+    line = dict(metric=METRIC, value=value, unit="samples/s", n_gpus=world, steps=args.steps,
+                warmup=args.warmup, ms_per_step=ms / args.steps, higher_is_better=True, scaling="weak",
+                vs_baseline=None, dtype="u32/f64", data="synthetic",
+                config=dict(workload=WORKLOAD if args.traces == N_TRACES else
+                            WORKLOAD.replace(str(N_TRACES), str(args.traces)), traces_per_gpu=ts.n_traces, intervals=N_INTERVALS, policies=1,
+                            outputs="energy, EDP, time, change count, change hash, hf count, full change log",
+                            l2="inputs 1.64 GB per GPU > 126 MB L2 (no flush needed)",
+                            parallelism=f"dp{world} (traces sharded, no collective)"),
+                roofline=roofline, gpu_launches=k_n, clocks=clk)
+
+    if rank == 0 and not args.no_plain:
+        # the plain form: one launch per trace, one thread per policy, literal FP64
+        k = 16
+        sub = tracegen.TraceSet(ts.lengths[:k], ts.offsets[:k], ts.data[:int(ts.offsets[k])])
+        d_sub = d_tr[:int(ts.offsets[k])]
+        rp.plain(d_sub, sub.lengths, [policy], stream=stream)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        rp.plain(d_sub, sub.lengths, [policy], stream=stream)
+        torch.cuda.synchronize(dev)
+        pdt = time.perf_counter() - t0
+        plain_rate = sub.n_samples / pdt
+        line["plain_launch"] = dict(value=plain_rate, unit="samples/s", sample=f"{k} traces, {k} launches",
+                                    speedup=value / world / plain_rate)
+
+    if rank == 0 and not args.no_e2e:
+        # end to end through the public API with host buffers: pinned host traces in,
+        # host outputs back, copies inside the timed region
+        pinned = torch.from_numpy(ts.data.view(np.int32)).pin_memory()
+        host_tr = pinned.numpy().view(np.uint32)
+        n_pairs = ts.n_traces
+        hout = {k: torch.zeros(n_pairs, dtype=torch.float64).pin_memory().numpy()
+                for k in ("energy_j", "edp_js", "time_s")}
+        for k in ("n_changes", "change_hash", "n_hf"):
+            hout[k] = torch.zeros(n_pairs, dtype=torch.int64).pin_memory().numpy().view(np.uint64)
+        rp.run_host(host_tr, ts.lengths, [policy], out=hout)
+        ksteps = max(1, min(args.steps, 5))
+        t0 = time.perf_counter()
+        for _ in range(ksteps):
+            rp.run_host(host_tr, ts.lengths, [policy], out=hout)
+        edt = time.perf_counter() - t0
+        line["e2e"] = dict(value=samples_per_step * ksteps / edt, unit="samples/s",
+                           h2d_bytes_per_step=int(ts.data.nbytes), d2h_bytes_per_step=48 * n_pairs,
+                           steps=ksteps, api="magus_replay_run_host")
+        rp.kernel_time()
+
+    if rank == 0 and not args.no_cpu_baseline:
+        rate, used, sample = cpu_oracle_sample(ts, policy, model)
+        line["cpu_baseline"] = dict(value=rate, unit="samples/s", cores=used, kind="oracle", sample=sample)
+
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    rp.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

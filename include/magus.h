@@ -164,9 +164,10 @@ int magus_replay_detail(magus_replay_t *h, const uint32_t *trace, uint64_t n,
  * device wait that gave up), then clear them. */
 int magus_replay_status(magus_replay_t *h, void *stream);
 
-/* Device time of the most recent batched-kernel launch of this handle (CUDA events recorded
- * on the launching stream right before and after the kernel); waits for that launch. */
-int magus_replay_kernel_ms(magus_replay_t *h, float *ms);
+/* Device time of the batched-kernel launches of this handle since the previous call (CUDA
+ * events recorded on the launching stream right before and after each kernel, up to 4096
+ * launches; later ones overwrite the last record).  Waits for those launches, then resets. */
+int magus_replay_kernel_time(magus_replay_t *h, double *total_ms, int32_t *launches);
 
 /* Tile shape of the batched kernel: warps per policy that split a trace chunk in time
  * (time_groups) x policies per CTA (policy_slots); time_groups * policy_slots = 8.

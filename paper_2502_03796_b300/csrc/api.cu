@@ -41,8 +41,9 @@ struct magus_replay {
     // host-memory runs: copy / compute streams, per-slot events
     cudaStream_t hs_copy = nullptr, hs_comp = nullptr;
     cudaEvent_t hs_ready[2] = {nullptr, nullptr}, hs_done[2] = {nullptr, nullptr};
-    cudaEvent_t k_ev[2] = {nullptr, nullptr};  // around the last batched-kernel launch
-    bool k_timed = false;
+    // events around batched-kernel launches since the last magus_replay_kernel_time()
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> k_ev;
+    size_t k_used = 0;
     int tile_tg = 0, tile_cw = 0;     // 0: automatic
     std::map<int, std::pair<int, int>> tuned;
 };
@@ -251,10 +252,17 @@ int launch_plan(magus_replay *h, const Plan &pl, const uint32_t *traces, const O
         CK(cudaEventRecord(e0, stream), "cudaEventRecord");
     }
     if (n_items) {
-        CK(cudaEventRecord(h->k_ev[0], stream), "cudaEventRecord");
+        if (h->k_used == h->k_ev.size() && h->k_used < 4096) {
+            cudaEvent_t a, b;
+            CK(cudaEventCreate(&a), "cudaEventCreate");
+            CK(cudaEventCreate(&b), "cudaEventCreate");
+            h->k_ev.push_back({a, b});
+        }
+        const size_t slot_k = h->k_used < h->k_ev.size() ? h->k_used : h->k_ev.size() - 1;
+        CK(cudaEventRecord(h->k_ev[slot_k].first, stream), "cudaEventRecord");
         CK(launch_replay_tp(pl.tg, pl.cw, p, grid, stream), "replay kernel launch");
-        CK(cudaEventRecord(h->k_ev[1], stream), "cudaEventRecord");
-        h->k_timed = true;
+        CK(cudaEventRecord(h->k_ev[slot_k].second, stream), "cudaEventRecord");
+        if (h->k_used < h->k_ev.size()) h->k_used++;
     }
     if (ms_out) {
         CK(cudaEventRecord(e1, stream), "cudaEventRecord");
@@ -274,7 +282,7 @@ int check_run_args(magus_replay *h, const uint32_t *traces, const uint64_t *leng
     if (n_traces < 0) { set_error("n_traces must be >= 0"); return MAGUS_EINVAL; }
     if (n_traces > 0 && (!lengths || !traces)) { set_error("traces and lengths are required"); return MAGUS_EINVAL; }
     if (((uintptr_t)traces & 15u) != 0) { set_error("traces must be 16-byte aligned"); return MAGUS_EINVAL; }
-    if (!e || !edp) { set_error("out_energy and out_edp are required"); return MAGUS_EINVAL; }
+    if (n_traces > 0 && (!e || !edp)) { set_error("out_energy and out_edp are required"); return MAGUS_EINVAL; }
     if (log && log->entries && log->capacity == 0) { set_error("log capacity must be >= 1"); return MAGUS_EINVAL; }
     for (int i = 0; i < n_traces; i++) {
         if (lengths[i] >= (1ull << 40)) { set_error("trace length too large"); return MAGUS_EINVAL; }
@@ -417,7 +425,6 @@ int magus_replay_open(magus_replay_t **out, const magus_model_t *model, int devi
     if (e == cudaSuccess) e = cudaMemset(h->status, 0, 256);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ws_ev, cudaEventDisableTiming);
     for (int s = 0; s < 2 && e == cudaSuccess; s++) e = cudaEventCreateWithFlags(&h->pin_ev[s], cudaEventDisableTiming);
-    for (int s = 0; s < 2 && e == cudaSuccess; s++) e = cudaEventCreate(&h->k_ev[s]);
     if (e != cudaSuccess) {
         cudaGetLastError();
         magus_replay_close(h);
@@ -439,10 +446,13 @@ int magus_replay_close(magus_replay_t *h) {
     for (int s = 0; s < 2; s++) {
         if (h->hs_ready[s]) cudaEventDestroy(h->hs_ready[s]);
         if (h->hs_done[s]) cudaEventDestroy(h->hs_done[s]);
-        if (h->k_ev[s]) cudaEventDestroy(h->k_ev[s]);
     }
     if (h->hs_copy) cudaStreamDestroy(h->hs_copy);
     if (h->hs_comp) cudaStreamDestroy(h->hs_comp);
+    for (auto &ev : h->k_ev) {
+        cudaEventDestroy(ev.first);
+        cudaEventDestroy(ev.second);
+    }
     if (h->ws) cudaFree(h->ws);
     if (h->scratch) cudaFree(h->scratch);
     if (h->status) cudaFree(h->status);
@@ -487,12 +497,19 @@ int magus_replay_run(magus_replay_t *h, const uint32_t *traces, const uint64_t *
     }
 }
 
-int magus_replay_kernel_ms(magus_replay_t *h, float *ms) {
-    if (!h || !ms) { set_error("NULL argument"); return MAGUS_EINVAL; }
-    if (!h->k_timed) { set_error("no batched kernel launched yet"); return MAGUS_EINVAL; }
+int magus_replay_kernel_time(magus_replay_t *h, double *total_ms, int32_t *launches) {
+    if (!h || !total_ms || !launches) { set_error("NULL argument"); return MAGUS_EINVAL; }
     CK(cudaSetDevice(h->device), "cudaSetDevice");
-    CK(cudaEventSynchronize(h->k_ev[1]), "cudaEventSynchronize");
-    CK(cudaEventElapsedTime(ms, h->k_ev[0], h->k_ev[1]), "cudaEventElapsedTime");
+    double tot = 0;
+    for (size_t i = 0; i < h->k_used; i++) {
+        float ms = 0;
+        CK(cudaEventSynchronize(h->k_ev[i].second), "cudaEventSynchronize");
+        CK(cudaEventElapsedTime(&ms, h->k_ev[i].first, h->k_ev[i].second), "cudaEventElapsedTime");
+        tot += ms;
+    }
+    *total_ms = tot;
+    *launches = (int32_t)h->k_used;
+    h->k_used = 0;
     return MAGUS_OK;
 }
 

@@ -23,13 +23,14 @@
 #include <stdint.h>
 
 #include "magus_internal.h"
+#include "replay_core.cuh"
 
 namespace magus {
 namespace {
 
 constexpr int HALO = 64;            // deltas kept before each stage (>= max W)
 constexpr int SB = 1024;            // rounds per warp sub-block: 32 rows x 32
-constexpr uint32_t FULL = 0xffffffffu;
+using core::FULL;
 constexpr unsigned long long kWaitNs = 2000000000ull;  // bounded waits: 2 s
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -80,52 +81,6 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
 __device__ __forceinline__ void group_sync(int id, int nthreads) {
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
 }
-__device__ __forceinline__ uint32_t rotl(uint32_t x, int s) { return __funnelshift_l(x, x, s); }
-__device__ __forceinline__ uint32_t rotr(uint32_t x, int s) { return __funnelshift_r(x, x, s); }
-
-// SplitMix64 output function (Steele, Lea, Flood 2014): hashes change-log entries.
-__device__ __forceinline__ uint64_t mix64(uint64_t z) {
-    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
-    z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
-    return z ^ (z >> 31);
-}
-__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v) {
-#pragma unroll
-    for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(FULL, v, d);
-    return v;
-}
-
-// Alg. 2 over one row: bit p of the result = high-frequency state of round p.
-// H: flags of the 64 rounds before the row (bit q = round q - 64); FL: flags of the row.
-__device__ __forceinline__ uint32_t hf_row(uint64_t H, uint32_t FL, int L, int kmin) {
-    // window ending just before the row: rounds -L .. -1
-    int cnt = __popcll(H >> (64 - L));
-    // most flags any window ending inside the row can hold
-    const int reach = (L > 1 ? __popcll(H >> (65 - L)) : 0) + __popc(FL);
-    if (reach < kmin) return 0u;
-    // bit p of LV = flag of round p - L (leaving the window at round p)
-    const int s = 64 - L;
-    const uint32_t LV = s == 0 ? (uint32_t)H : (uint32_t)((H >> s) | ((uint64_t)FL << (64 - s)));
-    uint32_t HF = 0;
-#pragma unroll
-    for (int p = 0; p < 32; p++) {
-        cnt += (int)((FL >> p) & 1u) - (int)((LV >> p) & 1u);
-        HF |= (uint32_t)(cnt >= kmin) << p;
-    }
-    return HF;
-}
-
-// Latch over one row: SETM = rounds that leave the level at the top, SET0 = at the bottom
-// (disjoint), cin = level before the row (1 = top).  Returns Lm: bit p = level after
-// round p.  Adding SETM to ~SET0 carries from every set-to-top bit through the following
-// hold bits and stops at the next set-to-bottom bit.
-__device__ __forceinline__ uint32_t latch_row(uint32_t SETM, uint32_t SET0, uint32_t cin) {
-    const uint32_t A = ~SET0;
-    const uint64_t sum = (uint64_t)A + (uint64_t)SETM + (uint64_t)cin;
-    const uint32_t carry_in = (uint32_t)sum ^ A ^ SETM;  // carry into each bit position
-    return (carry_in | SETM) & ~SET0;
-}
-
 struct GroupCarry {
     uint64_t hist;      // flags of the 64 rounds before the chunk
     uint64_t count;     // change-log entries emitted so far for the pair
@@ -235,8 +190,8 @@ __global__ void __launch_bounds__(TG * CW * 32) replay_tp_kernel(const TpParams 
         };
         if (tid == 0 && nchunks > 0) issue(0, seq);
 
-        uint32_t acc_n0 = 0, acc_nm = 0, acc_hf = 0;
-        unsigned long long acc_s0 = 0, acc_sm = 0, acc_hash = 0;
+        core::Acc acc;
+        core::acc_zero(acc);
 
         for (uint32_t c = 0; c < nchunks; c++) {
             const uint32_t sq = seq + c;
@@ -268,51 +223,10 @@ __global__ void __launch_bounds__(TG * CW * 32) replay_tp_kernel(const TpParams 
             const uint32_t *row = st + HALO + g * SB + 32 * lane;
             const int64_t r0 = (int64_t)c * CH + g * SB + 32 * lane;  // row start (local)
             const int64_t left = (int64_t)n - r0;
-            const uint32_t vmask = left >= 32 ? FULL : (left <= 0 ? 0u : ((1u << left) - 1u));
-            uint32_t pmask = vmask;  // rounds whose FIFO holds W+1 samples
-            {
-                const uint64_t gstart = n_seen0 + (uint64_t)r0;
-                if (gstart < (uint64_t)P.W) {
-                    const uint32_t wm = (uint32_t)((uint64_t)P.W - gstart);
-                    pmask &= wm >= 32 ? 0u : (FULL << wm);
-                }
-            }
-            uint32_t UPr = 0, DNr = 0, S0r = 0, SMr = 0, BDr = 0;
-#pragma unroll
-            for (int i = 0; i < 32; i++) {
-                const int k = (i + lane) & 31;
-                const uint32_t a = row[k];
-                const uint32_t b = row[k - P.W];
-                const long long m = (long long)a - (long long)b;
-                UPr |= (uint32_t)(m > P.up_mid) << i;
-                DNr |= (uint32_t)(m < P.dn_mid) << i;
-                const uint32_t m32 = a - b;
-                BDr |= (uint32_t)(((m32 - P.up_lo) <= P.up_w) | ((m32 - P.dn_lo) <= P.dn_w)) << i;
-                S0r |= (uint32_t)(a > M.thr0) << i;
-                SMr |= (uint32_t)(a > M.thrM) << i;
-            }
-            // rounds near a decision boundary: exact FP64 evaluation of Alg. 1
-            {
-                uint32_t todo = BDr & rotr(pmask, lane);
-                if (__any_sync(FULL, todo != 0)) {
-                    while (todo) {
-                        const int i = __ffs(todo) - 1;
-                        todo &= todo - 1;
-                        const int k = (i + lane) & 31;
-                        const uint32_t a = row[k], b = row[k - P.W];
-                        const double xa = __ddiv_rn(__dmul_rn(M.bpc, (double)a), M.q);
-                        const double xb = __ddiv_rn(__dmul_rn(M.bpc, (double)b), M.q);
-                        const double der = __ddiv_rn(__dsub_rn(xa, xb), (double)P.W);
-                        const uint32_t bit = 1u << i;
-                        UPr = (der > P.inc) ? (UPr | bit) : (UPr & ~bit);
-                        DNr = (der < P.dec) ? (DNr | bit) : (DNr & ~bit);
-                    }
-                }
-            }
-            const uint32_t UP = rotl(UPr, lane) & pmask;
-            const uint32_t DN = rotl(DNr, lane) & pmask;
-            const uint32_t S0 = rotl(S0r, lane) & vmask;
-            const uint32_t SM = rotl(SMr, lane) & vmask;
+            const uint32_t vmask = core::valid_mask(left);
+            const uint32_t pmask = core::predict_mask(vmask, n_seen0 + (uint64_t)r0, P.W);
+            const core::RowPred rp = core::row_predict(row, lane, P, M, vmask, pmask);
+            const uint32_t UP = rp.UP, DN = rp.DN;
             const uint32_t FL = UP | DN;   // uncore_tune_ls entries of the row
             {
                 const uint32_t f30 = __shfl_sync(FULL, FL, 30), f31 = __shfl_sync(FULL, FL, 31);
@@ -323,11 +237,8 @@ __global__ void __launch_bounds__(TG * CW * 32) replay_tp_kernel(const TpParams 
             // ---------------------------------------------------------------- phase B
             const GroupCarry cr = sh.carry[cw][c & 1];
             const uint64_t tailH = (g == 0) ? cr.hist : sh.xf[cw][g > 0 ? g - 1 : 0];
-            const uint32_t p1 = __shfl_up_sync(FULL, FL, 1), p2 = __shfl_up_sync(FULL, FL, 2);
-            const uint64_t H = lane >= 2 ? ((uint64_t)p2 | ((uint64_t)p1 << 32))
-                             : lane == 1 ? ((tailH >> 32) | ((uint64_t)p1 << 32))
-                                         : tailH;
-            const uint32_t HF = hf_row(H, FL, P.L, P.kmin) & vmask;
+            const uint64_t H = core::row_history(FL, tailH, lane);
+            const uint32_t HF = core::hf_row(H, FL, P.L, P.kmin) & vmask;
             const uint32_t SETM = HF | UP;
             const uint32_t SET0 = DN & ~HF;
             const uint32_t EV = SETM | SET0;
@@ -344,7 +255,7 @@ __global__ void __launch_bounds__(TG * CW * 32) replay_tp_kernel(const TpParams 
                 uint32_t det = 0;
                 if (prior || has) {
                     const uint32_t ca = prior ? cin_prior : firstv;
-                    const uint32_t lm = latch_row(SETM, SET0, ca);
+                    const uint32_t lm = core::latch_row(SETM, SET0, ca);
                     det = __popc((lm ^ ((lm << 1) | ca)) & vmask);
                 }
                 const uint32_t wdet = __reduce_add_sync(FULL, det);
@@ -369,33 +280,12 @@ __global__ void __launch_bounds__(TG * CW * 32) replay_tp_kernel(const TpParams 
                 }
             }
             const uint32_t cin = prior ? cin_prior : wcin;
-            const uint32_t Lm = latch_row(SETM, SET0, cin);  // level after each round
+            const uint32_t Lm = core::latch_row(SETM, SET0, cin);  // level after each round
             const uint32_t Flev = (Lm << 1) | cin;            // level during each round
             const uint32_t CHG = (Lm ^ Flev) & vmask;
 
-            acc_n0 += __popc(~Flev & ~S0 & vmask);
-            acc_nm += __popc(Flev & ~SM & vmask);
-            acc_hf += __popc(HF);
-            {
-                const uint32_t M0 = ~Flev & S0 & vmask;
-                if (__any_sync(FULL, M0 != 0)) {
-                    const uint32_t Mr = rotr(M0, lane);
-#pragma unroll
-                    for (int i = 0; i < 32; i++) {
-                        const uint32_t a = row[(i + lane) & 31];
-                        acc_s0 += ((Mr >> i) & 1u) ? a : 0u;
-                    }
-                }
-                const uint32_t MM = Flev & SM & vmask;
-                if (__any_sync(FULL, MM != 0)) {
-                    const uint32_t Mr = rotr(MM, lane);
-#pragma unroll
-                    for (int i = 0; i < 32; i++) {
-                        const uint32_t a = row[(i + lane) & 31];
-                        acc_sm += ((Mr >> i) & 1u) ? a : 0u;
-                    }
-                }
-            }
+            core::row_energy(row, lane, Flev, rp, vmask, acc);
+            acc.hf += __popc(HF);
             // frequency-change log
             if (__any_sync(FULL, CHG != 0)) {
                 const uint32_t nch = __popc(CHG);
@@ -414,7 +304,7 @@ __global__ void __launch_bounds__(TG * CW * 32) replay_tp_kernel(const TpParams 
                     const uint32_t lv = ((Lm >> q) & 1u) ? topK : 0u;
                     if (p.log_entries && off < p.log_cap)
                         p.log_entries[(uint64_t)pair * p.log_cap + off] = (uint32_t)(when << 5) | lv;
-                    acc_hash += mix64((when << 8) | lv);
+                    acc.hash += core::mix64((when << 8) | lv);
                     off++;
                 }
             }
@@ -449,12 +339,12 @@ __global__ void __launch_bounds__(TG * CW * 32) replay_tp_kernel(const TpParams 
 
         // ------------------------------------------------------------------ totals
         {
-            const uint32_t n0 = __reduce_add_sync(FULL, acc_n0);
-            const uint32_t nm = __reduce_add_sync(FULL, acc_nm);
-            const uint32_t hf = __reduce_add_sync(FULL, acc_hf);
-            const unsigned long long s0 = warp_sum_u64(acc_s0);
-            const unsigned long long smv = warp_sum_u64(acc_sm);
-            const unsigned long long hs = warp_sum_u64(acc_hash);
+            const uint32_t n0 = __reduce_add_sync(FULL, acc.n0);
+            const uint32_t nm = __reduce_add_sync(FULL, acc.nm);
+            const uint32_t hf = __reduce_add_sync(FULL, acc.hf);
+            const unsigned long long s0 = core::warp_sum_u64(acc.s0);
+            const unsigned long long smv = core::warp_sum_u64(acc.sm);
+            const unsigned long long hs = core::warp_sum_u64(acc.hash);
             if (lane == 0) {
                 sh.red_n0[warp] = n0;
                 sh.red_nm[warp] = nm;
@@ -476,10 +366,8 @@ __global__ void __launch_bounds__(TG * CW * 32) replay_tp_kernel(const TpParams 
                 SMs += sh.red_sm[w];
                 HS += sh.red_hash[w];
             }
-            const double t0 = M.dt * (double)N0 + M.a0 * (double)S0;   // seconds at the bottom
-            const double tM = M.dt * (double)NM + M.aM * (double)SMs;  // seconds at the top
-            const double T = t0 + tM;
-            const double E = M.P0 * t0 + M.PM * tM;
+            double E, T;
+            core::totals(M, N0, NM, S0, SMs, &E, &T);
             p.energy[pair] = E;
             p.edp[pair] = E * T;
             if (p.time) p.time[pair] = T;

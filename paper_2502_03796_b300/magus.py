@@ -78,7 +78,7 @@ SIGNATURES = {
     "magus_replay_detail": ([P, P, _U64, P, P, P, P, P, P, P, P], ctypes.c_int),
     "magus_replay_status": ([P, P], ctypes.c_int),
     "magus_replay_set_tile": ([P, _I32, _I32], ctypes.c_int),
-    "magus_replay_kernel_ms": ([P, ctypes.POINTER(ctypes.c_float)], ctypes.c_int),
+    "magus_replay_kernel_time": ([P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
     "magus_replay_autotune": ([P, P, P, _I32, P, _I32, P, P, P], ctypes.c_int),
     "magus_replay_close": ([P], ctypes.c_int),
     "magus_packed_size": ([P, _I32, P, P], ctypes.c_int),
@@ -294,11 +294,12 @@ class Replay:
     def status(self, stream=None) -> int:
         return lib().magus_replay_status(self.h, _stream(stream))
 
-    def kernel_ms(self) -> float:
-        """Device time of the last batched-kernel launch (waits for it)."""
-        ms = ctypes.c_float()
-        check(lib().magus_replay_kernel_ms(self.h, ctypes.byref(ms)))
-        return ms.value
+    def kernel_time(self):
+        """(total ms, launches) of batched-kernel launches since the previous call."""
+        ms = ctypes.c_double()
+        n = ctypes.c_int32()
+        check(lib().magus_replay_kernel_time(self.h, ctypes.byref(ms), ctypes.byref(n)))
+        return ms.value, n.value
 
     def set_tile(self, time_groups: int, policy_slots: int):
         check(lib().magus_replay_set_tile(self.h, time_groups, policy_slots))
