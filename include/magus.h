@@ -253,6 +253,15 @@ int magus_serve_stats(magus_serve_t *s, magus_serve_stats_t *out);
 /* Export all stream states (host, n_streams entries) for checkpointing. */
 int magus_serve_export(magus_serve_t *s, magus_state_t *out_states);
 
+/* Open-loop load driver (benchmarks): submit request i at arrival_s[i] seconds after the
+ * call starts (host busy-wait), stream stream_id[i], size[i] deltas read from
+ * payload + payload_off[i] (host); then drain and poll every request.  out_latency_s (host,
+ * n_req, optional) receives each latency, -1 for requests refused by admission control;
+ * out_wall_s the time from the first arrival to the end of the drain. */
+int magus_serve_load(magus_serve_t *s, const double *arrival_s, const uint32_t *stream_id,
+                     const uint32_t *size, const uint32_t *payload, const uint64_t *payload_off,
+                     int64_t n_req, double *out_latency_s, double *out_wall_s);
+
 int magus_serve_close(magus_serve_t *s);
 
 #ifdef __cplusplus

@@ -92,6 +92,7 @@ SIGNATURES = {
     "magus_serve_drain": ([P], ctypes.c_int),
     "magus_serve_stats": ([P, ctypes.POINTER(ServeStats)], ctypes.c_int),
     "magus_serve_export": ([P, P], ctypes.c_int),
+    "magus_serve_load": ([P, P, P, P, P, P, _I64, P, P], ctypes.c_int),
     "magus_serve_close": ([P], ctypes.c_int),
 }
 
@@ -318,3 +319,75 @@ def decode_log(entries: np.ndarray):
     """Split FULL-log entries into (interval index t+1, level)."""
     e = np.asarray(entries, dtype=np.uint32)
     return (e >> 5).astype(np.uint64), (e & 31).astype(np.uint8)
+
+
+class Serve:
+    """Serving runtime handle (magus_serve_open / _close) with thin wrappers."""
+
+    def __init__(self, model: Dict, policy: Dict, n_streams: int, mem_budget: int = 0, device: int = 0,
+                 max_batch_requests: int = 0, max_batch_samples: int = 0):
+        self._mh = ModelHolder(model)
+        self._pol = make_policy(policy)
+        self.n_streams = n_streams
+        h = ctypes.c_void_p()
+        check(lib().magus_serve_open(ctypes.byref(h), ctypes.byref(self._mh.m), ctypes.byref(self._pol),
+                                     n_streams, mem_budget, device, max_batch_requests, max_batch_samples))
+        self.h = h
+
+    def submit(self, stream_id: int, deltas: np.ndarray) -> int:
+        d = np.ascontiguousarray(deltas, dtype=np.uint32)
+        rid = ctypes.c_uint64()
+        check(lib().magus_serve_submit(self.h, stream_id, d.ctypes.data, len(d), ctypes.byref(rid)))
+        return rid.value
+
+    def try_submit(self, stream_id: int, deltas: np.ndarray):
+        """Returns the request id, or the negative status (e.g. EBUSY) without raising."""
+        d = np.ascontiguousarray(deltas, dtype=np.uint32)
+        rid = ctypes.c_uint64()
+        rc = lib().magus_serve_submit(self.h, stream_id, d.ctypes.data, len(d), ctypes.byref(rid))
+        return rid.value if rc == OK else rc
+
+    def poll(self, req_id: int):
+        """Result dict, or None while the request is not done (EAGAIN)."""
+        r = Result()
+        rc = lib().magus_serve_poll(self.h, req_id, ctypes.byref(r))
+        if rc == EAGAIN:
+            return None
+        check(rc)
+        return {k: getattr(r, k) for k, _ in Result._fields_ if k != "reserved"}
+
+    def drain(self):
+        check(lib().magus_serve_drain(self.h))
+
+    def stats(self) -> Dict:
+        st = ServeStats()
+        check(lib().magus_serve_stats(self.h, ctypes.byref(st)))
+        return {k: getattr(st, k) for k, _ in ServeStats._fields_}
+
+    def export(self) -> np.ndarray:
+        out = np.zeros(self.n_streams * STATE_BYTES, dtype=np.uint8)
+        check(lib().magus_serve_export(self.h, out.ctypes.data))
+        return out
+
+    def load(self, arrival_s, stream_id, size, payload, payload_off):
+        a = np.ascontiguousarray(arrival_s, dtype=np.float64)
+        sid = np.ascontiguousarray(stream_id, dtype=np.uint32)
+        sz = np.ascontiguousarray(size, dtype=np.uint32)
+        pay = np.ascontiguousarray(payload, dtype=np.uint32)
+        off = np.ascontiguousarray(payload_off, dtype=np.uint64)
+        lat = np.zeros(len(a))
+        wall = ctypes.c_double()
+        check(lib().magus_serve_load(self.h, a.ctypes.data, sid.ctypes.data, sz.ctypes.data, pay.ctypes.data,
+                                     off.ctypes.data, len(a), lat.ctypes.data, ctypes.byref(wall)))
+        return lat, wall.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().magus_serve_close(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
