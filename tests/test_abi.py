@@ -1,0 +1,111 @@
+"""Host-side checks of the C ABI (no GPU needed): the library loads and exports every
+symbol include/magus.h declares; host helpers (packed layout, decision bounds) are right."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import tracegen
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def mg():
+    from paper_2502_03796_b300 import build, magus
+    build.build()
+    return magus
+
+
+def declared_symbols():
+    src = open(os.path.join(ROOT, "include", "magus.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(magus_[a-z_]+)\s*\(", src)))
+
+
+def test_every_declared_symbol_is_exported(mg):
+    lib = ctypes.CDLL(mg.LIB_PATH)
+    names = declared_symbols()
+    assert len(names) >= 20
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+    # the binding knows every one of them
+    assert set(names) <= set(mg.SIGNATURES), set(names) - set(mg.SIGNATURES)
+
+
+def test_version_and_error_strings(mg):
+    assert b"sm_103a" in mg.lib().magus_version()
+    with pytest.raises(mg.MagusError):
+        mg.policy_bounds(dict(tracegen.default_policy(), direv_length=0), tracegen.default_model())
+    assert b"direv_length" in mg.lib().magus_last_error()
+
+
+def test_packed_layout(mg):
+    off, tot = mg.packed_offsets([0, 1, 5, 8, 3])
+    assert off.tolist() == [0, 0, 4, 12, 20] and tot == 24
+    ts = tracegen.make_traces(np.array([3, 9, 1], dtype=np.uint64))
+    off, tot = mg.packed_offsets(ts.lengths)
+    assert np.array_equal(off, ts.offsets) and tot == len(ts.data)
+
+
+def exact_decision(a, b, W, thr, model, up=True):
+    """Algorithm 1 comparison evaluated in IEEE double (Python floats), as the oracle does."""
+    q = model["dt_s"] * 1e9
+    bpc = float(model["bytes_per_count"])
+    d = ((bpc * a) / q - (bpc * b) / q) / float(W)
+    return d > thr if up else d < thr
+
+
+@pytest.mark.parametrize("model_kind", ["default", "odd"])
+def test_decision_bounds_against_ieee_double(mg, model_kind):
+    """Outside the band the integer rule must equal the FP64 rule for every base value."""
+    model = tracegen.default_model()
+    if model_kind == "odd":
+        model = dict(model, dt_s=0.037, bytes_per_count=3)
+    rng = np.random.default_rng(1)
+    base = tracegen.default_policy()
+    for pol in [base, dict(base, direv_length=7, inc_threshold=3.3, dec_threshold=-0.7),
+                dict(base, direv_length=64, inc_threshold=1e-7, dec_threshold=-123.456),
+                dict(base, direv_length=1, inc_threshold=-2.0, dec_threshold=-9.0)]:
+        m_up, m_dn, kmin, band = (int(x) for x in mg.policy_bounds(pol, model))
+        W = pol["direv_length"]
+        for _ in range(300):
+            b = int(rng.integers(0, 2**32 - 2**20))
+            for m in range(m_up - band - 4, m_up + band + 6):
+                a = b + m
+                if not 0 <= a < 2**32:
+                    continue
+                ref = exact_decision(a, b, W, pol["inc_threshold"], model, up=True)
+                if m > m_up + band:
+                    assert ref, (pol, a, b)
+                elif m <= m_up - band:
+                    assert not ref, (pol, a, b)
+            for m in range(m_dn - band - 6, m_dn + band + 4):
+                a = b + m
+                if not 0 <= a < 2**32:
+                    continue
+                ref = exact_decision(a, b, W, pol["dec_threshold"], model, up=False)
+                if m < m_dn - band:
+                    assert ref, (pol, a, b)
+                elif m >= m_dn + band:
+                    assert not ref, (pol, a, b)
+
+
+def test_kmin_matches_algorithm_2(mg):
+    model = tracegen.default_model()
+    for L in (1, 2, 3, 10, 33, 64):
+        for th in (-1.0, 0.0, 0.05, 0.3, 0.5, 0.6, 0.6000000001, 0.7, 1.0, 1.5):
+            k = int(mg.policy_bounds(dict(tracegen.default_policy(), tune_window=L, high_freq_threshold=th),
+                                     model)[2])
+            ref = next((c for c in range(L + 1) if c / L >= th), L + 1)
+            assert k == ref, (L, th)
+
+
+def test_model_validation(mg):
+    bad = dict(tracegen.default_model(), f_ghz=[1.0, 0.9])
+    with pytest.raises(mg.MagusError):
+        mg.policy_bounds(tracegen.default_policy(), bad)
+    with pytest.raises(mg.MagusError):
+        mg.policy_bounds(tracegen.default_policy(), dict(tracegen.default_model(), dt_s=0.0))
