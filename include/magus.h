@@ -184,6 +184,35 @@ int magus_replay_autotune(magus_replay_t *h, const uint32_t *traces, const uint6
 
 int magus_replay_close(magus_replay_t *h);
 
+/* Size of the fixed device scratch used by magus_replay_run_static (4 MiB). */
+#define MAGUS_STATIC_SCRATCH_BYTES (4u << 20)
+
+/* Batched replay without any device allocation (the paper has no counterpart: this is a
+ * service for callers of this library).  Some callers cannot call cudaMalloc when they
+ * want a replay -- code running inside another framework's memory pool, a process whose
+ * device memory is reserved up front, a plug-in handed only ready-made buffers -- so they
+ * cannot open a handle (magus_replay_open allocates).  This entry point takes the model
+ * directly and runs the same kernel and computation as magus_replay_run on the CURRENT
+ * device; its planning scratch (policy table, work list, trace offsets/lengths, work
+ * counter, status word) lives in a fixed file-scope device array of
+ * MAGUS_STATIC_SCRATCH_BYTES that every GPU loading the library holds until the process
+ * exits.  It calls no cudaMalloc / cudaFree.
+ *   - Arguments and outputs as magus_replay_run (traces, outputs, log, io_state: device).
+ *   - Workloads whose plan does not fit the scratch (roughly: 64 B per policy plus
+ *     24 B per trace x ceil(policies / 8)) are rejected with EINVAL and a message.
+ *   - The first call on a device looks up the array's device address (set-up, once per
+ *     device); make that first call before any stream capture on that device.
+ *   - Every call shares the one array: the call uploads the plan on `stream`, zeroes the
+ *     work counter and status word, runs the kernel and waits for `stream` before
+ *     returning, so sequential calls are safe, but calls that overlap on the GPU (other
+ *     threads or streams at the same time) race on the scratch and give wrong results.
+ *   - Returns device-side input errors (EINVAL for a carried level that is neither 0 nor
+ *     K-1) directly. */
+int magus_replay_run_static(const magus_model_t *model, const uint32_t *traces, const uint64_t *lengths,
+                            int32_t n_traces, const magus_policy_t *configs, int32_t n_configs,
+                            const magus_freq_log_t *log, double *out_energy, double *out_edp,
+                            double *out_time, magus_state_t *io_state, void *stream);
+
 /* ---------------------------------------------------------------------------------------
  * Helpers (host only, no device needed)
  * ------------------------------------------------------------------------------------- */

@@ -81,6 +81,7 @@ SIGNATURES = {
     "magus_replay_kernel_time": ([P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
     "magus_replay_autotune": ([P, P, P, _I32, P, _I32, P, P, P], ctypes.c_int),
     "magus_replay_close": ([P], ctypes.c_int),
+    "magus_replay_run_static": ([ctypes.POINTER(Model), P, P, _I32, P, _I32, P, P, P, P, P, P], ctypes.c_int),
     "magus_packed_size": ([P, _I32, P, P], ctypes.c_int),
     "magus_policy_bounds": ([ctypes.POINTER(Policy), ctypes.POINTER(Model), P], ctypes.c_int),
     "magus_last_error": ([], ctypes.c_char_p),
