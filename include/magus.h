@@ -32,10 +32,11 @@
  *     errors detected by a kernel are reported by the next magus_replay_status().
  *
  * Packed trace layout (device or host): traces are stored back to back; trace i starts at
- * element offset off_i with off_0 = 0 and off_{i+1} = off_i + round_up(n_i, 4), so every
- * trace starts on a 16-byte boundary; the buffer holds magus_packed_size() elements
- * (padding elements are read but ignored).  Deltas are uint32 counts of bytes_per_count
- * bytes per interval.
+ * element offset off_i with off_0 = 0 and off_{i+1} = off_i + round_up(n_i, 32), so every
+ * trace starts on a 128-byte row of 32 deltas (the batched kernel reads rows of 32 with TMA
+ * tensor copies); the buffer holds magus_packed_size() elements (padding elements are read
+ * but ignored) and its base is 16-byte aligned.  Deltas are uint32 counts of
+ * bytes_per_count bytes per interval.
  */
 #ifndef MAGUS_H
 #define MAGUS_H

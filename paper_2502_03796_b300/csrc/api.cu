@@ -167,7 +167,7 @@ int build_plan(magus_replay *h, const uint64_t *lengths, int32_t n_traces, const
     uint64_t off = 0;
     for (int i = 0; i < n_traces; i++) {
         pl->offsets[i] = off;
-        off += (lengths[i] + 3) / 4 * 4;
+        off += (lengths[i] + kTraceAlign - 1) / kTraceAlign * kTraceAlign;
     }
     // longest traces first: the persistent CTAs take items in this order
     std::vector<int> order(n_traces);
@@ -251,6 +251,16 @@ int launch_plan(magus_replay *h, const Plan &pl, const uint32_t *traces, const O
         CK(cudaEventCreate(&e1), "cudaEventCreate");
         CK(cudaEventRecord(e0, stream), "cudaEventRecord");
     }
+    CUtensorMap tmap;
+    memset(&tmap, 0, sizeof(tmap));
+    if (n_items) {
+        uint64_t total_elems = 0;
+        for (size_t i = 0; i < pl.lengths.size(); i++)
+            total_elems += (pl.lengths[i] + kTraceAlign - 1) / kTraceAlign * kTraceAlign;
+        std::string err;
+        rc = make_trace_tmap(traces, total_elems, tp_box_rows(pl.tg), &tmap, &err);
+        if (rc) { set_error(err); return rc; }
+    }
     if (n_items) {
         if (h->k_used == h->k_ev.size() && h->k_used < 4096) {
             cudaEvent_t a, b;
@@ -260,7 +270,7 @@ int launch_plan(magus_replay *h, const Plan &pl, const uint32_t *traces, const O
         }
         const size_t slot_k = h->k_used < h->k_ev.size() ? h->k_used : h->k_ev.size() - 1;
         CK(cudaEventRecord(h->k_ev[slot_k].first, stream), "cudaEventRecord");
-        CK(launch_replay_tp(pl.tg, pl.cw, p, grid, stream), "replay kernel launch");
+        CK(launch_replay_tp(pl.tg, pl.cw, p, tmap, grid, stream), "replay kernel launch");
         CK(cudaEventRecord(h->k_ev[slot_k].second, stream), "cudaEventRecord");
         if (h->k_used < h->k_ev.size()) h->k_used++;
     }
@@ -355,7 +365,7 @@ int plain_impl(magus_replay *h, const uint32_t *traces, const uint64_t *lengths,
             p.level_log = level_log;
             p.deriv_log = deriv_log;
             CK(launch_replay_plain(p, s), "plain kernel launch");
-            off += (lengths[i] + 3) / 4 * 4;
+            off += (lengths[i] + kTraceAlign - 1) / kTraceAlign * kTraceAlign;
         }
         CK(cudaEventRecord(h->ws_ev, s), "cudaEventRecord");
         h->ws_ev_pending = true;
@@ -381,7 +391,7 @@ int magus_packed_size(const uint64_t *lengths, int32_t n_traces, uint64_t *offse
     uint64_t off = 0;
     for (int i = 0; i < n_traces; i++) {
         if (offsets) offsets[i] = off;
-        off += (lengths[i] + 3) / 4 * 4;
+        off += (lengths[i] + kTraceAlign - 1) / kTraceAlign * kTraceAlign;
     }
     *total = off;
     return MAGUS_OK;
@@ -636,7 +646,7 @@ int magus_replay_run_host(magus_replay_t *h, const uint32_t *traces, const uint6
             size_t bytes = 0;
             int j = i;
             while (j < n_traces) {
-                size_t add = align_up((lengths[j] + 3) / 4 * 4 * 4, 256) + align_up(per_pair * n_configs, 256) + 2048;
+                size_t add = align_up((lengths[j] + kTraceAlign - 1) / kTraceAlign * kTraceAlign * 4, 256) + align_up(per_pair * n_configs, 256) + 2048;
                 if (j > i && bytes + add > slot_bytes) break;
                 bytes += add;
                 j++;
@@ -656,7 +666,7 @@ int magus_replay_run_host(magus_replay_t *h, const uint32_t *traces, const uint6
             size_t b = 0;
             for (int i = 0; i < n_traces; i++) {
                 if (b < batches.size() && batches[b].first == i) first_off[b++] = off;
-                off += (lengths[i] + 3) / 4 * 4;
+                off += (lengths[i] + kTraceAlign - 1) / kTraceAlign * kTraceAlign;
             }
         }
         for (size_t b = 0; b < batches.size(); b++) {
@@ -664,7 +674,7 @@ int magus_replay_run_host(magus_replay_t *h, const uint32_t *traces, const uint6
             const int i0 = batches[b].first, i1 = batches[b].second, nt = i1 - i0;
             char *base = (char *)h->scratch + slot * slot_bytes;
             uint64_t words = 0;
-            for (int i = i0; i < i1; i++) words += (lengths[i] + 3) / 4 * 4;
+            for (int i = i0; i < i1; i++) words += (lengths[i] + kTraceAlign - 1) / kTraceAlign * kTraceAlign;
             uint32_t *d_tr = (uint32_t *)base;
             char *p = base + align_up(words * 4, 256);
             const size_t np = (size_t)nt * n_configs;

@@ -1,5 +1,6 @@
 // magus_internal.h - structures shared by the replay kernels and their host launchers.
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -63,8 +64,14 @@ struct TpParams {
     magus_state_t *state;
 };
 
-cudaError_t launch_replay_tp(int time_groups, int policy_slots, const TpParams &p, int grid,
-                             cudaStream_t stream);
+// Traces are read through a 2-D TMA tensor map over the packed buffer viewed as
+// [rows][32] uint32 (trace starts are multiples of 32 elements), 128-byte swizzle.
+constexpr int kTraceAlign = 32;
+int make_trace_tmap(const uint32_t *traces, uint64_t total_elems, int box_rows, CUtensorMap *out,
+                    std::string *err);
+int tp_box_rows(int time_groups);
+cudaError_t launch_replay_tp(int time_groups, int policy_slots, const TpParams &p, const CUtensorMap &tmap,
+                             int grid, cudaStream_t stream);
 int tp_max_ctas_per_sm(int time_groups, int policy_slots, int *smem_bytes);
 
 struct PlainParams {

@@ -117,7 +117,7 @@ extern "C" int magus_replay_run_static(const magus_model_t *model, const uint32_
     for (int i = 0; i < n_traces; i++) {
         offs[i] = o;
         lens[i] = lengths[i];
-        o += (lengths[i] + 3) / 4 * 4;
+        o += (lengths[i] + kTraceAlign - 1) / kTraceAlign * kTraceAlign;
     }
     cudaStream_t s = (cudaStream_t)stream;
     // the copy also zeroes the status word and the work counter (first 256 bytes)
@@ -153,7 +153,10 @@ extern "C" int magus_replay_run_static(const magus_model_t *model, const uint32_
         e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (e != cudaSuccess || per_sm <= 0) return fail("device query failed", MAGUS_ECUDA);
         const int grid = (int)std::max<size_t>(1, std::min<size_t>(n_items, (size_t)sms * per_sm));
-        e = launch_replay_tp(tg, cw, p, grid, s);
+        CUtensorMap tmap;
+        rc = make_trace_tmap(traces, o, tp_box_rows(tg), &tmap, &err);
+        if (rc) return fail(err, rc);
+        e = launch_replay_tp(tg, cw, p, tmap, grid, s);
         if (e != cudaSuccess) return fail(std::string("replay kernel launch: ") + cudaGetErrorString(e), MAGUS_ECUDA);
     }
     // synchronous: the scratch is reused by the next call, and device-side input errors

@@ -2,9 +2,12 @@
 // batched kernel (replay_tp.cu) and the serving kernel (serve.cu).
 //
 // A "row" is 32 consecutive rounds owned by one lane; bit p of every mask is round p of the
-// row.  Rows sit in shared memory with at least 64 earlier deltas before them, and lanes
-// read their rows in rotated order k = (i + lane) & 31 so that the 32 lanes of a warp hit
-// 32 different banks.
+// row.  Rows sit in shared memory in the 128-byte swizzled layout that a TMA tensor copy
+// with CU_TENSOR_MAP_SWIZZLE_128B writes: the 16-byte chunk c of row R lives at chunk
+// position c ^ (R & 7).  A lane reading its own row chunk by chunk therefore touches a
+// different bank group than the 7 other lanes of its quarter-warp, and the chunk index --
+// hence the register index -- stays a compile-time constant.  Data row 0 of a sub-block is
+// 1024-byte aligned and rows -1 and -2 (the 64 deltas before it) are always readable.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -15,6 +18,7 @@ namespace magus {
 namespace core {
 
 constexpr uint32_t FULL = 0xffffffffu;
+constexpr int32_t kFastLimit = 1 << 30;   // fast path: every delta below 2^30
 
 __device__ __forceinline__ uint32_t rotl(uint32_t x, int s) { return __funnelshift_l(x, x, s); }
 __device__ __forceinline__ uint32_t rotr(uint32_t x, int s) { return __funnelshift_r(x, x, s); }
@@ -32,6 +36,36 @@ __device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v)
     return v;
 }
 
+// ------------------------------------------------------------------ swizzled shared memory
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+// byte address of chunk c (0..7) of row R (may be -1, -2) relative to data row 0 at `base`
+__device__ __forceinline__ uint32_t swz_chunk(uint32_t base, int R, int c) {
+    return base + (uint32_t)(R * 128) + ((uint32_t)((c ^ R) & 7) << 4);
+}
+// byte address of element E (>= -64) relative to data row 0
+__device__ __forceinline__ uint32_t swz_elem(uint32_t base, int E) {
+    const int R = E >> 5;
+    return swz_chunk(base, R, (E >> 2) & 7) + ((uint32_t)(E & 3) << 2);
+}
+__device__ __forceinline__ void lds128(uint32_t addr, uint32_t &a, uint32_t &b, uint32_t &c, uint32_t &d) {
+    asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];" : "=r"(a), "=r"(b), "=r"(c), "=r"(d) : "r"(addr));
+}
+__device__ __forceinline__ uint32_t lds32(uint32_t addr) {
+    uint32_t v;
+    asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(addr));
+    return v;
+}
+__device__ __forceinline__ void sts32(uint32_t addr, uint32_t v) {
+    asm volatile("st.shared.u32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
+}
+// the 32 deltas of row R, in order
+__device__ __forceinline__ void load_row(uint32_t base, int R, uint32_t (&v)[32]) {
+#pragma unroll
+    for (int c = 0; c < 8; c++) lds128(swz_chunk(base, R, c), v[4 * c], v[4 * c + 1], v[4 * c + 2], v[4 * c + 3]);
+}
+
 // Valid-round mask of a row with `left` rounds remaining from its start.
 __device__ __forceinline__ uint32_t valid_mask(int64_t left) {
     return left >= 32 ? FULL : (left <= 0 ? 0u : ((1u << left) - 1u));
@@ -47,66 +81,145 @@ __device__ __forceinline__ uint32_t predict_mask(uint32_t vmask, uint64_t gstart
 struct RowPred {
     uint32_t UP, DN;   // Alg. 1 returned +1 / -1
     uint32_t S0, SM;   // interval stretched at the bottom / top level (x > C(f))
+    bool fast;         // every delta of the row and its window below 2^30
 };
 
-// Alg. 1 for the 32 rounds of a row: derivative = (x_t - x_{t-W}) / W against inc / dec,
-// decided on the integer difference of the deltas outside the narrow band the host derived
-// (plan.cu) and by the exact FP64 evaluation inside it.
-__device__ __forceinline__ RowPred row_predict(const uint32_t *row, int lane, const DevPolicy &P,
-                                               const DevModel &M, uint32_t vmask, uint32_t pmask) {
-    uint32_t UPr = 0, DNr = 0, S0r = 0, SMr = 0, BDr = 0;
-#pragma unroll
-    for (int i = 0; i < 32; i++) {
-        const int k = (i + lane) & 31;
-        const uint32_t a = row[k];
-        const uint32_t b = row[k - P.W];
+// Integer decision points clamped to the fast path's reach (|m| < 2^30): beyond it the
+// comparison is constant over every reachable m, so clamping does not change it.
+__device__ __forceinline__ int32_t clamp_mid(int64_t v) {
+    const int64_t lim = (int64_t)kFastLimit + 8;
+    return (int32_t)(v > lim ? lim : (v < -lim ? -lim : v));
+}
+__device__ __forceinline__ int32_t clamp_thr(uint32_t t) {
+    return (int32_t)(t > (uint32_t)kFastLimit + 8u ? (uint32_t)kFastLimit + 8u : t);
+}
+
+// Alg. 1 for one row, exact for any deltas: 64-bit integer decisions outside the band the
+// host derived (plan.cu) and the FP64 evaluation, in the oracle's order, inside it.
+static __device__ __noinline__ void row_predict_general(uint32_t base, int lane, const DevPolicy &P, const DevModel &M,
+                                                 uint32_t &UP, uint32_t &DN, uint32_t &S0, uint32_t &SM) {
+    UP = DN = S0 = SM = 0;
+    for (int k = 0; k < 32; k++) {
+        const int E = 32 * lane + k;
+        const uint32_t a = lds32(swz_elem(base, E));
+        const uint32_t b = lds32(swz_elem(base, E - P.W));
         const long long m = (long long)a - (long long)b;
-        UPr |= (uint32_t)(m > P.up_mid) << i;
-        DNr |= (uint32_t)(m < P.dn_mid) << i;
+        bool up = m > P.up_mid, dn = m < P.dn_mid;
         const uint32_t m32 = a - b;
-        BDr |= (uint32_t)(((m32 - P.up_lo) <= P.up_w) | ((m32 - P.dn_lo) <= P.dn_w)) << i;
-        S0r |= (uint32_t)(a > M.thr0) << i;
-        SMr |= (uint32_t)(a > M.thrM) << i;
-    }
-    uint32_t todo = BDr & rotr(pmask, lane);
-    if (__any_sync(FULL, todo != 0)) {
-        while (todo) {
-            const int i = __ffs(todo) - 1;
-            todo &= todo - 1;
-            const int k = (i + lane) & 31;
-            const uint32_t a = row[k], b = row[k - P.W];
+        if (((m32 - P.up_lo) <= P.up_w) || ((m32 - P.dn_lo) <= P.dn_w)) {
             const double xa = __ddiv_rn(__dmul_rn(M.bpc, (double)a), M.q);
             const double xb = __ddiv_rn(__dmul_rn(M.bpc, (double)b), M.q);
             const double der = __ddiv_rn(__dsub_rn(xa, xb), (double)P.W);
-            const uint32_t bit = 1u << i;
-            UPr = (der > P.inc) ? (UPr | bit) : (UPr & ~bit);
-            DNr = (der < P.dec) ? (DNr | bit) : (DNr & ~bit);
+            up = der > P.inc;
+            dn = der < P.dec;
         }
+        UP |= (uint32_t)up << k;
+        DN |= (uint32_t)dn << k;
+        S0 |= (uint32_t)(a > M.thr0) << k;
+        SM |= (uint32_t)(a > M.thrM) << k;
     }
+}
+
+// Fast path, S = (-W) mod 4.  t = c - a + b has its sign bit set exactly when the integer
+// comparison holds (no overflow while every delta is below 2^30); a funnel shift pushes that
+// bit into the mask, so round k ends up at bit 31 - k.
+template <int S>
+__device__ __forceinline__ void row_predict_fast(uint32_t base, int lane, int W, int32_t upc, int32_t dnc,
+                                                 int32_t thr0c, uint32_t &UPr, uint32_t &DNr, uint32_t &S0r,
+                                                 uint32_t &guard, uint32_t &band, uint32_t &amax,
+                                                 uint32_t (&v)[32]) {
+    load_row(base, lane, v);
+    // window of the deltas W rounds earlier: 36 deltas from the 4-aligned element E0
+    uint32_t u[36];
+    const int E0 = 32 * lane - (W + S);
+#pragma unroll
+    for (int c = 0; c < 9; c++) {
+        const int E = E0 + 4 * c;
+        lds128(swz_chunk(base, E >> 5, (E >> 2) & 7), u[4 * c], u[4 * c + 1], u[4 * c + 2], u[4 * c + 3]);
+    }
+    uint32_t g = 0, bd = 0xffffffffu, mx = 0;
+#pragma unroll
+    for (int k = 0; k < 32; k++) {
+        const uint32_t a = v[k], b = u[k + S];
+        const int32_t tu = upc - (int32_t)a + (int32_t)b;     // < 0  <=>  m > up_mid
+        const int32_t td = (int32_t)a - (int32_t)b - dnc;     // < 0  <=>  m < dn_mid
+        const int32_t ts = thr0c - (int32_t)a;                // < 0  <=>  a > thr0
+        UPr = __funnelshift_l((uint32_t)tu, UPr, 1);
+        DNr = __funnelshift_l((uint32_t)td, DNr, 1);
+        S0r = __funnelshift_l((uint32_t)ts, S0r, 1);
+        bd = __viaddmin_u32((uint32_t)tu, 3u, bd);            // up band: tu in [-3, 2]
+        bd = __viaddmin_u32((uint32_t)td, 2u, bd);            // dn band: td in [-2, 3]
+        g |= a | b;
+        mx = max(mx, a);
+    }
+    guard = g;
+    band = bd;
+    amax = mx;
+}
+
+template <int S>
+__device__ __forceinline__ bool row_predict_fast_dispatch(uint32_t base, int lane, const DevPolicy &P,
+                                                          const DevModel &M, RowPred &r, uint32_t (&v)[32]) {
+    uint32_t UPr = 0, DNr = 0, S0r = 0, guard, band, amax;
+    row_predict_fast<S>(base, lane, P.W, clamp_mid(P.up_mid), clamp_mid(P.dn_mid), clamp_thr(M.thr0), UPr, DNr,
+                        S0r, guard, band, amax, v);
+    // fall back when a delta reaches 2^30 or a round lies in a decision band
+    if (__any_sync(FULL, guard >= (uint32_t)kFastLimit || band <= 5u)) return false;
+    r.UP = __brev(UPr);
+    r.DN = __brev(DNr);
+    r.S0 = __brev(S0r);
+    r.SM = 0;
+    if (__any_sync(FULL, amax > M.thrM)) {
+        uint32_t SMr = 0;
+        const int32_t tm = clamp_thr(M.thrM);
+#pragma unroll
+        for (int k = 0; k < 32; k++) SMr = __funnelshift_l((uint32_t)(tm - (int32_t)v[k]), SMr, 1);
+        r.SM = __brev(SMr);
+    }
+    return true;
+}
+
+// Alg. 1 predictions and stretch bits of this lane's row (rows of the sub-block at `base`).
+__device__ __forceinline__ RowPred row_predict(uint32_t base, int lane, const DevPolicy &P, const DevModel &M,
+                                               uint32_t vmask, uint32_t pmask) {
     RowPred r;
-    r.UP = rotl(UPr, lane) & pmask;
-    r.DN = rotl(DNr, lane) & pmask;
-    r.S0 = rotl(S0r, lane) & vmask;
-    r.SM = rotl(SMr, lane) & vmask;
+    uint32_t v[32];
+    bool ok;
+    switch ((-P.W) & 3) {
+        case 0: ok = row_predict_fast_dispatch<0>(base, lane, P, M, r, v); break;
+        case 1: ok = row_predict_fast_dispatch<1>(base, lane, P, M, r, v); break;
+        case 2: ok = row_predict_fast_dispatch<2>(base, lane, P, M, r, v); break;
+        default: ok = row_predict_fast_dispatch<3>(base, lane, P, M, r, v); break;
+    }
+    r.fast = ok;
+    if (!ok) row_predict_general(base, lane, P, M, r.UP, r.DN, r.S0, r.SM);
+    r.UP &= pmask;
+    r.DN &= pmask;
+    r.S0 &= vmask;
+    r.SM &= vmask;
     return r;
 }
 
-// Alg. 2 over one row: bit p of the result = high-frequency state of round p.
-// H: flags of the 64 rounds before the row (bit q = round q - 64); FL: flags of the row.
+// Alg. 2 over one row: bit p of the result = high-frequency state of round p, i.e. at
+// least kmin flags among rounds p-L+1 .. p.  H: flags of the 64 rounds before the row
+// (bit q = round q - 64); FL: flags of the row.  The counts of rounds p, p+8, p+16, p+24
+// advance together, one per byte of a 32-bit word (counts <= 64 never carry across bytes).
 __device__ __forceinline__ uint32_t hf_row(uint64_t H, uint32_t FL, int L, int kmin) {
-    // window ending just before the row: rounds -L .. -1
-    int cnt = __popcll(H >> (64 - L));
-    // most flags any window ending inside the row can hold
-    const int reach = (L > 1 ? __popcll(H >> (65 - L)) : 0) + __popc(FL);
-    if (reach < kmin) return 0u;
-    // bit p of LV = flag of round p - L (leaving the window at round p)
     const int s = 64 - L;
+    // bit p of LV = flag of round p - L (leaving the window at round p)
     const uint32_t LV = s == 0 ? (uint32_t)H : (uint32_t)((H >> s) | ((uint64_t)FL << (64 - s)));
+    const uint32_t c0 = __popcll(H >> s);                    // window ending at round -1
+    const uint32_t d0 = __popc(FL & 0xffu) - __popc(LV & 0xffu);
+    const uint32_t d1 = __popc(FL & 0xff00u) - __popc(LV & 0xff00u);
+    const uint32_t d2 = __popc(FL & 0xff0000u) - __popc(LV & 0xff0000u);
+    const uint32_t c1 = c0 + d0, c2 = c1 + d1, c3 = c2 + d2; // windows ending at 7, 15, 23
+    // byte b holds count + 128 - kmin: bit 7 of the byte <=> count >= kmin
+    uint32_t e4 = (c0 | (c1 << 8) | (c2 << 16) | (c3 << 24)) + (uint32_t)(128 - kmin) * 0x01010101u;
     uint32_t HF = 0;
 #pragma unroll
-    for (int p = 0; p < 32; p++) {
-        cnt += (int)((FL >> p) & 1u) - (int)((LV >> p) & 1u);
-        HF |= (uint32_t)(cnt >= kmin) << p;
+    for (int p = 0; p < 8; p++) {
+        e4 = e4 + ((FL >> p) & 0x01010101u) - ((LV >> p) & 0x01010101u);
+        HF = (HF >> 1) | (e4 & 0x80808080u);
     }
     return HF;
 }
@@ -131,14 +244,23 @@ __device__ __forceinline__ uint32_t latch_row(uint32_t SETM, uint32_t SET0, uint
     return (carry_in | SETM) & ~SET0;
 }
 
-// Sum of the row's deltas at the rounds selected by mask M (bit p = round p).
-__device__ __forceinline__ unsigned long long row_masked_sum(const uint32_t *row, int lane, uint32_t M) {
+// Sum of the row's deltas at the rounds selected by mask Msel (bit p = round p).
+__device__ __forceinline__ unsigned long long row_masked_sum(uint32_t base, int lane, uint32_t Msel, bool fast) {
+    uint32_t v[32];
+    load_row(base, lane, v);
     unsigned long long s = 0;
-    const uint32_t Mr = rotr(M, lane);
+    if (fast) {
+        // every delta < 2^30: four of them fit a 32-bit partial sum
 #pragma unroll
-    for (int i = 0; i < 32; i++) {
-        const uint32_t a = row[(i + lane) & 31];
-        s += ((Mr >> i) & 1u) ? a : 0u;
+        for (int c = 0; c < 8; c++) {
+            uint32_t part = 0;
+#pragma unroll
+            for (int e = 0; e < 4; e++) part += ((Msel >> (4 * c + e)) & 1u) ? v[4 * c + e] : 0u;
+            s += part;
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < 32; k++) s += ((Msel >> k) & 1u) ? v[k] : 0u;
     }
     return s;
 }
@@ -155,14 +277,15 @@ __device__ __forceinline__ void acc_zero(Acc &a) {
 }
 
 // Energy bookkeeping of a row once its levels Flev (bit p = level during round p) are known.
-__device__ __forceinline__ void row_energy(const uint32_t *row, int lane, uint32_t Flev, const RowPred &r,
+__device__ __forceinline__ void row_energy(uint32_t base, int lane, uint32_t Flev, const RowPred &r,
                                            uint32_t vmask, Acc &acc) {
     acc.n0 += __popc(~Flev & ~r.S0 & vmask);
     acc.nm += __popc(Flev & ~r.SM & vmask);
+    const bool fast = __all_sync(FULL, r.fast);
     const uint32_t M0 = ~Flev & r.S0 & vmask;
-    if (__any_sync(FULL, M0 != 0)) acc.s0 += row_masked_sum(row, lane, M0);
+    if (__any_sync(FULL, M0 != 0)) acc.s0 += row_masked_sum(base, lane, M0, fast);
     const uint32_t MM = Flev & r.SM & vmask;
-    if (__any_sync(FULL, MM != 0)) acc.sm += row_masked_sum(row, lane, MM);
+    if (__any_sync(FULL, MM != 0)) acc.sm += row_masked_sum(base, lane, MM, fast);
 }
 
 // Energy and time totals from the integer accumulators (energy model: an interval at level
@@ -173,6 +296,11 @@ __device__ __forceinline__ void totals(const DevModel &M, uint64_t N0, uint64_t 
     const double tM = M.dt * (double)NM + M.aM * (double)SMs;   // seconds at the top
     *T = t0 + tM;
     *E = M.P0 * t0 + M.PM * tM;
+}
+
+// The 64 deltas ending at element `last` (relative to data row 0), oldest first.
+__device__ __forceinline__ void read_hist(uint32_t base, int last, uint32_t *out) {
+    for (int k = 0; k < 64; k++) out[k] = lds32(swz_elem(base, last - 63 + k));
 }
 
 }  // namespace core

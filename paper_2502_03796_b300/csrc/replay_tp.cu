@@ -12,10 +12,12 @@
 // set-to-bottom bit).  Rows are chained by a ballot scan inside the warp, warps of a
 // chunk by a short exchange through shared memory, chunks by a carried level.
 //
-// Data path: the CTA streams one trace through a two-stage shared-memory ring with 1-D
-// bulk copies (cp.async.bulk + mbarrier complete_tx); each stage keeps the 64 deltas that
-// precede it so the window W <= 64 never reaches outside shared memory.  One staged chunk
-// feeds every policy the CTA holds (policy_slots groups of time_groups warps).
+// Data path: the CTA streams one trace through a two-stage shared-memory ring with 2-D TMA
+// tensor copies (cp.async.bulk.tensor + mbarrier complete_tx) of time_groups x 32 rows of
+// 32 deltas, 128-byte swizzled so that every lane reads its own row with conflict-free
+// 128-bit loads; each stage keeps the 2 rows (64 deltas) that precede it so the window
+// W <= 64 never reaches outside shared memory.  One staged chunk feeds every policy the
+// CTA holds (policy_slots groups of time_groups warps).
 //
 // Energy: per level the kernel counts unstretched intervals and sums the deltas of
 // stretched ones (integers, exact); the FP64 totals are formed once per pair.
@@ -33,9 +35,8 @@ constexpr int SB = 1024;            // rounds per warp sub-block: 32 rows x 32
 using core::FULL;
 constexpr unsigned long long kWaitNs = 2000000000ull;  // bounded waits: 2 s
 
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
+using core::smem_u32;
+
 __device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
 }
@@ -71,11 +72,12 @@ __device__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
         if (globaltimer() - t0 > kWaitNs) return false;
     }
 }
-__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+// 2-D tensor copy of box (32 deltas x rows) at row y of the trace buffer into shared memory.
+__device__ __forceinline__ void tma_rows(uint32_t dst, const CUtensorMap *tmap, int y, uint64_t *bar) {
     asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-            smem_u32(dst)),
-        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            dst),
+        "l"(tmap), "r"(0), "r"(y), "r"(smem_u32(bar))
         : "memory");
 }
 __device__ __forceinline__ void group_sync(int id, int nthreads) {
@@ -100,22 +102,32 @@ struct Shared {
     int abort;
 };
 
+// Stage: a 1024-byte block whose last two rows hold the preceding 64 deltas, then the
+// chunk's TG * 32 rows; both 1024-byte aligned (the 128-byte swizzle repeats every 8 rows).
+template <int TG>
+__host__ __device__ constexpr size_t stage_bytes() {
+    return 1024 + (size_t)TG * SB * sizeof(uint32_t);
+}
 template <int TG, int CW>
 __host__ __device__ constexpr size_t stage_offset() {
-    return (sizeof(Shared<TG, CW>) + 127) / 128 * 128;
+    return (sizeof(Shared<TG, CW>) + 1023) / 1024 * 1024;
 }
 template <int TG, int CW>
 __host__ __device__ constexpr size_t smem_bytes() {
-    return stage_offset<TG, CW>() + 2 * (size_t)(HALO + TG * SB) * sizeof(uint32_t);
+    return 1024 /* alignment slack */ + stage_offset<TG, CW>() + 2 * stage_bytes<TG>();
 }
 
 template <int TG, int CW>
-__global__ void __launch_bounds__(TG * CW * 32) replay_tp_kernel(const TpParams p) {
+__global__ void __launch_bounds__(TG * CW * 32) replay_tp_kernel(const TpParams p,
+                                                                   const __grid_constant__ CUtensorMap tmap) {
     constexpr int CH = TG * SB;              // rounds per chunk
-    constexpr int STAGE = HALO + CH;         // words per stage
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    Shared<TG, CW> &sh = *reinterpret_cast<Shared<TG, CW> *>(smem_raw);
-    uint32_t *stages = reinterpret_cast<uint32_t *>(smem_raw + stage_offset<TG, CW>());
+    constexpr int CH_ROWS = TG * 32;         // 32-delta rows per chunk
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char *smem_al = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023);
+    Shared<TG, CW> &sh = *reinterpret_cast<Shared<TG, CW> *>(smem_al);
+    // data row 0 of stage s (shared-window byte address)
+    const uint32_t stage0 = smem_u32(smem_al + stage_offset<TG, CW>()) + 1024;
+    auto stage_base = [&](int s_) { return stage0 + (uint32_t)s_ * (uint32_t)stage_bytes<TG>(); };
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int cw = warp / TG, g = warp % TG;
@@ -143,7 +155,6 @@ __global__ void __launch_bounds__(TG * CW * 32) replay_tp_kernel(const TpParams 
         const int cfg = (int)wi.cfg0 + cw;
         const bool active = cfg < p.n_pols;
         const uint64_t n = p.lengths[wi.trace];
-        const uint32_t *src = p.traces + p.offsets[wi.trace];
         const int64_t pair = (int64_t)wi.trace * p.n_pols + (active ? cfg : (int)wi.cfg0);
         const int64_t pair0 = (int64_t)wi.trace * p.n_pols + (int64_t)wi.cfg0;
 
@@ -170,22 +181,19 @@ __global__ void __launch_bounds__(TG * CW * 32) replay_tp_kernel(const TpParams 
             c0.pad = 0;
             sh.carry[cw][0] = c0;
         }
-        // Deltas before the first chunk (the first policy's carried history).
-        uint32_t *st_first = stages + (seq & 1) * STAGE;
+        // Deltas before the first chunk (the first policy's carried history), rows -2, -1.
         if (warp == 0) {
-            for (int k = lane; k < HALO; k += 32) st_first[k] = p.state ? p.state[pair0].hist[k] : 0u;
+            const uint32_t b0 = stage_base(seq & 1);
+            for (int k = lane; k < HALO; k += 32)
+                core::sts32(core::swz_elem(b0, k - HALO), p.state ? p.state[pair0].hist[k] : 0u);
         }
         __syncthreads();
 
         const uint32_t nchunks = (uint32_t)((n + CH - 1) / CH);
+        const int row0 = (int)(p.offsets[wi.trace] / 32);   // first tensor row of the trace
         auto issue = [&](uint32_t c, uint32_t sq) {
-            const uint64_t t0 = (uint64_t)c * CH;
-            const uint64_t left = n - t0;
-            const uint32_t words = (uint32_t)(left < (uint64_t)CH ? left : (uint64_t)CH);
-            const uint32_t bytes = ((words + 3u) & ~3u) * 4u;
-            uint32_t *dst = stages + (sq & 1) * STAGE + HALO;
-            mbar_expect_tx(&sh.bar[sq & 1], bytes);
-            bulk_g2s(dst, src + t0, bytes, &sh.bar[sq & 1]);
+            mbar_expect_tx(&sh.bar[sq & 1], (uint32_t)CH_ROWS * 128u);
+            tma_rows(stage_base(sq & 1), &tmap, row0 + (int)c * CH_ROWS, &sh.bar[sq & 1]);
             pend[sq & 1] = (int)((sq >> 1) & 1);
         };
         if (tid == 0 && nchunks > 0) issue(0, seq);
@@ -196,7 +204,7 @@ __global__ void __launch_bounds__(TG * CW * 32) replay_tp_kernel(const TpParams 
         for (uint32_t c = 0; c < nchunks; c++) {
             const uint32_t sq = seq + c;
             const int s = (int)(sq & 1);
-            uint32_t *st = stages + s * STAGE;
+            const uint32_t sbase = stage_base(s);
             if (tid == 0) {
                 if (!mbar_wait_bounded(&sh.bar[s], (sq >> 1) & 1)) {
                     atomicCAS(p.status, 0, MAGUS_ETIMEDOUT);
@@ -210,8 +218,10 @@ __global__ void __launch_bounds__(TG * CW * 32) replay_tp_kernel(const TpParams 
             // every thread observes the completed phase (acquire of the bulk-copy data)
             if (tid != 0) (void)mbar_wait_bounded(&sh.bar[s], (sq >> 1) & 1);
             if (c > 0 && warp == 0) {
-                const uint32_t *prev = stages + (s ^ 1) * STAGE + HALO + CH - HALO;
-                for (int k = lane; k < HALO; k += 32) st[k] = prev[k];
+                // the previous chunk's last two rows become rows -2, -1 (same swizzle phase:
+                // CH_ROWS is a multiple of 8)
+                const uint32_t prev = stage_base(s ^ 1) + (uint32_t)(CH_ROWS - 2) * 128u;
+                for (int k = lane; k < HALO; k += 32) core::sts32(sbase - 256u + 4u * k, core::lds32(prev + 4u * k));
             }
             __syncthreads();
             if (tid == 0 && c + 1 < nchunks) issue(c + 1, sq + 1);
@@ -220,12 +230,12 @@ __global__ void __launch_bounds__(TG * CW * 32) replay_tp_kernel(const TpParams 
             // ---------------------------------------------------------------- phase A
             // predictions (Alg. 1) and stretch bits of this lane's row, read in rotated
             // order k = (i + lane) & 31 so the 32 lanes hit 32 different banks.
-            const uint32_t *row = st + HALO + g * SB + 32 * lane;
+            const uint32_t sub = sbase + (uint32_t)g * (SB * 4u);   // data row 0 of the sub-block
             const int64_t r0 = (int64_t)c * CH + g * SB + 32 * lane;  // row start (local)
             const int64_t left = (int64_t)n - r0;
             const uint32_t vmask = core::valid_mask(left);
             const uint32_t pmask = core::predict_mask(vmask, n_seen0 + (uint64_t)r0, P.W);
-            const core::RowPred rp = core::row_predict(row, lane, P, M, vmask, pmask);
+            const core::RowPred rp = core::row_predict(sub, lane, P, M, vmask, pmask);
             const uint32_t UP = rp.UP, DN = rp.DN;
             const uint32_t FL = UP | DN;   // uncore_tune_ls entries of the row
             {
@@ -284,7 +294,7 @@ __global__ void __launch_bounds__(TG * CW * 32) replay_tp_kernel(const TpParams 
             const uint32_t Flev = (Lm << 1) | cin;            // level during each round
             const uint32_t CHG = (Lm ^ Flev) & vmask;
 
-            core::row_energy(row, lane, Flev, rp, vmask, acc);
+            core::row_energy(sub, lane, Flev, rp, vmask, acc);
             acc.hf += __popc(HF);
             // frequency-change log
             if (__any_sync(FULL, CHG != 0)) {
@@ -331,7 +341,7 @@ __global__ void __launch_bounds__(TG * CW * 32) replay_tp_kernel(const TpParams 
                 so.n_seen = n_seen0 + n;
                 so.level = ((Lm >> pl) & 1u) ? topK : 0u;
                 so.flags = (H >> (pl + 1)) | ((uint64_t)FL << (63 - pl));
-                for (int k = 0; k < 64; k++) so.hist[k] = row[pl - 63 + k];
+                core::read_hist(sub, 32 * lane + pl, so.hist);
             }
         }
         if (sh.abort) break;
@@ -385,12 +395,12 @@ __global__ void __launch_bounds__(TG * CW * 32) replay_tp_kernel(const TpParams 
 }
 
 template <int TG, int CW>
-cudaError_t launch_t(const TpParams &p, int grid, cudaStream_t stream) {
+cudaError_t launch_t(const TpParams &p, const CUtensorMap &tmap, int grid, cudaStream_t stream) {
     const size_t smem = smem_bytes<TG, CW>();
     cudaError_t e = cudaFuncSetAttribute(replay_tp_kernel<TG, CW>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    replay_tp_kernel<TG, CW><<<grid, TG * CW * 32, smem, stream>>>(p);
+    replay_tp_kernel<TG, CW><<<grid, TG * CW * 32, smem, stream>>>(p, tmap);
     return cudaGetLastError();
 }
 
@@ -410,11 +420,14 @@ int occ_t(int *smem_out) {
 
 }  // namespace
 
-cudaError_t launch_replay_tp(int tg, int cw, const TpParams &p, int grid, cudaStream_t stream) {
-    if (tg == 8 && cw == 1) return launch_t<8, 1>(p, grid, stream);
-    if (tg == 4 && cw == 2) return launch_t<4, 2>(p, grid, stream);
-    if (tg == 2 && cw == 4) return launch_t<2, 4>(p, grid, stream);
-    if (tg == 1 && cw == 8) return launch_t<1, 8>(p, grid, stream);
+int tp_box_rows(int tg) { return tg * 32; }
+
+cudaError_t launch_replay_tp(int tg, int cw, const TpParams &p, const CUtensorMap &tmap, int grid,
+                             cudaStream_t stream) {
+    if (tg == 8 && cw == 1) return launch_t<8, 1>(p, tmap, grid, stream);
+    if (tg == 4 && cw == 2) return launch_t<4, 2>(p, tmap, grid, stream);
+    if (tg == 2 && cw == 4) return launch_t<2, 4>(p, tmap, grid, stream);
+    if (tg == 1 && cw == 8) return launch_t<1, 8>(p, tmap, grid, stream);
     return cudaErrorInvalidValue;
 }
 

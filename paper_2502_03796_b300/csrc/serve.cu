@@ -67,10 +67,13 @@ struct ServeParams {
     DevModel M;
 };
 
-// One warp per request; state loaded from and stored back to the stream table.
+// One warp per request; state loaded from and stored back to the stream table.  Each warp
+// owns a 5 KB shared buffer: a 1024-byte block whose last two rows hold the 64 deltas
+// before the current sub-block, then 32 rows of 32 deltas in the 128-byte swizzled layout
+// of replay_core.cuh (written here with plain stores).
 __global__ void __launch_bounds__(SERVE_WARPS * 32) serve_kernel(const ServeParams p) {
     using namespace core;
-    __shared__ __align__(16) uint32_t buf[SERVE_WARPS][HALO + SB];
+    __shared__ __align__(1024) uint32_t buf[SERVE_WARPS][(1024 + SB * 4) / 4];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const ServeHeader *hdr = (const ServeHeader *)p.batch;
     const uint32_t n_req = hdr->n_req;
@@ -80,14 +83,14 @@ __global__ void __launch_bounds__(SERVE_WARPS * 32) serve_kernel(const ServePara
     const DevModel &M = p.M;
     const uint32_t topK = (uint32_t)(M.K - 1);
     const uint32_t lanemask_lt = (1u << lane) - 1u;
-    uint32_t *sb = buf[wib];
+    const uint32_t base = smem_u32(buf[wib]) + 1024;   // data row 0
     for (uint32_t r = blockIdx.x * SERVE_WARPS + wib; r < n_req; r += gridDim.x * SERVE_WARPS) {
         const ServeReq rq = reqs[r];
         magus_state_t &st = p.table[rq.stream];
         const uint64_t n_seen0 = st.n_seen;
         uint64_t tailH = st.flags;
         uint32_t level = st.level ? 1u : 0u;
-        for (int k = lane; k < HALO; k += 32) sb[k] = st.hist[k];
+        for (int k = lane; k < HALO; k += 32) sts32(swz_elem(base, k - HALO), st.hist[k]);
         const uint32_t *src = payload + rq.off;
         const uint64_t n = rq.n;
         Acc acc;
@@ -95,21 +98,21 @@ __global__ void __launch_bounds__(SERVE_WARPS * 32) serve_kernel(const ServePara
         uint32_t nch = 0;
         for (uint64_t c0 = 0; c0 < n; c0 += SB) {
             if (c0 > 0) {
+                // rows 30, 31 become rows -2, -1 (same swizzle phase)
                 __syncwarp();
-                const uint32_t h0 = sb[HALO + SB - HALO + lane], h1 = sb[HALO + SB - 32 + lane];
+                const uint32_t h0 = lds32(base + 30 * 128 + 4 * lane), h1 = lds32(base + 30 * 128 + 128 + 4 * lane);
                 __syncwarp();
-                sb[lane] = h0;
-                sb[32 + lane] = h1;
+                sts32(base - 256 + 4 * lane, h0);
+                sts32(base - 128 + 4 * lane, h1);
             }
             const uint64_t cnt = n - c0 < (uint64_t)SB ? n - c0 : (uint64_t)SB;
-            for (uint32_t k = lane; k < SB; k += 32) sb[HALO + k] = k < cnt ? src[c0 + k] : 0u;
+            for (uint32_t k = lane; k < SB; k += 32) sts32(swz_elem(base, (int)k), k < cnt ? src[c0 + k] : 0u);
             __syncwarp();
-            const uint32_t *row = sb + HALO + 32 * lane;
             const int64_t r0 = (int64_t)c0 + 32 * lane;
             const int64_t left = (int64_t)n - r0;
             const uint32_t vmask = valid_mask(left);
             const uint32_t pmask = predict_mask(vmask, n_seen0 + (uint64_t)r0, P.W);
-            const RowPred rp = row_predict(row, lane, P, M, vmask, pmask);
+            const RowPred rp = row_predict(base, lane, P, M, vmask, pmask);
             const uint32_t FL = rp.UP | rp.DN;
             const uint64_t H = row_history(FL, tailH, lane);
             const uint32_t HF = hf_row(H, FL, P.L, P.kmin) & vmask;
@@ -124,7 +127,7 @@ __global__ void __launch_bounds__(SERVE_WARPS * 32) serve_kernel(const ServePara
             const uint32_t Lm = latch_row(SETM, SET0, cin);
             const uint32_t Flev = (Lm << 1) | cin;
             const uint32_t CHG = (Lm ^ Flev) & vmask;
-            row_energy(row, lane, Flev, rp, vmask, acc);
+            row_energy(base, lane, Flev, rp, vmask, acc);
             acc.hf += __popc(HF);
             nch += __popc(CHG);
             uint32_t bits = CHG;
@@ -141,7 +144,7 @@ __global__ void __launch_bounds__(SERVE_WARPS * 32) serve_kernel(const ServePara
                 st.n_seen = n_seen0 + n;
                 st.level = ((Lm >> pl) & 1u) ? topK : 0u;
                 st.flags = (H >> (pl + 1)) | ((uint64_t)FL << (63 - pl));
-                for (int k = 0; k < 64; k++) st.hist[k] = row[pl - 63 + k];
+                read_hist(base, 32 * lane + pl, st.hist);
             }
             // carry into the next sub-block
             const uint32_t fl30 = __shfl_sync(FULL, FL, 30), fl31 = __shfl_sync(FULL, FL, 31);
@@ -158,7 +161,7 @@ __global__ void __launch_bounds__(SERVE_WARPS * 32) serve_kernel(const ServePara
             double E, T;
             totals(M, n0, nm, s0, smv, &E, &T);
             o.n_seen = n_seen0 + n;
-            o.level = (n == 0) ? st.level : (level ? topK : 0u);
+            o.level = level ? topK : 0u;
             o.n_changes = ch;
             o.hash = hs;
             o.n_hf = hf;
@@ -362,7 +365,7 @@ void launcher_main(magus_serve *s) {
             rqs[k].n = (uint32_t)batch[k]->data.size();
             rqs[k].off = off;
             memcpy(pay + off, batch[k]->data.data(), batch[k]->data.size() * 4);
-            off += (batch[k]->data.size() + 3) / 4 * 4;
+            off += (batch[k]->data.size() + 3) / 4 * 4;   // 16-byte aligned request payloads
         }
         hdr->n_req = (uint32_t)batch.size();
         hdr->pad = 0;

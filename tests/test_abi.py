@@ -44,7 +44,7 @@ def test_version_and_error_strings(mg):
 
 def test_packed_layout(mg):
     off, tot = mg.packed_offsets([0, 1, 5, 8, 3])
-    assert off.tolist() == [0, 0, 4, 12, 20] and tot == 24
+    assert off.tolist() == [0, 0, 32, 64, 96] and tot == 128
     ts = tracegen.make_traces(np.array([3, 9, 1], dtype=np.uint64))
     off, tot = mg.packed_offsets(ts.lengths)
     assert np.array_equal(off, ts.offsets) and tot == len(ts.data)

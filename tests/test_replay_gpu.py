@@ -130,9 +130,7 @@ def test_decision_band_exhaustive(rp, mg, model_kind):
             tr = band_trace(pol["direv_length"], ms, bases)
             traces.append((tr, flagpol))
     for tr, pol in traces:
-        ts = tracegen.TraceSet(lengths=np.array([len(tr)], dtype=np.uint64),
-                               offsets=np.zeros(1, dtype=np.uint64),
-                               data=np.concatenate([tr, np.zeros(4, dtype=np.uint32)]))
+        ts = tracegen.single_trace_set(tr)
         out = to_numpy(handle.run(to_device(ts), ts.lengths, [pol], log_capacity=len(tr)))
         ref = oracle.replay(tr, pol, model)
         assert_pair(out, 0, ref, cap=len(tr), tag=f"band {pol}")
@@ -157,8 +155,7 @@ def test_split_replay_with_state(rp, mg):
     hsh = [0] * len(pols)
     for a, b in zip(cuts[:-1], cuts[1:]):
         piece = full[a:b]
-        ts = tracegen.TraceSet(lengths=np.array([len(piece)], dtype=np.uint64), offsets=np.zeros(1, dtype=np.uint64),
-                               data=np.concatenate([piece, np.zeros(4, dtype=np.uint32)]))
+        ts = tracegen.single_trace_set(piece)
         cap = max(len(piece), 1)
         out = to_numpy(rp.run(to_device(ts), ts.lengths, pols, log_capacity=cap, state=state))
         for c in range(len(pols)):

@@ -104,7 +104,8 @@ def sweep_policies() -> List[dict]:
 @dataclasses.dataclass
 class TraceSet:
     """Traces stored back to back; trace i occupies data[offsets[i] : offsets[i] + lengths[i]].
-    Every offset is a multiple of 4 elements (16 bytes)."""
+    Every offset is a multiple of 32 elements (128 bytes) and the buffer is padded to a
+    multiple of 32 elements."""
     lengths: np.ndarray   # uint64 [n_traces]
     offsets: np.ndarray   # uint64 [n_traces]
     data: np.ndarray      # uint32 [total]
@@ -129,7 +130,7 @@ class TraceSet:
         return h.hexdigest()
 
 
-def aligned_offsets(lengths: np.ndarray, align: int = 4) -> np.ndarray:
+def aligned_offsets(lengths: np.ndarray, align: int = 32) -> np.ndarray:
     lengths = np.asarray(lengths, dtype=np.uint64)
     padded = (lengths + np.uint64(align - 1)) // np.uint64(align) * np.uint64(align)
     off = np.zeros_like(padded)
@@ -146,9 +147,9 @@ def make_traces(lengths, seed: int = 0, mean_phase: float = 40.0, mean_phase_b: 
     lib = _load()
     lengths = np.ascontiguousarray(lengths, dtype=np.uint64)
     offsets = aligned_offsets(lengths)
-    total = int(offsets[-1] + ((lengths[-1] + 3) // 4) * 4) if len(lengths) else 0
+    total = int(offsets[-1] + ((lengths[-1] + 31) // 32) * 32) if len(lengths) else 0
     if out is None:
-        data = np.zeros(total, dtype=np.uint32)
+        data = np.zeros(max(total, 32), dtype=np.uint32)
     else:
         data = out[:total]
     if ids is None:
@@ -203,3 +204,12 @@ def requests(n_req: int, rate_per_s: float = 200_000.0, n_streams: int = 100_000
     z = np.zeros(n_req, dtype=np.uint32)
     lib.tg_requests(seed, n_req, rate_per_s, n_streams, size_lo, size_hi, _ptr(a), _ptr(s), _ptr(z))
     return RequestStream(a, s, z)
+
+
+def single_trace_set(deltas) -> TraceSet:
+    """Wrap one hand-built trace in the packed layout (zero padding to 32 elements)."""
+    d = np.asarray(deltas, dtype=np.uint32)
+    n = len(d)
+    data = np.zeros(max((n + 31) // 32 * 32, 32), dtype=np.uint32)
+    data[:n] = d
+    return TraceSet(lengths=np.array([n], dtype=np.uint64), offsets=np.zeros(1, dtype=np.uint64), data=data)
