@@ -34,7 +34,7 @@ struct DevModel {
     double dt;
     int32_t K;
     uint32_t thr0, thrM;   // delta > thr -> interval stretched at level 0 / K-1 (0xffffffff: never)
-    int32_t pad;
+    int32_t one;           // 1, read at run time: lets the kernels express adds as IMADs
     double a0, aM;         // seconds per stretched delta unit at level 0 / K-1
     double P0, PM;         // power at level 0 / K-1
     double cap[MAGUS_MAX_LEVELS];  // capacity per level, GB/s (plain kernel)

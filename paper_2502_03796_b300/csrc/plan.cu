@@ -45,6 +45,7 @@ int derive_model(const magus_model_t &m, DevModel *out, std::string *err) {
     d.bpc = (double)m.bytes_per_count;
     d.dt = m.dt_s;
     d.K = m.n_levels;
+    d.one = 1;
     for (int k = 0; k < m.n_levels; k++) {
         double fr = m.f_ghz[k] / m.f_ref_ghz;
         d.cap[k] = m.bw_ref_gbs * fr;

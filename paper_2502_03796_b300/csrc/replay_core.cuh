@@ -122,11 +122,14 @@ static __device__ __noinline__ void row_predict_general(uint32_t base, int lane,
 
 // Fast path, S = (-W) mod 4.  t = c - a + b has its sign bit set exactly when the integer
 // comparison holds (no overflow while every delta is below 2^30); a funnel shift pushes that
-// bit into the mask, so round k ends up at bit 31 - k.
+// bit into the mask, so round k ends up at bit 31 - k.  The stretch test is written as a
+// multiply-add with a run-time multiplier of -1 so that it issues on the FMA pipe: the
+// kernel is bound by the half-rate integer ALU pipe (measured: this form is the fastest of
+// the all-ALU, all-IMAD and mixed forms).
 template <int S>
-__device__ __forceinline__ void row_predict_fast(uint32_t base, int lane, int W, int32_t upc, int32_t dnc,
-                                                 int32_t thr0c, uint32_t &UPr, uint32_t &DNr, uint32_t &S0r,
-                                                 uint32_t &guard, uint32_t &band, uint32_t &amax,
+__device__ __forceinline__ void row_predict_fast(uint32_t base, int lane, int W, uint32_t one, int32_t upc,
+                                                 int32_t dnc, int32_t thr0c, uint32_t &UPr, uint32_t &DNr,
+                                                 uint32_t &S0r, uint32_t &band, uint32_t &amax,
                                                  uint32_t (&v)[32]) {
     load_row(base, lane, v);
     // window of the deltas W rounds earlier: 36 deltas from the 4-aligned element E0
@@ -137,22 +140,21 @@ __device__ __forceinline__ void row_predict_fast(uint32_t base, int lane, int W,
         const int E = E0 + 4 * c;
         lds128(swz_chunk(base, E >> 5, (E >> 2) & 7), u[4 * c], u[4 * c + 1], u[4 * c + 2], u[4 * c + 3]);
     }
-    uint32_t g = 0, bd = 0xffffffffu, mx = 0;
+    const uint32_t neg1 = 0u - one;
+    uint32_t bd = 0xffffffffu, mx = 0;
 #pragma unroll
     for (int k = 0; k < 32; k++) {
         const uint32_t a = v[k], b = u[k + S];
-        const int32_t tu = upc - (int32_t)a + (int32_t)b;     // < 0  <=>  m > up_mid
-        const int32_t td = (int32_t)a - (int32_t)b - dnc;     // < 0  <=>  m < dn_mid
-        const int32_t ts = thr0c - (int32_t)a;                // < 0  <=>  a > thr0
-        UPr = __funnelshift_l((uint32_t)tu, UPr, 1);
-        DNr = __funnelshift_l((uint32_t)td, DNr, 1);
-        S0r = __funnelshift_l((uint32_t)ts, S0r, 1);
-        bd = __viaddmin_u32((uint32_t)tu, 3u, bd);            // up band: tu in [-3, 2]
-        bd = __viaddmin_u32((uint32_t)td, 2u, bd);            // dn band: td in [-2, 3]
-        g |= a | b;
+        const uint32_t tu = (uint32_t)upc - a + b;        // < 0  <=>  m > up_mid
+        const uint32_t td = a - b - (uint32_t)dnc;        // < 0  <=>  m < dn_mid
+        const uint32_t ts = a * neg1 + (uint32_t)thr0c;   // < 0  <=>  a > thr0 (an IMAD)
+        UPr = __funnelshift_l(tu, UPr, 1);
+        DNr = __funnelshift_l(td, DNr, 1);
+        S0r = __funnelshift_l(ts, S0r, 1);
+        bd = __viaddmin_u32(tu, 3u, bd);            // up band: tu in [-3, 2]
+        bd = __viaddmin_u32(td, 2u, bd);            // dn band: td in [-2, 3]
         mx = max(mx, a);
     }
-    guard = g;
     band = bd;
     amax = mx;
 }
@@ -160,11 +162,15 @@ __device__ __forceinline__ void row_predict_fast(uint32_t base, int lane, int W,
 template <int S>
 __device__ __forceinline__ bool row_predict_fast_dispatch(uint32_t base, int lane, const DevPolicy &P,
                                                           const DevModel &M, RowPred &r, uint32_t (&v)[32]) {
-    uint32_t UPr = 0, DNr = 0, S0r = 0, guard, band, amax;
-    row_predict_fast<S>(base, lane, P.W, clamp_mid(P.up_mid), clamp_mid(P.dn_mid), clamp_thr(M.thr0), UPr, DNr,
-                        S0r, guard, band, amax, v);
+    uint32_t UPr = 0, DNr = 0, S0r = 0, band, amax;
+    row_predict_fast<S>(base, lane, P.W, (uint32_t)M.one, clamp_mid(P.up_mid), clamp_mid(P.dn_mid),
+                        clamp_thr(M.thr0), UPr, DNr, S0r, band, amax, v);
+    // every delta of the sub-block is some lane's row element; the 64 before it (rows -1, -2)
+    // are checked here: the fast path needs all of them below 2^30
+    const uint32_t h0 = lds32(swz_elem(base, lane - 64)), h1 = lds32(swz_elem(base, lane - 32));
+    const uint32_t hx = max(max(h0, h1), amax);
     // fall back when a delta reaches 2^30 or a round lies in a decision band
-    if (__any_sync(FULL, guard >= (uint32_t)kFastLimit || band <= 5u)) return false;
+    if (__any_sync(FULL, hx >= (uint32_t)kFastLimit || band <= 5u)) return false;
     r.UP = __brev(UPr);
     r.DN = __brev(DNr);
     r.S0 = __brev(S0r);
