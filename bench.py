@@ -21,7 +21,6 @@ import argparse
 import hashlib
 import json
 import os
-import subprocess
 import sys
 import threading
 import time
@@ -73,55 +72,58 @@ def ncu_traffic() -> float | None:
 
 
 class ClockSampler:
-    """nvidia-smi clocks / throttle reasons sampled every 200 ms during the timed region."""
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
-              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    """SM clock and clock-event (throttle) reasons polled through NVML every 2 ms while the
+    timed region runs (read-only queries; no setting is changed)."""
+    REASONS = {"hw_slowdown": "nvmlClocksEventReasonHwSlowdown",
+               "hw_thermal_slowdown": "nvmlClocksEventReasonHwThermalSlowdown",
+               "sw_thermal_slowdown": "nvmlClocksEventReasonSwThermalSlowdown",
+               "sw_power_cap": "nvmlClocksEventReasonSwPowerCap",
+               "hw_power_brake_slowdown": "nvmlClocksEventReasonHwPowerBrakeSlowdown"}
 
     def __init__(self, index: int):
         self.index = index
-        self.proc = None
-        self.lines = []
+        self.samples, self.reasons = [], set()
+        self.max_mhz = None
+        self.ok = False
+        try:
+            import pynvml
+            pynvml.nvmlInit()
+            vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+            phys = int(vis.split(",")[index]) if vis and vis.split(",")[index].isdigit() else index
+            self.h = pynvml.nvmlDeviceGetHandleByIndex(phys)
+            self.nv = pynvml
+            self.max_mhz = float(pynvml.nvmlDeviceGetMaxClockInfo(self.h, pynvml.NVML_CLOCK_SM))
+            self.ok = True
+        except Exception:
+            self.ok = False
+
+    def _poll(self):
+        nv = self.nv
+        while not self.stop_flag.is_set():
+            try:
+                self.samples.append(float(nv.nvmlDeviceGetClockInfo(self.h, nv.NVML_CLOCK_SM)))
+                r = nv.nvmlDeviceGetCurrentClocksEventReasons(self.h)
+                for name, attr in self.REASONS.items():
+                    if r & getattr(nv, attr, 0):
+                        self.reasons.add(name)
+            except Exception:
+                pass
+            time.sleep(0.002)
 
     def start(self):
-        try:
-            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
-                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
-            self.thread = threading.Thread(target=self._read, daemon=True)
-            self.thread.start()
-        except OSError:
-            self.proc = None
-
-    def _read(self):
-        for line in self.proc.stdout:
-            self.lines.append(line.strip())
+        if not self.ok:
+            return
+        self.stop_flag = threading.Event()
+        self.thread = threading.Thread(target=self._poll, daemon=True)
+        self.thread.start()
 
     def stop(self) -> dict:
-        if self.proc is None:
-            return dict(sm_mhz=None, sm_max_mhz=None, reasons=["nvidia-smi unavailable"])
-        self.proc.terminate()
-        try:
-            self.proc.wait(timeout=5)
-        except subprocess.TimeoutExpired:
-            self.proc.kill()
+        if not self.ok:
+            return dict(sm_mhz=None, sm_max_mhz=None, reasons=["nvml unavailable"], samples=0)
+        self.stop_flag.set()
         self.thread.join(timeout=2)
-        sm, mx, reasons = [], None, set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
-            parts = [x.strip() for x in ln.split(",")]
-            if len(parts) < 9:
-                continue
-            try:
-                sm.append(float(parts[1]))
-                mx = float(parts[2])
-            except ValueError:
-                continue
-            for nm, v in zip(names, parts[5:9]):
-                if v.lower().startswith("active"):
-                    reasons.add(nm)
-        return dict(sm_mhz=float(np.median(sm)) if sm else None, sm_max_mhz=mx, reasons=sorted(reasons),
-                    samples=len(sm))
+        return dict(sm_mhz=float(np.median(self.samples)) if self.samples else None, sm_max_mhz=self.max_mhz,
+                    reasons=sorted(self.reasons), samples=len(self.samples), source="nvml, 2 ms polling")
 
 
 def dist_setup():
@@ -176,6 +178,38 @@ def cpu_oracle_sample(ts: tracegen.TraceSet, policy, model, target_s: float = 6.
     return samples / dt, used, f"first {k2} of {ts.n_traces} traces x {N_INTERVALS} intervals, 1 policy ({dt:.1f} s wall)"
 
 
+def bench_serve(seconds: float = 1.0, baseline_seconds: float = 0.25, device: int = 0) -> dict:
+    """Serving workload: 100,000 node streams, Poisson arrivals at 200k requests/s, request
+    sizes log-uniform in 1..4096 deltas, 8 GB admission budget; continuous batching (CUDA
+    graph per launch) against one launch per request on the same arrival process."""
+    from paper_2502_03796_b300 import magus
+    model, policy = tracegen.default_model(), tracegen.default_policy()
+    n_streams, rate = 100_000, 200_000.0
+    pool = tracegen.batched(n_traces=64, n=1_000_000, seed=7).data        # delta pool
+    out = {}
+    for name, secs, max_req in (("batched", seconds, 0), ("per_request_launch", baseline_seconds, 1)):
+        rq = tracegen.requests(int(rate * secs), rate_per_s=rate, n_streams=n_streams, seed=11)
+        rng = np.random.default_rng(3)
+        off = rng.integers(0, len(pool) - 4096, size=len(rq.size)).astype(np.uint64)
+        sv = magus.Serve(model, policy, n_streams, mem_budget=8 << 30, device=device, max_batch_requests=max_req)
+        # warm-up: a short burst through the same runtime
+        sv.load(rq.arrival_s[:2000] * 0.0, rq.stream_id[:2000], rq.size[:2000], pool, off[:2000])
+        st0 = sv.stats()
+        lat, wall = sv.load(rq.arrival_s, rq.stream_id, rq.size, pool, off)
+        st = sv.stats()
+        sv.close()
+        ok = lat[lat >= 0]
+        samples = int(rq.size.sum())
+        out[name] = dict(requests=int(len(lat)), offered_req_per_s=rate, duration_s=float(rq.arrival_s[-1]),
+                         wall_s=wall, p50_ms=float(np.percentile(ok, 50) * 1e3), p99_ms=float(np.percentile(ok, 99) * 1e3),
+                         p999_ms=float(np.percentile(ok, 99.9) * 1e3), max_ms=float(ok.max() * 1e3),
+                         samples_per_s=samples / wall, launches=int(st["launches"] - st0["launches"]),
+                         rejected=int(st["rejected"] - st0["rejected"]))
+    out["streams"] = n_streams
+    out["unit"] = "ms latency, samples/s"
+    return out
+
+
 def run_reference(args, world, rank):
     if rank != 0:
         return 0
@@ -209,22 +243,127 @@ def run_reference(args, world, rank):
     return 0
 
 
+def time_steps(fn, steps: int, warmup: int, stream) -> float:
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def run_other(args, world, rank, local) -> int:
+    """Lines for the other replay workloads: policy sweep, uneven lengths, single trace."""
+    import torch
+    from paper_2502_03796_b300 import magus
+    import oracle
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    model = tracegen.default_model()
+    if args.workload == "sweep":
+        ts = tracegen.sweep(first_id=rank * 1024)
+        pols = tracegen.sweep_policies()
+        desc = "policy sweep: 1024 traces x 200000 intervals (bursty mean 10 / long mean 500 regimes), 256 policies"
+    elif args.workload == "uneven":
+        ts = tracegen.uneven(seed=rank)
+        pols = tracegen.sweep_policies()[:16]
+        desc = "uneven lengths: 16384 traces, log-uniform 1e3..1e6 intervals, 16 policies"
+    else:
+        ts = tracegen.single_trace()
+        pols = [tracegen.default_policy()]
+        desc = "single trace: 20000 intervals, 1 policy"
+    d_tr = torch.from_numpy(ts.data.view(np.int32)).to(dev)
+    rp = magus.Replay(model, device=local, mem_budget=4 << 30)
+    stream = torch.cuda.current_stream(dev)
+    n_pairs = ts.n_traces * len(pols)
+    outs = rp.alloc(n_pairs, log_capacity=0)
+    tuned = None
+    if args.workload in ("sweep", "uneven"):
+        tuned, tms = rp.autotune(d_tr, ts.lengths, pols, stream=stream)
+    rp.kernel_time()
+    ms = time_steps(lambda: rp.run(d_tr, ts.lengths, pols, stream=stream, out=outs), args.steps, args.warmup, stream)
+    k_ms, k_n = rp.kernel_time()
+    pair_steps = ts.n_samples * len(pols)
+    value = pair_steps * world / (ms * 1e-3)
+    alg_bytes = 4 * ts.n_samples + 48 * n_pairs
+    k_avg = k_ms / max(k_n, 1)
+    peaks = measured_peaks()
+    line = dict(metric=METRIC, value=value, unit="pair-interval samples/s", n_gpus=world, steps=args.steps,
+                warmup=args.warmup, ms_per_step=ms, higher_is_better=True, scaling="weak", vs_baseline=None,
+                dtype="u32/f64", data="synthetic",
+                config=dict(workload=desc, traces=ts.n_traces, samples=ts.n_samples, policies=len(pols),
+                            tile=list(tuned) if tuned else None, outputs="energy, EDP, time, counts, hash (no entries)"),
+                roofline=dict(bound="alu" if len(pols) > 1 else "hbm", achieved=alg_bytes / (k_avg * 1e-3) / 1e9,
+                              peak=peaks["hbm_gbs"], unit="GB/s", frac=alg_bytes / (k_avg * 1e-3) / 1e9 / peaks["hbm_gbs"],
+                              traffic=None, kernel_ms=k_avg, alg_bytes_per_launch=alg_bytes),
+                gpu_launches=k_n)
+    # one launch per trace (time-parallel kernel) on a sample of traces
+    k = min(256, ts.n_traces)
+    per_ms = 0.0
+    for i in range(k):
+        sub_len = ts.lengths[i:i + 1]
+        o = int(ts.offsets[i])
+        sub = d_tr[o:o + int((sub_len[0] + 31) // 32 * 32) + 32]
+        if i == 0:
+            rp.run(sub, sub_len, pols, stream=stream)
+        t0 = torch.cuda.Event(enable_timing=True); t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        rp.run(sub, sub_len, pols, stream=stream)
+        t1.record(stream)
+        torch.cuda.synchronize()
+        per_ms += t0.elapsed_time(t1)
+    line["one_launch_per_trace"] = dict(value=float(ts.lengths[:k].sum()) * len(pols) / (per_ms * 1e-3),
+                                        unit="pair-interval samples/s", sample=f"first {k} traces, one launch each")
+    # plain form (one launch per trace, literal FP64) on a small sample
+    kp = 4 if args.workload != "single" else 1
+    sub = d_tr[:int(ts.offsets[kp - 1]) + int((ts.lengths[kp - 1] + 31) // 32 * 32)] if kp > 1 else d_tr
+    rp.plain(sub, ts.lengths[:kp], pols, stream=stream)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    rp.plain(sub, ts.lengths[:kp], pols, stream=stream)
+    torch.cuda.synchronize()
+    line["plain_launch"] = dict(value=float(ts.lengths[:kp].sum()) * len(pols) / (time.perf_counter() - t0),
+                                unit="pair-interval samples/s", sample=f"first {kp} traces")
+    if rank == 0:
+        # CPU oracle on a bounded sample
+        kc = min(ts.n_traces, 8 if args.workload != "single" else 1)
+        t0 = time.perf_counter()
+        _, used = oracle.replay_batch(ts.data, ts.offsets[:kc], ts.lengths[:kc], pols, model)
+        dt = time.perf_counter() - t0
+        line["cpu_baseline"] = dict(value=float(ts.lengths[:kc].sum()) * len(pols) / dt, unit="pair-interval samples/s",
+                                    cores=used, kind="oracle", sample=f"first {kc} traces x {len(pols)} policies")
+        print(json.dumps(line), flush=True)
+    rp.close()
+    return 0
+
+
 def main() -> int:
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="magus", choices=["magus", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--tile", default="", help="time_groups,policy_slots (default: automatic)")
     ap.add_argument("--traces", type=int, default=N_TRACES, help="traces per GPU (profiling runs use fewer)")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--workload", default="batched", choices=["batched", "sweep", "uneven", "single"],
+                    help="batched (default, the headline line); sweep / uneven / single print their own line")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     world, rank, local = dist_setup()
     if args.impl == "reference":
         return run_reference(args, world, rank)
+    if args.workload != "batched":
+        return run_other(args, world, rank, local)
 
     import torch
     from paper_2502_03796_b300 import magus
@@ -327,6 +466,9 @@ def main() -> int:
                            h2d_bytes_per_step=int(ts.data.nbytes), d2h_bytes_per_step=48 * n_pairs,
                            steps=ksteps, api="magus_replay_run_host")
         rp.kernel_time()
+
+    if rank == 0 and not args.no_serve:
+        line["serve"] = bench_serve(device=local)
 
     if rank == 0 and not args.no_cpu_baseline:
         rate, used, sample = cpu_oracle_sample(ts, policy, model)

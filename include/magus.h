@@ -170,15 +170,18 @@ int magus_replay_status(magus_replay_t *h, void *stream);
  * launches; later ones overwrite the last record).  Waits for those launches, then resets. */
 int magus_replay_kernel_time(magus_replay_t *h, double *total_ms, int32_t *launches);
 
-/* Tile shape of the batched kernel: warps per policy that split a trace chunk in time
- * (time_groups) x policies per CTA (policy_slots); time_groups * policy_slots = 8.
- * (0, 0) restores the automatic choice.  EINVAL for unsupported shapes. */
+/* Tile shape of the batched kernel: warps that split a trace chunk in time (time_groups) x
+ * policy groups per CTA (policy_slots); time_groups * policy_slots = 8.  Policies sharing
+ * Algorithm 1's parameters (W, inc, dec) are grouped (up to 4 per group, predictions made
+ * once per group) whenever that at least halves the group count.  (0, 0) restores the
+ * automatic choice.  EINVAL for unsupported shapes. */
 int magus_replay_set_tile(magus_replay_t *h, int32_t time_groups, int32_t policy_slots);
 
-/* Autotuner: time every supported tile shape on the given (device, packed) workload and
- * keep the fastest for later calls with the same policy count.  out_best (host, 2 ints,
- * optional) receives {time_groups, policy_slots}; out_ms (host, optional) the best time.
- * Outputs go to the handle's workspace only.  Synchronous. */
+/* Autotuner: time every supported tile shape (time_groups x policy_slots x group size 1 or
+ * 4) on the given (device, packed) workload and keep the fastest for later calls with the
+ * same policy count.  out_best (host, 3 ints, optional) receives {time_groups,
+ * policy_slots, group_size}; out_ms (host, optional) the best time.  Outputs go to the
+ * handle's workspace only.  Synchronous. */
 int magus_replay_autotune(magus_replay_t *h, const uint32_t *traces, const uint64_t *lengths,
                           int32_t n_traces, const magus_policy_t *configs, int32_t n_configs,
                           int32_t *out_best, float *out_ms, void *stream);

@@ -2,6 +2,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -45,7 +46,7 @@ struct magus_replay {
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> k_ev;
     size_t k_used = 0;
     int tile_tg = 0, tile_cw = 0;     // 0: automatic
-    std::map<int, std::pair<int, int>> tuned;
+    std::map<int, std::array<int, 3>> tuned;   // policies -> {time_groups, policy_slots, group size}
 };
 
 namespace {
@@ -133,35 +134,46 @@ int check_policies(magus_replay *h, const magus_policy_t *configs, int32_t n_con
 
 struct Plan {
     std::vector<DevPolicy> pols;
+    std::vector<PolicyGroup> groups;
     std::vector<WorkItem> items;
     std::vector<uint64_t> offsets, lengths;
-    int tg = 8, cw = 1;
+    int tg = 8, cw = 1, gp = 1;
 };
 
-void choose_tile(magus_replay *h, int n_configs, int *tg, int *cw) {
+// Tile for a workload: group size 4 when policies share predictions, then as many policy
+// slots per CTA as there are groups (up to 8), the remaining warps splitting time.
+void choose_tile(magus_replay *h, const std::vector<DevPolicy> &pols, int *tg, int *cw, int *gp) {
+    const int n_configs = (int)pols.size();
+    auto it = h->tuned.find(n_configs);
+    if (!h->tile_tg && it != h->tuned.end()) {
+        *tg = it->second[0];
+        *cw = it->second[1];
+        *gp = it->second[2];
+        return;
+    }
+    std::vector<PolicyGroup> g4;
+    form_groups(pols, kMaxGroup, &g4);
+    *gp = (2 * g4.size() <= pols.size()) ? kMaxGroup : 1;
+    const int n_groups = *gp == 1 ? n_configs : (int)g4.size();
     if (h->tile_tg) {
         *tg = h->tile_tg;
         *cw = h->tile_cw;
         return;
     }
-    auto it = h->tuned.find(n_configs);
-    if (it != h->tuned.end()) {
-        *tg = it->second.first;
-        *cw = it->second.second;
-        return;
-    }
     int c = 1;
-    while (c * 2 <= std::min(8, n_configs)) c *= 2;
+    while (c * 2 <= std::min(8, n_groups)) c *= 2;
     *cw = c;
     *tg = 8 / c;
 }
 
 int build_plan(magus_replay *h, const uint64_t *lengths, int32_t n_traces, const magus_policy_t *configs,
-               int32_t n_configs, int tg, int cw, Plan *pl) {
+               int32_t n_configs, int tg, int cw, int gp, Plan *pl) {
     int rc = check_policies(h, configs, n_configs, &pl->pols, true);
     if (rc) return rc;
     pl->tg = tg;
     pl->cw = cw;
+    pl->gp = gp;
+    form_groups(pl->pols, gp, &pl->groups);
     pl->offsets.resize(n_traces);
     pl->lengths.assign(lengths, lengths + n_traces);
     uint64_t off = 0;
@@ -173,7 +185,8 @@ int build_plan(magus_replay *h, const uint64_t *lengths, int32_t n_traces, const
     std::vector<int> order(n_traces);
     for (int i = 0; i < n_traces; i++) order[i] = i;
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return lengths[a] > lengths[b]; });
-    const int blocks = (n_configs + cw - 1) / cw;
+    const int n_groups = (int)pl->groups.size();
+    const int blocks = (n_groups + cw - 1) / cw;
     pl->items.clear();
     pl->items.reserve((size_t)n_traces * blocks);
     for (int i : order)
@@ -194,9 +207,10 @@ int launch_plan(magus_replay *h, const Plan &pl, const uint32_t *traces, const O
                 float *ms_out = nullptr) {
     const size_t n_items = pl.items.size();
     const size_t sz_pol = align_up(pl.pols.size() * sizeof(DevPolicy), 256);
+    const size_t sz_grp = align_up(std::max<size_t>(pl.groups.size(), 1) * sizeof(PolicyGroup), 256);
     const size_t sz_items = align_up(std::max<size_t>(n_items, 1) * sizeof(WorkItem), 256);
     const size_t sz_off = align_up(std::max<size_t>(pl.offsets.size(), 1) * 8, 256);
-    const size_t total = sz_pol + sz_items + 2 * sz_off;
+    const size_t total = sz_pol + sz_grp + sz_items + 2 * sz_off;
     int rc = ensure_ws(h, &h->ws, &h->ws_size, total);
     if (rc) return rc;
     const int slot = h->pin_next;
@@ -205,10 +219,11 @@ int launch_plan(magus_replay *h, const Plan &pl, const uint32_t *traces, const O
     if (rc) return rc;
     char *pin = (char *)h->pin[slot];
     memcpy(pin, pl.pols.data(), pl.pols.size() * sizeof(DevPolicy));
-    if (n_items) memcpy(pin + sz_pol, pl.items.data(), n_items * sizeof(WorkItem));
+    memcpy(pin + sz_pol, pl.groups.data(), pl.groups.size() * sizeof(PolicyGroup));
+    if (n_items) memcpy(pin + sz_pol + sz_grp, pl.items.data(), n_items * sizeof(WorkItem));
     if (!pl.offsets.empty()) {
-        memcpy(pin + sz_pol + sz_items, pl.offsets.data(), pl.offsets.size() * 8);
-        memcpy(pin + sz_pol + sz_items + sz_off, pl.lengths.data(), pl.lengths.size() * 8);
+        memcpy(pin + sz_pol + sz_grp + sz_items, pl.offsets.data(), pl.offsets.size() * 8);
+        memcpy(pin + sz_pol + sz_grp + sz_items + sz_off, pl.lengths.data(), pl.lengths.size() * 8);
     }
     if (h->ws_ev_pending) CK(cudaStreamWaitEvent(stream, h->ws_ev, 0), "cudaStreamWaitEvent");
     char *ws = (char *)h->ws;
@@ -222,9 +237,11 @@ int launch_plan(magus_replay *h, const Plan &pl, const uint32_t *traces, const O
     p.traces = traces;
     p.pols = (const DevPolicy *)ws;
     p.n_pols = (int32_t)pl.pols.size();
-    p.items = (const WorkItem *)(ws + sz_pol);
-    p.offsets = (const uint64_t *)(ws + sz_pol + sz_items);
-    p.lengths = (const uint64_t *)(ws + sz_pol + sz_items + sz_off);
+    p.groups = (const PolicyGroup *)(ws + sz_pol);
+    p.n_groups = (int32_t)pl.groups.size();
+    p.items = (const WorkItem *)(ws + sz_pol + sz_grp);
+    p.offsets = (const uint64_t *)(ws + sz_pol + sz_grp + sz_items);
+    p.lengths = (const uint64_t *)(ws + sz_pol + sz_grp + sz_items + sz_off);
     p.n_items = (int32_t)n_items;
     p.queue = h->queue;
     p.status = h->status;
@@ -239,7 +256,7 @@ int launch_plan(magus_replay *h, const Plan &pl, const uint32_t *traces, const O
     p.n_hf = o.n_hf;
     p.state = o.state;
     int smem = 0;
-    const int per_sm = tp_max_ctas_per_sm(pl.tg, pl.cw, &smem);
+    const int per_sm = tp_max_ctas_per_sm(pl.tg, pl.cw, pl.gp, &smem);
     if (per_sm <= 0) {
         set_error("tile shape does not fit on this device");
         return MAGUS_ECUDA;
@@ -270,7 +287,7 @@ int launch_plan(magus_replay *h, const Plan &pl, const uint32_t *traces, const O
         }
         const size_t slot_k = h->k_used < h->k_ev.size() ? h->k_used : h->k_ev.size() - 1;
         CK(cudaEventRecord(h->k_ev[slot_k].first, stream), "cudaEventRecord");
-        CK(launch_replay_tp(pl.tg, pl.cw, p, tmap, grid, stream), "replay kernel launch");
+        CK(launch_replay_tp(pl.tg, pl.cw, pl.gp, p, tmap, grid, stream), "replay kernel launch");
         CK(cudaEventRecord(h->k_ev[slot_k].second, stream), "cudaEventRecord");
         if (h->k_used < h->k_ev.size()) h->k_used++;
     }
@@ -494,10 +511,13 @@ int magus_replay_run(magus_replay_t *h, const uint32_t *traces, const uint64_t *
         int rc = check_run_args(h, traces, lengths, n_traces, log, out_energy, out_edp);
         if (rc) return rc;
         CK(cudaSetDevice(h->device), "cudaSetDevice");
-        int tg, cw;
-        choose_tile(h, n_configs, &tg, &cw);
+        std::vector<DevPolicy> pols;
+        rc = check_policies(h, configs, n_configs, &pols, true);
+        if (rc) return rc;
+        int tg, cw, gp;
+        choose_tile(h, pols, &tg, &cw, &gp);
         Plan pl;
-        rc = build_plan(h, lengths, n_traces, configs, n_configs, tg, cw, &pl);
+        rc = build_plan(h, lengths, n_traces, configs, n_configs, tg, cw, gp, &pl);
         if (rc) return rc;
         return launch_plan(h, pl, traces, outs_of(log, out_energy, out_edp, out_time, io_state),
                            (cudaStream_t)stream);
@@ -552,13 +572,21 @@ int magus_replay_autotune(magus_replay_t *h, const uint32_t *traces, const uint6
         memset(&o, 0, sizeof(o));
         o.energy = (double *)h->scratch;
         o.edp = o.energy + pairs;
-        static const int shapes[4][2] = {{8, 1}, {4, 2}, {2, 4}, {1, 8}};
+        static const int shapes[8][3] = {{8, 1, 1}, {4, 2, 1}, {2, 4, 1}, {1, 8, 1},
+                                         {8, 1, 4}, {4, 2, 4}, {2, 4, 4}, {1, 8, 4}};
         float best = 1e30f;
-        int bt = 8, bc = 1;
+        int bt = 8, bc = 1, bg = 1;
+        std::vector<DevPolicy> pols;
+        rc = check_policies(h, configs, n_configs, &pols, true);
+        if (rc) return rc;
+        std::vector<PolicyGroup> g4;
+        form_groups(pols, kMaxGroup, &g4);
         for (auto &sh : shapes) {
-            if (sh[1] > 1 && sh[1] / 2 >= n_configs) continue;  // more policy slots than policies
+            const int n_groups = sh[2] == 1 ? n_configs : (int)g4.size();
+            if (sh[2] > 1 && g4.size() == (size_t)n_configs) continue;   // nothing to share
+            if (sh[1] > 1 && sh[1] / 2 >= n_groups) continue;            // more slots than groups
             Plan pl;
-            rc = build_plan(h, lengths, n_traces, configs, n_configs, sh[0], sh[1], &pl);
+            rc = build_plan(h, lengths, n_traces, configs, n_configs, sh[0], sh[1], sh[2], &pl);
             if (rc) return rc;
             float ms = 0, mn = 1e30f;
             for (int rep = 0; rep < 3; rep++) {
@@ -570,12 +598,14 @@ int magus_replay_autotune(magus_replay_t *h, const uint32_t *traces, const uint6
                 best = mn;
                 bt = sh[0];
                 bc = sh[1];
+                bg = sh[2];
             }
         }
-        h->tuned[n_configs] = {bt, bc};
+        h->tuned[n_configs] = {bt, bc, bg};
         if (out_best) {
             out_best[0] = bt;
             out_best[1] = bc;
+            out_best[2] = bg;
         }
         if (out_ms) *out_ms = best;
         return MAGUS_OK;
@@ -630,8 +660,11 @@ int magus_replay_run_host(magus_replay_t *h, const uint32_t *traces, const uint6
                 CK(cudaEventCreateWithFlags(&h->hs_done[s], cudaEventDisableTiming), "cudaEventCreate");
             }
         }
-        int tg, cw;
-        choose_tile(h, n_configs, &tg, &cw);
+        std::vector<DevPolicy> pols;
+        rc = check_policies(h, configs, n_configs, &pols, true);
+        if (rc) return rc;
+        int tg, cw, gp;
+        choose_tile(h, pols, &tg, &cw, &gp);
         const bool has_log = log != nullptr;
         const uint64_t cap = (has_log && log->entries) ? log->capacity : 0;
         const size_t per_pair = 16 + (out_time ? 8 : 0) +
@@ -697,7 +730,7 @@ int magus_replay_run_host(magus_replay_t *h, const uint32_t *traces, const uint6
             CK(cudaEventRecord(h->hs_ready[slot], h->hs_copy), "cudaEventRecord");
             CK(cudaStreamWaitEvent(h->hs_comp, h->hs_ready[slot], 0), "cudaStreamWaitEvent");
             Plan pl;
-            rc = build_plan(h, lengths + i0, nt, configs, n_configs, tg, cw, &pl);
+            rc = build_plan(h, lengths + i0, nt, configs, n_configs, tg, cw, gp, &pl);
             if (rc) return rc;
             rc = launch_plan(h, pl, d_tr, outs_of(has_log ? &dl : nullptr, d_e, d_edp, d_t, nullptr), h->hs_comp);
             if (rc) return rc;

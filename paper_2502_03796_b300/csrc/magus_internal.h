@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "magus.h"
 
@@ -43,7 +44,16 @@ struct DevModel {
 
 struct WorkItem {
     uint32_t trace;
-    uint32_t cfg0;         // first policy of the block
+    uint32_t cfg0;         // first policy group of the block
+};
+
+// Policies sharing Alg. 1's parameters (W, inc, dec): their predictions coincide, so the
+// batched kernel makes them once per group.
+constexpr int kMaxGroup = 4;
+struct PolicyGroup {
+    int32_t count;                 // 1..kMaxGroup
+    int32_t member[kMaxGroup];     // policy indices (unused slots repeat member[0])
+    int32_t pad[3];
 };
 
 struct TpParams {
@@ -54,6 +64,9 @@ struct TpParams {
     int32_t n_pols;
     int32_t n_items;
     const WorkItem *items;
+    const PolicyGroup *groups;
+    int32_t n_groups;
+    int32_t pad0;
     unsigned int *queue;   // work counter (zeroed before launch)
     int *status;           // device status word (0 ok, else MAGUS_E*)
     DevModel model;
@@ -70,9 +83,12 @@ constexpr int kTraceAlign = 32;
 int make_trace_tmap(const uint32_t *traces, uint64_t total_elems, int box_rows, CUtensorMap *out,
                     std::string *err);
 int tp_box_rows(int time_groups);
-cudaError_t launch_replay_tp(int time_groups, int policy_slots, const TpParams &p, const CUtensorMap &tmap,
-                             int grid, cudaStream_t stream);
-int tp_max_ctas_per_sm(int time_groups, int policy_slots, int *smem_bytes);
+// Tile: time_groups warps split a chunk in time for each of policy_slots policy groups of
+// up to group_size members (time_groups * policy_slots = 8; group_size 1 or 4).
+bool tp_tile_supported(int time_groups, int policy_slots, int group_size);
+cudaError_t launch_replay_tp(int time_groups, int policy_slots, int group_size, const TpParams &p,
+                             const CUtensorMap &tmap, int grid, cudaStream_t stream);
+int tp_max_ctas_per_sm(int time_groups, int policy_slots, int group_size, int *smem_bytes);
 
 struct PlainParams {
     const uint32_t *trace;
@@ -91,6 +107,7 @@ struct PlainParams {
 cudaError_t launch_replay_plain(const PlainParams &p, cudaStream_t stream);
 
 // Host planning (plan.cu).
+void form_groups(const std::vector<DevPolicy> &pols, int gp, std::vector<PolicyGroup> *out);
 int derive_policy(const magus_policy_t &in, const magus_model_t &m, DevPolicy *out, std::string *err);
 int derive_model(const magus_model_t &m, DevModel *out, std::string *err);
 

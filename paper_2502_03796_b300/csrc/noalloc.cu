@@ -66,15 +66,22 @@ extern "C" int magus_replay_run_static(const magus_model_t *model, const uint32_
         if (log && log->entries && lengths[i] >= (1ull << 27) - 1)
             return fail("change-log entries hold interval indices below 2^27", MAGUS_EINVAL);
     }
-    // tile: as many policy slots as there are policies (up to 8), the rest split time
+    // policies sharing predictions form groups of up to 4; as many group slots per CTA as
+    // there are groups (up to 8), the rest of the warps split time
+    std::vector<PolicyGroup> groups;
+    form_groups(pols, kMaxGroup, &groups);
+    const int gp = (2 * groups.size() <= pols.size()) ? kMaxGroup : 1;
+    if (gp == 1) form_groups(pols, 1, &groups);
+    const int n_groups = (int)groups.size();
     int cw = 1;
-    while (cw * 2 <= std::min(8, n_configs)) cw *= 2;
+    while (cw * 2 <= std::min(8, n_groups)) cw *= 2;
     const int tg = 8 / cw;
-    const size_t blocks = (size_t)(n_configs + cw - 1) / cw;
+    const size_t blocks = (size_t)(n_groups + cw - 1) / cw;
     const size_t n_items = (size_t)n_traces * blocks;
-    // scratch layout: [status, counter | policies | items | offsets | lengths]
+    // scratch layout: [status, counter | policies | groups | items | offsets | lengths]
     const size_t off_pol = 256;
-    const size_t off_items = off_pol + align_up(pols.size() * sizeof(DevPolicy), 256);
+    const size_t off_grp = off_pol + align_up(pols.size() * sizeof(DevPolicy), 256);
+    const size_t off_items = off_grp + align_up(groups.size() * sizeof(PolicyGroup), 256);
     const size_t off_off = off_items + align_up(std::max<size_t>(n_items, 1) * sizeof(WorkItem), 256);
     const size_t off_len = off_off + align_up(std::max<int>(n_traces, 1) * 8, 256);
     const size_t total = off_len + align_up(std::max<int>(n_traces, 1) * 8, 256);
@@ -104,6 +111,7 @@ extern "C" int magus_replay_run_static(const magus_model_t *model, const uint32_
     // host image of the plan (host memory only)
     std::vector<unsigned char> img(total, 0);
     memcpy(img.data() + off_pol, pols.data(), pols.size() * sizeof(DevPolicy));
+    memcpy(img.data() + off_grp, groups.data(), groups.size() * sizeof(PolicyGroup));
     std::vector<int> order(n_traces);
     for (int i = 0; i < n_traces; i++) order[i] = i;
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return lengths[a] > lengths[b]; });
@@ -129,6 +137,8 @@ extern "C" int magus_replay_run_static(const magus_model_t *model, const uint32_
         p.traces = traces;
         p.pols = (const DevPolicy *)(scratch + off_pol);
         p.n_pols = n_configs;
+        p.groups = (const PolicyGroup *)(scratch + off_grp);
+        p.n_groups = n_groups;
         p.items = (const WorkItem *)(scratch + off_items);
         p.n_items = (int32_t)n_items;
         p.offsets = (const uint64_t *)(scratch + off_off);
@@ -148,7 +158,7 @@ extern "C" int magus_replay_run_static(const magus_model_t *model, const uint32_
         }
         p.state = io_state;
         int smem = 0;
-        const int per_sm = tp_max_ctas_per_sm(tg, cw, &smem);
+        const int per_sm = tp_max_ctas_per_sm(tg, cw, gp, &smem);
         int sms = 0;
         e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (e != cudaSuccess || per_sm <= 0) return fail("device query failed", MAGUS_ECUDA);
@@ -156,7 +166,7 @@ extern "C" int magus_replay_run_static(const magus_model_t *model, const uint32_
         CUtensorMap tmap;
         rc = make_trace_tmap(traces, o, tp_box_rows(tg), &tmap, &err);
         if (rc) return fail(err, rc);
-        e = launch_replay_tp(tg, cw, p, tmap, grid, s);
+        e = launch_replay_tp(tg, cw, gp, p, tmap, grid, s);
         if (e != cudaSuccess) return fail(std::string("replay kernel launch: ") + cudaGetErrorString(e), MAGUS_ECUDA);
     }
     // synchronous: the scratch is reused by the next call, and device-side input errors

@@ -14,7 +14,9 @@
 // is off by at most one for |c| < 2^33, absorbed by the margins above).
 #include <cmath>
 #include <cstring>
+#include <algorithm>
 #include <string>
+#include <vector>
 
 #include "magus_internal.h"
 
@@ -106,6 +108,40 @@ int derive_policy(const magus_policy_t &p, const magus_model_t &m, DevPolicy *ou
     }
     *out = d;
     return MAGUS_OK;
+}
+
+// Group policies whose Alg. 1 parameters coincide (same W, inc, dec: identical predictions),
+// at most gp members per group, keeping the policies' order within each group.
+void form_groups(const std::vector<DevPolicy> &pols, int gp, std::vector<PolicyGroup> *out) {
+    out->clear();
+    std::vector<int> order(pols.size());
+    for (size_t i = 0; i < pols.size(); i++) order[i] = (int)i;
+    auto key_less = [&](int a, int b) {
+        const DevPolicy &x = pols[a], &y = pols[b];
+        if (x.W != y.W) return x.W < y.W;
+        if (x.up_mid != y.up_mid) return x.up_mid < y.up_mid;
+        if (x.dn_mid != y.dn_mid) return x.dn_mid < y.dn_mid;
+        if (memcmp(&x.inc, &y.inc, 8)) return memcmp(&x.inc, &y.inc, 8) < 0;
+        if (memcmp(&x.dec, &y.dec, 8)) return memcmp(&x.dec, &y.dec, 8) < 0;
+        return a < b;
+    };
+    auto same = [&](int a, int b) {
+        const DevPolicy &x = pols[a], &y = pols[b];
+        return x.W == y.W && x.up_mid == y.up_mid && x.dn_mid == y.dn_mid && !memcmp(&x.inc, &y.inc, 8) &&
+               !memcmp(&x.dec, &y.dec, 8);
+    };
+    if (gp > 1) std::stable_sort(order.begin(), order.end(), key_less);
+    for (size_t i = 0; i < order.size();) {
+        PolicyGroup g;
+        memset(&g, 0, sizeof(g));
+        g.count = 0;
+        size_t j = i;
+        while (j < order.size() && g.count < gp && (g.count == 0 || same(order[i], order[j])))
+            g.member[g.count++] = order[j++];
+        for (int m = g.count; m < kMaxGroup; m++) g.member[m] = g.member[0];
+        out->push_back(g);
+        i = j;
+    }
 }
 
 }  // namespace magus

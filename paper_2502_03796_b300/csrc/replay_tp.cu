@@ -19,6 +19,11 @@
 // W <= 64 never reaches outside shared memory.  One staged chunk feeds every policy the
 // CTA holds (policy_slots groups of time_groups warps).
 //
+// Policies that share Alg. 1's parameters (W, inc, dec) make identical predictions and
+// flags; they differ only in Alg. 2 (L, threshold).  A slot therefore holds a policy group
+// of up to GP such policies: the row predictions are made once and Alg. 2, the latch, the
+// energy charge and the log run per member.
+//
 // Energy: per level the kernel counts unstretched intervals and sums the deltas of
 // stretched ones (integers, exact); the FP64 totals are formed once per pair.
 #include <cuda_runtime.h>
@@ -83,21 +88,21 @@ __device__ __forceinline__ void tma_rows(uint32_t dst, const CUtensorMap *tmap, 
 __device__ __forceinline__ void group_sync(int id, int nthreads) {
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
 }
-struct GroupCarry {
-    uint64_t hist;      // flags of the 64 rounds before the chunk
+struct MemberCarry {
     uint64_t count;     // change-log entries emitted so far for the pair
     uint32_t level;     // level (0 bottom / 1 top) governing the chunk's first round
     uint32_t pad;
 };
 
-template <int TG, int CW>
+template <int TG, int CW, int GP>
 struct Shared {
     uint64_t bar[2];
     uint64_t xf[CW][TG];              // flags of the last 64 rounds of each sub-block
-    uint32_t xs[CW][TG];              // sub-block summary: has | exit<<1 | first<<2 | nch<<3
-    GroupCarry carry[CW][2];          // per policy slot, double-buffered by chunk parity
-    unsigned long long red_s0[TG * CW], red_sm[TG * CW], red_hash[TG * CW];
-    uint32_t red_n0[TG * CW], red_nm[TG * CW], red_hf[TG * CW];
+    uint64_t hist[CW][2];             // flags of the 64 rounds before the chunk (by parity)
+    uint32_t xs[CW][GP][TG];          // sub-block summary: has | exit<<1 | first<<2 | nch<<3
+    MemberCarry carry[CW][GP][2];     // per member, double-buffered by chunk parity
+    unsigned long long red_s0[TG * CW][GP], red_sm[TG * CW][GP], red_hash[TG * CW][GP];
+    uint32_t red_n0[TG * CW][GP], red_nm[TG * CW][GP], red_hf[TG * CW][GP];
     int item;
     int abort;
 };
@@ -108,25 +113,25 @@ template <int TG>
 __host__ __device__ constexpr size_t stage_bytes() {
     return 1024 + (size_t)TG * SB * sizeof(uint32_t);
 }
-template <int TG, int CW>
+template <int TG, int CW, int GP>
 __host__ __device__ constexpr size_t stage_offset() {
-    return (sizeof(Shared<TG, CW>) + 1023) / 1024 * 1024;
+    return (sizeof(Shared<TG, CW, GP>) + 1023) / 1024 * 1024;
 }
-template <int TG, int CW>
+template <int TG, int CW, int GP>
 __host__ __device__ constexpr size_t smem_bytes() {
-    return 1024 /* alignment slack */ + stage_offset<TG, CW>() + 2 * stage_bytes<TG>();
+    return 1024 /* alignment slack */ + stage_offset<TG, CW, GP>() + 2 * stage_bytes<TG>();
 }
 
-template <int TG, int CW>
+template <int TG, int CW, int GP>
 __global__ void __launch_bounds__(TG * CW * 32) replay_tp_kernel(const TpParams p,
                                                                    const __grid_constant__ CUtensorMap tmap) {
     constexpr int CH = TG * SB;              // rounds per chunk
     constexpr int CH_ROWS = TG * 32;         // 32-delta rows per chunk
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *smem_al = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023);
-    Shared<TG, CW> &sh = *reinterpret_cast<Shared<TG, CW> *>(smem_al);
+    Shared<TG, CW, GP> &sh = *reinterpret_cast<Shared<TG, CW, GP> *>(smem_al);
     // data row 0 of stage s (shared-window byte address)
-    const uint32_t stage0 = smem_u32(smem_al + stage_offset<TG, CW>()) + 1024;
+    const uint32_t stage0 = smem_u32(smem_al + stage_offset<TG, CW, GP>()) + 1024;
     auto stage_base = [&](int s_) { return stage0 + (uint32_t)s_ * (uint32_t)stage_bytes<TG>(); };
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -152,36 +157,46 @@ __global__ void __launch_bounds__(TG * CW * 32) replay_tp_kernel(const TpParams 
         const int item = sh.item;
         if (item >= p.n_items || sh.abort) break;
         const WorkItem wi = p.items[item];
-        const int cfg = (int)wi.cfg0 + cw;
-        const bool active = cfg < p.n_pols;
+        const int grp = (int)wi.cfg0 + cw;
+        const bool active = grp < p.n_groups;
+        const PolicyGroup G = p.groups[active ? grp : (int)wi.cfg0];
+        const int cnt = G.count;
         const uint64_t n = p.lengths[wi.trace];
-        const int64_t pair = (int64_t)wi.trace * p.n_pols + (active ? cfg : (int)wi.cfg0);
-        const int64_t pair0 = (int64_t)wi.trace * p.n_pols + (int64_t)wi.cfg0;
+        const int64_t pbase = (int64_t)wi.trace * p.n_pols;
+        const int64_t pair0 = pbase + p.groups[wi.cfg0].member[0];   // the block's first pair
 
-        const DevPolicy P = p.pols[active ? cfg : (int)wi.cfg0];
-        uint64_t n_seen0 = 0;
-        if (p.state) n_seen0 = p.state[pair].n_seen;
-
-        // Carried per-pair state: level, flag history, log count.
-        if (g == 0 && lane == 0) {
-            uint32_t lv = 0;
-            uint64_t fl = 0;
-            if (p.state && active) {
-                lv = p.state[pair].level;
-                fl = p.state[pair].flags;
-                if (lv != 0 && lv != topK) {
-                    atomicCAS(p.status, 0, MAGUS_EINVAL);
-                    lv = 0;
-                }
-            }
-            GroupCarry c0;
-            c0.hist = fl;
-            c0.count = 0;
-            c0.level = lv ? 1u : 0u;
-            c0.pad = 0;
-            sh.carry[cw][0] = c0;
+        const DevPolicy P = p.pols[G.member[0]];     // Alg. 1 parameters of the group
+        int Lm[GP], Km[GP];
+#pragma unroll
+        for (int m = 0; m < GP; m++) {
+            const int id = G.member[m < cnt ? m : 0];
+            Lm[m] = p.pols[id].L;
+            Km[m] = p.pols[id].kmin;
         }
-        // Deltas before the first chunk (the first policy's carried history), rows -2, -1.
+        uint64_t n_seen0 = 0;
+        if (p.state) n_seen0 = p.state[pbase + G.member[0]].n_seen;
+
+        // Carried state per member: level and log count; per group: the flag history.
+        if (g == 0 && lane == 0) {
+            sh.hist[cw][0] = (p.state && active) ? p.state[pbase + G.member[0]].flags : 0ull;
+#pragma unroll
+            for (int m = 0; m < GP; m++) {
+                uint32_t lv = 0;
+                if (p.state && active && m < cnt) {
+                    lv = p.state[pbase + G.member[m]].level;
+                    if (lv != 0 && lv != topK) {
+                        atomicCAS(p.status, 0, MAGUS_EINVAL);
+                        lv = 0;
+                    }
+                }
+                MemberCarry c0;
+                c0.count = 0;
+                c0.level = lv ? 1u : 0u;
+                c0.pad = 0;
+                sh.carry[cw][m][0] = c0;
+            }
+        }
+        // Deltas before the first chunk (the first pair's carried history), rows -2, -1.
         if (warp == 0) {
             const uint32_t b0 = stage_base(seq & 1);
             for (int k = lane; k < HALO; k += 32)
@@ -198,8 +213,9 @@ __global__ void __launch_bounds__(TG * CW * 32) replay_tp_kernel(const TpParams 
         };
         if (tid == 0 && nchunks > 0) issue(0, seq);
 
-        core::Acc acc;
-        core::acc_zero(acc);
+        core::Acc acc[GP];
+#pragma unroll
+        for (int m = 0; m < GP; m++) core::acc_zero(acc[m]);
 
         for (uint32_t c = 0; c < nchunks; c++) {
             const uint32_t sq = seq + c;
@@ -228,8 +244,7 @@ __global__ void __launch_bounds__(TG * CW * 32) replay_tp_kernel(const TpParams 
             if (!active) continue;
 
             // ---------------------------------------------------------------- phase A
-            // predictions (Alg. 1) and stretch bits of this lane's row, read in rotated
-            // order k = (i + lane) & 31 so the 32 lanes hit 32 different banks.
+            // Alg. 1 predictions and stretch bits of this lane's row (shared by the group)
             const uint32_t sub = sbase + (uint32_t)g * (SB * 4u);   // data row 0 of the sub-block
             const int64_t r0 = (int64_t)c * CH + g * SB + 32 * lane;  // row start (local)
             const int64_t left = (int64_t)n - r0;
@@ -243,145 +258,153 @@ __global__ void __launch_bounds__(TG * CW * 32) replay_tp_kernel(const TpParams 
                 if (lane == 0) sh.xf[cw][g] = (uint64_t)f30 | ((uint64_t)f31 << 32);
             }
             if (TG > 1) group_sync(1 + cw, TG * 32); else __syncwarp();
-
-            // ---------------------------------------------------------------- phase B
-            const GroupCarry cr = sh.carry[cw][c & 1];
-            const uint64_t tailH = (g == 0) ? cr.hist : sh.xf[cw][g > 0 ? g - 1 : 0];
+            const uint64_t tailH = (g == 0) ? sh.hist[cw][c & 1] : sh.xf[cw][g > 0 ? g - 1 : 0];
             const uint64_t H = core::row_history(FL, tailH, lane);
-            const uint32_t HF = core::hf_row(H, FL, P.L, P.kmin) & vmask;
-            const uint32_t SETM = HF | UP;
-            const uint32_t SET0 = DN & ~HF;
-            const uint32_t EV = SETM | SET0;
-            const bool has = EV != 0;
-            const uint32_t exitv = has ? (SETM >> (31 - __clz(EV))) & 1u : 0u;
-            const uint32_t firstv = has ? (SETM >> (__ffs(EV) - 1)) & 1u : 0u;
-            const uint32_t bev = __ballot_sync(FULL, has), bex = __ballot_sync(FULL, exitv);
-            const uint32_t prior = bev & lanemask_lt;
-            const uint32_t cin_prior = prior ? (bex >> (31 - __clz(prior))) & 1u : 0u;
-            {
-                // changes that do not depend on the level entering the sub-block: rows after
-                // the first event row are fixed; the first event row is counted as if it
-                // entered at its own first event's level (no change at that event)
-                uint32_t det = 0;
-                if (prior || has) {
-                    const uint32_t ca = prior ? cin_prior : firstv;
-                    const uint32_t lm = core::latch_row(SETM, SET0, ca);
-                    det = __popc((lm ^ ((lm << 1) | ca)) & vmask);
-                }
-                const uint32_t wdet = __reduce_add_sync(FULL, det);
-                const int fl_lane = bev ? __ffs(bev) - 1 : 0;
-                const uint32_t wfirst = __shfl_sync(FULL, firstv, fl_lane);
-                if (lane == 0) {
-                    const uint32_t whas = bev != 0;
-                    const uint32_t wexit = whas ? (bex >> (31 - __clz(bev))) & 1u : 0u;
-                    sh.xs[cw][g] = whas | (wexit << 1) | (wfirst << 2) | (wdet << 3);
-                }
-            }
-            if (TG > 1) group_sync(1 + cw, TG * 32); else __syncwarp();
 
-            // ---------------------------------------------------------------- phase C
-            uint32_t wcin = cr.level;
-            uint64_t before = 0;   // changes of earlier sub-blocks of this chunk
-            for (int gg = 0; gg < g; gg++) {
-                const uint32_t sv = sh.xs[cw][gg];
-                if (sv & 1u) {
-                    before += (sv >> 3) + ((((sv >> 2) & 1u) != wcin) ? 1u : 0u);
-                    wcin = (sv >> 1) & 1u;
-                }
-            }
-            const uint32_t cin = prior ? cin_prior : wcin;
-            const uint32_t Lm = core::latch_row(SETM, SET0, cin);  // level after each round
-            const uint32_t Flev = (Lm << 1) | cin;            // level during each round
-            const uint32_t CHG = (Lm ^ Flev) & vmask;
-
-            core::row_energy(sub, lane, Flev, rp, vmask, acc);
-            acc.hf += __popc(HF);
-            // frequency-change log
-            if (__any_sync(FULL, CHG != 0)) {
-                const uint32_t nch = __popc(CHG);
-                uint32_t incl = nch;
 #pragma unroll
-                for (int d = 1; d < 32; d <<= 1) {
-                    const uint32_t t = __shfl_up_sync(FULL, incl, d);
-                    if (lane >= d) incl += t;
+            for (int m = 0; m < GP; m++) {
+                if (m >= cnt) break;   // uniform across the group's warps
+                // ------------------------------------------------------------ phase B
+                const uint32_t HF = core::hf_row(H, FL, Lm[m], Km[m]) & vmask;
+                const uint32_t SETM = HF | UP;
+                const uint32_t SET0 = DN & ~HF;
+                const uint32_t EV = SETM | SET0;
+                const bool has = EV != 0;
+                const uint32_t exitv = has ? (SETM >> (31 - __clz(EV))) & 1u : 0u;
+                const uint32_t firstv = has ? (SETM >> (__ffs(EV) - 1)) & 1u : 0u;
+                const uint32_t bev = __ballot_sync(FULL, has), bex = __ballot_sync(FULL, exitv);
+                const uint32_t prior = bev & lanemask_lt;
+                const uint32_t cin_prior = prior ? (bex >> (31 - __clz(prior))) & 1u : 0u;
+                {
+                    // changes that do not depend on the level entering the sub-block: rows
+                    // after the first event row are fixed; the first event row is counted as
+                    // if it entered at its own first event's level (no change at that event)
+                    uint32_t det = 0;
+                    if (prior || has) {
+                        const uint32_t ca = prior ? cin_prior : firstv;
+                        const uint32_t lm = core::latch_row(SETM, SET0, ca);
+                        det = __popc((lm ^ ((lm << 1) | ca)) & vmask);
+                    }
+                    const uint32_t wdet = __reduce_add_sync(FULL, det);
+                    const int fl_lane = bev ? __ffs(bev) - 1 : 0;
+                    const uint32_t wfirst = __shfl_sync(FULL, firstv, fl_lane);
+                    if (lane == 0) {
+                        const uint32_t whas = bev != 0;
+                        const uint32_t wexit = whas ? (bex >> (31 - __clz(bev))) & 1u : 0u;
+                        sh.xs[cw][m][g] = whas | (wexit << 1) | (wfirst << 2) | (wdet << 3);
+                    }
                 }
-                uint64_t off = cr.count + before + (incl - nch);
-                uint32_t bits = CHG;
-                while (bits) {
-                    const int q = __ffs(bits) - 1;
-                    bits &= bits - 1;
-                    const uint64_t when = n_seen0 + (uint64_t)r0 + (uint64_t)q + 1;
-                    const uint32_t lv = ((Lm >> q) & 1u) ? topK : 0u;
-                    if (p.log_entries && off < p.log_cap)
-                        p.log_entries[(uint64_t)pair * p.log_cap + off] = (uint32_t)(when << 5) | lv;
-                    acc.hash += core::mix64((when << 8) | lv);
-                    off++;
+                if (TG > 1) group_sync(1 + cw, TG * 32); else __syncwarp();
+
+                // ------------------------------------------------------------ phase C
+                const MemberCarry cr = sh.carry[cw][m][c & 1];
+                uint32_t wcin = cr.level;
+                uint64_t before = 0;   // changes of earlier sub-blocks of this chunk
+                for (int gg = 0; gg < g; gg++) {
+                    const uint32_t sv = sh.xs[cw][m][gg];
+                    if (sv & 1u) {
+                        before += (sv >> 3) + ((((sv >> 2) & 1u) != wcin) ? 1u : 0u);
+                        wcin = (sv >> 1) & 1u;
+                    }
                 }
-            }
-            // carry into the next chunk
-            if (g == TG - 1 && lane == 0) {
-                uint32_t lv = wcin;
-                uint64_t cnt = before;
-                const uint32_t sv = sh.xs[cw][g];
-                if (sv & 1u) {
-                    cnt += (sv >> 3) + ((((sv >> 2) & 1u) != lv) ? 1u : 0u);
-                    lv = (sv >> 1) & 1u;
+                const uint32_t cin = prior ? cin_prior : wcin;
+                const uint32_t Lv = core::latch_row(SETM, SET0, cin);  // level after each round
+                const uint32_t Flev = (Lv << 1) | cin;            // level during each round
+                const uint32_t CHG = (Lv ^ Flev) & vmask;
+
+                core::row_energy(sub, lane, Flev, rp, vmask, acc[m]);
+                acc[m].hf += __popc(HF);
+                const int64_t pair = pbase + G.member[m];
+                // frequency-change log
+                if (__any_sync(FULL, CHG != 0)) {
+                    const uint32_t nch = __popc(CHG);
+                    uint32_t incl = nch;
+#pragma unroll
+                    for (int d = 1; d < 32; d <<= 1) {
+                        const uint32_t t = __shfl_up_sync(FULL, incl, d);
+                        if (lane >= d) incl += t;
+                    }
+                    uint64_t off = cr.count + before + (incl - nch);
+                    uint32_t bits = CHG;
+                    while (bits) {
+                        const int q = __ffs(bits) - 1;
+                        bits &= bits - 1;
+                        const uint64_t when = n_seen0 + (uint64_t)r0 + (uint64_t)q + 1;
+                        const uint32_t lv = ((Lv >> q) & 1u) ? topK : 0u;
+                        if (p.log_entries && off < p.log_cap)
+                            p.log_entries[(uint64_t)pair * p.log_cap + off] = (uint32_t)(when << 5) | lv;
+                        acc[m].hash += core::mix64((when << 8) | lv);
+                        off++;
+                    }
                 }
-                GroupCarry nx;
-                nx.hist = sh.xf[cw][g];
-                nx.count = cr.count + cnt;
-                nx.level = lv;
-                nx.pad = 0;
-                sh.carry[cw][(c + 1) & 1] = nx;
-            }
-            // state after the last round of the trace
-            if (p.state && left >= 1 && left <= 32) {
-                const int pl = (int)left - 1;
-                magus_state_t &so = p.state[pair];
-                so.n_seen = n_seen0 + n;
-                so.level = ((Lm >> pl) & 1u) ? topK : 0u;
-                so.flags = (H >> (pl + 1)) | ((uint64_t)FL << (63 - pl));
-                core::read_hist(sub, 32 * lane + pl, so.hist);
+                // carry into the next chunk
+                if (g == TG - 1 && lane == 0) {
+                    uint32_t lv = wcin;
+                    uint64_t cntc = before;
+                    const uint32_t sv = sh.xs[cw][m][g];
+                    if (sv & 1u) {
+                        cntc += (sv >> 3) + ((((sv >> 2) & 1u) != lv) ? 1u : 0u);
+                        lv = (sv >> 1) & 1u;
+                    }
+                    MemberCarry nx;
+                    nx.count = cr.count + cntc;
+                    nx.level = lv;
+                    nx.pad = 0;
+                    sh.carry[cw][m][(c + 1) & 1] = nx;
+                    if (m == 0) sh.hist[cw][(c + 1) & 1] = sh.xf[cw][g];
+                }
+                // state after the last round of the trace
+                if (p.state && left >= 1 && left <= 32) {
+                    const int pl = (int)left - 1;
+                    magus_state_t &so = p.state[pair];
+                    so.n_seen = n_seen0 + n;
+                    so.level = ((Lv >> pl) & 1u) ? topK : 0u;
+                    so.flags = (H >> (pl + 1)) | ((uint64_t)FL << (63 - pl));
+                    core::read_hist(sub, 32 * lane + pl, so.hist);
+                }
             }
         }
         if (sh.abort) break;
         seq += nchunks;
 
         // ------------------------------------------------------------------ totals
-        {
-            const uint32_t n0 = __reduce_add_sync(FULL, acc.n0);
-            const uint32_t nm = __reduce_add_sync(FULL, acc.nm);
-            const uint32_t hf = __reduce_add_sync(FULL, acc.hf);
-            const unsigned long long s0 = core::warp_sum_u64(acc.s0);
-            const unsigned long long smv = core::warp_sum_u64(acc.sm);
-            const unsigned long long hs = core::warp_sum_u64(acc.hash);
+#pragma unroll
+        for (int m = 0; m < GP; m++) {
+            const uint32_t n0 = __reduce_add_sync(FULL, acc[m].n0);
+            const uint32_t nm = __reduce_add_sync(FULL, acc[m].nm);
+            const uint32_t hf = __reduce_add_sync(FULL, acc[m].hf);
+            const unsigned long long s0 = core::warp_sum_u64(acc[m].s0);
+            const unsigned long long smv = core::warp_sum_u64(acc[m].sm);
+            const unsigned long long hs = core::warp_sum_u64(acc[m].hash);
             if (lane == 0) {
-                sh.red_n0[warp] = n0;
-                sh.red_nm[warp] = nm;
-                sh.red_hf[warp] = hf;
-                sh.red_s0[warp] = s0;
-                sh.red_sm[warp] = smv;
-                sh.red_hash[warp] = hs;
+                sh.red_n0[warp][m] = n0;
+                sh.red_nm[warp][m] = nm;
+                sh.red_hf[warp][m] = hf;
+                sh.red_s0[warp][m] = s0;
+                sh.red_sm[warp][m] = smv;
+                sh.red_hash[warp][m] = hs;
             }
         }
         __syncthreads();
-        if (g == 0 && lane == 0 && active) {
+        if (g == 0 && lane < cnt && active) {
+            const int m = lane;
             uint64_t N0 = 0, NM = 0, NH = 0;
             unsigned long long S0 = 0, SMs = 0, HS = 0;
             for (int w = cw * TG; w < cw * TG + TG; w++) {
-                N0 += sh.red_n0[w];
-                NM += sh.red_nm[w];
-                NH += sh.red_hf[w];
-                S0 += sh.red_s0[w];
-                SMs += sh.red_sm[w];
-                HS += sh.red_hash[w];
+                N0 += sh.red_n0[w][m];
+                NM += sh.red_nm[w][m];
+                NH += sh.red_hf[w][m];
+                S0 += sh.red_s0[w][m];
+                SMs += sh.red_sm[w][m];
+                HS += sh.red_hash[w][m];
             }
             double E, T;
             core::totals(M, N0, NM, S0, SMs, &E, &T);
+            const int64_t pair = pbase + G.member[m];
             p.energy[pair] = E;
             p.edp[pair] = E * T;
             if (p.time) p.time[pair] = T;
-            if (p.n_changes) p.n_changes[pair] = sh.carry[cw][nchunks & 1].count;
+            if (p.n_changes) p.n_changes[pair] = sh.carry[cw][m][nchunks & 1].count;
             if (p.change_hash) p.change_hash[pair] = HS;
             if (p.n_hf) p.n_hf[pair] = NH;
         }
@@ -394,48 +417,55 @@ __global__ void __launch_bounds__(TG * CW * 32) replay_tp_kernel(const TpParams 
     }
 }
 
-template <int TG, int CW>
+template <int TG, int CW, int GP>
 cudaError_t launch_t(const TpParams &p, const CUtensorMap &tmap, int grid, cudaStream_t stream) {
-    const size_t smem = smem_bytes<TG, CW>();
-    cudaError_t e = cudaFuncSetAttribute(replay_tp_kernel<TG, CW>,
+    const size_t smem = smem_bytes<TG, CW, GP>();
+    cudaError_t e = cudaFuncSetAttribute(replay_tp_kernel<TG, CW, GP>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    replay_tp_kernel<TG, CW><<<grid, TG * CW * 32, smem, stream>>>(p, tmap);
+    replay_tp_kernel<TG, CW, GP><<<grid, TG * CW * 32, smem, stream>>>(p, tmap);
     return cudaGetLastError();
 }
 
-template <int TG, int CW>
+template <int TG, int CW, int GP>
 int occ_t(int *smem_out) {
-    const size_t smem = smem_bytes<TG, CW>();
+    const size_t smem = smem_bytes<TG, CW, GP>();
     if (smem_out) *smem_out = (int)smem;
-    if (cudaFuncSetAttribute(replay_tp_kernel<TG, CW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if (cudaFuncSetAttribute(replay_tp_kernel<TG, CW, GP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem) != cudaSuccess)
         return 0;
     int blocks = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, replay_tp_kernel<TG, CW>, TG * CW * 32,
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, replay_tp_kernel<TG, CW, GP>, TG * CW * 32,
                                                       smem) != cudaSuccess)
         return 0;
     return blocks;
 }
 
+#define MAGUS_TILES(X) X(8, 1, 1) X(4, 2, 1) X(2, 4, 1) X(1, 8, 1) X(8, 1, 4) X(4, 2, 4) X(2, 4, 4) X(1, 8, 4)
+
 }  // namespace
 
 int tp_box_rows(int tg) { return tg * 32; }
 
-cudaError_t launch_replay_tp(int tg, int cw, const TpParams &p, const CUtensorMap &tmap, int grid,
+bool tp_tile_supported(int tg, int cw, int gp) {
+#define MAGUS_IS(a, b, c) if (tg == a && cw == b && gp == c) return true;
+    MAGUS_TILES(MAGUS_IS)
+#undef MAGUS_IS
+    return false;
+}
+
+cudaError_t launch_replay_tp(int tg, int cw, int gp, const TpParams &p, const CUtensorMap &tmap, int grid,
                              cudaStream_t stream) {
-    if (tg == 8 && cw == 1) return launch_t<8, 1>(p, tmap, grid, stream);
-    if (tg == 4 && cw == 2) return launch_t<4, 2>(p, tmap, grid, stream);
-    if (tg == 2 && cw == 4) return launch_t<2, 4>(p, tmap, grid, stream);
-    if (tg == 1 && cw == 8) return launch_t<1, 8>(p, tmap, grid, stream);
+#define MAGUS_LAUNCH(a, b, c) if (tg == a && cw == b && gp == c) return launch_t<a, b, c>(p, tmap, grid, stream);
+    MAGUS_TILES(MAGUS_LAUNCH)
+#undef MAGUS_LAUNCH
     return cudaErrorInvalidValue;
 }
 
-int tp_max_ctas_per_sm(int tg, int cw, int *smem) {
-    if (tg == 8 && cw == 1) return occ_t<8, 1>(smem);
-    if (tg == 4 && cw == 2) return occ_t<4, 2>(smem);
-    if (tg == 2 && cw == 4) return occ_t<2, 4>(smem);
-    if (tg == 1 && cw == 8) return occ_t<1, 8>(smem);
+int tp_max_ctas_per_sm(int tg, int cw, int gp, int *smem) {
+#define MAGUS_OCC(a, b, c) if (tg == a && cw == b && gp == c) return occ_t<a, b, c>(smem);
+    MAGUS_TILES(MAGUS_OCC)
+#undef MAGUS_OCC
     return 0;
 }
 

@@ -309,11 +309,11 @@ class Replay:
     def autotune(self, traces, lengths, policies: Sequence[Dict], stream=None):
         ln = np.ascontiguousarray(lengths, dtype=np.uint64)
         pols = policy_array(policies)
-        best = (ctypes.c_int32 * 2)()
+        best = (ctypes.c_int32 * 3)()
         ms = ctypes.c_float()
         check(lib().magus_replay_autotune(self.h, _ptr(traces), ln.ctypes.data, len(ln), ctypes.cast(pols, P),
                                           len(policies), ctypes.cast(best, P), ctypes.byref(ms), _stream(stream)))
-        return (best[0], best[1]), ms.value
+        return (best[0], best[1], best[2]), ms.value
 
 
 def decode_log(entries: np.ndarray):

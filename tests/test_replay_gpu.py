@@ -87,6 +87,44 @@ def test_ragged_batch_all_tiles(rp, tile):
         assert_pair(out, p, r, cap=cap, tag=f"tile{tile}")
 
 
+def grouped_policies():
+    """Three Alg. 1 settings x four Alg. 2 settings: policy groups of 4 share predictions."""
+    out = []
+    for W, inc, dec in [(5, 5.0, -5.0), (3, 2.0, -1.5), (40, 0.4, -0.4)]:
+        for L, th in [(10, 0.6), (1, 1.0), (64, 0.05), (7, 0.0)]:
+            out.append(dict(inc_threshold=inc, dec_threshold=dec, direv_length=W, tune_window=L,
+                            high_freq_threshold=th, step_mode=0))
+    # interleave so that group members are not adjacent in the caller's order
+    return out[::2] + out[1::2]
+
+
+@pytest.mark.parametrize("tile", TILES)
+def test_grouped_policies_all_tiles(rp, tile):
+    ts = ragged_set(seed=8)
+    model = tracegen.default_model()
+    pols = grouped_policies()
+    cap = 40_000
+    rp.set_tile(*tile)
+    try:
+        out = to_numpy(rp.run(to_device(ts), ts.lengths, pols, log_capacity=cap))
+    finally:
+        rp.set_tile(0, 0)
+    ref = oracle_pairs(ts, pols, model)
+    for p, r in ref.items():
+        assert_pair(out, p, r, cap=cap, tag=f"grouped tile{tile}")
+
+
+def test_autotune_picks_a_tile(rp):
+    ts = tracegen.sweep(n_traces=8, n=30_000, seed=2)
+    pols = tracegen.sweep_policies()[:32]
+    (tg, cw, gp), ms = rp.autotune(to_device(ts), ts.lengths, pols)
+    assert tg * cw == 8 and gp in (1, 4) and ms > 0
+    out = to_numpy(rp.run(to_device(ts), ts.lengths, pols))
+    ref, _ = oracle.replay_batch(ts.data, ts.offsets, ts.lengths, pols, tracegen.default_model())
+    assert np.array_equal(out["change_hash"], ref["change_hash"].astype(np.uint64))
+    np.testing.assert_allclose(out["energy_j"], ref["energy_j"], rtol=REL_TOL)
+
+
 def test_plain_kernel_matches_oracle(rp):
     ts = tracegen.make_traces(np.array([0, 1, 7, 100, 5000, 20000], dtype=np.uint64), seed=11)
     pols = edge_policies() + [dict(tracegen.default_policy(), step_mode=1, high_freq_threshold=0.9)]
@@ -138,7 +176,8 @@ def test_decision_band_exhaustive(rp, mg, model_kind):
         handle.close()
 
 
-def test_split_replay_with_state(rp, mg):
+@pytest.mark.parametrize("grouped", [False, True])
+def test_split_replay_with_state(rp, mg, grouped):
     """Feeding a trace in pieces with carried state reproduces the whole-trace log and
     additive energies (against the oracle's whole-trace replay)."""
     model = tracegen.default_model()
@@ -146,6 +185,8 @@ def test_split_replay_with_state(rp, mg):
     full = ts_all.trace(0)
     pols = [tracegen.default_policy(), dict(tracegen.default_policy(), direv_length=40, tune_window=50,
                                             high_freq_threshold=0.1)]
+    if grouped:
+        pols = grouped_policies()
     cuts = [0, 3, 4, 37, 64, 65, 1100, 8192, 8200, 20000, 30_000]
     state = torch.zeros(len(pols) * mg.STATE_BYTES, dtype=torch.uint8, device="cuda")
     E = np.zeros(len(pols))
