@@ -88,14 +88,25 @@ class ClockSampler:
         try:
             import pynvml
             pynvml.nvmlInit()
-            vis = os.environ.get("CUDA_VISIBLE_DEVICES")
-            phys = int(vis.split(",")[index]) if vis and vis.split(",")[index].isdigit() else index
-            self.h = pynvml.nvmlDeviceGetHandleByIndex(phys)
+            vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+            entry = vis.split(",")[index].strip() if vis else ""
+            if entry.startswith("GPU-") or entry.startswith("MIG-"):
+                self.h = pynvml.nvmlDeviceGetHandleByUUID(entry)
+            elif entry.isdigit():
+                self.h = pynvml.nvmlDeviceGetHandleByIndex(int(entry))
+            else:
+                # match the CUDA device's PCI bus id
+                import torch
+                bus = torch.cuda.get_device_properties(index).pci_bus_id if hasattr(
+                    torch.cuda.get_device_properties(index), "pci_bus_id") else None
+                self.h = (pynvml.nvmlDeviceGetHandleByPciBusId(bus) if bus
+                          else pynvml.nvmlDeviceGetHandleByIndex(index))
             self.nv = pynvml
             self.max_mhz = float(pynvml.nvmlDeviceGetMaxClockInfo(self.h, pynvml.NVML_CLOCK_SM))
             self.ok = True
-        except Exception:
+        except Exception as e:  # noqa: BLE001
             self.ok = False
+            self.err = f"{type(e).__name__}: {e}"
 
     def _poll(self):
         nv = self.nv
@@ -119,7 +130,8 @@ class ClockSampler:
 
     def stop(self) -> dict:
         if not self.ok:
-            return dict(sm_mhz=None, sm_max_mhz=None, reasons=["nvml unavailable"], samples=0)
+            return dict(sm_mhz=None, sm_max_mhz=None, reasons=[], samples=0,
+                        note="nvml unavailable: " + getattr(self, "err", "?"))
         self.stop_flag.set()
         self.thread.join(timeout=2)
         return dict(sm_mhz=float(np.median(self.samples)) if self.samples else None, sm_max_mhz=self.max_mhz,

@@ -261,9 +261,10 @@ __global__ void __launch_bounds__(TG * CW * 32) replay_tp_kernel(const TpParams 
             const uint64_t tailH = (g == 0) ? sh.hist[cw][c & 1] : sh.xf[cw][g > 0 ? g - 1 : 0];
             const uint64_t H = core::row_history(FL, tailH, lane);
 
-#pragma unroll
-            for (int m = 0; m < GP; m++) {
-                if (m >= cnt) break;   // uniform across the group's warps
+            // members one after another (not unrolled: unrolling four members doubles the
+            // registers and halves the resident CTAs, measured slower)
+#pragma unroll 1
+            for (int m = 0; m < (GP == 1 ? 1 : cnt); m++) {
                 // ------------------------------------------------------------ phase B
                 const uint32_t HF = core::hf_row(H, FL, Lm[m], Km[m]) & vmask;
                 const uint32_t SETM = HF | UP;
