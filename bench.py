@@ -71,53 +71,70 @@ def ncu_traffic() -> float | None:
     return float(e["dram_bytes_per_launch"])
 
 
+class _Nvml:
+    """Read-only NVML queries through ctypes (libnvidia-ml ships with the driver)."""
+    CLOCK_SM = 1
+    REASON_BITS = {"sw_power_cap": 0x4, "hw_slowdown": 0x8, "sw_thermal_slowdown": 0x20,
+                   "hw_thermal_slowdown": 0x40, "hw_power_brake_slowdown": 0x80}
+
+    def __init__(self):
+        import ctypes
+        self.c = ctypes
+        self.lib = ctypes.CDLL("libnvidia-ml.so.1")
+        if self.lib.nvmlInit_v2() != 0:
+            raise RuntimeError("nvmlInit failed")
+
+    def handle(self, index: int):
+        c = self.c
+        h = c.c_void_p()
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+        entry = vis.split(",")[index].strip() if vis else ""
+        if entry.startswith("GPU-") or entry.startswith("MIG-"):
+            rc = self.lib.nvmlDeviceGetHandleByUUID(entry.encode(), c.byref(h))
+        else:
+            rc = self.lib.nvmlDeviceGetHandleByIndex_v2(int(entry) if entry.isdigit() else index, c.byref(h))
+        if rc != 0:
+            raise RuntimeError(f"nvml handle lookup failed ({rc})")
+        return h
+
+    def clock(self, h, kind=CLOCK_SM, max_=False):
+        v = self.c.c_uint()
+        fn = self.lib.nvmlDeviceGetMaxClockInfo if max_ else self.lib.nvmlDeviceGetClockInfo
+        if fn(h, kind, self.c.byref(v)) != 0:
+            raise RuntimeError("nvml clock query failed")
+        return float(v.value)
+
+    def reasons(self, h):
+        v = self.c.c_ulonglong()
+        fn = getattr(self.lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            self.lib.nvmlDeviceGetCurrentClocksThrottleReasons
+        if fn(h, self.c.byref(v)) != 0:
+            return set()
+        return {n for n, bit in self.REASON_BITS.items() if v.value & bit}
+
+
 class ClockSampler:
     """SM clock and clock-event (throttle) reasons polled through NVML every 2 ms while the
     timed region runs (read-only queries; no setting is changed)."""
-    REASONS = {"hw_slowdown": "nvmlClocksEventReasonHwSlowdown",
-               "hw_thermal_slowdown": "nvmlClocksEventReasonHwThermalSlowdown",
-               "sw_thermal_slowdown": "nvmlClocksEventReasonSwThermalSlowdown",
-               "sw_power_cap": "nvmlClocksEventReasonSwPowerCap",
-               "hw_power_brake_slowdown": "nvmlClocksEventReasonHwPowerBrakeSlowdown"}
 
     def __init__(self, index: int):
-        self.index = index
         self.samples, self.reasons = [], set()
         self.max_mhz = None
-        self.ok = False
         try:
-            import pynvml
-            pynvml.nvmlInit()
-            vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
-            entry = vis.split(",")[index].strip() if vis else ""
-            if entry.startswith("GPU-") or entry.startswith("MIG-"):
-                self.h = pynvml.nvmlDeviceGetHandleByUUID(entry)
-            elif entry.isdigit():
-                self.h = pynvml.nvmlDeviceGetHandleByIndex(int(entry))
-            else:
-                # match the CUDA device's PCI bus id
-                import torch
-                bus = torch.cuda.get_device_properties(index).pci_bus_id if hasattr(
-                    torch.cuda.get_device_properties(index), "pci_bus_id") else None
-                self.h = (pynvml.nvmlDeviceGetHandleByPciBusId(bus) if bus
-                          else pynvml.nvmlDeviceGetHandleByIndex(index))
-            self.nv = pynvml
-            self.max_mhz = float(pynvml.nvmlDeviceGetMaxClockInfo(self.h, pynvml.NVML_CLOCK_SM))
+            self.nv = _Nvml()
+            self.h = self.nv.handle(index)
+            self.max_mhz = self.nv.clock(self.h, max_=True)
             self.ok = True
         except Exception as e:  # noqa: BLE001
             self.ok = False
             self.err = f"{type(e).__name__}: {e}"
 
     def _poll(self):
-        nv = self.nv
         while not self.stop_flag.is_set():
             try:
-                self.samples.append(float(nv.nvmlDeviceGetClockInfo(self.h, nv.NVML_CLOCK_SM)))
-                r = nv.nvmlDeviceGetCurrentClocksEventReasons(self.h)
-                for name, attr in self.REASONS.items():
-                    if r & getattr(nv, attr, 0):
-                        self.reasons.add(name)
-            except Exception:
+                self.samples.append(self.nv.clock(self.h))
+                self.reasons |= self.nv.reasons(self.h)
+            except Exception:  # noqa: BLE001
                 pass
             time.sleep(0.002)
 
