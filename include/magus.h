@@ -202,8 +202,9 @@ int magus_replay_close(magus_replay_t *h);
  * MAGUS_STATIC_SCRATCH_BYTES that every GPU loading the library holds until the process
  * exits.  It calls no cudaMalloc / cudaFree.
  *   - Arguments and outputs as magus_replay_run (traces, outputs, log, io_state: device).
- *   - Workloads whose plan does not fit the scratch (roughly: 64 B per policy plus
- *     24 B per trace x ceil(policies / 8)) are rejected with EINVAL and a message.
+ *   - Workloads whose plan does not fit the scratch (about 100 B per policy, 16 B per
+ *     trace and 8 B per trace for every block of up to 8 policy groups) are rejected with
+ *     EINVAL and a message.
  *   - The first call on a device looks up the array's device address (set-up, once per
  *     device); make that first call before any stream capture on that device.
  *   - Every call shares the one array: the call uploads the plan on `stream`, zeroes the
