@@ -208,20 +208,23 @@ __device__ __forceinline__ RowPred row_predict(uint32_t base, int lane, const De
 
 // Alg. 2 over one row: bit p of the result = high-frequency state of round p, i.e. at
 // least kmin flags among rounds p-L+1 .. p.  H: flags of the 64 rounds before the row
-// (bit q = round q - 64); FL: flags of the row.  The counts of rounds p, p+8, p+16, p+24
-// advance together, one per byte of a 32-bit word (counts <= 64 never carry across bytes).
+// (bit q = round q - 64); FL: flags of the row.
+// The counts of rounds p, p+8, p+16, p+24 advance together, one per byte of a 32-bit word
+// holding count + 128 - kmin: the top bit of a byte is set exactly when count >= kmin
+// (counts <= 64, so bytes never carry into each other).  (A nibble-wide variant with 8
+// counts per word measured slower: it needs twice the population counts to seed.)
 __device__ __forceinline__ uint32_t hf_row(uint64_t H, uint32_t FL, int L, int kmin) {
     const int s = 64 - L;
     // bit p of LV = flag of round p - L (leaving the window at round p)
     const uint32_t LV = s == 0 ? (uint32_t)H : (uint32_t)((H >> s) | ((uint64_t)FL << (64 - s)));
     const uint32_t c0 = __popcll(H >> s);                    // window ending at round -1
+    uint32_t HF = 0;
     const uint32_t d0 = __popc(FL & 0xffu) - __popc(LV & 0xffu);
     const uint32_t d1 = __popc(FL & 0xff00u) - __popc(LV & 0xff00u);
     const uint32_t d2 = __popc(FL & 0xff0000u) - __popc(LV & 0xff0000u);
     const uint32_t c1 = c0 + d0, c2 = c1 + d1, c3 = c2 + d2; // windows ending at 7, 15, 23
     // byte b holds count + 128 - kmin: bit 7 of the byte <=> count >= kmin
     uint32_t e4 = (c0 | (c1 << 8) | (c2 << 16) | (c3 << 24)) + (uint32_t)(128 - kmin) * 0x01010101u;
-    uint32_t HF = 0;
 #pragma unroll
     for (int p = 0; p < 8; p++) {
         e4 = e4 + ((FL >> p) & 0x01010101u) - ((LV >> p) & 0x01010101u);
@@ -248,6 +251,64 @@ __device__ __forceinline__ uint32_t latch_row(uint32_t SETM, uint32_t SET0, uint
     const uint64_t sum = (uint64_t)A + (uint64_t)SETM + (uint64_t)cin;
     const uint32_t carry_in = (uint32_t)sum ^ A ^ SETM;  // carry into each bit position
     return (carry_in | SETM) & ~SET0;
+}
+
+// Change-log entries of a warp's 32 rows.  Up to 32 changes: one pass, lane i takes the
+// warp's i-th change (rows in order, rounds in order within a row), found by a binary search
+// over the inclusive prefix counts of the rows; more changes: each lane walks its own row.  CHG / Lv: this lane's change mask and level
+// after each round; row0: global interval index of round 0 of row 0 (rows follow every 32
+// rounds); log: the pair's log (NULL: hash only); first: entries of the pair before this
+// warp's rows.  Entries are written to consecutive slots (coalesced stores).
+__device__ __forceinline__ void emit_changes(uint32_t CHG, uint32_t Lv, uint64_t row0, uint32_t topK,
+                                             uint32_t *log, uint64_t log_cap, uint64_t first,
+                                             unsigned long long &hash, int lane) {
+    const uint32_t nch = __popc(CHG);
+    uint32_t incl = nch;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t t = __shfl_up_sync(FULL, incl, d);
+        if (lane >= d) incl += t;
+    }
+    const uint32_t total = __shfl_sync(FULL, incl, 31);
+    if (total > 32) {
+        // dense changes: every lane walks its own row (fewer steps than several passes)
+        uint64_t off = first + (incl - nch);
+        uint32_t bits = CHG;
+        while (bits) {
+            const int q = __ffs(bits) - 1;
+            bits &= bits - 1;
+            const uint64_t when = row0 + 32u * (uint32_t)lane + (uint32_t)q + 1u;
+            const uint32_t lv = ((Lv >> q) & 1u) ? topK : 0u;
+            if (log && off < log_cap) log[off] = (uint32_t)(when << 5) | lv;
+            hash += mix64((when << 8) | lv);
+            off++;
+        }
+        return;
+    }
+    for (uint32_t base = 0; base < total; base += 32) {
+        const uint32_t idx = base + (uint32_t)lane;
+        // row r: the first row whose inclusive count exceeds idx
+        int r = 0;
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1) {
+            const uint32_t v = __shfl_sync(FULL, incl, r + step - 1);
+            if (v <= idx) r += step;
+        }
+        r = r > 31 ? 31 : r;
+        const uint32_t chg_r = __shfl_sync(FULL, CHG, r);
+        const uint32_t lv_r = __shfl_sync(FULL, Lv, r);
+        const uint32_t excl_r = __shfl_sync(FULL, incl - nch, r);
+        if (idx < total) {
+            uint32_t m = chg_r;
+            for (uint32_t j = excl_r; j < idx; j++) m &= m - 1;   // drop the earlier changes
+            const int q = __ffs(m) - 1;
+            const uint64_t when = row0 + 32u * (uint32_t)r + (uint32_t)q + 1u;
+            const uint32_t lv = ((lv_r >> q) & 1u) ? topK : 0u;
+            const uint64_t off = first + idx;
+            if (log && off < log_cap) log[off] = (uint32_t)(when << 5) | lv;
+            hash += mix64((when << 8) | lv);
+        }
+    }
 }
 
 // Sum of the row's deltas at the rounds selected by mask Msel (bit p = round p).

@@ -317,27 +317,10 @@ __global__ void __launch_bounds__(TG * CW * 32) replay_tp_kernel(const TpParams 
                 acc[m].hf += __popc(HF);
                 const int64_t pair = pbase + G.member[m];
                 // frequency-change log
-                if (__any_sync(FULL, CHG != 0)) {
-                    const uint32_t nch = __popc(CHG);
-                    uint32_t incl = nch;
-#pragma unroll
-                    for (int d = 1; d < 32; d <<= 1) {
-                        const uint32_t t = __shfl_up_sync(FULL, incl, d);
-                        if (lane >= d) incl += t;
-                    }
-                    uint64_t off = cr.count + before + (incl - nch);
-                    uint32_t bits = CHG;
-                    while (bits) {
-                        const int q = __ffs(bits) - 1;
-                        bits &= bits - 1;
-                        const uint64_t when = n_seen0 + (uint64_t)r0 + (uint64_t)q + 1;
-                        const uint32_t lv = ((Lv >> q) & 1u) ? topK : 0u;
-                        if (p.log_entries && off < p.log_cap)
-                            p.log_entries[(uint64_t)pair * p.log_cap + off] = (uint32_t)(when << 5) | lv;
-                        acc[m].hash += core::mix64((when << 8) | lv);
-                        off++;
-                    }
-                }
+                if (__any_sync(FULL, CHG != 0))
+                    core::emit_changes(CHG, Lv, n_seen0 + (uint64_t)c * CH + (uint64_t)g * SB, topK,
+                                       p.log_entries ? p.log_entries + (uint64_t)pair * p.log_cap : nullptr,
+                                       p.log_cap, cr.count + before, acc[m].hash, lane);
                 // carry into the next chunk
                 if (g == TG - 1 && lane == 0) {
                     uint32_t lv = wcin;

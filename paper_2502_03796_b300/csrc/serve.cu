@@ -130,14 +130,8 @@ __global__ void __launch_bounds__(SERVE_WARPS * 32) serve_kernel(const ServePara
             row_energy(base, lane, Flev, rp, vmask, acc);
             acc.hf += __popc(HF);
             nch += __popc(CHG);
-            uint32_t bits = CHG;
-            while (bits) {
-                const int q = __ffs(bits) - 1;
-                bits &= bits - 1;
-                const uint64_t when = n_seen0 + (uint64_t)r0 + (uint64_t)q + 1;
-                const uint32_t lv = ((Lm >> q) & 1u) ? topK : 0u;
-                acc.hash += mix64((when << 8) | lv);
-            }
+            if (__any_sync(FULL, CHG != 0))
+                emit_changes(CHG, Lm, n_seen0 + c0, topK, nullptr, 0, 0, acc.hash, lane);
             // final state of the request, written by the lane holding its last round
             if (left >= 1 && left <= 32) {
                 const int pl = (int)left - 1;
