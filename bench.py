@@ -36,8 +36,8 @@ METRIC = "policy-step samples/s & % HBM roofline vs plain launch; serve p50/p99 
 N_TRACES, N_INTERVALS = 4096, 100_000
 LOG_CAP = 8192
 WORKLOAD = "batched replay: 4096 traces x 100000 intervals (phase mean 40), 1 policy (W=5, inc=5, dec=-5, L=10, th=0.6)"
-KERNEL_SOURCES = ["paper_2502_03796_b300/csrc/replay_tp.cu", "paper_2502_03796_b300/csrc/replay_core.cuh",
-                  "paper_2502_03796_b300/csrc/magus_internal.h"]
+KERNEL_SOURCES = ["paper_2502_03796_b300/csrc/replay_tp.cu", "paper_2502_03796_b300/csrc/replay_seg.cu",
+                  "paper_2502_03796_b300/csrc/replay_core.cuh", "paper_2502_03796_b300/csrc/magus_internal.h"]
 
 
 def kernel_sha() -> str:
@@ -57,15 +57,15 @@ def measured_peaks() -> dict:
     return dict(hbm_gbs=6400.0, source="fallback")
 
 
-def ncu_traffic() -> float | None:
-    """Per-launch DRAM bytes of the batched kernel from the committed ncu summary, if it was
+def ncu_traffic(key: str) -> float | None:
+    """Per-launch DRAM bytes of the batched replay from the committed ncu summary, if it was
     taken on the current kernel source."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
     with open(p) as f:
         d = json.load(f)
-    e = d.get("replay_tp_batched")
+    e = d.get(key)
     if not e or e.get("kernel_sha") != kernel_sha():
         return None
     return float(e["dram_bytes_per_launch"])
@@ -288,7 +288,8 @@ def time_steps(fn, steps: int, warmup: int, stream) -> float:
 
 
 def run_other(args, world, rank, local) -> int:
-    """Lines for the other replay workloads: policy sweep, uneven lengths, single trace."""
+    """Lines for the other replay workloads: policy sweep, uneven lengths, single trace, few
+    long traces."""
     import torch
     from paper_2502_03796_b300 import magus
     import oracle
@@ -299,6 +300,10 @@ def run_other(args, world, rank, local) -> int:
         ts = tracegen.sweep(first_id=rank * 1024)
         pols = tracegen.sweep_policies()
         desc = "policy sweep: 1024 traces x 200000 intervals (bursty mean 10 / long mean 500 regimes), 256 policies"
+    elif args.workload == "long":
+        ts = tracegen.batched(n_traces=16, n=4_000_000, seed=rank, first_id=rank * 16)
+        pols = [tracegen.default_policy()]
+        desc = "few long traces: 16 traces x 4000000 intervals (phase mean 40), 1 policy"
     elif args.workload == "uneven":
         ts = tracegen.uneven(seed=rank)
         pols = tracegen.sweep_policies()[:16]
@@ -313,11 +318,14 @@ def run_other(args, world, rank, local) -> int:
     n_pairs = ts.n_traces * len(pols)
     outs = rp.alloc(n_pairs, log_capacity=0)
     tuned = None
-    if args.workload in ("sweep", "uneven"):
+    if args.tile:
+        rp.set_tile(*[int(x) for x in args.tile.split(",")])
+    rp.set_segments(args.segments)
+    if args.workload in ("sweep", "uneven") and not args.tile and args.segments < 0:
         tuned, tms = rp.autotune(d_tr, ts.lengths, pols, stream=stream)
     rp.kernel_time()
     ms = time_steps(lambda: rp.run(d_tr, ts.lengths, pols, stream=stream, out=outs), args.steps, args.warmup, stream)
-    k_ms, k_n = rp.kernel_time()
+    k_ms, k_main, k_n, k_kernels = rp.kernel_time(detail=True)
     pair_steps = ts.n_samples * len(pols)
     value = pair_steps * world / (ms * 1e-3)
     alg_bytes = 4 * ts.n_samples + 48 * n_pairs
@@ -330,8 +338,9 @@ def run_other(args, world, rank, local) -> int:
                             tile=list(tuned) if tuned else None, outputs="energy, EDP, time, counts, hash (no entries)"),
                 roofline=dict(bound="alu" if len(pols) > 1 else "hbm", achieved=alg_bytes / (k_avg * 1e-3) / 1e9,
                               peak=peaks["hbm_gbs"], unit="GB/s", frac=alg_bytes / (k_avg * 1e-3) / 1e9 / peaks["hbm_gbs"],
-                              traffic=None, kernel_ms=k_avg, alg_bytes_per_launch=alg_bytes),
-                gpu_launches=k_n)
+                              traffic=None, kernel_ms=k_avg, main_kernel_ms=k_main / max(k_n, 1),
+                              alg_bytes_per_launch=alg_bytes),
+                gpu_launches=k_kernels)
     # one launch per trace (time-parallel kernel) on a sample of traces
     k = min(256, ts.n_traces)
     per_ms = 0.0
@@ -350,15 +359,20 @@ def run_other(args, world, rank, local) -> int:
     line["one_launch_per_trace"] = dict(value=float(ts.lengths[:k].sum()) * len(pols) / (per_ms * 1e-3),
                                         unit="pair-interval samples/s", sample=f"first {k} traces, one launch each")
     # plain form (one launch per trace, literal FP64) on a small sample
-    kp = 4 if args.workload != "single" else 1
+    if args.workload == "long":
+        kp, p_len = 1, np.array([200_000], dtype=np.uint64)     # a prefix of the first trace
+    else:
+        kp = 4 if args.workload != "single" else 1
+        p_len = ts.lengths[:kp]
     sub = d_tr[:int(ts.offsets[kp - 1]) + int((ts.lengths[kp - 1] + 31) // 32 * 32)] if kp > 1 else d_tr
-    rp.plain(sub, ts.lengths[:kp], pols, stream=stream)
+    rp.plain(sub, p_len, pols, stream=stream)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    rp.plain(sub, ts.lengths[:kp], pols, stream=stream)
+    rp.plain(sub, p_len, pols, stream=stream)
     torch.cuda.synchronize()
-    line["plain_launch"] = dict(value=float(ts.lengths[:kp].sum()) * len(pols) / (time.perf_counter() - t0),
-                                unit="pair-interval samples/s", sample=f"first {kp} traces")
+    line["plain_launch"] = dict(value=float(p_len.sum()) * len(pols) / (time.perf_counter() - t0),
+                                unit="pair-interval samples/s",
+                                sample=f"first {kp} traces" if args.workload != "long" else "first 200000 intervals of trace 0")
     if rank == 0:
         # CPU oracle on a bounded sample
         kc = min(ts.n_traces, 8 if args.workload != "single" else 1)
@@ -382,9 +396,11 @@ def main() -> int:
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--tile", default="", help="time_groups,policy_slots (default: automatic)")
+    ap.add_argument("--segments", type=int, default=-1,
+                    help="-1 automatic, 0 tile kernel, >0 segment kernel with this many rounds per segment")
     ap.add_argument("--traces", type=int, default=N_TRACES, help="traces per GPU (profiling runs use fewer)")
     ap.add_argument("--no-serve", action="store_true")
-    ap.add_argument("--workload", default="batched", choices=["batched", "sweep", "uneven", "single"],
+    ap.add_argument("--workload", default="batched", choices=["batched", "sweep", "uneven", "single", "long"],
                     help="batched (default, the headline line); sweep / uneven / single print their own line")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -406,6 +422,7 @@ def main() -> int:
     rp = magus.Replay(model, device=local, mem_budget=2 << 30)
     if args.tile:
         rp.set_tile(*[int(x) for x in args.tile.split(",")])
+    rp.set_segments(args.segments)
     outs = rp.alloc(ts.n_traces, log_capacity=LOG_CAP)
     stream = torch.cuda.current_stream(dev)
 
@@ -430,9 +447,10 @@ def main() -> int:
     clk = clocks.stop()
     ms = e0.elapsed_time(e1)
     ms = max_over_ranks(world, ms, dev)
-    k_ms, k_n = rp.kernel_time()
+    k_ms, k_main_ms, k_n, k_kernels = rp.kernel_time(detail=True)
     if rp.status() != 0:
         raise RuntimeError("device-side status error during the timed region")
+    seg_path = k_kernels > k_n
     value = samples_per_step * world * args.steps / (ms * 1e-3)
 
     # algorithmic bytes of one launch: every delta read once, per-pair totals written once,
@@ -442,12 +460,16 @@ def main() -> int:
     alg_bytes = 4 * samples_per_step + 48 * ts.n_traces + 4 * min(n_changes, LOG_CAP * ts.n_traces)
     k_avg_ms = k_ms / max(k_n, 1)
     peaks = measured_peaks()
+    # the replay (all of its kernels) against the HBM roofline: for the segment path the
+    # combine kernel's time is included, so the fraction is the replay's, not flattering
     achieved = alg_bytes / (k_avg_ms * 1e-3) / 1e9
-    traffic = ncu_traffic()
+    traffic = ncu_traffic("replay_seg_batched" if seg_path else "replay_tp_batched")
     roofline = dict(bound="hbm", achieved=achieved, peak=peaks["hbm_gbs"], unit="GB/s",
                     frac=achieved / peaks["hbm_gbs"], traffic=traffic,
                     peak_source=f"{peaks['source']} (MEASURED_PEAKS.json hbm_gbs)" if peaks["source"] == "measured"
-                    else "fallback 6.4 TB/s", kernel="replay_tp_kernel<8,1>", kernel_ms=k_avg_ms,
+                    else "fallback 6.4 TB/s",
+                    kernel=("replay_seg_kernel<1> + combine_kernel" if seg_path else "replay_tp_kernel<8,1>"),
+                    kernel_ms=k_avg_ms, main_kernel_ms=k_main_ms / max(k_n, 1),
                     alg_bytes_per_launch=alg_bytes, frac_of_nominal_8tbs=achieved / 8000.0)
 
     line = dict(metric=METRIC, value=value, unit="samples/s", n_gpus=world, steps=args.steps,
@@ -458,7 +480,7 @@ def main() -> int:
                             outputs="energy, EDP, time, change count, change hash, hf count, full change log",
                             l2="inputs 1.64 GB per GPU > 126 MB L2 (no flush needed)",
                             parallelism=f"dp{world} (traces sharded, no collective)"),
-                roofline=roofline, gpu_launches=k_n, clocks=clk)
+                roofline=roofline, gpu_launches=k_kernels, clocks=clk)
 
     if rank == 0 and not args.no_plain:
         # the plain form: one launch per trace, one thread per policy, literal FP64

@@ -165,10 +165,14 @@ int magus_replay_detail(magus_replay_t *h, const uint32_t *trace, uint64_t n,
  * device wait that gave up), then clear them. */
 int magus_replay_status(magus_replay_t *h, void *stream);
 
-/* Device time of the batched-kernel launches of this handle since the previous call (CUDA
- * events recorded on the launching stream right before and after each kernel, up to 4096
- * launches; later ones overwrite the last record).  Waits for those launches, then resets. */
-int magus_replay_kernel_time(magus_replay_t *h, double *total_ms, int32_t *launches);
+/* Device time of the batched replays of this handle since the previous call (CUDA events
+ * recorded on the launching stream around each replay's kernels, up to 4096 replays; later
+ * ones overwrite the last record).  total_ms: all kernels of those replays; main_ms
+ * (optional): the replay kernel alone (tile kernel, or segment kernel without its combine
+ * kernel); runs: timed replays; kernels (optional): kernels they launched.  Waits for those
+ * launches, then resets. */
+int magus_replay_kernel_time(magus_replay_t *h, double *total_ms, double *main_ms, int32_t *runs,
+                             int32_t *kernels);
 
 /* Tile shape of the batched kernel: warps that split a trace chunk in time (time_groups) x
  * policy groups per CTA (policy_slots); time_groups * policy_slots = 8.  Policies sharing
@@ -177,11 +181,21 @@ int magus_replay_kernel_time(magus_replay_t *h, double *total_ms, int32_t *launc
  * automatic choice.  EINVAL for unsupported shapes. */
 int magus_replay_set_tile(magus_replay_t *h, int32_t time_groups, int32_t policy_slots);
 
+/* Kernel choice: seg_rounds > 0 (a multiple of 1024) selects the segment kernel -- every warp
+ * replays one (trace, policy group, segment of seg_rounds rounds) on its own, a combine
+ * kernel then joins each pair's segments in order; 0 selects the tile kernel (CTAs of 8
+ * warps sharing each trace chunk, shaped by magus_replay_set_tile); -1 (the default)
+ * restores the automatic choice (the autotuner's pick, else the tile kernel, or the segment
+ * kernel with 16,384-round segments when a few long traces would leave SMs idle).  EINVAL
+ * otherwise. */
+int magus_replay_set_segments(magus_replay_t *h, int32_t seg_rounds);
+
 /* Autotuner: time every supported tile shape (time_groups x policy_slots x group size 1 or
- * 4) on the given (device, packed) workload and keep the fastest for later calls with the
- * same policy count.  out_best (host, 3 ints, optional) receives {time_groups,
- * policy_slots, group_size}; out_ms (host, optional) the best time.  Outputs go to the
- * handle's workspace only.  Synchronous. */
+ * 4) of the tile kernel and the segment kernel (segments of 8,192 / 16,384 / 32,768 rounds,
+ * group size 1 or 4) on the given (device, packed) workload and keep the fastest for later
+ * calls with the same policy count.  out_best (host, 4 ints, optional) receives
+ * {time_groups, policy_slots, group_size, segment_rounds (0: tile kernel)}; out_ms (host,
+ * optional) the best time.  Outputs go to the handle's workspace only.  Synchronous. */
 int magus_replay_autotune(magus_replay_t *h, const uint32_t *traces, const uint64_t *lengths,
                           int32_t n_traces, const magus_policy_t *configs, int32_t n_configs,
                           int32_t *out_best, float *out_ms, void *stream);

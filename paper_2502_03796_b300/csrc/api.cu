@@ -43,10 +43,18 @@ struct magus_replay {
     cudaStream_t hs_copy = nullptr, hs_comp = nullptr;
     cudaEvent_t hs_ready[2] = {nullptr, nullptr}, hs_done[2] = {nullptr, nullptr};
     // events around batched-kernel launches since the last magus_replay_kernel_time()
-    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> k_ev;
+    struct KEv {
+        cudaEvent_t a, m, b;          // before the main kernel, after it, after the last kernel
+        int kernels;                  // kernels launched between a and b
+    };
+    std::vector<KEv> k_ev;
     size_t k_used = 0;
     int tile_tg = 0, tile_cw = 0;     // 0: automatic
-    std::map<int, std::array<int, 3>> tuned;   // policies -> {time_groups, policy_slots, group size}
+    int seg_rounds = -1;              // -1: automatic; 0: tile kernel; > 0: segment kernel
+    void *segbuf = nullptr;           // segment summaries, tails, log scratch
+    size_t seg_size = 0;
+    // policies -> {time_groups, policy_slots, group size, segment rounds (0: tile kernel)}
+    std::map<int, std::array<int, 4>> tuned;
 };
 
 namespace {
@@ -64,13 +72,27 @@ int cuda_fail(cudaError_t e, const char *what) {
         if (e_ != cudaSuccess) return cuda_fail(e_, what); \
     } while (0)
 
+// Event slot for one timed replay (up to 4096 per kernel_time() period; later ones reuse
+// the last slot).
+int kev_slot(magus_replay *h, size_t *slot) {
+    if (h->k_used == h->k_ev.size() && h->k_used < 4096) {
+        magus_replay::KEv e{};
+        CK(cudaEventCreate(&e.a), "cudaEventCreate");
+        CK(cudaEventCreate(&e.m), "cudaEventCreate");
+        CK(cudaEventCreate(&e.b), "cudaEventCreate");
+        h->k_ev.push_back(e);
+    }
+    *slot = h->k_used < h->k_ev.size() ? h->k_used : h->k_ev.size() - 1;
+    return MAGUS_OK;
+}
+
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 // Device-memory growth inside the handle budget.  Waits for the previous user first.
 int ensure_ws(magus_replay *h, void **buf, size_t *size, size_t need) {
     if (need <= *size) return MAGUS_OK;
     size_t want = std::max(need, *size * 2);
-    size_t other = (buf == &h->ws ? h->scratch_size : h->ws_size);
+    size_t other = h->ws_size + h->scratch_size + h->seg_size - *size;
     if (want + other > h->budget) want = need;
     if (want + other > h->budget) {
         set_error("device workspace of " + std::to_string(need) + " bytes exceeds the handle's memory budget");
@@ -132,23 +154,30 @@ int check_policies(magus_replay *h, const magus_policy_t *configs, int32_t n_con
     return MAGUS_OK;
 }
 
+// Segment length of the automatic choice (the fastest of 8,192 / 16,384 / 32,768 rounds on
+// the 4,096 x 100,000 batched workload).
+constexpr int kDefaultSegRounds = 16384;
+
 struct Plan {
     std::vector<DevPolicy> pols;
     std::vector<PolicyGroup> groups;
     std::vector<WorkItem> items;
     std::vector<uint64_t> offsets, lengths;
     int tg = 8, cw = 1, gp = 1;
+    int seg_len = 0;                   // > 0: segment kernel with this many rounds per segment
 };
 
 // Tile for a workload: group size 4 when policies share predictions, then as many policy
 // slots per CTA as there are groups (up to 8), the remaining warps splitting time.
-void choose_tile(magus_replay *h, const std::vector<DevPolicy> &pols, int *tg, int *cw, int *gp) {
+void choose_tile(magus_replay *h, const std::vector<DevPolicy> &pols, const uint64_t *lengths, int n_traces, int *tg,
+                 int *cw, int *gp, int *seg) {
     const int n_configs = (int)pols.size();
     auto it = h->tuned.find(n_configs);
-    if (!h->tile_tg && it != h->tuned.end()) {
+    if (!h->tile_tg && h->seg_rounds < 0 && it != h->tuned.end()) {   // the autotuner's pick
         *tg = it->second[0];
         *cw = it->second[1];
         *gp = it->second[2];
+        *seg = it->second[3];
         return;
     }
     std::vector<PolicyGroup> g4;
@@ -158,21 +187,62 @@ void choose_tile(magus_replay *h, const std::vector<DevPolicy> &pols, int *tg, i
     if (h->tile_tg) {
         *tg = h->tile_tg;
         *cw = h->tile_cw;
+    } else {
+        int c = 1;
+        while (c * 2 <= std::min(8, n_groups)) c *= 2;
+        *cw = c;
+        *tg = 8 / c;
+    }
+    // an explicit tile shape selects the tile kernel unless segments were asked for as well
+    if (h->seg_rounds >= 0 || h->tile_tg) {
+        *seg = h->seg_rounds > 0 ? h->seg_rounds : 0;
         return;
     }
-    int c = 1;
-    while (c * 2 <= std::min(8, n_groups)) c *= 2;
-    *cw = c;
-    *tg = 8 / c;
+    // automatic: the tile kernel replays a trace's chunks one after another in one CTA, so
+    // a few long traces leave most SMs idle; the segment kernel (about 15% more work per
+    // round) splits them in time.  Take it when the longest trace's chain of chunks exceeds
+    // 1.3x the chunks each resident CTA gets on average.
+    *seg = 0;
+    int smem = 0;
+    const int per_sm = tp_max_ctas_per_sm(*tg, *cw, *gp, &smem);
+    if (per_sm <= 0 || n_traces <= 0) return;
+    const uint64_t chunk = (uint64_t)*tg * 1024;
+    const uint64_t blocks = (uint64_t)(n_groups + *cw - 1) / *cw;
+    uint64_t longest = 0, total = 0;
+    for (int i = 0; i < n_traces; i++) {
+        const uint64_t c = (lengths[i] + chunk - 1) / chunk;
+        longest = std::max(longest, c);
+        total += c * blocks;
+    }
+    const double per_cta = (double)total / ((double)h->sms * per_sm);
+    if (!((double)longest > 1.3 * per_cta && longest * chunk >= 2 * (uint64_t)kDefaultSegRounds)) return;
+    // segment length: work items are taken from a queue, so the launch lasts about
+    // ceil(items / warps) items; pick the length that minimises that (plus a fixed cost of
+    // 256 rounds per segment for its prehistory, summary and combine step)
+    const int seg_ctas = seg_max_ctas_per_sm(*gp);
+    if (seg_ctas <= 0) return;
+    const double warps = (double)h->sms * seg_ctas * seg_warps_per_cta();
+    double best = 1e300;
+    for (int L = 2048; L <= 65536; L += 1024) {
+        uint64_t items = 0;
+        for (int i = 0; i < n_traces; i++) items += (lengths[i] + L - 1) / L;
+        items *= (uint64_t)n_groups;
+        const double cost = std::ceil((double)items / warps) * (L + 256.0);
+        if (cost < best * 0.999) {   // ties go to the shorter segment
+            best = cost;
+            *seg = L;
+        }
+    }
 }
 
 int build_plan(magus_replay *h, const uint64_t *lengths, int32_t n_traces, const magus_policy_t *configs,
-               int32_t n_configs, int tg, int cw, int gp, Plan *pl) {
+               int32_t n_configs, int tg, int cw, int gp, int seg, Plan *pl) {
     int rc = check_policies(h, configs, n_configs, &pl->pols, true);
     if (rc) return rc;
     pl->tg = tg;
     pl->cw = cw;
     pl->gp = gp;
+    pl->seg_len = seg;
     form_groups(pl->pols, gp, &pl->groups);
     pl->offsets.resize(n_traces);
     pl->lengths.assign(lengths, lengths + n_traces);
@@ -203,8 +273,16 @@ struct Outs {
 };
 
 // Upload the plan through pinned staging and launch the batched kernel on `stream`.
+int launch_seg_plan(magus_replay *h, const Plan &pl, const uint32_t *traces, const Outs &o, cudaStream_t stream,
+                    float *ms_out);
+constexpr int kUseTile = 1;   // launch_seg_plan: the segment buffers exceed the budget
+
 int launch_plan(magus_replay *h, const Plan &pl, const uint32_t *traces, const Outs &o, cudaStream_t stream,
                 float *ms_out = nullptr) {
+    if (pl.seg_len > 0) {
+        const int rc = launch_seg_plan(h, pl, traces, o, stream, ms_out);
+        if (rc != kUseTile) return rc;
+    }
     const size_t n_items = pl.items.size();
     const size_t sz_pol = align_up(pl.pols.size() * sizeof(DevPolicy), 256);
     const size_t sz_grp = align_up(std::max<size_t>(pl.groups.size(), 1) * sizeof(PolicyGroup), 256);
@@ -279,18 +357,168 @@ int launch_plan(magus_replay *h, const Plan &pl, const uint32_t *traces, const O
         if (rc) { set_error(err); return rc; }
     }
     if (n_items) {
-        if (h->k_used == h->k_ev.size() && h->k_used < 4096) {
-            cudaEvent_t a, b;
-            CK(cudaEventCreate(&a), "cudaEventCreate");
-            CK(cudaEventCreate(&b), "cudaEventCreate");
-            h->k_ev.push_back({a, b});
-        }
-        const size_t slot_k = h->k_used < h->k_ev.size() ? h->k_used : h->k_ev.size() - 1;
-        CK(cudaEventRecord(h->k_ev[slot_k].first, stream), "cudaEventRecord");
+        size_t slot_k;
+        rc = kev_slot(h, &slot_k);
+        if (rc) return rc;
+        CK(cudaEventRecord(h->k_ev[slot_k].a, stream), "cudaEventRecord");
         CK(launch_replay_tp(pl.tg, pl.cw, pl.gp, p, tmap, grid, stream), "replay kernel launch");
-        CK(cudaEventRecord(h->k_ev[slot_k].second, stream), "cudaEventRecord");
+        CK(cudaEventRecord(h->k_ev[slot_k].m, stream), "cudaEventRecord");
+        CK(cudaEventRecord(h->k_ev[slot_k].b, stream), "cudaEventRecord");
+        h->k_ev[slot_k].kernels = 1;
         if (h->k_used < h->k_ev.size()) h->k_used++;
     }
+    if (ms_out) {
+        CK(cudaEventRecord(e1, stream), "cudaEventRecord");
+        CK(cudaEventSynchronize(e1), "cudaEventSynchronize");
+        CK(cudaEventElapsedTime(ms_out, e0, e1), "cudaEventElapsedTime");
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+    }
+    CK(cudaEventRecord(h->ws_ev, stream), "cudaEventRecord");
+    h->ws_ev_pending = true;
+    return MAGUS_OK;
+}
+
+// Segment kernel: every warp replays one (trace, policy group, time segment) at a time; a
+// combine kernel resolves each pair's segments in order (replay_seg.cu).
+int launch_seg_plan(magus_replay *h, const Plan &pl, const uint32_t *traces, const Outs &o, cudaStream_t stream,
+                    float *ms_out) {
+    const int n_traces = (int)pl.lengths.size();
+    const int n_pols = (int)pl.pols.size();
+    const uint64_t seg_len = (uint64_t)pl.seg_len;
+    std::vector<uint64_t> seg_base(std::max(n_traces, 1), 0);
+    uint64_t total_segs = 0;
+    for (int i = 0; i < n_traces; i++) {
+        seg_base[i] = total_segs;
+        total_segs += (pl.lengths[i] + seg_len - 1) / seg_len;
+    }
+    std::vector<int> order(n_traces);
+    for (int i = 0; i < n_traces; i++) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return pl.lengths[a] > pl.lengths[b]; });
+    std::vector<SegItem> items;
+    items.reserve((size_t)total_segs * pl.groups.size());
+    for (int i : order) {
+        const uint32_t nseg = (uint32_t)((pl.lengths[i] + seg_len - 1) / seg_len);
+        for (uint32_t g = 0; g < pl.groups.size(); g++)
+            for (uint32_t k = 0; k < nseg; k++) items.push_back(SegItem{(uint32_t)i, g, k, 0});
+    }
+    const size_t n_items = items.size();
+    if (n_items > (size_t)INT32_MAX) {
+        set_error("too many segment work items");
+        return MAGUS_EINVAL;
+    }
+    // change entries after each segment's first event: in the pair's own log when it holds
+    // the whole trace, else in scratch (only the first log_cap of a segment can be kept)
+    const bool has_log = o.log_entries && o.log_cap > 0;
+    const uint64_t seg_cap = has_log ? std::min<uint64_t>(seg_len, o.log_cap) : 0;
+    std::vector<uint64_t> scratch_base(std::max(n_traces, 1), 0);
+    uint64_t scratch_entries = 0;
+    for (int i = 0; i < n_traces && has_log; i++) {
+        if (pl.lengths[i] <= o.log_cap) {
+            scratch_base[i] = kInPlace;
+        } else {
+            scratch_base[i] = scratch_entries;
+            scratch_entries += (pl.lengths[i] + seg_len - 1) / seg_len * (uint64_t)n_pols * seg_cap;
+        }
+    }
+    // plan workspace: policies | groups | items | offsets | lengths | segment bases | scratch bases
+    const size_t sz_pol = align_up(pl.pols.size() * sizeof(DevPolicy), 256);
+    const size_t sz_grp = align_up(std::max<size_t>(pl.groups.size(), 1) * sizeof(PolicyGroup), 256);
+    const size_t sz_items = align_up(std::max<size_t>(n_items, 1) * sizeof(SegItem), 256);
+    const size_t sz_off = align_up(std::max<size_t>(n_traces, 1) * 8, 256);
+    const size_t total = sz_pol + sz_grp + sz_items + 4 * sz_off;
+    // device buffers: summaries | tails | change-log scratch
+    const uint64_t n_pairs = (uint64_t)n_traces * n_pols;
+    const size_t sz_sum = align_up(std::max<uint64_t>(total_segs * n_pols, 1) * sizeof(SegSummary), 256);
+    const size_t sz_tail = align_up(std::max<uint64_t>(n_pairs, 1) * sizeof(SegTail), 256);
+    const size_t sz_log = align_up(scratch_entries * 4, 256);
+    const size_t seg_need = sz_sum + sz_tail + sz_log;
+    // the tile kernel needs none of the segment buffers: take it when they do not fit
+    if (std::max(total, h->ws_size) + h->scratch_size + std::max(seg_need, h->seg_size) > h->budget) return kUseTile;
+    int rc = ensure_ws(h, &h->ws, &h->ws_size, total);
+    if (rc) return rc;
+    rc = ensure_ws(h, &h->segbuf, &h->seg_size, seg_need);
+    if (rc) return rc;
+    const int slot = h->pin_next;
+    h->pin_next ^= 1;
+    rc = ensure_pin(h, slot, total);
+    if (rc) return rc;
+    char *pin = (char *)h->pin[slot];
+    memcpy(pin, pl.pols.data(), pl.pols.size() * sizeof(DevPolicy));
+    memcpy(pin + sz_pol, pl.groups.data(), pl.groups.size() * sizeof(PolicyGroup));
+    if (n_items) memcpy(pin + sz_pol + sz_grp, items.data(), n_items * sizeof(SegItem));
+    if (n_traces) {
+        memcpy(pin + sz_pol + sz_grp + sz_items, pl.offsets.data(), n_traces * 8);
+        memcpy(pin + sz_pol + sz_grp + sz_items + sz_off, pl.lengths.data(), n_traces * 8);
+        memcpy(pin + sz_pol + sz_grp + sz_items + 2 * sz_off, seg_base.data(), n_traces * 8);
+        memcpy(pin + sz_pol + sz_grp + sz_items + 3 * sz_off, scratch_base.data(), n_traces * 8);
+    }
+    if (h->ws_ev_pending) CK(cudaStreamWaitEvent(stream, h->ws_ev, 0), "cudaStreamWaitEvent");
+    char *ws = (char *)h->ws;
+    CK(cudaMemcpyAsync(ws, pin, total, cudaMemcpyHostToDevice, stream), "cudaMemcpyAsync(plan)");
+    CK(cudaEventRecord(h->pin_ev[slot], stream), "cudaEventRecord");
+    h->pin_pending[slot] = true;
+    CK(cudaMemsetAsync(h->queue, 0, sizeof(unsigned int), stream), "cudaMemsetAsync");
+
+    SegParams p;
+    memset(&p, 0, sizeof(p));
+    p.traces = traces;
+    p.pols = (const DevPolicy *)ws;
+    p.n_pols = n_pols;
+    p.groups = (const PolicyGroup *)(ws + sz_pol);
+    p.items = (const SegItem *)(ws + sz_pol + sz_grp);
+    p.n_items = (int32_t)n_items;
+    p.offsets = (const uint64_t *)(ws + sz_pol + sz_grp + sz_items);
+    p.lengths = (const uint64_t *)(ws + sz_pol + sz_grp + sz_items + sz_off);
+    p.seg_base = (const uint64_t *)(ws + sz_pol + sz_grp + sz_items + 2 * sz_off);
+    p.seg_len = (uint32_t)seg_len;
+    p.queue = h->queue;
+    p.status = h->status;
+    p.model = h->dm;
+    p.summ = (SegSummary *)h->segbuf;
+    p.tails = (SegTail *)((char *)h->segbuf + sz_sum);
+    p.scratch_base = has_log ? (const uint64_t *)(ws + sz_pol + sz_grp + sz_items + 3 * sz_off) : nullptr;
+    p.scratch_log = scratch_entries ? (uint32_t *)((char *)h->segbuf + sz_sum + sz_tail) : nullptr;
+    p.seg_cap = seg_cap;
+    p.log = has_log ? o.log_entries : nullptr;
+    p.log_cap = has_log ? o.log_cap : 0;
+    p.state = o.state;
+    CUtensorMap tmap;
+    memset(&tmap, 0, sizeof(tmap));
+    if (n_items) {
+        uint64_t total_elems = 0;
+        for (int i = 0; i < n_traces; i++)
+            total_elems += (pl.lengths[i] + kTraceAlign - 1) / kTraceAlign * kTraceAlign;
+        std::string err;
+        rc = make_trace_tmap(traces, total_elems, 32, &tmap, &err);
+        if (rc) { set_error(err); return rc; }
+    }
+    const int per_sm = seg_max_ctas_per_sm(pl.gp);
+    if (per_sm <= 0) {
+        set_error("segment kernel does not fit on this device");
+        return MAGUS_ECUDA;
+    }
+    const size_t warps = (size_t)h->sms * per_sm * seg_warps_per_cta();
+    const int grid = (int)std::max<size_t>(1, std::min<size_t>((n_items + seg_warps_per_cta() - 1) / seg_warps_per_cta(),
+                                                               warps / seg_warps_per_cta()));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (ms_out) {
+        CK(cudaEventCreate(&e0), "cudaEventCreate");
+        CK(cudaEventCreate(&e1), "cudaEventCreate");
+        CK(cudaEventRecord(e0, stream), "cudaEventRecord");
+    }
+    size_t slot_k;
+    rc = kev_slot(h, &slot_k);
+    if (rc) return rc;
+    CK(cudaEventRecord(h->k_ev[slot_k].a, stream), "cudaEventRecord");
+    if (n_items) CK(launch_replay_seg(pl.gp, p, tmap, grid, stream), "segment kernel launch");
+    CK(cudaEventRecord(h->k_ev[slot_k].m, stream), "cudaEventRecord");
+    if (n_pairs)
+        CK(launch_combine(p, (int64_t)n_pairs, o.energy, o.edp, o.time, o.n_changes, o.change_hash, o.n_hf, stream),
+           "combine kernel launch");
+    CK(cudaEventRecord(h->k_ev[slot_k].b, stream), "cudaEventRecord");
+    h->k_ev[slot_k].kernels = (n_items ? 1 : 0) + (n_pairs ? 1 : 0);
+    if (h->k_used < h->k_ev.size()) h->k_used++;
     if (ms_out) {
         CK(cudaEventRecord(e1, stream), "cudaEventRecord");
         CK(cudaEventSynchronize(e1), "cudaEventSynchronize");
@@ -477,11 +705,13 @@ int magus_replay_close(magus_replay_t *h) {
     if (h->hs_copy) cudaStreamDestroy(h->hs_copy);
     if (h->hs_comp) cudaStreamDestroy(h->hs_comp);
     for (auto &ev : h->k_ev) {
-        cudaEventDestroy(ev.first);
-        cudaEventDestroy(ev.second);
+        cudaEventDestroy(ev.a);
+        cudaEventDestroy(ev.m);
+        cudaEventDestroy(ev.b);
     }
     if (h->ws) cudaFree(h->ws);
     if (h->scratch) cudaFree(h->scratch);
+    if (h->segbuf) cudaFree(h->segbuf);
     if (h->status) cudaFree(h->status);
     if (h->ws_ev) cudaEventDestroy(h->ws_ev);
     delete h;
@@ -503,6 +733,16 @@ int magus_replay_set_tile(magus_replay_t *h, int32_t tg, int32_t cw) {
     return MAGUS_OK;
 }
 
+int magus_replay_set_segments(magus_replay_t *h, int32_t seg_rounds) {
+    if (!h) { set_error("NULL handle"); return MAGUS_EINVAL; }
+    if (seg_rounds < -1 || (seg_rounds > 0 && (seg_rounds % 1024 != 0 || seg_rounds > (1 << 24)))) {
+        set_error("segment rounds must be -1 (automatic), 0 (tile kernel) or a multiple of 1024 up to 2^24");
+        return MAGUS_EINVAL;
+    }
+    h->seg_rounds = seg_rounds;
+    return MAGUS_OK;
+}
+
 int magus_replay_run(magus_replay_t *h, const uint32_t *traces, const uint64_t *lengths, int32_t n_traces,
                      const magus_policy_t *configs, int32_t n_configs, const magus_freq_log_t *log,
                      double *out_energy, double *out_edp, double *out_time, magus_state_t *io_state,
@@ -514,10 +754,10 @@ int magus_replay_run(magus_replay_t *h, const uint32_t *traces, const uint64_t *
         std::vector<DevPolicy> pols;
         rc = check_policies(h, configs, n_configs, &pols, true);
         if (rc) return rc;
-        int tg, cw, gp;
-        choose_tile(h, pols, &tg, &cw, &gp);
+        int tg, cw, gp, seg;
+        choose_tile(h, pols, lengths, n_traces, &tg, &cw, &gp, &seg);
         Plan pl;
-        rc = build_plan(h, lengths, n_traces, configs, n_configs, tg, cw, gp, &pl);
+        rc = build_plan(h, lengths, n_traces, configs, n_configs, tg, cw, gp, seg, &pl);
         if (rc) return rc;
         return launch_plan(h, pl, traces, outs_of(log, out_energy, out_edp, out_time, io_state),
                            (cudaStream_t)stream);
@@ -527,18 +767,25 @@ int magus_replay_run(magus_replay_t *h, const uint32_t *traces, const uint64_t *
     }
 }
 
-int magus_replay_kernel_time(magus_replay_t *h, double *total_ms, int32_t *launches) {
-    if (!h || !total_ms || !launches) { set_error("NULL argument"); return MAGUS_EINVAL; }
+int magus_replay_kernel_time(magus_replay_t *h, double *total_ms, double *main_ms, int32_t *runs,
+                             int32_t *kernels) {
+    if (!h || !total_ms || !runs) { set_error("NULL argument"); return MAGUS_EINVAL; }
     CK(cudaSetDevice(h->device), "cudaSetDevice");
-    double tot = 0;
+    double tot = 0, mn = 0;
+    int32_t nk = 0;
     for (size_t i = 0; i < h->k_used; i++) {
-        float ms = 0;
-        CK(cudaEventSynchronize(h->k_ev[i].second), "cudaEventSynchronize");
-        CK(cudaEventElapsedTime(&ms, h->k_ev[i].first, h->k_ev[i].second), "cudaEventElapsedTime");
+        float ms = 0, ms_main = 0;
+        CK(cudaEventSynchronize(h->k_ev[i].b), "cudaEventSynchronize");
+        CK(cudaEventElapsedTime(&ms, h->k_ev[i].a, h->k_ev[i].b), "cudaEventElapsedTime");
+        CK(cudaEventElapsedTime(&ms_main, h->k_ev[i].a, h->k_ev[i].m), "cudaEventElapsedTime");
         tot += ms;
+        mn += ms_main;
+        nk += h->k_ev[i].kernels;
     }
     *total_ms = tot;
-    *launches = (int32_t)h->k_used;
+    if (main_ms) *main_ms = mn;
+    *runs = (int32_t)h->k_used;
+    if (kernels) *kernels = nk;
     h->k_used = 0;
     return MAGUS_OK;
 }
@@ -572,10 +819,12 @@ int magus_replay_autotune(magus_replay_t *h, const uint32_t *traces, const uint6
         memset(&o, 0, sizeof(o));
         o.energy = (double *)h->scratch;
         o.edp = o.energy + pairs;
-        static const int shapes[8][3] = {{8, 1, 1}, {4, 2, 1}, {2, 4, 1}, {1, 8, 1},
-                                         {8, 1, 4}, {4, 2, 4}, {2, 4, 4}, {1, 8, 4}};
+        static const int shapes[14][4] = {{8, 1, 1, 0}, {4, 2, 1, 0}, {2, 4, 1, 0}, {1, 8, 1, 0},
+                                          {8, 1, 4, 0}, {4, 2, 4, 0}, {2, 4, 4, 0}, {1, 8, 4, 0},
+                                          {8, 1, 1, 8192}, {8, 1, 1, 16384}, {8, 1, 1, 32768},
+                                          {8, 1, 4, 8192}, {8, 1, 4, 16384}, {8, 1, 4, 32768}};
         float best = 1e30f;
-        int bt = 8, bc = 1, bg = 1;
+        int bt = 8, bc = 1, bg = 1, bs = 0;
         std::vector<DevPolicy> pols;
         rc = check_policies(h, configs, n_configs, &pols, true);
         if (rc) return rc;
@@ -586,7 +835,7 @@ int magus_replay_autotune(magus_replay_t *h, const uint32_t *traces, const uint6
             if (sh[2] > 1 && g4.size() == (size_t)n_configs) continue;   // nothing to share
             if (sh[1] > 1 && sh[1] / 2 >= n_groups) continue;            // more slots than groups
             Plan pl;
-            rc = build_plan(h, lengths, n_traces, configs, n_configs, sh[0], sh[1], sh[2], &pl);
+            rc = build_plan(h, lengths, n_traces, configs, n_configs, sh[0], sh[1], sh[2], sh[3], &pl);
             if (rc) return rc;
             float ms = 0, mn = 1e30f;
             for (int rep = 0; rep < 3; rep++) {
@@ -599,13 +848,15 @@ int magus_replay_autotune(magus_replay_t *h, const uint32_t *traces, const uint6
                 bt = sh[0];
                 bc = sh[1];
                 bg = sh[2];
+                bs = sh[3];
             }
         }
-        h->tuned[n_configs] = {bt, bc, bg};
+        h->tuned[n_configs] = {bt, bc, bg, bs};
         if (out_best) {
             out_best[0] = bt;
             out_best[1] = bc;
             out_best[2] = bg;
+            out_best[3] = bs;
         }
         if (out_ms) *out_ms = best;
         return MAGUS_OK;
@@ -663,8 +914,8 @@ int magus_replay_run_host(magus_replay_t *h, const uint32_t *traces, const uint6
         std::vector<DevPolicy> pols;
         rc = check_policies(h, configs, n_configs, &pols, true);
         if (rc) return rc;
-        int tg, cw, gp;
-        choose_tile(h, pols, &tg, &cw, &gp);
+        int tg, cw, gp, seg;
+        choose_tile(h, pols, lengths, n_traces, &tg, &cw, &gp, &seg);
         const bool has_log = log != nullptr;
         const uint64_t cap = (has_log && log->entries) ? log->capacity : 0;
         const size_t per_pair = 16 + (out_time ? 8 : 0) +
@@ -730,7 +981,7 @@ int magus_replay_run_host(magus_replay_t *h, const uint32_t *traces, const uint6
             CK(cudaEventRecord(h->hs_ready[slot], h->hs_copy), "cudaEventRecord");
             CK(cudaStreamWaitEvent(h->hs_comp, h->hs_ready[slot], 0), "cudaStreamWaitEvent");
             Plan pl;
-            rc = build_plan(h, lengths + i0, nt, configs, n_configs, tg, cw, gp, &pl);
+            rc = build_plan(h, lengths + i0, nt, configs, n_configs, tg, cw, gp, seg, &pl);
             if (rc) return rc;
             rc = launch_plan(h, pl, d_tr, outs_of(has_log ? &dl : nullptr, d_e, d_edp, d_t, nullptr), h->hs_comp);
             if (rc) return rc;

@@ -90,6 +90,72 @@ cudaError_t launch_replay_tp(int time_groups, int policy_slots, int group_size, 
                              const CUtensorMap &tmap, int grid, cudaStream_t stream);
 int tp_max_ctas_per_sm(int time_groups, int policy_slots, int group_size, int *smem_bytes);
 
+// ---- segment-parallel replay (replay_seg.cu)
+struct SegItem {
+    uint32_t trace;
+    uint32_t grp;          // policy group
+    uint32_t seg;          // time segment of the trace
+    uint32_t pad;
+};
+
+// What one time segment of one pair contributes; the rounds before the segment's first
+// event ("prefix") are charged for both possible entering levels.
+struct SegSummary {
+    unsigned long long s0, sm;       // stretched delta sums at bottom / top after the first event
+    unsigned long long p_s0, p_sm;   // the prefix's stretched sums if it ran at bottom / top
+    unsigned long long hash;         // hash of the change entries after the first event
+    uint32_t n0, nm;                 // unstretched rounds at bottom / top after the first event
+    uint32_t p_n0, p_nm;             // the prefix's unstretched rounds if at bottom / top
+    uint32_t nhf;                    // high-frequency rounds
+    uint32_t n_det;                  // change entries after the first event
+    uint32_t first_pos;              // segment round of the first event, 0xffffffff if none
+    uint32_t vals;                   // bit 0 first event's level, bit 1 level at the end, bit 2 known
+};
+
+// Flags and deltas after a trace's last round (for the carried state).
+struct SegTail {
+    uint64_t flags;
+    uint32_t hist[MAGUS_MAX_WINDOW];
+};
+
+struct SegParams {
+    const uint32_t *traces;
+    const uint64_t *offsets;
+    const uint64_t *lengths;
+    const DevPolicy *pols;
+    int32_t n_pols;
+    int32_t n_items;
+    const PolicyGroup *groups;
+    const SegItem *items;
+    const uint64_t *seg_base;        // per trace: index of its first segment
+    uint32_t seg_len;                // rounds per segment (a multiple of 1024)
+    uint32_t pad0;
+    unsigned int *queue;
+    int *status;
+    DevModel model;
+    SegSummary *summ;                // [segments * n_pols]
+    SegTail *tails;                  // [pairs]
+    // Change entries after each segment's first event, before the combine kernel compacts
+    // them.  Per trace, scratch_base[trace] == kInPlace: segment k of a pair writes them to
+    // the pair's own log at slot k * seg_len (the log holds at least the trace's length);
+    // otherwise to scratch_log + scratch_base[trace] + (k * n_pols + policy) * seg_cap.
+    const uint64_t *scratch_base;    // per trace, or NULL without a log
+    uint32_t *scratch_log;
+    uint64_t seg_cap;
+    uint32_t *log;                   // the caller's log [pairs * log_cap] or NULL
+    uint64_t log_cap;
+    magus_state_t *state;
+};
+
+constexpr uint64_t kInPlace = ~0ull;
+
+int seg_warps_per_cta();
+int seg_max_ctas_per_sm(int group_size);
+cudaError_t launch_replay_seg(int group_size, const SegParams &p, const CUtensorMap &tmap, int grid,
+                              cudaStream_t stream);
+cudaError_t launch_combine(const SegParams &p, int64_t n_pairs, double *energy, double *edp, double *time,
+                           uint64_t *n_changes, uint64_t *change_hash, uint64_t *n_hf, cudaStream_t stream);
+
 struct PlainParams {
     const uint32_t *trace;
     uint64_t n;

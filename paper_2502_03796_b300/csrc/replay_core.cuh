@@ -94,8 +94,24 @@ __device__ __forceinline__ int32_t clamp_thr(uint32_t t) {
     return (int32_t)(t > (uint32_t)kFastLimit + 8u ? (uint32_t)kFastLimit + 8u : t);
 }
 
-// Alg. 1 for one row, exact for any deltas: 64-bit integer decisions outside the band the
-// host derived (plan.cu) and the FP64 evaluation, in the oracle's order, inside it.
+// Alg. 1 for one round, exact for any deltas: the 64-bit integer decision outside the band
+// the host derived (plan.cu), the FP64 evaluation in the oracle's order inside it.
+__device__ __forceinline__ void predict_exact(uint32_t a, uint32_t b, const DevPolicy &P, const DevModel &M,
+                                              bool &up, bool &dn) {
+    const long long m = (long long)a - (long long)b;
+    up = m > P.up_mid;
+    dn = m < P.dn_mid;
+    const uint32_t m32 = a - b;
+    if (((m32 - P.up_lo) <= P.up_w) || ((m32 - P.dn_lo) <= P.dn_w)) {
+        const double xa = __ddiv_rn(__dmul_rn(M.bpc, (double)a), M.q);
+        const double xb = __ddiv_rn(__dmul_rn(M.bpc, (double)b), M.q);
+        const double der = __ddiv_rn(__dsub_rn(xa, xb), (double)P.W);
+        up = der > P.inc;
+        dn = der < P.dec;
+    }
+}
+
+// Alg. 1 for one row, exact for any deltas (the fallback of the fast path below).
 static __device__ __noinline__ void row_predict_general(uint32_t base, int lane, const DevPolicy &P, const DevModel &M,
                                                  uint32_t &UP, uint32_t &DN, uint32_t &S0, uint32_t &SM) {
     UP = DN = S0 = SM = 0;
@@ -103,16 +119,8 @@ static __device__ __noinline__ void row_predict_general(uint32_t base, int lane,
         const int E = 32 * lane + k;
         const uint32_t a = lds32(swz_elem(base, E));
         const uint32_t b = lds32(swz_elem(base, E - P.W));
-        const long long m = (long long)a - (long long)b;
-        bool up = m > P.up_mid, dn = m < P.dn_mid;
-        const uint32_t m32 = a - b;
-        if (((m32 - P.up_lo) <= P.up_w) || ((m32 - P.dn_lo) <= P.dn_w)) {
-            const double xa = __ddiv_rn(__dmul_rn(M.bpc, (double)a), M.q);
-            const double xb = __ddiv_rn(__dmul_rn(M.bpc, (double)b), M.q);
-            const double der = __ddiv_rn(__dsub_rn(xa, xb), (double)P.W);
-            up = der > P.inc;
-            dn = der < P.dec;
-        }
+        bool up, dn;
+        predict_exact(a, b, P, M, up, dn);
         UP |= (uint32_t)up << k;
         DN |= (uint32_t)dn << k;
         S0 |= (uint32_t)(a > M.thr0) << k;
@@ -353,6 +361,26 @@ __device__ __forceinline__ void row_energy(uint32_t base, int lane, uint32_t Fle
     if (__any_sync(FULL, M0 != 0)) acc.s0 += row_masked_sum(base, lane, M0, fast);
     const uint32_t MM = Flev & r.SM & vmask;
     if (__any_sync(FULL, MM != 0)) acc.sm += row_masked_sum(base, lane, MM, fast);
+}
+
+// Rounds of a row whose level is not known yet (before the first event of a time segment):
+// their charge is kept for both possible levels.
+struct PAcc {
+    uint32_t n0, nm;                     // unstretched rounds if at the bottom / at the top
+    unsigned long long s0, sm;           // stretched delta sums if at the bottom / at the top
+};
+
+__device__ __forceinline__ void pacc_zero(PAcc &a) {
+    a.n0 = a.nm = 0;
+    a.s0 = a.sm = 0;
+}
+
+__device__ __forceinline__ void row_energy_prefix(uint32_t base, int lane, uint32_t PM, const RowPred &r, PAcc &pa) {
+    pa.n0 += __popc(PM & ~r.S0);
+    pa.nm += __popc(PM & ~r.SM);
+    const bool fast = __all_sync(FULL, r.fast);
+    if (__any_sync(FULL, (PM & r.S0) != 0)) pa.s0 += row_masked_sum(base, lane, PM & r.S0, fast);
+    if (__any_sync(FULL, (PM & r.SM) != 0)) pa.sm += row_masked_sum(base, lane, PM & r.SM, fast);
 }
 
 // Energy and time totals from the integer accumulators (energy model: an interval at level

@@ -78,7 +78,9 @@ SIGNATURES = {
     "magus_replay_detail": ([P, P, _U64, P, P, P, P, P, P, P, P], ctypes.c_int),
     "magus_replay_status": ([P, P], ctypes.c_int),
     "magus_replay_set_tile": ([P, _I32, _I32], ctypes.c_int),
-    "magus_replay_kernel_time": ([P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
+    "magus_replay_set_segments": ([P, _I32], ctypes.c_int),
+    "magus_replay_kernel_time": ([P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                  ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
     "magus_replay_autotune": ([P, P, P, _I32, P, _I32, P, P, P], ctypes.c_int),
     "magus_replay_close": ([P], ctypes.c_int),
     "magus_replay_run_static": ([ctypes.POINTER(Model), P, P, _I32, P, _I32, P, P, P, P, P, P], ctypes.c_int),
@@ -296,12 +298,22 @@ class Replay:
     def status(self, stream=None) -> int:
         return lib().magus_replay_status(self.h, _stream(stream))
 
-    def kernel_time(self):
-        """(total ms, launches) of batched-kernel launches since the previous call."""
+    def kernel_time(self, detail: bool = False):
+        """(total ms, replays) of the batched replays since the previous call; with detail,
+        (total ms, replay-kernel ms, replays, kernels launched)."""
         ms = ctypes.c_double()
+        main = ctypes.c_double()
         n = ctypes.c_int32()
-        check(lib().magus_replay_kernel_time(self.h, ctypes.byref(ms), ctypes.byref(n)))
+        k = ctypes.c_int32()
+        check(lib().magus_replay_kernel_time(self.h, ctypes.byref(ms), ctypes.byref(main), ctypes.byref(n),
+                                             ctypes.byref(k)))
+        if detail:
+            return ms.value, main.value, n.value, k.value
         return ms.value, n.value
+
+    def set_segments(self, seg_rounds: int):
+        """-1 automatic, 0 tile kernel, > 0 segment kernel with that many rounds per segment."""
+        check(lib().magus_replay_set_segments(self.h, seg_rounds))
 
     def set_tile(self, time_groups: int, policy_slots: int):
         check(lib().magus_replay_set_tile(self.h, time_groups, policy_slots))
@@ -309,11 +321,11 @@ class Replay:
     def autotune(self, traces, lengths, policies: Sequence[Dict], stream=None):
         ln = np.ascontiguousarray(lengths, dtype=np.uint64)
         pols = policy_array(policies)
-        best = (ctypes.c_int32 * 3)()
+        best = (ctypes.c_int32 * 4)()
         ms = ctypes.c_float()
         check(lib().magus_replay_autotune(self.h, _ptr(traces), ln.ctypes.data, len(ln), ctypes.cast(pols, P),
                                           len(policies), ctypes.cast(best, P), ctypes.byref(ms), _stream(stream)))
-        return (best[0], best[1], best[2]), ms.value
+        return (best[0], best[1], best[2], best[3]), ms.value
 
 
 def decode_log(entries: np.ndarray):

@@ -117,8 +117,8 @@ def test_grouped_policies_all_tiles(rp, tile):
 def test_autotune_picks_a_tile(rp):
     ts = tracegen.sweep(n_traces=8, n=30_000, seed=2)
     pols = tracegen.sweep_policies()[:32]
-    (tg, cw, gp), ms = rp.autotune(to_device(ts), ts.lengths, pols)
-    assert tg * cw == 8 and gp in (1, 4) and ms > 0
+    (tg, cw, gp, seg), ms = rp.autotune(to_device(ts), ts.lengths, pols)
+    assert tg * cw == 8 and gp in (1, 4) and seg in (0, 8192, 16384, 32768) and ms > 0
     out = to_numpy(rp.run(to_device(ts), ts.lengths, pols))
     ref, _ = oracle.replay_batch(ts.data, ts.offsets, ts.lengths, pols, tracegen.default_model())
     assert np.array_equal(out["change_hash"], ref["change_hash"].astype(np.uint64))
@@ -176,10 +176,20 @@ def test_decision_band_exhaustive(rp, mg, model_kind):
         handle.close()
 
 
+@pytest.mark.parametrize("seg", [0, 1024, 16384])
 @pytest.mark.parametrize("grouped", [False, True])
-def test_split_replay_with_state(rp, mg, grouped):
+def test_split_replay_with_state(rp, mg, grouped, seg):
     """Feeding a trace in pieces with carried state reproduces the whole-trace log and
-    additive energies (against the oracle's whole-trace replay)."""
+    additive energies (against the oracle's whole-trace replay); tile kernel (seg 0) and
+    segment kernel."""
+    rp.set_segments(seg)
+    try:
+        _split_replay(rp, mg, grouped)
+    finally:
+        rp.set_segments(-1)
+
+
+def _split_replay(rp, mg, grouped):
     model = tracegen.default_model()
     ts_all = tracegen.make_traces(np.array([30_000], dtype=np.uint64), seed=5, mean_phase=9.0)
     full = ts_all.trace(0)
@@ -219,6 +229,102 @@ def test_split_replay_with_state(rp, mg, grouped):
     assert int(st[0]) == 30_000
 
 
+SEGS = [1024, 2048, 16384]
+
+
+@pytest.mark.parametrize("seg", SEGS)
+def test_ragged_batch_segments(rp, seg):
+    """Segment kernel: ragged lengths across segment and sub-block borders, edge policies."""
+    ts = ragged_set()
+    model = tracegen.default_model()
+    pols = edge_policies()
+    cap = 40_000
+    rp.set_segments(seg)
+    try:
+        out = to_numpy(rp.run(to_device(ts), ts.lengths, pols, log_capacity=cap))
+    finally:
+        rp.set_segments(-1)
+    assert rp.status() == 0
+    ref = oracle_pairs(ts, pols, model)
+    for p, r in ref.items():
+        assert_pair(out, p, r, cap=cap, tag=f"seg{seg}")
+
+
+@pytest.mark.parametrize("seg", [1024, 8192])
+def test_grouped_policies_segments(rp, seg):
+    ts = ragged_set(seed=8)
+    model = tracegen.default_model()
+    pols = grouped_policies()
+    cap = 40_000
+    rp.set_segments(seg)
+    try:
+        out = to_numpy(rp.run(to_device(ts), ts.lengths, pols, log_capacity=cap))
+    finally:
+        rp.set_segments(-1)
+    ref = oracle_pairs(ts, pols, model)
+    for p, r in ref.items():
+        assert_pair(out, p, r, cap=cap, tag=f"grouped seg{seg}")
+
+
+@pytest.mark.parametrize("seg", [0, 1024])
+def test_short_log_capacity(rp, seg):
+    """A log shorter than the pair's changes keeps the first entries; counts, hash and
+    energy still cover every change."""
+    ts = tracegen.make_traces(np.array([5000, 12000, 3], dtype=np.uint64), seed=21, mean_phase=3.0)
+    model = tracegen.default_model()
+    pols = edge_policies()[:4]
+    cap = 37
+    rp.set_segments(seg)
+    try:
+        out = to_numpy(rp.run(to_device(ts), ts.lengths, pols, log_capacity=cap))
+    finally:
+        rp.set_segments(-1)
+    ref = oracle_pairs(ts, pols, model)
+    assert max(r["n_changes"] for r in ref.values()) > cap
+    for p, r in ref.items():
+        assert_pair(out, p, r, cap=cap, tag=f"short log seg{seg}")
+
+
+@pytest.mark.parametrize("extra", [0, 5, -1000])
+def test_dense_changes_segment_log(rp, mg, extra):
+    """A change at every round (square wave, no high-frequency state): a segment's log
+    entries are compacted right behind all earlier ones.  The second piece starts with a
+    change (carried state), so each segment's entries move one slot to the right of where the
+    segment kernel wrote them in the caller's log (extra >= 0: the log holds the trace);
+    extra < 0 takes the scratch path."""
+    model = tracegen.default_model()
+    pol = dict(tracegen.default_policy(), high_freq_threshold=1.5)
+    n, cut = 6000, 3001
+    full = np.array([10_000_000 if t % 2 == 0 else 200_000_000 for t in range(n)], dtype=np.uint32)
+    ref = oracle.replay(full, pol, model)
+    assert ref["n_changes"] == n - 5
+    state = torch.zeros(mg.STATE_BYTES, dtype=torch.uint8, device="cuda")
+    rp.set_segments(1024)
+    logs, E = [], 0.0
+    try:
+        for a, b in ((0, cut), (cut, n)):
+            ts = tracegen.single_trace_set(full[a:b])
+            cap = (b - a) + extra
+            out = to_numpy(rp.run(to_device(ts), ts.lengths, [pol], log_capacity=cap, state=state))
+            k = int(out["n_changes"][0])
+            assert k == min(b, n) - max(a, 5)
+            logs.append(out["log"][:min(k, cap)])
+            E += out["energy_j"][0]
+    finally:
+        rp.set_segments(-1)
+    assert rp.status() == 0
+    ent = np.concatenate(logs).astype(np.uint32)
+    t = (ent >> 5).astype(np.uint64)
+    if extra >= 0:
+        assert np.array_equal(t, ref["log_t"])
+        assert np.array_equal((ent & 31).astype(np.uint8), ref["log_level"])
+    else:
+        k0 = cut - 5
+        assert np.array_equal(t[:len(logs[0])], ref["log_t"][:len(logs[0])])
+        assert np.array_equal(t[len(logs[0]):], ref["log_t"][k0:k0 + len(logs[1])])
+    assert abs(E - ref["energy_j"]) <= REL_TOL * ref["energy_j"]
+
+
 def test_invalid_carried_level_reports_einval(rp, mg):
     ts = tracegen.make_traces(np.array([100], dtype=np.uint64), seed=1)
     state = torch.zeros(mg.STATE_BYTES, dtype=torch.uint8, device="cuda")
@@ -240,6 +346,9 @@ def test_argument_errors(rp, mg):
         rp.run(d[1:], ts.lengths, [tracegen.default_policy()])   # misaligned base
     with pytest.raises(mg.MagusError):
         rp.run(d, ts.lengths, [dict(tracegen.default_policy(), inc_threshold=float("nan"))])
+    for bad in (-2, 1000, 1025, 1 << 25):
+        with pytest.raises(mg.MagusError):
+            rp.set_segments(bad)
 
 
 def test_empty_inputs(rp):
