@@ -128,12 +128,15 @@ static __device__ __noinline__ void row_predict_general(uint32_t base, int lane,
     }
 }
 
-// Fast path, S = (-W) mod 4.  t = c - a + b has its sign bit set exactly when the integer
-// comparison holds (no overflow while every delta is below 2^30); a funnel shift pushes that
-// bit into the mask, so round k ends up at bit 31 - k.  The stretch test is written as a
-// multiply-add with a run-time multiplier of -1 so that it issues on the FMA pipe: the
-// kernel is bound by the half-rate integer ALU pipe (measured: this form is the fastest of
-// the all-ALU, all-IMAD and mixed forms).
+// Fast path, S = (-W) mod 4.  With m = a - b, tu = (up_mid + 3) - m and td = m - (dn_mid - 2)
+// are negative exactly outside the decision bands on the +1 / -1 side (no overflow while
+// every delta is below 2^30), and lie in [0, 5] exactly inside the bands [up_mid - 2,
+// up_mid + 3] and [dn_mid - 2, dn_mid + 3], where the caller falls back to the exact path:
+// one three-input minimum tracks both bands.  A funnel shift pushes each sign bit into its
+// mask, so round k ends up at bit 31 - k.  The stretch test is written as a multiply-add
+// with a run-time multiplier of -1 so that it issues on the FMA pipe: the kernel is bound by
+// the half-rate integer ALU pipe (measured: this form is the fastest of the all-ALU,
+// all-IMAD and mixed forms).
 template <int S>
 __device__ __forceinline__ void row_predict_fast(uint32_t base, int lane, int W, uint32_t one, int32_t upc,
                                                  int32_t dnc, int32_t thr0c, uint32_t &UPr, uint32_t &DNr,
@@ -149,19 +152,19 @@ __device__ __forceinline__ void row_predict_fast(uint32_t base, int lane, int W,
         lds128(swz_chunk(base, E >> 5, (E >> 2) & 7), u[4 * c], u[4 * c + 1], u[4 * c + 2], u[4 * c + 3]);
     }
     const uint32_t neg1 = 0u - one;
+    const uint32_t up3 = (uint32_t)upc + 3u, dn2 = (uint32_t)dnc - 2u;
     uint32_t bd = 0xffffffffu, mx = 0;
 #pragma unroll
     for (int k = 0; k < 32; k++) {
         const uint32_t a = v[k], b = u[k + S];
-        const uint32_t tu = (uint32_t)upc - a + b;        // < 0  <=>  m > up_mid
-        const uint32_t td = a - b - (uint32_t)dnc;        // < 0  <=>  m < dn_mid
+        const uint32_t tu = up3 - a + b;                  // < 0: +1;  in [0, 5]: up band
+        const uint32_t td = a - b - dn2;                  // < 0: -1;  in [0, 5]: dn band
         const uint32_t ts = a * neg1 + (uint32_t)thr0c;   // < 0  <=>  a > thr0 (an IMAD)
         UPr = __funnelshift_l(tu, UPr, 1);
         DNr = __funnelshift_l(td, DNr, 1);
         S0r = __funnelshift_l(ts, S0r, 1);
-        bd = __viaddmin_u32(tu, 3u, bd);            // up band: tu in [-3, 2]
-        bd = __viaddmin_u32(td, 2u, bd);            // dn band: td in [-2, 3]
-        mx = max(mx, a);
+        bd = __vimin3_u32(bd, tu, td);
+        if (k & 1) mx = __vimax3_u32(mx, v[k - 1], a);
     }
     band = bd;
     amax = mx;
