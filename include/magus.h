@@ -99,7 +99,8 @@ typedef struct {
 /* Frequency-change log.  Entry = ((t + 1) << 5) | level: from interval t+1 on (global
  * interval index, counting n_seen) the uncore runs at ladder index `level`.  Entries of a
  * pair are in time order at entries[pair * capacity ...]; entries beyond capacity are
- * counted and hashed but not stored.  change_hash = sum over entries of
+ * counted and hashed but not stored; slots past a pair's n_changes hold unspecified values
+ * (the segment kernel uses them as scratch).  change_hash = sum over entries of
  * SplitMix64-mix(((t + 1) << 8) | level) mod 2^64 (order-free, additive over splits). */
 typedef struct {
     uint32_t *entries;          /* device [pairs * capacity] or NULL */
