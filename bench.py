@@ -272,6 +272,27 @@ def run_reference(args, world, rank):
     return 0
 
 
+def static_savings(rp, d_tr, ts, policy, model, stream) -> dict:
+    """The paper's metrics (Sec. 5.4) of the controlled policy against the static maximum
+    (the default setting it is compared with, Sec. 5.3), per trace, averaged over traces;
+    the static minimum (Sec. 6.3) for contrast.  One untimed replay of three policies."""
+    import torch
+    K = len(model["f_ghz"])
+    pols = [policy, dict(policy, pin_level=K), dict(policy, pin_level=1)]
+    out = rp.run(d_tr, ts.lengths, pols, stream=stream)
+    torch.cuda.synchronize()
+    E = out["energy_j"].view(-1, 3).cpu().numpy()
+    T = out["time_s"].view(-1, 3).cpu().numpy()
+    def metrics(k):
+        e, t, e0, t0 = E[:, k], T[:, k], E[:, 1], T[:, 1]
+        return dict(energy_saving_pct=float(np.mean(1 - e / e0) * 100),
+                    edp_saving_pct=float(np.mean(1 - (e * t) / (e0 * t0)) * 100),
+                    perf_loss_pct=float(np.mean(t / t0 - 1) * 100),
+                    power_saving_pct=float(np.mean(1 - (e / t) / (e0 / t0)) * 100))
+    return dict(policy=metrics(0), static_min=metrics(2),
+                note="energy model of the synthetic workload, per-trace mean; not the paper's measured savings")
+
+
 def time_steps(fn, steps: int, warmup: int, stream) -> float:
     import torch
     for _ in range(warmup):
@@ -400,6 +421,7 @@ def main() -> int:
                     help="-1 automatic, 0 tile kernel, >0 segment kernel with this many rounds per segment")
     ap.add_argument("--traces", type=int, default=N_TRACES, help="traces per GPU (profiling runs use fewer)")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-savings", action="store_true")
     ap.add_argument("--workload", default="batched", choices=["batched", "sweep", "uneven", "single", "long"],
                     help="batched (default, the headline line); sweep / uneven / single print their own line")
     args = ap.parse_args()
@@ -517,6 +539,9 @@ def main() -> int:
                            h2d_bytes_per_step=int(ts.data.nbytes), d2h_bytes_per_step=48 * n_pairs,
                            steps=ksteps, api="magus_replay_run_host")
         rp.kernel_time()
+
+    if rank == 0 and not args.no_savings:
+        line["savings_vs_static_max"] = static_savings(rp, d_tr, ts, policy, model, stream)
 
     if rank == 0 and not args.no_serve:
         line["serve"] = bench_serve(device=local)

@@ -69,7 +69,14 @@ typedef struct {
     double high_freq_threshold; /* Alg. 2 high_freq_threshold (paper: 0.6) */
     int32_t step_mode;          /* 0: jump to the ladder bounds (Sec. 6.1); 1: one rung per
                                    decision (only magus_replay_plain / _detail) */
-    int32_t reserved;           /* must be 0 */
+    int32_t pin_level;          /* 0: MAGUS control.  k in 1..n_levels: a static baseline that
+                                   holds ladder index k-1 for every interval and runs no
+                                   control (no changes, no high-frequency rounds; the
+                                   predictions still feed the carried flag state).  k =
+                                   n_levels is the default setting the paper compares
+                                   against (uncore at its maximum, Sec. 5.3), k = 1 the
+                                   minimum (Sec. 6.3).  The batched, segment and serving
+                                   kernels take 0, 1 or n_levels; the plain kernel any k. */
 } magus_policy_t;
 
 /* Ladder and energy model. */

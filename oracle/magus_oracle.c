@@ -64,6 +64,10 @@ int or_replay(const uint32_t *deltas, uint64_t n, const or_policy *pol, const or
               uint64_t log_cap, uint8_t *level_log, double *deriv_log) {
     const int W = pol->direv_length, L = pol->tune_window, K = m->n_levels;
     if (W < 1 || W > OR_MAX_WINDOW || L < 1 || L > OR_MAX_WINDOW || K < 1 || K > 32) return -1;
+    if (pol->pin_level < 0 || pol->pin_level > K) return -1;
+    /* A static baseline (Sec. 5.3, Sec. 6.3) runs no control: its level is fixed. */
+    const int pinned = pol->pin_level > 0;
+    if (pinned) st->level = pol->pin_level - 1;
     const double q = m->dt_s * 1e9;
     memset(res, 0, sizeof(*res));
     double E = 0.0, T = 0.0;
@@ -100,11 +104,13 @@ int or_replay(const uint32_t *deltas, uint64_t n, const or_policy *pol, const or
         memmove(st->uncore_tune_ls, st->uncore_tune_ls + 1, (size_t)(L - 1));
         st->uncore_tune_ls[L - 1] = (uint8_t)(pred != 0);
         int hf = high_freq_detection(pol->high_freq_threshold, st->uncore_tune_ls, L);
+        if (pinned) hf = 0;
         res->n_hf += (uint64_t)hf;
 
         /* Decision: high-frequency state overrides the temporary decision with the max. */
         int next;
-        if (hf) next = K - 1;
+        if (pinned) next = f;
+        else if (hf) next = K - 1;
         else if (pred == 1) next = pol->step_mode == 0 ? K - 1 : (f + 1 < K ? f + 1 : K - 1);
         else if (pred == -1) next = pol->step_mode == 0 ? 0 : (f > 0 ? f - 1 : 0);
         else next = f;

@@ -23,7 +23,9 @@ typedef struct {
     int32_t tune_window;         /* Alg. 2: length L of uncore_tune_ls, 1..64 */
     double high_freq_threshold;  /* Alg. 2: rate threshold (paper: 0.6) */
     int32_t step_mode;           /* 0: jump to ladder bounds (Sec. 6.1); 1: one ladder step */
-    int32_t pad;
+    int32_t pin_level;           /* 0: MAGUS control; k in 1..K: a static baseline that holds
+                                    ladder index k-1 throughout (K = the maximum, the default
+                                    setting of Sec. 5.3; 1 = the minimum of Sec. 6.3) */
 } or_policy;
 
 typedef struct {

@@ -150,6 +150,12 @@ int check_policies(magus_replay *h, const magus_policy_t *configs, int32_t n_con
             set_error("the batched kernel supports step_mode 0 only (use magus_replay_plain)");
             return MAGUS_EINVAL;
         }
+        if (jump_only && configs[c].pin_level != 0 && configs[c].pin_level != 1 &&
+            configs[c].pin_level != h->model.n_levels) {
+            set_error("the batched kernel pins to the ladder bounds only: pin_level 0, 1 or n_levels "
+                      "(use magus_replay_plain)");
+            return MAGUS_EINVAL;
+        }
     }
     return MAGUS_OK;
 }

@@ -25,7 +25,8 @@ struct alignas(16) DevPolicy {
     int32_t kmin;          // smallest flag count c with c / L >= high_freq_threshold
     int32_t step_mode;
     double th;             // Alg. 2 threshold (the plain kernel evaluates it literally)
-    int32_t pad[2];
+    int32_t pin;           // 0: controlled; k > 0: static baseline at ladder index k - 1
+    int32_t pad;
 };
 
 // Ladder / energy model as the kernels use it.

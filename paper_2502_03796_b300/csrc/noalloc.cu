@@ -60,6 +60,8 @@ extern "C" int magus_replay_run_static(const magus_model_t *model, const uint32_
         rc = derive_policy(configs[c], *model, &pols[c], &err);
         if (rc) return fail("policy " + std::to_string(c) + ": " + err, rc);
         if (configs[c].step_mode != 0) return fail("step_mode must be 0", MAGUS_EINVAL);
+        if (configs[c].pin_level != 0 && configs[c].pin_level != 1 && configs[c].pin_level != model->n_levels)
+            return fail("pin_level must be 0, 1 or n_levels", MAGUS_EINVAL);
     }
     for (int i = 0; i < n_traces; i++) {
         if (lengths[i] >= (1ull << 40)) return fail("trace length too large", MAGUS_EINVAL);

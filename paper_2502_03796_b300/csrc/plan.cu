@@ -79,7 +79,7 @@ int derive_policy(const magus_policy_t &p, const magus_model_t &m, DevPolicy *ou
         *err = "thresholds must not be NaN"; return MAGUS_EINVAL;
     }
     if (p.step_mode != 0 && p.step_mode != 1) { *err = "step_mode must be 0 or 1"; return MAGUS_EINVAL; }
-    if (p.reserved != 0) { *err = "reserved must be 0"; return MAGUS_EINVAL; }
+    if (p.pin_level < 0 || p.pin_level > m.n_levels) { *err = "pin_level must be 0..n_levels"; return MAGUS_EINVAL; }
     DevPolicy d;
     memset(&d, 0, sizeof(d));
     d.W = p.direv_length;
@@ -88,6 +88,7 @@ int derive_policy(const magus_policy_t &p, const magus_model_t &m, DevPolicy *ou
     d.dec = p.dec_threshold;
     d.th = p.high_freq_threshold;
     d.step_mode = p.step_mode;
+    d.pin = p.pin_level;
     // q is the FP64 product dt * 1e9 that both the oracle and the kernels divide by
     const long double qd = (long double)(m.dt_s * 1e9);
     auto crossing = [&](double thr, int64_t *mid, uint32_t *lo, uint32_t *w) {

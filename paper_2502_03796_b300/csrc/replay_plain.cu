@@ -33,7 +33,9 @@ __global__ void replay_plain_kernel(const PlainParams p) {
     int ls_len = 0, ls_head = 0;       // head = index of the oldest entry
     uint64_t tune = 0;                 // uncore_tune_ls, bit 0 = newest
     const uint64_t tmask = L == 64 ? ~0ull : ((1ull << L) - 1ull);
-    int level = 0;
+    // a static baseline (Sec. 5.3, Sec. 6.3) holds its ladder index and runs no control
+    const bool pinned = P.pin > 0;
+    int level = pinned ? P.pin - 1 : 0;
     double E = 0.0, T = 0.0;
     uint64_t nch = 0, hash = 0, nhf = 0;
     for (uint64_t t = 0; t < p.n; t++) {
@@ -65,10 +67,11 @@ __global__ void replay_plain_kernel(const PlainParams p) {
         // Alg. 2: FIFO of L flags, zero-filled
         tune = ((tune << 1) | (pred != 0 ? 1ull : 0ull)) & tmask;
         const double freq = __ddiv_rn((double)__popcll(tune), (double)L);
-        const bool hf = freq >= P.th;
+        const bool hf = !pinned && freq >= P.th;
         nhf += hf ? 1 : 0;
         int next;
-        if (hf) next = K - 1;
+        if (pinned) next = level;
+        else if (hf) next = K - 1;
         else if (pred == 1) next = P.step_mode == 0 ? K - 1 : (level + 1 < K ? level + 1 : K - 1);
         else if (pred == -1) next = P.step_mode == 0 ? 0 : (level > 0 ? level - 1 : 0);
         else next = level;

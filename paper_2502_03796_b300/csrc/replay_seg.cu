@@ -172,13 +172,18 @@ __global__ void __launch_bounds__(SEG_WARPS * 32) replay_seg_kernel(const SegPar
 #pragma unroll
         for (int m = 0; m < GP; m++) {
             const int id = G.member[m < cnt ? m : 0];
-            Lm[m] = p.pols[id].L;
+            // bit 8 marks a static baseline (no control), bit 9 one pinned at the top; L
+            // itself is at most 64
+            Lm[m] = p.pols[id].L | (p.pols[id].pin ? 0x100 : 0) | (p.pols[id].pin > 1 ? 0x200 : 0);
             Km[m] = p.pols[id].kmin;
             core::acc_zero(acc[m]);
             core::pacc_zero(pacc[m]);
-            run[m].known = wi.seg == 0 ? 1u : 0u;
+            // a static baseline knows its level in every segment
+            run[m].known = (wi.seg == 0 || (Lm[m] & 0x100)) ? 1u : 0u;
             uint32_t lv = 0;
-            if (wi.seg == 0 && p.state && m < cnt) {
+            if (Lm[m] & 0x100) {
+                lv = (Lm[m] & 0x200) ? topK : 0u;
+            } else if (wi.seg == 0 && p.state && m < cnt) {
                 lv = p.state[pbase + G.member[m]].level;
                 if (lv != 0 && lv != topK) {
                     if (lane == 0) atomicCAS(p.status, 0, MAGUS_EINVAL);
@@ -225,9 +230,10 @@ __global__ void __launch_bounds__(SEG_WARPS * 32) replay_seg_kernel(const SegPar
 
 #pragma unroll 1
             for (int m = 0; m < (GP == 1 ? 1 : cnt); m++) {
-                const uint32_t HF = core::hf_row(H, FL, Lm[m], Km[m]) & vmask;
-                const uint32_t SETM = HF | UP;
-                const uint32_t SET0 = DN & ~HF;
+                const uint32_t act = (Lm[m] & 0x100) ? 0u : FULL;
+                const uint32_t HF = core::hf_row(H, FL, Lm[m] & 0xff, Km[m]) & vmask & act;
+                const uint32_t SETM = (HF | UP) & act;
+                const uint32_t SET0 = DN & ~HF & act;
                 const uint32_t EV = SETM | SET0;
                 const bool has = EV != 0;
                 const uint32_t exitv = has ? (SETM >> (31 - __clz(EV))) & 1u : 0u;
@@ -359,6 +365,7 @@ __global__ void __launch_bounds__(256) combine_kernel(const SegParams p, int64_t
         n_seen_base = p.state[pair].n_seen;
         level = (p.state[pair].level == topK) ? 1u : 0u;
     }
+    if (p.pols[pol].pin) level = p.pols[pol].pin > 1 ? 1u : 0u;
     uint32_t *const plog = p.log ? p.log + (uint64_t)pair * p.log_cap : nullptr;
     const uint64_t log_cap = p.log_cap;
     const uint64_t sbase = p.scratch_base ? p.scratch_base[trace] : 0;

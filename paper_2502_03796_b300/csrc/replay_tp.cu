@@ -170,7 +170,9 @@ __global__ void __launch_bounds__(TG * CW * 32) replay_tp_kernel(const TpParams 
 #pragma unroll
         for (int m = 0; m < GP; m++) {
             const int id = G.member[m < cnt ? m : 0];
-            Lm[m] = p.pols[id].L;
+            // bit 8 marks a static baseline (no control), bit 9 one pinned at the top; L
+            // itself is at most 64
+            Lm[m] = p.pols[id].L | (p.pols[id].pin ? 0x100 : 0) | (p.pols[id].pin > 1 ? 0x200 : 0);
             Km[m] = p.pols[id].kmin;
         }
         uint64_t n_seen0 = 0;
@@ -182,7 +184,9 @@ __global__ void __launch_bounds__(TG * CW * 32) replay_tp_kernel(const TpParams 
 #pragma unroll
             for (int m = 0; m < GP; m++) {
                 uint32_t lv = 0;
-                if (p.state && active && m < cnt) {
+                if (Lm[m] & 0x100) {
+                    lv = (Lm[m] & 0x200) ? topK : 0u;   // a static baseline ignores the carried level
+                } else if (p.state && active && m < cnt) {
                     lv = p.state[pbase + G.member[m]].level;
                     if (lv != 0 && lv != topK) {
                         atomicCAS(p.status, 0, MAGUS_EINVAL);
@@ -266,9 +270,10 @@ __global__ void __launch_bounds__(TG * CW * 32) replay_tp_kernel(const TpParams 
 #pragma unroll 1
             for (int m = 0; m < (GP == 1 ? 1 : cnt); m++) {
                 // ------------------------------------------------------------ phase B
-                const uint32_t HF = core::hf_row(H, FL, Lm[m], Km[m]) & vmask;
-                const uint32_t SETM = HF | UP;
-                const uint32_t SET0 = DN & ~HF;
+                const uint32_t act = (Lm[m] & 0x100) ? 0u : FULL;
+                const uint32_t HF = core::hf_row(H, FL, Lm[m] & 0xff, Km[m]) & vmask & act;
+                const uint32_t SETM = (HF | UP) & act;
+                const uint32_t SET0 = DN & ~HF & act;
                 const uint32_t EV = SETM | SET0;
                 const bool has = EV != 0;
                 const uint32_t exitv = has ? (SETM >> (31 - __clz(EV))) & 1u : 0u;

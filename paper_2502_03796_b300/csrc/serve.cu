@@ -90,6 +90,7 @@ __global__ void __launch_bounds__(SERVE_WARPS * 32) serve_kernel(const ServePara
         const uint64_t n_seen0 = st.n_seen;
         uint64_t tailH = st.flags;
         uint32_t level = st.level ? 1u : 0u;
+        if (P.pin) level = P.pin > 1 ? 1u : 0u;   // a static baseline holds its level
         for (int k = lane; k < HALO; k += 32) sts32(swz_elem(base, k - HALO), st.hist[k]);
         const uint32_t *src = payload + rq.off;
         const uint64_t n = rq.n;
@@ -115,9 +116,10 @@ __global__ void __launch_bounds__(SERVE_WARPS * 32) serve_kernel(const ServePara
             const RowPred rp = row_predict(base, lane, P, M, vmask, pmask);
             const uint32_t FL = rp.UP | rp.DN;
             const uint64_t H = row_history(FL, tailH, lane);
-            const uint32_t HF = hf_row(H, FL, P.L, P.kmin) & vmask;
-            const uint32_t SETM = HF | rp.UP;
-            const uint32_t SET0 = rp.DN & ~HF;
+            const uint32_t act = P.pin ? 0u : FULL;   // static baselines run no control
+            const uint32_t HF = hf_row(H, FL, P.L, P.kmin) & vmask & act;
+            const uint32_t SETM = (HF | rp.UP) & act;
+            const uint32_t SET0 = rp.DN & ~HF & act;
             const uint32_t EV = SETM | SET0;
             const bool has = EV != 0;
             const uint32_t exitv = has ? (SETM >> (31 - __clz(EV))) & 1u : 0u;
@@ -404,6 +406,8 @@ int magus_serve_open(magus_serve_t **out, const magus_model_t *model, const magu
     rc = derive_policy(*policy, *model, &dp, &err);
     if (rc) return serve_fail(nullptr, err, rc);
     if (policy->step_mode != 0) return serve_fail(nullptr, "serving supports step_mode 0", MAGUS_EINVAL);
+    if (policy->pin_level != 0 && policy->pin_level != 1 && policy->pin_level != model->n_levels)
+        return serve_fail(nullptr, "serving pins to the ladder bounds only: pin_level 0, 1 or n_levels", MAGUS_EINVAL);
     magus_serve *s = new (std::nothrow) magus_serve();
     if (!s) return serve_fail(nullptr, "out of host memory", MAGUS_ENOMEM);
     s->device = device;

@@ -30,7 +30,7 @@ class Policy(ctypes.Structure):
     _fields_ = [("inc_threshold", ctypes.c_double), ("dec_threshold", ctypes.c_double),
                 ("direv_length", ctypes.c_int32), ("tune_window", ctypes.c_int32),
                 ("high_freq_threshold", ctypes.c_double), ("step_mode", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("pin_level", ctypes.c_int32)]
 
 
 class Model(ctypes.Structure):
@@ -128,7 +128,8 @@ def check(rc: int) -> int:
 
 def make_policy(d: Dict) -> Policy:
     return Policy(float(d["inc_threshold"]), float(d["dec_threshold"]), int(d["direv_length"]),
-                  int(d["tune_window"]), float(d["high_freq_threshold"]), int(d.get("step_mode", 0)), 0)
+                  int(d["tune_window"]), float(d["high_freq_threshold"]), int(d.get("step_mode", 0)),
+                  int(d.get("pin_level", 0)))
 
 
 def policy_array(pols: Sequence[Dict]):

@@ -206,14 +206,15 @@ def test_ladder_step_mode(model):
 
 
 # ----------------------------------------------------------------------------- brute force
-def naive_exact(deltas, W, L, inc, dec, th, model):
+def naive_exact(deltas, W, L, inc, dec, th, model, pin=0):
     """Second, naive restatement in exact rationals: the window is rebuilt from the raw
-    trace every round, the comparisons are exact."""
+    trace every round, the comparisons are exact.  pin > 0: a static baseline that holds
+    ladder index pin - 1 and runs no control (Sec. 5.3, Sec. 6.3)."""
     q = Fraction(model["dt_s"]) * 10**9
     bpc = model["bytes_per_count"]
     xs = [Fraction(bpc * int(d)) / q for d in deltas]
     inc, dec, th = Fraction(inc), Fraction(dec), Fraction(th)
-    level, preds, levels, log = 0, [], [], []
+    level, preds, levels, log = (pin - 1 if pin else 0), [], [], []
     n_hf = 0
     for t in range(len(deltas)):
         levels.append(level)
@@ -224,9 +225,9 @@ def naive_exact(deltas, W, L, inc, dec, th, model):
             pred = 0
         preds.append(pred)
         window = [1 if p != 0 else 0 for p in preds[max(0, t - L + 1):t + 1]]
-        hf = Fraction(sum(window), L) >= th
+        hf = Fraction(sum(window), L) >= th and not pin
         n_hf += hf
-        nxt = TOP if hf else (TOP if pred == 1 else (0 if pred == -1 else level))
+        nxt = level if pin else (TOP if hf else (TOP if pred == 1 else (0 if pred == -1 else level)))
         if nxt != level:
             log.append((t + 1, nxt))
         level = nxt
@@ -254,6 +255,61 @@ def test_brute_force_tiny_traces(model):
                     assert close(r["energy_j"], E) and close(r["time_s"], T)
                 cases += 1
     assert cases > 20000
+
+
+def test_brute_force_static_baselines(model):
+    """Pinned policies on every trace of length <= 4 over the alphabet: constant level,
+    no log, no high-frequency rounds, exact energy of that level (Sec. 5.3, Sec. 6.3)."""
+    alphabet = [0, 10_000_000, 30_000_000, 100_000_000]
+    for n in range(1, 5):
+        for tr in itertools.product(alphabet, repeat=n):
+            d = np.array(tr, dtype=np.uint32)
+            for pin, step_mode in [(1, 0), (K, 0), (9, 1), (2, 1)]:
+                pol = dict(inc_threshold=5.0, dec_threshold=-3.3, direv_length=1, tune_window=2,
+                           high_freq_threshold=0.5, step_mode=step_mode, pin_level=pin)
+                r = oracle.replay(d, pol, model, detail=True)
+                levels, log, n_hf = naive_exact(tr, 1, 2, 5.0, -3.3, 0.5, model, pin=pin)
+                assert levels == [pin - 1] * n and log == [] and n_hf == 0
+                assert r["level_log"].tolist() == levels
+                assert r["n_changes"] == 0 and r["n_hf"] == 0
+                E, T = exact_energy(tr, levels, model)
+                assert close(r["energy_j"], E) and close(r["time_s"], T)
+
+
+def test_static_max_closed_form_and_carried_level(model, policy):
+    """Default setting of Sec. 5.3: uncore at the maximum for the whole run; it ignores a
+    carried level and stays additive over split replays."""
+    d = tracegen.single_trace().trace(0)
+    pol = dict(policy, pin_level=K)
+    x = 64.0 * d.astype(np.float64) / 1e8
+    capM = 200 * 2.4 / 2.4
+    pwM = 15 + 10 * (2.4 / 2.4) ** 2
+    T = math.fsum(0.1 * np.maximum(1.0, x / capM))
+    st = oracle.new_state()
+    r = oracle.replay(d, pol, model, state=st)
+    assert r["n_changes"] == 0 and r["n_hf"] == 0
+    assert math.isclose(r["time_s"], T, rel_tol=1e-11)
+    assert math.isclose(r["energy_j"], pwM * T, rel_tol=1e-11)
+    # split at 7,000 with a state whose level was left at the bottom by a controlled run
+    st2 = oracle.new_state()
+    a = oracle.replay(d[:7000], policy, model, state=st2)
+    b = oracle.replay(d[7000:], pol, model, state=st2)
+    Tb = math.fsum(0.1 * np.maximum(1.0, x[7000:] / capM))
+    assert math.isclose(b["time_s"], Tb, rel_tol=1e-11) and b["n_changes"] == 0
+    assert a["n_changes"] > 0
+
+
+def test_static_baselines_bracket_controlled_energy(model, policy):
+    """Static minimum draws the least power but stretches the most; static maximum never
+    stretches more than any other level (capacity grows with the level)."""
+    d = tracegen.single_trace().trace(0)
+    lo = oracle.replay(d, dict(policy, pin_level=1), model)
+    hi = oracle.replay(d, dict(policy, pin_level=K), model)
+    mg = oracle.replay(d, policy, model)
+    assert hi["time_s"] <= mg["time_s"] <= lo["time_s"]
+    pw0, pwM = 15 + 10 * (0.8 / 2.4) ** 2, 25.0
+    assert lo["energy_j"] / lo["time_s"] == pytest.approx(pw0, rel=1e-12)
+    assert hi["energy_j"] / hi["time_s"] == pytest.approx(pwM, rel=1e-12)
 
 
 # ----------------------------------------------------------------------------- invariants

@@ -45,6 +45,8 @@ def edge_policies():
         dict(base, direv_length=7, tune_window=33, inc_threshold=3.3, dec_threshold=-1.25,
              high_freq_threshold=0.3),
         dict(base, inc_threshold=-1.0, dec_threshold=-2.0),                      # negative inc
+        dict(base, pin_level=17),                                                # static maximum
+        dict(base, direv_length=7, high_freq_threshold=0.0, pin_level=1),        # static minimum
     ]
 
 
@@ -127,7 +129,8 @@ def test_autotune_picks_a_tile(rp):
 
 def test_plain_kernel_matches_oracle(rp):
     ts = tracegen.make_traces(np.array([0, 1, 7, 100, 5000, 20000], dtype=np.uint64), seed=11)
-    pols = edge_policies() + [dict(tracegen.default_policy(), step_mode=1, high_freq_threshold=0.9)]
+    pols = edge_policies() + [dict(tracegen.default_policy(), step_mode=1, high_freq_threshold=0.9),
+                              dict(tracegen.default_policy(), step_mode=1, pin_level=9)]   # mid-ladder pin
     cap = 20_000
     out = to_numpy(rp.plain(to_device(ts), ts.lengths, pols, log_capacity=cap))
     ref = oracle_pairs(ts, pols, tracegen.default_model())
@@ -194,7 +197,8 @@ def _split_replay(rp, mg, grouped):
     ts_all = tracegen.make_traces(np.array([30_000], dtype=np.uint64), seed=5, mean_phase=9.0)
     full = ts_all.trace(0)
     pols = [tracegen.default_policy(), dict(tracegen.default_policy(), direv_length=40, tune_window=50,
-                                            high_freq_threshold=0.1)]
+                                            high_freq_threshold=0.1),
+            dict(tracegen.default_policy(), pin_level=17)]
     if grouped:
         pols = grouped_policies()
     cuts = [0, 3, 4, 37, 64, 65, 1100, 8192, 8200, 20000, 30_000]
@@ -349,6 +353,9 @@ def test_argument_errors(rp, mg):
     for bad in (-2, 1000, 1025, 1 << 25):
         with pytest.raises(mg.MagusError):
             rp.set_segments(bad)
+    for pin in (-1, 9, 18):   # the batched kernels pin to the ladder bounds only
+        with pytest.raises(mg.MagusError):
+            rp.run(d, ts.lengths, [dict(tracegen.default_policy(), pin_level=pin)])
 
 
 def test_empty_inputs(rp):

@@ -92,6 +92,28 @@ def test_requests_match_oracle_and_mix(mg):
         alone.close()
 
 
+@pytest.mark.parametrize("pin", [1, 17])
+def test_static_baseline_stream(mg, pin):
+    """A serving handle pinned to a ladder bound (the static baselines of Sec. 5.3 and
+    Sec. 6.3): no changes, no high-frequency rounds, the oracle's energy per request."""
+    model = tracegen.default_model()
+    pol = dict(tracegen.default_policy(), pin_level=pin)
+    rng = np.random.default_rng(3)
+    ts = tracegen.make_traces(np.full(4, 5000, dtype=np.uint64), seed=4, mean_phase=10.0)
+    sv = mg.Serve(model, pol, 4)
+    for s in range(4):
+        cuts = stream_requests(ts.trace(s), rng)
+        ids = [sv.submit(s, ts.trace(s)[a:b]) for a, b in cuts]
+        sv.drain()
+        for rid, ref in zip(ids, oracle_split(ts.trace(s), cuts, pol, model)):
+            r = sv.poll(rid)
+            same(r, ref)
+            assert r["n_changes"] == 0 and r["level"] == pin - 1
+    sv.close()
+    with pytest.raises(mg.MagusError):
+        mg.Serve(model, dict(pol, pin_level=5), 4)
+
+
 def test_admission_and_errors(mg):
     model, pol = tracegen.default_model(), tracegen.default_policy()
     sv = mg.Serve(model, pol, 4, mem_budget=4 * 1000)
