@@ -67,8 +67,12 @@ typedef struct {
     int32_t direv_length;       /* Alg. 1 direv_length W, 1..64 */
     int32_t tune_window;        /* Alg. 2 len(uncore_tune_ls) L, 1..64 */
     double high_freq_threshold; /* Alg. 2 high_freq_threshold (paper: 0.6) */
-    int32_t step_mode;          /* 0: jump to the ladder bounds (Sec. 6.1); 1: one rung per
-                                   decision (only magus_replay_plain / _detail) */
+    int32_t step_mode;          /* bit 0 clear: jump to the ladder bounds (Sec. 6.1); set: one
+                                   rung per decision.  Bit 1 set: closed loop -- the monitor
+                                   reads min(demand, capacity at the level in effect), the
+                                   throughput a throttled uncore delivers (Sec. 6.3), instead
+                                   of the recorded demand.  The batched, segment and serving
+                                   kernels take 0; magus_replay_plain / _detail take 0..3. */
     int32_t pin_level;          /* 0: MAGUS control.  k in 1..n_levels: a static baseline that
                                    holds ladder index k-1 for every interval and runs no
                                    control (no changes, no high-frequency rounds; the
@@ -153,7 +157,7 @@ int magus_replay_run_host(magus_replay_t *h, const uint32_t *traces, const uint6
 
 /* The plain form: one kernel launch per trace, one thread per policy, literal FP64
  * arithmetic in the order of the rounds above, global-memory loads.  Same arguments and
- * outputs as magus_replay_run (no io_state); supports step_mode 1. */
+ * outputs as magus_replay_run (no io_state); supports step_mode 0..3 and any pin_level. */
 int magus_replay_plain(magus_replay_t *h, const uint32_t *traces, const uint64_t *lengths,
                        int32_t n_traces, const magus_policy_t *configs, int32_t n_configs,
                        const magus_freq_log_t *log, double *out_energy, double *out_edp,

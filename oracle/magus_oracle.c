@@ -65,6 +65,8 @@ int or_replay(const uint32_t *deltas, uint64_t n, const or_policy *pol, const or
     const int W = pol->direv_length, L = pol->tune_window, K = m->n_levels;
     if (W < 1 || W > OR_MAX_WINDOW || L < 1 || L > OR_MAX_WINDOW || K < 1 || K > 32) return -1;
     if (pol->pin_level < 0 || pol->pin_level > K) return -1;
+    if (pol->step_mode < 0 || pol->step_mode > 3) return -1;
+    const int ladder = pol->step_mode & 1, closed = (pol->step_mode >> 1) & 1;
     /* A static baseline (Sec. 5.3, Sec. 6.3) runs no control: its level is fixed. */
     const int pinned = pol->pin_level > 0;
     if (pinned) st->level = pol->pin_level - 1;
@@ -92,7 +94,8 @@ int or_replay(const uint32_t *deltas, uint64_t n, const or_policy *pol, const or
             memmove(st->mem_throughput_ls, st->mem_throughput_ls + 1, (size_t)W * sizeof(double));
             st->ls_len = W;
         }
-        st->mem_throughput_ls[st->ls_len++] = x;
+        /* Closed loop: the monitor sees at most what the uncore at level f delivered. */
+        st->mem_throughput_ls[st->ls_len++] = (closed && x > cap) ? cap : x;
         int pred = 0;
         double derivative = NAN;
         if (st->ls_len == W + 1)
@@ -111,8 +114,8 @@ int or_replay(const uint32_t *deltas, uint64_t n, const or_policy *pol, const or
         int next;
         if (pinned) next = f;
         else if (hf) next = K - 1;
-        else if (pred == 1) next = pol->step_mode == 0 ? K - 1 : (f + 1 < K ? f + 1 : K - 1);
-        else if (pred == -1) next = pol->step_mode == 0 ? 0 : (f > 0 ? f - 1 : 0);
+        else if (pred == 1) next = !ladder ? K - 1 : (f + 1 < K ? f + 1 : K - 1);
+        else if (pred == -1) next = !ladder ? 0 : (f > 0 ? f - 1 : 0);
         else next = f;
 
         if (next != f) {

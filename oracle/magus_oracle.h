@@ -22,7 +22,12 @@ typedef struct {
     int32_t direv_length;        /* Alg. 1: derivative window W (intervals), 1..64 */
     int32_t tune_window;         /* Alg. 2: length L of uncore_tune_ls, 1..64 */
     double high_freq_threshold;  /* Alg. 2: rate threshold (paper: 0.6) */
-    int32_t step_mode;           /* 0: jump to ladder bounds (Sec. 6.1); 1: one ladder step */
+    int32_t step_mode;           /* bit 0 clear: jump to the ladder bounds (Sec. 6.1); set:
+                                    one ladder step per decision.  Bit 1 set: closed loop --
+                                    the monitor reads the throughput the uncore delivered,
+                                    min(demand, capacity at the level in effect), instead of
+                                    the recorded demand (Sec. 6.3 discusses the throttled
+                                    throughput at low uncore frequency) */
     int32_t pin_level;           /* 0: MAGUS control; k in 1..K: a static baseline that holds
                                     ladder index k-1 throughout (K = the maximum, the default
                                     setting of Sec. 5.3; 1 = the minimum of Sec. 6.3) */

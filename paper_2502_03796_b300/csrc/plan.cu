@@ -78,7 +78,7 @@ int derive_policy(const magus_policy_t &p, const magus_model_t &m, DevPolicy *ou
     if (std::isnan(p.inc_threshold) || std::isnan(p.dec_threshold) || std::isnan(p.high_freq_threshold)) {
         *err = "thresholds must not be NaN"; return MAGUS_EINVAL;
     }
-    if (p.step_mode != 0 && p.step_mode != 1) { *err = "step_mode must be 0 or 1"; return MAGUS_EINVAL; }
+    if (p.step_mode < 0 || p.step_mode > 3) { *err = "step_mode must be 0..3"; return MAGUS_EINVAL; }
     if (p.pin_level < 0 || p.pin_level > m.n_levels) { *err = "pin_level must be 0..n_levels"; return MAGUS_EINVAL; }
     DevPolicy d;
     memset(&d, 0, sizeof(d));

@@ -35,6 +35,7 @@ __global__ void replay_plain_kernel(const PlainParams p) {
     const uint64_t tmask = L == 64 ? ~0ull : ((1ull << L) - 1ull);
     // a static baseline (Sec. 5.3, Sec. 6.3) holds its ladder index and runs no control
     const bool pinned = P.pin > 0;
+    const bool ladder = (P.step_mode & 1) != 0, closed = (P.step_mode & 2) != 0;
     int level = pinned ? P.pin - 1 : 0;
     double E = 0.0, T = 0.0;
     uint64_t nch = 0, hash = 0, nhf = 0;
@@ -54,7 +55,8 @@ __global__ void replay_plain_kernel(const PlainParams p) {
         }
         int tail = ls_head + ls_len;
         if (tail > W) tail -= W + 1;
-        ls[tail] = x;
+        // closed loop: the monitor reads what the uncore at `level` delivered
+        ls[tail] = (closed && x > M.cap[level]) ? M.cap[level] : x;
         ls_len++;
         int pred = 0;
         double der = __longlong_as_double(0x7ff8000000000000ll);
@@ -72,8 +74,8 @@ __global__ void replay_plain_kernel(const PlainParams p) {
         int next;
         if (pinned) next = level;
         else if (hf) next = K - 1;
-        else if (pred == 1) next = P.step_mode == 0 ? K - 1 : (level + 1 < K ? level + 1 : K - 1);
-        else if (pred == -1) next = P.step_mode == 0 ? 0 : (level > 0 ? level - 1 : 0);
+        else if (pred == 1) next = !ladder ? K - 1 : (level + 1 < K ? level + 1 : K - 1);
+        else if (pred == -1) next = !ladder ? 0 : (level > 0 ? level - 1 : 0);
         else next = level;
         if (next != level) {
             const uint64_t when = t + 1;

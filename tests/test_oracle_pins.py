@@ -206,20 +206,24 @@ def test_ladder_step_mode(model):
 
 
 # ----------------------------------------------------------------------------- brute force
-def naive_exact(deltas, W, L, inc, dec, th, model, pin=0):
+def naive_exact(deltas, W, L, inc, dec, th, model, pin=0, closed=False, ladder=False):
     """Second, naive restatement in exact rationals: the window is rebuilt from the raw
     trace every round, the comparisons are exact.  pin > 0: a static baseline that holds
-    ladder index pin - 1 and runs no control (Sec. 5.3, Sec. 6.3)."""
+    ladder index pin - 1 and runs no control (Sec. 5.3, Sec. 6.3).  closed: the monitor
+    sees min(demand, capacity at the level in effect).  ladder: one rung per decision."""
     q = Fraction(model["dt_s"]) * 10**9
     bpc = model["bytes_per_count"]
+    cap, _ = exact_model(model)
     xs = [Fraction(bpc * int(d)) / q for d in deltas]
+    obs = []
     inc, dec, th = Fraction(inc), Fraction(dec), Fraction(th)
     level, preds, levels, log = (pin - 1 if pin else 0), [], [], []
     n_hf = 0
     for t in range(len(deltas)):
         levels.append(level)
+        obs.append(min(xs[t], cap[level]) if closed else xs[t])
         if t >= W:
-            der = (xs[t] - xs[t - W]) / W
+            der = (obs[t] - obs[t - W]) / W
             pred = 1 if der > inc else (-1 if der < dec else 0)
         else:
             pred = 0
@@ -227,7 +231,8 @@ def naive_exact(deltas, W, L, inc, dec, th, model, pin=0):
         window = [1 if p != 0 else 0 for p in preds[max(0, t - L + 1):t + 1]]
         hf = Fraction(sum(window), L) >= th and not pin
         n_hf += hf
-        nxt = level if pin else (TOP if hf else (TOP if pred == 1 else (0 if pred == -1 else level)))
+        up, dn = (min(level + 1, TOP), max(level - 1, 0)) if ladder else (TOP, 0)
+        nxt = level if pin else (TOP if hf else (up if pred == 1 else (dn if pred == -1 else level)))
         if nxt != level:
             log.append((t + 1, nxt))
         level = nxt
@@ -255,6 +260,45 @@ def test_brute_force_tiny_traces(model):
                     assert close(r["energy_j"], E) and close(r["time_s"], T)
                 cases += 1
     assert cases > 20000
+
+
+def test_brute_force_closed_loop(model):
+    """Closed loop on every trace of length <= 6 over an alphabet whose larger demands
+    exceed the bottom capacity (66.7 GB/s) but not the top one (200 GB/s), jump and
+    ladder modes, against the exact-rational restatement."""
+    alphabet = [0, 10_000_000, 150_000_000, 250_000_000]   # 0, 6.4, 96, 160 GB/s
+    cases = 0
+    for n in range(1, 7):
+        for tr in itertools.product(alphabet, repeat=n):
+            d = np.array(tr, dtype=np.uint32)
+            for W, L, th, mode in [(1, 2, 0.5, 2), (2, 3, 0.6, 2), (3, 4, 0.75, 3), (1, 4, 1.0, 3)]:
+                pol = dict(inc_threshold=5.0, dec_threshold=-3.3, direv_length=W, tune_window=L,
+                           high_freq_threshold=th, step_mode=mode)
+                r = oracle.replay(d, pol, model, detail=True)
+                levels, log, n_hf = naive_exact(tr, W, L, 5.0, -3.3, th, model, closed=True,
+                                                ladder=bool(mode & 1))
+                assert r["level_log"].tolist() == levels
+                assert list(zip(r["log_t"].tolist(), r["log_level"].tolist())) == log
+                assert r["n_hf"] == n_hf
+                if n <= 3:
+                    E, T = exact_energy(tr, levels, model)
+                    assert close(r["energy_j"], E) and close(r["time_s"], T)
+                cases += 1
+    assert cases > 10000
+
+
+def test_closed_loop_equals_open_loop_below_capacity(model, policy):
+    """When no demand exceeds the bottom capacity the uncore never throttles, so the
+    closed and open loops see the same throughput and decide alike."""
+    d = tracegen.single_trace().trace(0)
+    capped = np.minimum(d, np.uint32(100_000_000))          # <= 64 GB/s < 66.7 GB/s
+    a = oracle.replay(capped, policy, model)
+    b = oracle.replay(capped, dict(policy, step_mode=2), model)
+    assert a["n_changes"] > 0 and a["change_hash"] == b["change_hash"] and a["energy_j"] == b["energy_j"]
+    # with demand above it, the closed loop decides differently on the generated trace
+    c = oracle.replay(d, dict(policy, step_mode=2), model)
+    o = oracle.replay(d, policy, model)
+    assert c["change_hash"] != o["change_hash"]
 
 
 def test_brute_force_static_baselines(model):

@@ -58,9 +58,11 @@ def ragged_set(seed=3):
     return tracegen.make_traces(np.array(RAGGED, dtype=np.uint64), seed=seed, mean_phase=12.0)
 
 
-def test_single_trace_detail_matches_oracle(rp):
+@pytest.mark.parametrize("mode", [0, 1, 2, 3])
+def test_single_trace_detail_matches_oracle(rp, mode):
+    """Per-interval levels and derivatives bit-exact: open / closed loop, jump / ladder."""
     ts = tracegen.single_trace()
-    model, pol = tracegen.default_model(), tracegen.default_policy()
+    model, pol = tracegen.default_model(), dict(tracegen.default_policy(), step_mode=mode)
     d = to_device(ts)
     n = int(ts.lengths[0])
     out = rp.detail(d, n, pol, log_capacity=n)
@@ -130,7 +132,10 @@ def test_autotune_picks_a_tile(rp):
 def test_plain_kernel_matches_oracle(rp):
     ts = tracegen.make_traces(np.array([0, 1, 7, 100, 5000, 20000], dtype=np.uint64), seed=11)
     pols = edge_policies() + [dict(tracegen.default_policy(), step_mode=1, high_freq_threshold=0.9),
-                              dict(tracegen.default_policy(), step_mode=1, pin_level=9)]   # mid-ladder pin
+                              dict(tracegen.default_policy(), step_mode=1, pin_level=9),   # mid-ladder pin
+                              dict(tracegen.default_policy(), step_mode=2),                # closed loop
+                              dict(tracegen.default_policy(), step_mode=3, high_freq_threshold=0.9,
+                                   direv_length=3)]                                        # closed, ladder
     cap = 20_000
     out = to_numpy(rp.plain(to_device(ts), ts.lengths, pols, log_capacity=cap))
     ref = oracle_pairs(ts, pols, tracegen.default_model())
@@ -344,8 +349,9 @@ def test_argument_errors(rp, mg):
     with pytest.raises(mg.MagusError) as e:
         rp.run(d, ts.lengths, [dict(tracegen.default_policy(), direv_length=65)])
     assert e.value.code == mg.EINVAL
-    with pytest.raises(mg.MagusError):
-        rp.run(d, ts.lengths, [dict(tracegen.default_policy(), step_mode=1)])
+    for mode in (1, 2, 3, 4):   # the batched kernels replay the open-loop jump mode
+        with pytest.raises(mg.MagusError):
+            rp.run(d, ts.lengths, [dict(tracegen.default_policy(), step_mode=mode)])
     with pytest.raises(mg.MagusError):
         rp.run(d[1:], ts.lengths, [tracegen.default_policy()])   # misaligned base
     with pytest.raises(mg.MagusError):
