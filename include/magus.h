@@ -71,16 +71,17 @@ typedef struct {
                                    rung per decision.  Bit 1 set: closed loop -- the monitor
                                    reads min(demand, capacity at the level in effect), the
                                    throughput a throttled uncore delivers (Sec. 6.3), instead
-                                   of the recorded demand.  The batched, segment and serving
-                                   kernels take 0; magus_replay_plain / _detail take 0..3. */
+                                   of the recorded demand.  magus_replay_run / _plain /
+                                   _detail take 0..3 (see magus_replay_run for which kernel
+                                   runs what); serving and magus_replay_run_static take 0. */
     int32_t pin_level;          /* 0: MAGUS control.  k in 1..n_levels: a static baseline that
                                    holds ladder index k-1 for every interval and runs no
                                    control (no changes, no high-frequency rounds; the
                                    predictions still feed the carried flag state).  k =
                                    n_levels is the default setting the paper compares
                                    against (uncore at its maximum, Sec. 5.3), k = 1 the
-                                   minimum (Sec. 6.3).  The batched, segment and serving
-                                   kernels take 0, 1 or n_levels; the plain kernel any k. */
+                                   minimum (Sec. 6.3).  Serving and magus_replay_run_static
+                                   take 0, 1 or n_levels; magus_replay_run / _plain any k. */
 } magus_policy_t;
 
 /* Ladder and energy model. */
@@ -132,8 +133,12 @@ typedef struct magus_replay magus_replay_t;
  * K out of range, ladder not strictly ascending, non-positive dt / capacities), ECUDA. */
 int magus_replay_open(magus_replay_t **h, const magus_model_t *model, int device, size_t mem_budget);
 
-/* Replay n_traces x n_configs (trace, policy) pairs (rounds above) with the time-parallel
- * batched kernel; every policy must have step_mode 0.
+/* Replay n_traces x n_configs (trace, policy) pairs (rounds above).  Policies in the open-loop
+ * jump mode (step_mode 0, pin_level 0, 1 or n_levels) run on the time-parallel kernels (tile
+ * or segment kernel); the others (one rung per decision, closed loop, a pin inside the
+ * ladder) run in the same call on the literal kernel, one thread per pair.  With io_state a
+ * closed-loop policy needs a fresh state (n_seen 0; else EINVAL through
+ * magus_replay_status): its throughput FIFO would need past levels.
  *   traces     device, packed layout; base address 16-byte aligned
  *   lengths    host [n_traces] intervals per trace (0 allowed)
  *   configs    host [n_configs], 1 <= n_configs <= 4096

@@ -146,16 +146,7 @@ int check_policies(magus_replay *h, const magus_policy_t *configs, int32_t n_con
             set_error("policy " + std::to_string(c) + ": " + err);
             return rc;
         }
-        if (jump_only && configs[c].step_mode != 0) {
-            set_error("the batched kernel supports step_mode 0 only (use magus_replay_plain)");
-            return MAGUS_EINVAL;
-        }
-        if (jump_only && configs[c].pin_level != 0 && configs[c].pin_level != 1 &&
-            configs[c].pin_level != h->model.n_levels) {
-            set_error("the batched kernel pins to the ladder bounds only: pin_level 0, 1 or n_levels "
-                      "(use magus_replay_plain)");
-            return MAGUS_EINVAL;
-        }
+        (void)jump_only;   // every valid policy runs: see tp_policy() for the routing
     }
     return MAGUS_OK;
 }
@@ -166,6 +157,8 @@ constexpr int kDefaultSegRounds = 16384;
 
 struct Plan {
     std::vector<DevPolicy> pols;
+    std::vector<char> tp;              // per policy: replayed by the time-parallel kernels
+    std::vector<int32_t> lit;          // the other policies: the literal kernel
     std::vector<PolicyGroup> groups;
     std::vector<WorkItem> items;
     std::vector<uint64_t> offsets, lengths;
@@ -186,10 +179,13 @@ void choose_tile(magus_replay *h, const std::vector<DevPolicy> &pols, const uint
         *seg = it->second[3];
         return;
     }
+    std::vector<char> tp(pols.size());
+    int n_tp = 0;
+    for (size_t i = 0; i < pols.size(); i++) n_tp += (tp[i] = tp_policy(pols[i], h->model.n_levels) ? 1 : 0);
     std::vector<PolicyGroup> g4;
-    form_groups(pols, kMaxGroup, &g4);
-    *gp = (2 * g4.size() <= pols.size()) ? kMaxGroup : 1;
-    const int n_groups = *gp == 1 ? n_configs : (int)g4.size();
+    form_groups(pols, kMaxGroup, &g4, &tp);
+    *gp = (2 * g4.size() <= (size_t)n_tp) ? kMaxGroup : 1;
+    const int n_groups = std::max(1, *gp == 1 ? n_tp : (int)g4.size());
     if (h->tile_tg) {
         *tg = h->tile_tg;
         *cw = h->tile_cw;
@@ -249,7 +245,13 @@ int build_plan(magus_replay *h, const uint64_t *lengths, int32_t n_traces, const
     pl->cw = cw;
     pl->gp = gp;
     pl->seg_len = seg;
-    form_groups(pl->pols, gp, &pl->groups);
+    pl->tp.resize(pl->pols.size());
+    pl->lit.clear();
+    for (size_t i = 0; i < pl->pols.size(); i++) {
+        pl->tp[i] = tp_policy(pl->pols[i], h->model.n_levels) ? 1 : 0;
+        if (!pl->tp[i]) pl->lit.push_back((int32_t)i);
+    }
+    form_groups(pl->pols, gp, &pl->groups, &pl->tp);
     pl->offsets.resize(n_traces);
     pl->lengths.assign(lengths, lengths + n_traces);
     uint64_t off = 0;
@@ -279,6 +281,36 @@ struct Outs {
 };
 
 // Upload the plan through pinned staging and launch the batched kernel on `stream`.
+// The policies the time-parallel kernels do not replay: one thread per pair, all traces in
+// one launch (replay_plain.cu).  d_*: the plan as uploaded to the workspace.
+int launch_literal_part(magus_replay *h, const Plan &pl, const uint32_t *traces, const Outs &o,
+                        const DevPolicy *d_pols, const uint64_t *d_off, const uint64_t *d_len, const int32_t *d_lit,
+                        cudaStream_t stream) {
+    LiteralParams lp;
+    memset(&lp, 0, sizeof(lp));
+    lp.traces = traces;
+    lp.offsets = d_off;
+    lp.lengths = d_len;
+    lp.n_traces = (int32_t)pl.lengths.size();
+    lp.n_pols = (int32_t)pl.pols.size();
+    lp.pols = d_pols;
+    lp.lit = d_lit;
+    lp.n_lit = (int32_t)pl.lit.size();
+    lp.model = h->dm;
+    lp.energy = o.energy;
+    lp.edp = o.edp;
+    lp.time = o.time;
+    lp.log_entries = o.log_entries;
+    lp.log_cap = o.log_cap;
+    lp.n_changes = o.n_changes;
+    lp.change_hash = o.change_hash;
+    lp.n_hf = o.n_hf;
+    lp.state = o.state;
+    lp.status = h->status;
+    CK(launch_replay_literal(lp, stream), "literal kernel launch");
+    return MAGUS_OK;
+}
+
 int launch_seg_plan(magus_replay *h, const Plan &pl, const uint32_t *traces, const Outs &o, cudaStream_t stream,
                     float *ms_out);
 constexpr int kUseTile = 1;   // launch_seg_plan: the segment buffers exceed the budget
@@ -294,7 +326,8 @@ int launch_plan(magus_replay *h, const Plan &pl, const uint32_t *traces, const O
     const size_t sz_grp = align_up(std::max<size_t>(pl.groups.size(), 1) * sizeof(PolicyGroup), 256);
     const size_t sz_items = align_up(std::max<size_t>(n_items, 1) * sizeof(WorkItem), 256);
     const size_t sz_off = align_up(std::max<size_t>(pl.offsets.size(), 1) * 8, 256);
-    const size_t total = sz_pol + sz_grp + sz_items + 2 * sz_off;
+    const size_t sz_lit = align_up(std::max<size_t>(pl.lit.size(), 1) * 4, 256);
+    const size_t total = sz_pol + sz_grp + sz_items + 2 * sz_off + sz_lit;
     int rc = ensure_ws(h, &h->ws, &h->ws_size, total);
     if (rc) return rc;
     const int slot = h->pin_next;
@@ -309,6 +342,7 @@ int launch_plan(magus_replay *h, const Plan &pl, const uint32_t *traces, const O
         memcpy(pin + sz_pol + sz_grp + sz_items, pl.offsets.data(), pl.offsets.size() * 8);
         memcpy(pin + sz_pol + sz_grp + sz_items + sz_off, pl.lengths.data(), pl.lengths.size() * 8);
     }
+    if (!pl.lit.empty()) memcpy(pin + sz_pol + sz_grp + sz_items + 2 * sz_off, pl.lit.data(), pl.lit.size() * 4);
     if (h->ws_ev_pending) CK(cudaStreamWaitEvent(stream, h->ws_ev, 0), "cudaStreamWaitEvent");
     char *ws = (char *)h->ws;
     CK(cudaMemcpyAsync(ws, pin, total, cudaMemcpyHostToDevice, stream), "cudaMemcpyAsync(plan)");
@@ -362,15 +396,21 @@ int launch_plan(magus_replay *h, const Plan &pl, const uint32_t *traces, const O
         rc = make_trace_tmap(traces, total_elems, tp_box_rows(pl.tg), &tmap, &err);
         if (rc) { set_error(err); return rc; }
     }
-    if (n_items) {
+    const bool has_lit = !pl.lit.empty() && !pl.lengths.empty();
+    if (n_items || has_lit) {
         size_t slot_k;
         rc = kev_slot(h, &slot_k);
         if (rc) return rc;
         CK(cudaEventRecord(h->k_ev[slot_k].a, stream), "cudaEventRecord");
-        CK(launch_replay_tp(pl.tg, pl.cw, pl.gp, p, tmap, grid, stream), "replay kernel launch");
+        if (n_items) CK(launch_replay_tp(pl.tg, pl.cw, pl.gp, p, tmap, grid, stream), "replay kernel launch");
         CK(cudaEventRecord(h->k_ev[slot_k].m, stream), "cudaEventRecord");
+        if (has_lit) {
+            rc = launch_literal_part(h, pl, traces, o, p.pols, p.offsets, p.lengths,
+                                     (const int32_t *)(ws + sz_pol + sz_grp + sz_items + 2 * sz_off), stream);
+            if (rc) return rc;
+        }
         CK(cudaEventRecord(h->k_ev[slot_k].b, stream), "cudaEventRecord");
-        h->k_ev[slot_k].kernels = 1;
+        h->k_ev[slot_k].kernels = (n_items ? 1 : 0) + (has_lit ? 1 : 0);
         if (h->k_used < h->k_ev.size()) h->k_used++;
     }
     if (ms_out) {
@@ -432,7 +472,8 @@ int launch_seg_plan(magus_replay *h, const Plan &pl, const uint32_t *traces, con
     const size_t sz_grp = align_up(std::max<size_t>(pl.groups.size(), 1) * sizeof(PolicyGroup), 256);
     const size_t sz_items = align_up(std::max<size_t>(n_items, 1) * sizeof(SegItem), 256);
     const size_t sz_off = align_up(std::max<size_t>(n_traces, 1) * 8, 256);
-    const size_t total = sz_pol + sz_grp + sz_items + 4 * sz_off;
+    const size_t sz_lit = align_up(std::max<size_t>(pl.lit.size(), 1) * 4, 256);
+    const size_t total = sz_pol + sz_grp + sz_items + 4 * sz_off + sz_lit;
     // device buffers: summaries | tails | change-log scratch
     const uint64_t n_pairs = (uint64_t)n_traces * n_pols;
     const size_t sz_sum = align_up(std::max<uint64_t>(total_segs * n_pols, 1) * sizeof(SegSummary), 256);
@@ -459,6 +500,7 @@ int launch_seg_plan(magus_replay *h, const Plan &pl, const uint32_t *traces, con
         memcpy(pin + sz_pol + sz_grp + sz_items + 2 * sz_off, seg_base.data(), n_traces * 8);
         memcpy(pin + sz_pol + sz_grp + sz_items + 3 * sz_off, scratch_base.data(), n_traces * 8);
     }
+    if (!pl.lit.empty()) memcpy(pin + sz_pol + sz_grp + sz_items + 4 * sz_off, pl.lit.data(), pl.lit.size() * 4);
     if (h->ws_ev_pending) CK(cudaStreamWaitEvent(stream, h->ws_ev, 0), "cudaStreamWaitEvent");
     char *ws = (char *)h->ws;
     CK(cudaMemcpyAsync(ws, pin, total, cudaMemcpyHostToDevice, stream), "cudaMemcpyAsync(plan)");
@@ -519,11 +561,18 @@ int launch_seg_plan(magus_replay *h, const Plan &pl, const uint32_t *traces, con
     CK(cudaEventRecord(h->k_ev[slot_k].a, stream), "cudaEventRecord");
     if (n_items) CK(launch_replay_seg(pl.gp, p, tmap, grid, stream), "segment kernel launch");
     CK(cudaEventRecord(h->k_ev[slot_k].m, stream), "cudaEventRecord");
-    if (n_pairs)
+    const bool any_tp = pl.lit.size() < pl.pols.size();
+    if (n_pairs && any_tp)
         CK(launch_combine(p, (int64_t)n_pairs, o.energy, o.edp, o.time, o.n_changes, o.change_hash, o.n_hf, stream),
            "combine kernel launch");
+    const bool has_lit = !pl.lit.empty() && n_traces > 0;
+    if (has_lit) {
+        rc = launch_literal_part(h, pl, traces, o, p.pols, p.offsets, p.lengths,
+                                 (const int32_t *)(ws + sz_pol + sz_grp + sz_items + 4 * sz_off), stream);
+        if (rc) return rc;
+    }
     CK(cudaEventRecord(h->k_ev[slot_k].b, stream), "cudaEventRecord");
-    h->k_ev[slot_k].kernels = (n_items ? 1 : 0) + (n_pairs ? 1 : 0);
+    h->k_ev[slot_k].kernels = (n_items ? 1 : 0) + ((n_pairs && any_tp) ? 1 : 0) + (has_lit ? 1 : 0);
     if (h->k_used < h->k_ev.size()) h->k_used++;
     if (ms_out) {
         CK(cudaEventRecord(e1, stream), "cudaEventRecord");

@@ -173,8 +173,37 @@ struct PlainParams {
 };
 cudaError_t launch_replay_plain(const PlainParams &p, cudaStream_t stream);
 
+// The literal kernel over all traces for the policies listed in `lit` (one thread per pair).
+struct LiteralParams {
+    const uint32_t *traces;
+    const uint64_t *offsets;   // device, per trace
+    const uint64_t *lengths;   // device, per trace
+    int32_t n_traces;
+    int32_t n_pols;            // pair index = trace * n_pols + policy
+    const DevPolicy *pols;
+    const int32_t *lit;        // device: policy indices replayed here
+    int32_t n_lit;
+    int32_t pad;
+    DevModel model;
+    double *energy, *edp, *time;
+    uint32_t *log_entries;
+    uint64_t log_cap;
+    uint64_t *n_changes, *change_hash, *n_hf;
+    magus_state_t *state;
+    int *status;
+};
+cudaError_t launch_replay_literal(const LiteralParams &p, cudaStream_t stream);
+
+// Policies the time-parallel kernels replay: open-loop jump mode, pinned (if at all) to a
+// ladder bound.  The others go to the literal kernel.
+__host__ __device__ inline bool tp_policy(const DevPolicy &d, int n_levels) {
+    return d.step_mode == 0 && (d.pin == 0 || d.pin == 1 || d.pin == n_levels);
+}
+
 // Host planning (plan.cu).
-void form_groups(const std::vector<DevPolicy> &pols, int gp, std::vector<PolicyGroup> *out);
+// Groups over the policies with include[i] != 0 (all when include is NULL).
+void form_groups(const std::vector<DevPolicy> &pols, int gp, std::vector<PolicyGroup> *out,
+                 const std::vector<char> *include = nullptr);
 int derive_policy(const magus_policy_t &in, const magus_model_t &m, DevPolicy *out, std::string *err);
 int derive_model(const magus_model_t &m, DevModel *out, std::string *err);
 

@@ -113,10 +113,13 @@ int derive_policy(const magus_policy_t &p, const magus_model_t &m, DevPolicy *ou
 
 // Group policies whose Alg. 1 parameters coincide (same W, inc, dec: identical predictions),
 // at most gp members per group, keeping the policies' order within each group.
-void form_groups(const std::vector<DevPolicy> &pols, int gp, std::vector<PolicyGroup> *out) {
+void form_groups(const std::vector<DevPolicy> &pols, int gp, std::vector<PolicyGroup> *out,
+                 const std::vector<char> *include) {
     out->clear();
-    std::vector<int> order(pols.size());
-    for (size_t i = 0; i < pols.size(); i++) order[i] = (int)i;
+    std::vector<int> order;
+    order.reserve(pols.size());
+    for (size_t i = 0; i < pols.size(); i++)
+        if (!include || (*include)[i]) order.push_back((int)i);
     auto key_less = [&](int a, int b) {
         const DevPolicy &x = pols[a], &y = pols[b];
         if (x.W != y.W) return x.W < y.W;

@@ -334,6 +334,64 @@ def test_dense_changes_segment_log(rp, mg, extra):
     assert abs(E - ref["energy_j"]) <= REL_TOL * ref["energy_j"]
 
 
+def literal_policies():
+    """Policies outside the time-parallel kernels' scope, replayed in the same call by the
+    literal kernel: one rung per decision, closed loop, a pin inside the ladder."""
+    base = tracegen.default_policy()
+    return [dict(base, step_mode=1, high_freq_threshold=0.9), dict(base, step_mode=2),
+            dict(base, step_mode=3, direv_length=3, high_freq_threshold=0.8), dict(base, pin_level=9),
+            dict(base, step_mode=1, pin_level=4)]
+
+
+@pytest.mark.parametrize("seg", [0, 1024])
+def test_mixed_modes_one_call(rp, seg):
+    """Jump-mode policies (tile or segment kernel) and literal-path policies in one call:
+    every pair against the oracle."""
+    ts = tracegen.make_traces(np.array([0, 1, 33, 1025, 5000, 20000], dtype=np.uint64), seed=13, mean_phase=20.0)
+    model = tracegen.default_model()
+    pols = [p for pair in zip(edge_policies()[:5], literal_policies()) for p in pair]
+    cap = 20_000
+    rp.set_segments(seg)
+    try:
+        out = to_numpy(rp.run(to_device(ts), ts.lengths, pols, log_capacity=cap))
+        tot, main, runs, kernels = rp.kernel_time(detail=True)
+    finally:
+        rp.set_segments(-1)
+    assert rp.status() == 0 and kernels >= 2
+    ref = oracle_pairs(ts, pols, model)
+    for p, r in ref.items():
+        assert_pair(out, p, r, cap=cap, tag=f"mixed seg{seg}")
+
+
+def test_literal_split_replay_with_state(rp, mg):
+    """Ladder mode and an inner pin carry their state across calls (open loop); a closed
+    loop can only start from a fresh state (EINVAL otherwise)."""
+    model = tracegen.default_model()
+    full = tracegen.make_traces(np.array([12_000], dtype=np.uint64), seed=6, mean_phase=9.0).trace(0)
+    base = tracegen.default_policy()
+    pols = [dict(base, step_mode=1, high_freq_threshold=0.9), dict(base, pin_level=9), base]
+    state = torch.zeros(len(pols) * mg.STATE_BYTES, dtype=torch.uint8, device="cuda")
+    E = np.zeros(len(pols))
+    logs = [[] for _ in pols]
+    for a, b in zip([0, 5, 70, 4000], [5, 70, 4000, 12_000]):
+        ts = tracegen.single_trace_set(full[a:b])
+        cap = b - a
+        out = to_numpy(rp.run(to_device(ts), ts.lengths, pols, log_capacity=cap, state=state))
+        for c in range(len(pols)):
+            E[c] += out["energy_j"][c]
+            logs[c].append(out["log"][c * cap:c * cap + int(out["n_changes"][c])])
+    assert rp.status() == 0
+    for c, pol in enumerate(pols):
+        ref = oracle.replay(full, pol, model)
+        ent = np.concatenate(logs[c]).astype(np.uint32)
+        assert np.array_equal((ent >> 5).astype(np.uint64), ref["log_t"])
+        assert np.array_equal((ent & 31).astype(np.uint8), ref["log_level"])
+        assert abs(E[c] - ref["energy_j"]) <= REL_TOL * ref["energy_j"]
+    ts = tracegen.single_trace_set(full[:100])
+    rp.run(to_device(ts), ts.lengths, [dict(base, step_mode=2)] * 3, state=state)
+    assert rp.status() == mg.EINVAL
+
+
 def test_invalid_carried_level_reports_einval(rp, mg):
     ts = tracegen.make_traces(np.array([100], dtype=np.uint64), seed=1)
     state = torch.zeros(mg.STATE_BYTES, dtype=torch.uint8, device="cuda")
@@ -349,9 +407,8 @@ def test_argument_errors(rp, mg):
     with pytest.raises(mg.MagusError) as e:
         rp.run(d, ts.lengths, [dict(tracegen.default_policy(), direv_length=65)])
     assert e.value.code == mg.EINVAL
-    for mode in (1, 2, 3, 4):   # the batched kernels replay the open-loop jump mode
-        with pytest.raises(mg.MagusError):
-            rp.run(d, ts.lengths, [dict(tracegen.default_policy(), step_mode=mode)])
+    with pytest.raises(mg.MagusError):
+        rp.run(d, ts.lengths, [dict(tracegen.default_policy(), step_mode=4)])
     with pytest.raises(mg.MagusError):
         rp.run(d[1:], ts.lengths, [tracegen.default_policy()])   # misaligned base
     with pytest.raises(mg.MagusError):
@@ -359,7 +416,7 @@ def test_argument_errors(rp, mg):
     for bad in (-2, 1000, 1025, 1 << 25):
         with pytest.raises(mg.MagusError):
             rp.set_segments(bad)
-    for pin in (-1, 9, 18):   # the batched kernels pin to the ladder bounds only
+    for pin in (-1, 18):
         with pytest.raises(mg.MagusError):
             rp.run(d, ts.lengths, [dict(tracegen.default_policy(), pin_level=pin)])
 
