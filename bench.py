@@ -321,6 +321,12 @@ def run_other(args, world, rank, local) -> int:
         ts = tracegen.sweep(first_id=rank * 1024)
         pols = tracegen.sweep_policies()
         desc = "policy sweep: 1024 traces x 200000 intervals (bursty mean 10 / long mean 500 regimes), 256 policies"
+    elif args.workload in ("ladder", "closed"):
+        ts = tracegen.batched(seed=rank, first_id=rank * 4096)
+        mode = 1 if args.workload == "ladder" else 2
+        pols = [dict(tracegen.default_policy(), step_mode=mode)]
+        desc = (f"batched replay, {'one rung per decision (ladder kernel)' if mode == 1 else 'closed loop (literal kernel)'}: "
+                "4096 traces x 100000 intervals (phase mean 40), 1 policy")
     elif args.workload == "long":
         ts = tracegen.batched(n_traces=16, n=4_000_000, seed=rank, first_id=rank * 16)
         pols = [tracegen.default_policy()]
@@ -422,7 +428,7 @@ def main() -> int:
     ap.add_argument("--traces", type=int, default=N_TRACES, help="traces per GPU (profiling runs use fewer)")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-savings", action="store_true")
-    ap.add_argument("--workload", default="batched", choices=["batched", "sweep", "uneven", "single", "long"],
+    ap.add_argument("--workload", default="batched", choices=["batched", "sweep", "uneven", "single", "long", "ladder", "closed"],
                     help="batched (default, the headline line); sweep / uneven / single print their own line")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)

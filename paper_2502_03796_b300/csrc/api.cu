@@ -158,7 +158,8 @@ constexpr int kDefaultSegRounds = 16384;
 struct Plan {
     std::vector<DevPolicy> pols;
     std::vector<char> tp;              // per policy: replayed by the time-parallel kernels
-    std::vector<int32_t> lit;          // the other policies: the literal kernel
+    std::vector<int32_t> lit;          // policies for the literal kernel
+    std::vector<LadderItem> lad;       // (trace, one-rung policy) items, longest traces first
     std::vector<PolicyGroup> groups;
     std::vector<WorkItem> items;
     std::vector<uint64_t> offsets, lengths;
@@ -247,9 +248,12 @@ int build_plan(magus_replay *h, const uint64_t *lengths, int32_t n_traces, const
     pl->seg_len = seg;
     pl->tp.resize(pl->pols.size());
     pl->lit.clear();
+    std::vector<int32_t> lad_pols;
     for (size_t i = 0; i < pl->pols.size(); i++) {
         pl->tp[i] = tp_policy(pl->pols[i], h->model.n_levels) ? 1 : 0;
-        if (!pl->tp[i]) pl->lit.push_back((int32_t)i);
+        if (pl->tp[i]) continue;
+        if (ladder_policy(pl->pols[i])) lad_pols.push_back((int32_t)i);
+        else pl->lit.push_back((int32_t)i);
     }
     form_groups(pl->pols, gp, &pl->groups, &pl->tp);
     pl->offsets.resize(n_traces);
@@ -269,6 +273,10 @@ int build_plan(magus_replay *h, const uint64_t *lengths, int32_t n_traces, const
     pl->items.reserve((size_t)n_traces * blocks);
     for (int i : order)
         for (int b = 0; b < blocks; b++) pl->items.push_back(WorkItem{(uint32_t)i, (uint32_t)(b * cw)});
+    pl->lad.clear();
+    pl->lad.reserve((size_t)n_traces * lad_pols.size());
+    for (int i : order)
+        for (int32_t c : lad_pols) pl->lad.push_back(LadderItem{(uint32_t)i, (uint32_t)c});
     return MAGUS_OK;
 }
 
@@ -311,6 +319,51 @@ int launch_literal_part(magus_replay *h, const Plan &pl, const uint32_t *traces,
     return MAGUS_OK;
 }
 
+// The one-rung policies: one warp per (trace, policy) item (replay_ladder.cu).
+int launch_ladder_part(magus_replay *h, const Plan &pl, const uint32_t *traces, const Outs &o,
+                       const DevPolicy *d_pols, const uint64_t *d_off, const uint64_t *d_len,
+                       const LadderItem *d_items, cudaStream_t stream) {
+    uint64_t total_elems = 0;
+    for (size_t i = 0; i < pl.lengths.size(); i++)
+        total_elems += (pl.lengths[i] + kTraceAlign - 1) / kTraceAlign * kTraceAlign;
+    CUtensorMap tmap;
+    memset(&tmap, 0, sizeof(tmap));
+    std::string err;
+    int rc = make_trace_tmap(traces, total_elems, 32, &tmap, &err);
+    if (rc) { set_error(err); return rc; }
+    LadderParams lp;
+    memset(&lp, 0, sizeof(lp));
+    lp.traces = traces;
+    lp.offsets = d_off;
+    lp.lengths = d_len;
+    lp.pols = d_pols;
+    lp.n_pols = (int32_t)pl.pols.size();
+    lp.n_items = (int32_t)pl.lad.size();
+    lp.items = d_items;
+    lp.queue = h->queue;
+    lp.status = h->status;
+    lp.model = h->dm;
+    lp.energy = o.energy;
+    lp.edp = o.edp;
+    lp.time = o.time;
+    lp.log_entries = o.log_entries;
+    lp.log_cap = o.log_cap;
+    lp.n_changes = o.n_changes;
+    lp.change_hash = o.change_hash;
+    lp.n_hf = o.n_hf;
+    lp.state = o.state;
+    const int per_sm = ladder_max_ctas_per_sm();
+    if (per_sm <= 0) {
+        set_error("ladder kernel does not fit on this device");
+        return MAGUS_ECUDA;
+    }
+    const size_t ctas = (pl.lad.size() + ladder_warps_per_cta() - 1) / ladder_warps_per_cta();
+    const int grid = (int)std::max<size_t>(1, std::min<size_t>(ctas, (size_t)h->sms * per_sm));
+    CK(cudaMemsetAsync(h->queue, 0, sizeof(unsigned int), stream), "cudaMemsetAsync");
+    CK(launch_replay_ladder(lp, tmap, grid, stream), "ladder kernel launch");
+    return MAGUS_OK;
+}
+
 int launch_seg_plan(magus_replay *h, const Plan &pl, const uint32_t *traces, const Outs &o, cudaStream_t stream,
                     float *ms_out);
 constexpr int kUseTile = 1;   // launch_seg_plan: the segment buffers exceed the budget
@@ -327,7 +380,9 @@ int launch_plan(magus_replay *h, const Plan &pl, const uint32_t *traces, const O
     const size_t sz_items = align_up(std::max<size_t>(n_items, 1) * sizeof(WorkItem), 256);
     const size_t sz_off = align_up(std::max<size_t>(pl.offsets.size(), 1) * 8, 256);
     const size_t sz_lit = align_up(std::max<size_t>(pl.lit.size(), 1) * 4, 256);
-    const size_t total = sz_pol + sz_grp + sz_items + 2 * sz_off + sz_lit;
+    const size_t sz_lad = align_up(std::max<size_t>(pl.lad.size(), 1) * sizeof(LadderItem), 256);
+    const size_t off_lad = sz_pol + sz_grp + sz_items + 2 * sz_off + sz_lit;
+    const size_t total = off_lad + sz_lad;
     int rc = ensure_ws(h, &h->ws, &h->ws_size, total);
     if (rc) return rc;
     const int slot = h->pin_next;
@@ -343,6 +398,7 @@ int launch_plan(magus_replay *h, const Plan &pl, const uint32_t *traces, const O
         memcpy(pin + sz_pol + sz_grp + sz_items + sz_off, pl.lengths.data(), pl.lengths.size() * 8);
     }
     if (!pl.lit.empty()) memcpy(pin + sz_pol + sz_grp + sz_items + 2 * sz_off, pl.lit.data(), pl.lit.size() * 4);
+    if (!pl.lad.empty()) memcpy(pin + off_lad, pl.lad.data(), pl.lad.size() * sizeof(LadderItem));
     if (h->ws_ev_pending) CK(cudaStreamWaitEvent(stream, h->ws_ev, 0), "cudaStreamWaitEvent");
     char *ws = (char *)h->ws;
     CK(cudaMemcpyAsync(ws, pin, total, cudaMemcpyHostToDevice, stream), "cudaMemcpyAsync(plan)");
@@ -397,20 +453,35 @@ int launch_plan(magus_replay *h, const Plan &pl, const uint32_t *traces, const O
         if (rc) { set_error(err); return rc; }
     }
     const bool has_lit = !pl.lit.empty() && !pl.lengths.empty();
-    if (n_items || has_lit) {
+    const bool has_lad = !pl.lad.empty();
+    if (n_items || has_lit || has_lad) {
         size_t slot_k;
         rc = kev_slot(h, &slot_k);
         if (rc) return rc;
+        // event m follows the first kernel: the main kernel of this call
+        bool m_done = false;
+        auto mark = [&]() -> int {
+            if (!m_done) CK(cudaEventRecord(h->k_ev[slot_k].m, stream), "cudaEventRecord");
+            m_done = true;
+            return MAGUS_OK;
+        };
         CK(cudaEventRecord(h->k_ev[slot_k].a, stream), "cudaEventRecord");
-        if (n_items) CK(launch_replay_tp(pl.tg, pl.cw, pl.gp, p, tmap, grid, stream), "replay kernel launch");
-        CK(cudaEventRecord(h->k_ev[slot_k].m, stream), "cudaEventRecord");
+        if (n_items) {
+            CK(launch_replay_tp(pl.tg, pl.cw, pl.gp, p, tmap, grid, stream), "replay kernel launch");
+            if ((rc = mark())) return rc;
+        }
+        if (has_lad) {
+            rc = launch_ladder_part(h, pl, traces, o, p.pols, p.offsets, p.lengths, (const LadderItem *)(ws + off_lad),
+                                    stream);
+            if (rc || (rc = mark())) return rc;
+        }
         if (has_lit) {
             rc = launch_literal_part(h, pl, traces, o, p.pols, p.offsets, p.lengths,
                                      (const int32_t *)(ws + sz_pol + sz_grp + sz_items + 2 * sz_off), stream);
-            if (rc) return rc;
+            if (rc || (rc = mark())) return rc;
         }
         CK(cudaEventRecord(h->k_ev[slot_k].b, stream), "cudaEventRecord");
-        h->k_ev[slot_k].kernels = (n_items ? 1 : 0) + (has_lit ? 1 : 0);
+        h->k_ev[slot_k].kernels = (n_items ? 1 : 0) + (has_lad ? 1 : 0) + (has_lit ? 1 : 0);
         if (h->k_used < h->k_ev.size()) h->k_used++;
     }
     if (ms_out) {
@@ -473,7 +544,9 @@ int launch_seg_plan(magus_replay *h, const Plan &pl, const uint32_t *traces, con
     const size_t sz_items = align_up(std::max<size_t>(n_items, 1) * sizeof(SegItem), 256);
     const size_t sz_off = align_up(std::max<size_t>(n_traces, 1) * 8, 256);
     const size_t sz_lit = align_up(std::max<size_t>(pl.lit.size(), 1) * 4, 256);
-    const size_t total = sz_pol + sz_grp + sz_items + 4 * sz_off + sz_lit;
+    const size_t sz_lad = align_up(std::max<size_t>(pl.lad.size(), 1) * sizeof(LadderItem), 256);
+    const size_t off_lad = sz_pol + sz_grp + sz_items + 4 * sz_off + sz_lit;
+    const size_t total = off_lad + sz_lad;
     // device buffers: summaries | tails | change-log scratch
     const uint64_t n_pairs = (uint64_t)n_traces * n_pols;
     const size_t sz_sum = align_up(std::max<uint64_t>(total_segs * n_pols, 1) * sizeof(SegSummary), 256);
@@ -501,6 +574,7 @@ int launch_seg_plan(magus_replay *h, const Plan &pl, const uint32_t *traces, con
         memcpy(pin + sz_pol + sz_grp + sz_items + 3 * sz_off, scratch_base.data(), n_traces * 8);
     }
     if (!pl.lit.empty()) memcpy(pin + sz_pol + sz_grp + sz_items + 4 * sz_off, pl.lit.data(), pl.lit.size() * 4);
+    if (!pl.lad.empty()) memcpy(pin + off_lad, pl.lad.data(), pl.lad.size() * sizeof(LadderItem));
     if (h->ws_ev_pending) CK(cudaStreamWaitEvent(stream, h->ws_ev, 0), "cudaStreamWaitEvent");
     char *ws = (char *)h->ws;
     CK(cudaMemcpyAsync(ws, pin, total, cudaMemcpyHostToDevice, stream), "cudaMemcpyAsync(plan)");
@@ -558,21 +632,39 @@ int launch_seg_plan(magus_replay *h, const Plan &pl, const uint32_t *traces, con
     size_t slot_k;
     rc = kev_slot(h, &slot_k);
     if (rc) return rc;
+    // event m follows the main kernel: the segment kernel, else the first one launched
+    bool m_done = false;
+    auto mark = [&]() -> int {
+        if (!m_done) CK(cudaEventRecord(h->k_ev[slot_k].m, stream), "cudaEventRecord");
+        m_done = true;
+        return MAGUS_OK;
+    };
     CK(cudaEventRecord(h->k_ev[slot_k].a, stream), "cudaEventRecord");
-    if (n_items) CK(launch_replay_seg(pl.gp, p, tmap, grid, stream), "segment kernel launch");
-    CK(cudaEventRecord(h->k_ev[slot_k].m, stream), "cudaEventRecord");
-    const bool any_tp = pl.lit.size() < pl.pols.size();
-    if (n_pairs && any_tp)
+    if (n_items) {
+        CK(launch_replay_seg(pl.gp, p, tmap, grid, stream), "segment kernel launch");
+        if ((rc = mark())) return rc;
+    }
+    const bool any_tp = std::count(pl.tp.begin(), pl.tp.end(), (char)1) > 0;
+    if (n_pairs && any_tp) {
         CK(launch_combine(p, (int64_t)n_pairs, o.energy, o.edp, o.time, o.n_changes, o.change_hash, o.n_hf, stream),
            "combine kernel launch");
+        if ((rc = mark())) return rc;
+    }
+    const bool has_lad = !pl.lad.empty();
+    if (has_lad) {
+        rc = launch_ladder_part(h, pl, traces, o, p.pols, p.offsets, p.lengths, (const LadderItem *)(ws + off_lad),
+                                stream);
+        if (rc || (rc = mark())) return rc;
+    }
     const bool has_lit = !pl.lit.empty() && n_traces > 0;
     if (has_lit) {
         rc = launch_literal_part(h, pl, traces, o, p.pols, p.offsets, p.lengths,
                                  (const int32_t *)(ws + sz_pol + sz_grp + sz_items + 4 * sz_off), stream);
-        if (rc) return rc;
+        if (rc || (rc = mark())) return rc;
     }
+    if ((rc = mark())) return rc;
     CK(cudaEventRecord(h->k_ev[slot_k].b, stream), "cudaEventRecord");
-    h->k_ev[slot_k].kernels = (n_items ? 1 : 0) + ((n_pairs && any_tp) ? 1 : 0) + (has_lit ? 1 : 0);
+    h->k_ev[slot_k].kernels = (n_items ? 1 : 0) + ((n_pairs && any_tp) ? 1 : 0) + (has_lad ? 1 : 0) + (has_lit ? 1 : 0);
     if (h->k_used < h->k_ev.size()) h->k_used++;
     if (ms_out) {
         CK(cudaEventRecord(e1, stream), "cudaEventRecord");

@@ -41,6 +41,8 @@ struct DevModel {
     double P0, PM;         // power at level 0 / K-1
     double cap[MAGUS_MAX_LEVELS];  // capacity per level, GB/s (plain kernel)
     double pw[MAGUS_MAX_LEVELS];   // power per level, W (plain kernel)
+    uint32_t thr[MAGUS_MAX_LEVELS];  // per level: delta > thr -> stretched (ladder kernel)
+    double ak[MAGUS_MAX_LEVELS];     // per level: seconds per stretched delta unit
 };
 
 struct WorkItem {
@@ -195,10 +197,38 @@ struct LiteralParams {
 cudaError_t launch_replay_literal(const LiteralParams &p, cudaStream_t stream);
 
 // Policies the time-parallel kernels replay: open-loop jump mode, pinned (if at all) to a
-// ladder bound.  The others go to the literal kernel.
+// ladder bound.  The ladder kernel takes the open-loop one-rung mode; the literal kernel
+// the rest.
 __host__ __device__ inline bool tp_policy(const DevPolicy &d, int n_levels) {
     return d.step_mode == 0 && (d.pin == 0 || d.pin == 1 || d.pin == n_levels);
 }
+__host__ __device__ inline bool ladder_policy(const DevPolicy &d) { return d.step_mode == 1 && d.pin == 0; }
+
+// The one-rung (ladder) kernel: one warp per (trace, policy) item.
+struct LadderItem {
+    uint32_t trace;
+    uint32_t pol;
+};
+struct LadderParams {
+    const uint32_t *traces;
+    const uint64_t *offsets;
+    const uint64_t *lengths;
+    const DevPolicy *pols;
+    int32_t n_pols;
+    int32_t n_items;
+    const LadderItem *items;
+    unsigned int *queue;
+    int *status;
+    DevModel model;
+    double *energy, *edp, *time;
+    uint32_t *log_entries;
+    uint64_t log_cap;
+    uint64_t *n_changes, *change_hash, *n_hf;
+    magus_state_t *state;
+};
+int ladder_warps_per_cta();
+int ladder_max_ctas_per_sm();
+cudaError_t launch_replay_ladder(const LadderParams &p, const CUtensorMap &tmap, int grid, cudaStream_t stream);
 
 // Host planning (plan.cu).
 // Groups over the policies with include[i] != 0 (all when include is NULL).

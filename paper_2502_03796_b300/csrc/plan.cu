@@ -62,6 +62,10 @@ int derive_model(const magus_model_t &m, DevModel *out, std::string *err) {
         return (uint32_t)v;
     };
     const int top = m.n_levels - 1;
+    for (int k = 0; k < m.n_levels; k++) {
+        d.thr[k] = thr(d.cap[k]);
+        d.ak[k] = d.dt * d.bpc / (d.q * d.cap[k]);
+    }
     d.thr0 = thr(d.cap[0]);
     d.thrM = thr(d.cap[top]);
     d.a0 = d.dt * d.bpc / (d.q * d.cap[0]);

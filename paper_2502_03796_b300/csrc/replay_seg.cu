@@ -22,16 +22,22 @@
 
 #include "magus_internal.h"
 #include "replay_core.cuh"
+#include "tma.cuh"
 
 namespace magus {
 namespace {
+
+using tma::mbar_init;
+using tma::fence_mbar_init;
+using tma::mbar_expect_tx;
+using tma::mbar_wait_bounded;
+using tma::tma_rows;
 
 using core::FULL;
 using core::smem_u32;
 
 constexpr int SB = 1024;            // rounds per sub-block: 32 rows x 32
 constexpr int SEG_WARPS = 4;        // warps per CTA (independent)
-constexpr unsigned long long kWaitNs = 2000000000ull;
 constexpr uint32_t kNone = 0xffffffffu;
 
 // per-warp ring: 2 stages of [1024-byte block whose last 2 rows hold the 64 preceding
@@ -40,44 +46,6 @@ constexpr uint32_t kStageBytes = 1024 + SB * 4;
 constexpr uint32_t kWarpBytes = 2 * kStageBytes;
 constexpr size_t kSmemBytes = 1024 + SEG_WARPS * (size_t)kWarpBytes + 64;
 
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
-__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-__device__ __forceinline__ unsigned long long globaltimer() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-__device__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
-    if (mbar_try_wait(bar, parity)) return true;
-    const unsigned long long t0 = globaltimer();
-    while (true) {
-        if (mbar_try_wait(bar, parity)) return true;
-        if (globaltimer() - t0 > kWaitNs) return false;
-    }
-}
-__device__ __forceinline__ void tma_rows(uint32_t dst, const CUtensorMap *tmap, int y, uint64_t *bar) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
-            dst),
-        "l"(tmap), "r"(0), "r"(y), "r"(smem_u32(bar))
-        : "memory");
-}
 
 // Per member of the warp's policy group, kept across the sub-blocks of a segment.
 struct MemberRun {

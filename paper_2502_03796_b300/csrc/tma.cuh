@@ -1,0 +1,59 @@
+// tma.cuh - mbarrier and 2-D TMA tensor-copy helpers shared by the replay kernels.
+//
+// Every wait is bounded by the %globaltimer clock: a wait that gives up returns false and
+// the caller records MAGUS_ETIMEDOUT instead of spinning forever.
+#pragma once
+#include <cuda.h>
+#include <stdint.h>
+
+#include "replay_core.cuh"
+
+namespace magus {
+namespace tma {
+
+constexpr unsigned long long kWaitNs = 2000000000ull;  // bounded waits: 2 s
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(core::smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(core::smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(core::smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ unsigned long long globaltimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// Wait for `parity` of `bar` with a time limit; false on timeout.
+static __device__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = globaltimer();
+    while (true) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (globaltimer() - t0 > kWaitNs) return false;
+    }
+}
+// 2-D tensor copy of the box at (x = 0, y = row) of the trace buffer into shared memory.
+__device__ __forceinline__ void tma_rows(uint32_t dst, const CUtensorMap *tmap, int y, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            dst),
+        "l"(tmap), "r"(0), "r"(y), "r"(core::smem_u32(bar))
+        : "memory");
+}
+
+}  // namespace tma
+}  // namespace magus

@@ -363,6 +363,37 @@ def test_mixed_modes_one_call(rp, seg):
         assert_pair(out, p, r, cap=cap, tag=f"mixed seg{seg}")
 
 
+def ladder_policies():
+    base = dict(tracegen.default_policy(), step_mode=1)
+    return [base,
+            dict(base, high_freq_threshold=1.5),                                   # never hf: pure walk
+            dict(base, direv_length=1, tune_window=1, high_freq_threshold=1.0),    # hf <=> flag
+            dict(base, direv_length=2, inc_threshold=2.0, dec_threshold=-2.0, high_freq_threshold=0.9),
+            dict(base, direv_length=64, tune_window=64, inc_threshold=0.5, dec_threshold=-0.5),
+            dict(base, inc_threshold=-1.0, dec_threshold=-2.0, high_freq_threshold=0.95)]
+
+
+@pytest.mark.parametrize("n_levels", [2, 17, 32])
+def test_ladder_kernel_matches_oracle(mg, n_levels):
+    """One rung per decision on the time-parallel ladder kernel: ragged lengths, ladders of
+    2, 17 and 32 rungs (2 rungs: the jump mode's outcome), full and short logs."""
+    model = dict(tracegen.default_model(), f_ghz=[0.8 + 1.6 * k / (n_levels - 1) for k in range(n_levels)])
+    ts = ragged_set(seed=17)
+    pols = ladder_policies()
+    h = mg.Replay(model)
+    try:
+        for cap in (40_000, 9):
+            out = to_numpy(h.run(to_device(ts), ts.lengths, pols, log_capacity=cap))
+            assert h.status() == 0
+            ref = oracle_pairs(ts, pols, model)
+            for p, r in ref.items():
+                assert_pair(out, p, r, cap=cap, tag=f"ladder K={n_levels} cap={cap}")
+        tot, main, runs, kernels = h.kernel_time(detail=True)
+        assert runs == 2 and kernels == 2
+    finally:
+        h.close()
+
+
 def test_literal_split_replay_with_state(rp, mg):
     """Ladder mode and an inner pin carry their state across calls (open loop); a closed
     loop can only start from a fresh state (EINVAL otherwise)."""
