@@ -37,7 +37,8 @@ N_TRACES, N_INTERVALS = 4096, 100_000
 LOG_CAP = 8192
 WORKLOAD = "batched replay: 4096 traces x 100000 intervals (phase mean 40), 1 policy (W=5, inc=5, dec=-5, L=10, th=0.6)"
 KERNEL_SOURCES = ["paper_2502_03796_b300/csrc/replay_tp.cu", "paper_2502_03796_b300/csrc/replay_seg.cu",
-                  "paper_2502_03796_b300/csrc/replay_core.cuh", "paper_2502_03796_b300/csrc/magus_internal.h"]
+                  "paper_2502_03796_b300/csrc/replay_core.cuh", "paper_2502_03796_b300/csrc/magus_internal.h",
+                  "paper_2502_03796_b300/csrc/tma.cuh"]
 
 
 def kernel_sha() -> str:
