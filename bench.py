@@ -352,7 +352,10 @@ def run_other(args, world, rank, local) -> int:
     if args.workload in ("sweep", "uneven") and not args.tile and args.segments < 0:
         tuned, tms = rp.autotune(d_tr, ts.lengths, pols, stream=stream)
     rp.kernel_time()
+    clocks = ClockSampler(local)
+    clocks.start()
     ms = time_steps(lambda: rp.run(d_tr, ts.lengths, pols, stream=stream, out=outs), args.steps, args.warmup, stream)
+    clk = clocks.stop()
     k_ms, k_main, k_n, k_kernels = rp.kernel_time(detail=True)
     pair_steps = ts.n_samples * len(pols)
     value = pair_steps * world / (ms * 1e-3)
@@ -368,7 +371,7 @@ def run_other(args, world, rank, local) -> int:
                               peak=peaks["hbm_gbs"], unit="GB/s", frac=alg_bytes / (k_avg * 1e-3) / 1e9 / peaks["hbm_gbs"],
                               traffic=None, kernel_ms=k_avg, main_kernel_ms=k_main / max(k_n, 1),
                               alg_bytes_per_launch=alg_bytes),
-                gpu_launches=k_kernels)
+                gpu_launches=k_kernels, clocks=clk)
     # one launch per trace (time-parallel kernel) on a sample of traces
     k = min(256, ts.n_traces)
     per_ms = 0.0
