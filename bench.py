@@ -323,11 +323,11 @@ def run_other(args, world, rank, local) -> int:
         pols = tracegen.sweep_policies()
         desc = "policy sweep: 1024 traces x 200000 intervals (bursty mean 10 / long mean 500 regimes), 256 policies"
     elif args.workload in ("ladder", "closed"):
-        ts = tracegen.batched(seed=rank, first_id=rank * 4096)
+        ts = tracegen.batched(n_traces=args.traces, seed=rank, first_id=rank * args.traces)
         mode = 1 if args.workload == "ladder" else 2
         pols = [dict(tracegen.default_policy(), step_mode=mode)]
         desc = (f"batched replay, {'one rung per decision (ladder kernel)' if mode == 1 else 'closed loop (literal kernel)'}: "
-                "4096 traces x 100000 intervals (phase mean 40), 1 policy")
+                f"{args.traces} traces x 100000 intervals (phase mean 40), 1 policy")
     elif args.workload == "long":
         ts = tracegen.batched(n_traces=16, n=4_000_000, seed=rank, first_id=rank * 16)
         pols = [tracegen.default_policy()]

@@ -176,7 +176,11 @@ __global__ void __launch_bounds__(LW * 32) replay_ladder_kernel(const LadderPara
             const uint32_t FL = rp.UP | rp.DN;
             const uint64_t H = core::row_history(FL, tailH, lane);
             const uint32_t HF = core::hf_row(H, FL, P.L, P.kmin) & vmask;
-            const uint32_t UPm = rp.UP & ~HF, EV = HF | rp.UP | rp.DN;
+            // Decisions that can move the rung: +1 / -1 outside the high-frequency state, and
+            // the first round of every high-frequency run (it sets the top; the rest of the
+            // run keeps it there, so they are no-ops and are left out)
+            const uint32_t UPm = rp.UP & ~HF;
+            const uint32_t EV = ((rp.UP | rp.DN) & ~HF) | (HF & ~(HF << 1));
             nhf += __popc(HF);
 
             // ---- this row's decisions folded into one clamped shift; warp scan
