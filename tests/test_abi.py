@@ -109,3 +109,19 @@ def test_model_validation(mg):
         mg.policy_bounds(tracegen.default_policy(), bad)
     with pytest.raises(mg.MagusError):
         mg.policy_bounds(tracegen.default_policy(), dict(tracegen.default_model(), dt_s=0.0))
+
+
+def test_policy_field_validation(mg):
+    """Host-side checks of the mode fields (no device needed): step_mode 0..3, pin_level
+    0..n_levels; the ABI struct keeps the C layout."""
+    import ctypes
+    assert ctypes.sizeof(mg.Policy) == 40
+    assert mg.Policy.pin_level.offset == 36 and mg.Policy.step_mode.offset == 32
+    model = tracegen.default_model()
+    for ok in (dict(step_mode=3), dict(pin_level=17), dict(pin_level=1, step_mode=1)):
+        mg.policy_bounds(dict(tracegen.default_policy(), **ok), model)
+    for bad, word in ((dict(step_mode=4), b"step_mode"), (dict(step_mode=-1), b"step_mode"),
+                      (dict(pin_level=18), b"pin_level"), (dict(pin_level=-1), b"pin_level")):
+        with pytest.raises(mg.MagusError):
+            mg.policy_bounds(dict(tracegen.default_policy(), **bad), model)
+        assert word in mg.lib().magus_last_error()
