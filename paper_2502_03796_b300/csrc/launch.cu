@@ -1,0 +1,525 @@
+// launch.cu - planning (kernel choice, policy routing, work items) and the launches of the
+// replay kernels: tile or segment kernel for the jump mode, ladder kernel for the one-rung
+// mode, literal kernel for the rest.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "replay_host.h"
+
+namespace magus {
+namespace host {
+
+// Tile for a workload: group size 4 when policies share predictions, then as many policy
+// slots per CTA as there are groups (up to 8), the remaining warps splitting time.
+void choose_tile(magus_replay *h, const std::vector<DevPolicy> &pols, const uint64_t *lengths, int n_traces, int *tg,
+                 int *cw, int *gp, int *seg) {
+    const int n_configs = (int)pols.size();
+    auto it = h->tuned.find(n_configs);
+    if (!h->tile_tg && h->seg_rounds < 0 && it != h->tuned.end()) {   // the autotuner's pick
+        *tg = it->second[0];
+        *cw = it->second[1];
+        *gp = it->second[2];
+        *seg = it->second[3];
+        return;
+    }
+    std::vector<char> tp(pols.size());
+    int n_tp = 0;
+    for (size_t i = 0; i < pols.size(); i++) n_tp += (tp[i] = tp_policy(pols[i], h->model.n_levels) ? 1 : 0);
+    std::vector<PolicyGroup> g4;
+    form_groups(pols, kMaxGroup, &g4, &tp);
+    *gp = (2 * g4.size() <= (size_t)n_tp) ? kMaxGroup : 1;
+    const int n_groups = std::max(1, *gp == 1 ? n_tp : (int)g4.size());
+    if (h->tile_tg) {
+        *tg = h->tile_tg;
+        *cw = h->tile_cw;
+    } else {
+        int c = 1;
+        while (c * 2 <= std::min(8, n_groups)) c *= 2;
+        *cw = c;
+        *tg = 8 / c;
+    }
+    // an explicit tile shape selects the tile kernel unless segments were asked for as well
+    if (h->seg_rounds >= 0 || h->tile_tg) {
+        *seg = h->seg_rounds > 0 ? h->seg_rounds : 0;
+        return;
+    }
+    // automatic: the tile kernel replays a trace's chunks one after another in one CTA, so
+    // a few long traces leave most SMs idle; the segment kernel (about 15% more work per
+    // round) splits them in time.  Take it when the longest trace's chain of chunks exceeds
+    // 1.3x the chunks each resident CTA gets on average.
+    *seg = 0;
+    int smem = 0;
+    const int per_sm = tp_max_ctas_per_sm(*tg, *cw, *gp, &smem);
+    if (per_sm <= 0 || n_traces <= 0) return;
+    const uint64_t chunk = (uint64_t)*tg * 1024;
+    const uint64_t blocks = (uint64_t)(n_groups + *cw - 1) / *cw;
+    uint64_t longest = 0, total = 0;
+    for (int i = 0; i < n_traces; i++) {
+        const uint64_t c = (lengths[i] + chunk - 1) / chunk;
+        longest = std::max(longest, c);
+        total += c * blocks;
+    }
+    const double per_cta = (double)total / ((double)h->sms * per_sm);
+    if (!((double)longest > 1.3 * per_cta && longest * chunk >= 2 * (uint64_t)kDefaultSegRounds)) return;
+    // segment length: work items are taken from a queue, so the launch lasts about
+    // ceil(items / warps) items; pick the length that minimises that (plus a fixed cost of
+    // 256 rounds per segment for its prehistory, summary and combine step)
+    const int seg_ctas = seg_max_ctas_per_sm(*gp);
+    if (seg_ctas <= 0) return;
+    const double warps = (double)h->sms * seg_ctas * seg_warps_per_cta();
+    double best = 1e300;
+    for (int L = 2048; L <= 65536; L += 1024) {
+        uint64_t items = 0;
+        for (int i = 0; i < n_traces; i++) items += (lengths[i] + L - 1) / L;
+        items *= (uint64_t)n_groups;
+        const double cost = std::ceil((double)items / warps) * (L + 256.0);
+        if (cost < best * 0.999) {   // ties go to the shorter segment
+            best = cost;
+            *seg = L;
+        }
+    }
+}
+
+int build_plan(magus_replay *h, const uint64_t *lengths, int32_t n_traces, const magus_policy_t *configs,
+               int32_t n_configs, int tg, int cw, int gp, int seg, Plan *pl) {
+    int rc = check_policies(h, configs, n_configs, &pl->pols);
+    if (rc) return rc;
+    pl->tg = tg;
+    pl->cw = cw;
+    pl->gp = gp;
+    pl->seg_len = seg;
+    pl->tp.resize(pl->pols.size());
+    pl->lit.clear();
+    std::vector<int32_t> lad_pols;
+    for (size_t i = 0; i < pl->pols.size(); i++) {
+        pl->tp[i] = tp_policy(pl->pols[i], h->model.n_levels) ? 1 : 0;
+        if (pl->tp[i]) continue;
+        if (ladder_policy(pl->pols[i])) lad_pols.push_back((int32_t)i);
+        else pl->lit.push_back((int32_t)i);
+    }
+    form_groups(pl->pols, gp, &pl->groups, &pl->tp);
+    pl->offsets.resize(n_traces);
+    pl->lengths.assign(lengths, lengths + n_traces);
+    uint64_t off = 0;
+    for (int i = 0; i < n_traces; i++) {
+        pl->offsets[i] = off;
+        off += (lengths[i] + kTraceAlign - 1) / kTraceAlign * kTraceAlign;
+    }
+    // longest traces first: the persistent CTAs take items in this order
+    std::vector<int> order(n_traces);
+    for (int i = 0; i < n_traces; i++) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return lengths[a] > lengths[b]; });
+    const int n_groups = (int)pl->groups.size();
+    const int blocks = (n_groups + cw - 1) / cw;
+    pl->items.clear();
+    pl->items.reserve((size_t)n_traces * blocks);
+    for (int i : order)
+        for (int b = 0; b < blocks; b++) pl->items.push_back(WorkItem{(uint32_t)i, (uint32_t)(b * cw)});
+    if (pl->items.size() > (size_t)INT32_MAX || (size_t)n_traces * lad_pols.size() > (size_t)INT32_MAX) {
+        set_error("too many (trace, policy) work items");
+        return MAGUS_EINVAL;
+    }
+    pl->lad.clear();
+    pl->lad.reserve((size_t)n_traces * lad_pols.size());
+    for (int i : order)
+        for (int32_t c : lad_pols) pl->lad.push_back(LadderItem{(uint32_t)i, (uint32_t)c});
+    return MAGUS_OK;
+}
+
+
+// Upload the plan through pinned staging and launch the batched kernel on `stream`.
+// The policies the time-parallel kernels do not replay: one thread per pair, all traces in
+// one launch (replay_plain.cu).  d_*: the plan as uploaded to the workspace.
+int launch_literal_part(magus_replay *h, const Plan &pl, const uint32_t *traces, const Outs &o,
+                        const DevPolicy *d_pols, const uint64_t *d_off, const uint64_t *d_len, const int32_t *d_lit,
+                        cudaStream_t stream) {
+    LiteralParams lp;
+    memset(&lp, 0, sizeof(lp));
+    lp.traces = traces;
+    lp.offsets = d_off;
+    lp.lengths = d_len;
+    lp.n_traces = (int32_t)pl.lengths.size();
+    lp.n_pols = (int32_t)pl.pols.size();
+    lp.pols = d_pols;
+    lp.lit = d_lit;
+    lp.n_lit = (int32_t)pl.lit.size();
+    lp.model = h->dm;
+    lp.energy = o.energy;
+    lp.edp = o.edp;
+    lp.time = o.time;
+    lp.log_entries = o.log_entries;
+    lp.log_cap = o.log_cap;
+    lp.n_changes = o.n_changes;
+    lp.change_hash = o.change_hash;
+    lp.n_hf = o.n_hf;
+    lp.state = o.state;
+    lp.status = h->status;
+    CK(launch_replay_literal(lp, stream), "literal kernel launch");
+    return MAGUS_OK;
+}
+
+// The one-rung policies: one warp per (trace, policy) item (replay_ladder.cu).
+int launch_ladder_part(magus_replay *h, const Plan &pl, const uint32_t *traces, const Outs &o,
+                       const DevPolicy *d_pols, const uint64_t *d_off, const uint64_t *d_len,
+                       const LadderItem *d_items, cudaStream_t stream) {
+    uint64_t total_elems = 0;
+    for (size_t i = 0; i < pl.lengths.size(); i++)
+        total_elems += (pl.lengths[i] + kTraceAlign - 1) / kTraceAlign * kTraceAlign;
+    CUtensorMap tmap;
+    memset(&tmap, 0, sizeof(tmap));
+    std::string err;
+    int rc = make_trace_tmap(traces, total_elems, 32, &tmap, &err);
+    if (rc) { set_error(err); return rc; }
+    LadderParams lp;
+    memset(&lp, 0, sizeof(lp));
+    lp.traces = traces;
+    lp.offsets = d_off;
+    lp.lengths = d_len;
+    lp.pols = d_pols;
+    lp.n_pols = (int32_t)pl.pols.size();
+    lp.n_items = (int32_t)pl.lad.size();
+    lp.items = d_items;
+    lp.queue = h->queue;
+    lp.status = h->status;
+    lp.model = h->dm;
+    lp.energy = o.energy;
+    lp.edp = o.edp;
+    lp.time = o.time;
+    lp.log_entries = o.log_entries;
+    lp.log_cap = o.log_cap;
+    lp.n_changes = o.n_changes;
+    lp.change_hash = o.change_hash;
+    lp.n_hf = o.n_hf;
+    lp.state = o.state;
+    const int per_sm = ladder_max_ctas_per_sm();
+    if (per_sm <= 0) {
+        set_error("ladder kernel does not fit on this device");
+        return MAGUS_ECUDA;
+    }
+    const size_t ctas = (pl.lad.size() + ladder_warps_per_cta() - 1) / ladder_warps_per_cta();
+    const int grid = (int)std::max<size_t>(1, std::min<size_t>(ctas, (size_t)h->sms * per_sm));
+    CK(cudaMemsetAsync(h->queue, 0, sizeof(unsigned int), stream), "cudaMemsetAsync");
+    CK(launch_replay_ladder(lp, tmap, grid, stream), "ladder kernel launch");
+    return MAGUS_OK;
+}
+
+int launch_seg_plan(magus_replay *h, const Plan &pl, const uint32_t *traces, const Outs &o, cudaStream_t stream,
+                    float *ms_out);
+
+int launch_plan(magus_replay *h, const Plan &pl, const uint32_t *traces, const Outs &o, cudaStream_t stream,
+                float *ms_out) {
+    if (pl.seg_len > 0) {
+        const int rc = launch_seg_plan(h, pl, traces, o, stream, ms_out);
+        if (rc != kUseTile) return rc;
+    }
+    const size_t n_items = pl.items.size();
+    const size_t sz_pol = align_up(pl.pols.size() * sizeof(DevPolicy), 256);
+    const size_t sz_grp = align_up(std::max<size_t>(pl.groups.size(), 1) * sizeof(PolicyGroup), 256);
+    const size_t sz_items = align_up(std::max<size_t>(n_items, 1) * sizeof(WorkItem), 256);
+    const size_t sz_off = align_up(std::max<size_t>(pl.offsets.size(), 1) * 8, 256);
+    const size_t sz_lit = align_up(std::max<size_t>(pl.lit.size(), 1) * 4, 256);
+    const size_t sz_lad = align_up(std::max<size_t>(pl.lad.size(), 1) * sizeof(LadderItem), 256);
+    const size_t off_lad = sz_pol + sz_grp + sz_items + 2 * sz_off + sz_lit;
+    const size_t total = off_lad + sz_lad;
+    int rc = ensure_ws(h, &h->ws, &h->ws_size, total);
+    if (rc) return rc;
+    const int slot = h->pin_next;
+    h->pin_next ^= 1;
+    rc = ensure_pin(h, slot, total);
+    if (rc) return rc;
+    char *pin = (char *)h->pin[slot];
+    memcpy(pin, pl.pols.data(), pl.pols.size() * sizeof(DevPolicy));
+    memcpy(pin + sz_pol, pl.groups.data(), pl.groups.size() * sizeof(PolicyGroup));
+    if (n_items) memcpy(pin + sz_pol + sz_grp, pl.items.data(), n_items * sizeof(WorkItem));
+    if (!pl.offsets.empty()) {
+        memcpy(pin + sz_pol + sz_grp + sz_items, pl.offsets.data(), pl.offsets.size() * 8);
+        memcpy(pin + sz_pol + sz_grp + sz_items + sz_off, pl.lengths.data(), pl.lengths.size() * 8);
+    }
+    if (!pl.lit.empty()) memcpy(pin + sz_pol + sz_grp + sz_items + 2 * sz_off, pl.lit.data(), pl.lit.size() * 4);
+    if (!pl.lad.empty()) memcpy(pin + off_lad, pl.lad.data(), pl.lad.size() * sizeof(LadderItem));
+    if (h->ws_ev_pending) CK(cudaStreamWaitEvent(stream, h->ws_ev, 0), "cudaStreamWaitEvent");
+    char *ws = (char *)h->ws;
+    CK(cudaMemcpyAsync(ws, pin, total, cudaMemcpyHostToDevice, stream), "cudaMemcpyAsync(plan)");
+    CK(cudaEventRecord(h->pin_ev[slot], stream), "cudaEventRecord");
+    h->pin_pending[slot] = true;
+    CK(cudaMemsetAsync(h->queue, 0, sizeof(unsigned int), stream), "cudaMemsetAsync");
+
+    TpParams p;
+    memset(&p, 0, sizeof(p));
+    p.traces = traces;
+    p.pols = (const DevPolicy *)ws;
+    p.n_pols = (int32_t)pl.pols.size();
+    p.groups = (const PolicyGroup *)(ws + sz_pol);
+    p.n_groups = (int32_t)pl.groups.size();
+    p.items = (const WorkItem *)(ws + sz_pol + sz_grp);
+    p.offsets = (const uint64_t *)(ws + sz_pol + sz_grp + sz_items);
+    p.lengths = (const uint64_t *)(ws + sz_pol + sz_grp + sz_items + sz_off);
+    p.n_items = (int32_t)n_items;
+    p.queue = h->queue;
+    p.status = h->status;
+    p.model = h->dm;
+    p.energy = o.energy;
+    p.edp = o.edp;
+    p.time = o.time;
+    p.log_entries = o.log_entries;
+    p.log_cap = o.log_cap;
+    p.n_changes = o.n_changes;
+    p.change_hash = o.change_hash;
+    p.n_hf = o.n_hf;
+    p.state = o.state;
+    int smem = 0;
+    const int per_sm = tp_max_ctas_per_sm(pl.tg, pl.cw, pl.gp, &smem);
+    if (per_sm <= 0) {
+        set_error("tile shape does not fit on this device");
+        return MAGUS_ECUDA;
+    }
+    const int grid = (int)std::max<size_t>(1, std::min<size_t>(n_items, (size_t)h->sms * per_sm));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (ms_out) {
+        CK(cudaEventCreate(&e0), "cudaEventCreate");
+        CK(cudaEventCreate(&e1), "cudaEventCreate");
+        CK(cudaEventRecord(e0, stream), "cudaEventRecord");
+    }
+    CUtensorMap tmap;
+    memset(&tmap, 0, sizeof(tmap));
+    if (n_items) {
+        uint64_t total_elems = 0;
+        for (size_t i = 0; i < pl.lengths.size(); i++)
+            total_elems += (pl.lengths[i] + kTraceAlign - 1) / kTraceAlign * kTraceAlign;
+        std::string err;
+        rc = make_trace_tmap(traces, total_elems, tp_box_rows(pl.tg), &tmap, &err);
+        if (rc) { set_error(err); return rc; }
+    }
+    const bool has_lit = !pl.lit.empty() && !pl.lengths.empty();
+    const bool has_lad = !pl.lad.empty();
+    if (n_items || has_lit || has_lad) {
+        size_t slot_k;
+        rc = kev_slot(h, &slot_k);
+        if (rc) return rc;
+        // event m follows the first kernel: the main kernel of this call
+        bool m_done = false;
+        auto mark = [&]() -> int {
+            if (!m_done) CK(cudaEventRecord(h->k_ev[slot_k].m, stream), "cudaEventRecord");
+            m_done = true;
+            return MAGUS_OK;
+        };
+        CK(cudaEventRecord(h->k_ev[slot_k].a, stream), "cudaEventRecord");
+        if (n_items) {
+            CK(launch_replay_tp(pl.tg, pl.cw, pl.gp, p, tmap, grid, stream), "replay kernel launch");
+            if ((rc = mark())) return rc;
+        }
+        if (has_lad) {
+            rc = launch_ladder_part(h, pl, traces, o, p.pols, p.offsets, p.lengths, (const LadderItem *)(ws + off_lad),
+                                    stream);
+            if (rc || (rc = mark())) return rc;
+        }
+        if (has_lit) {
+            rc = launch_literal_part(h, pl, traces, o, p.pols, p.offsets, p.lengths,
+                                     (const int32_t *)(ws + sz_pol + sz_grp + sz_items + 2 * sz_off), stream);
+            if (rc || (rc = mark())) return rc;
+        }
+        CK(cudaEventRecord(h->k_ev[slot_k].b, stream), "cudaEventRecord");
+        h->k_ev[slot_k].kernels = (n_items ? 1 : 0) + (has_lad ? 1 : 0) + (has_lit ? 1 : 0);
+        if (h->k_used < h->k_ev.size()) h->k_used++;
+    }
+    if (ms_out) {
+        CK(cudaEventRecord(e1, stream), "cudaEventRecord");
+        CK(cudaEventSynchronize(e1), "cudaEventSynchronize");
+        CK(cudaEventElapsedTime(ms_out, e0, e1), "cudaEventElapsedTime");
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+    }
+    CK(cudaEventRecord(h->ws_ev, stream), "cudaEventRecord");
+    h->ws_ev_pending = true;
+    return MAGUS_OK;
+}
+
+// Segment kernel: every warp replays one (trace, policy group, time segment) at a time; a
+// combine kernel resolves each pair's segments in order (replay_seg.cu).
+int launch_seg_plan(magus_replay *h, const Plan &pl, const uint32_t *traces, const Outs &o, cudaStream_t stream,
+                    float *ms_out) {
+    const int n_traces = (int)pl.lengths.size();
+    const int n_pols = (int)pl.pols.size();
+    const uint64_t seg_len = (uint64_t)pl.seg_len;
+    std::vector<uint64_t> seg_base(std::max(n_traces, 1), 0);
+    uint64_t total_segs = 0;
+    for (int i = 0; i < n_traces; i++) {
+        seg_base[i] = total_segs;
+        total_segs += (pl.lengths[i] + seg_len - 1) / seg_len;
+    }
+    std::vector<int> order(n_traces);
+    for (int i = 0; i < n_traces; i++) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return pl.lengths[a] > pl.lengths[b]; });
+    std::vector<SegItem> items;
+    items.reserve((size_t)total_segs * pl.groups.size());
+    for (int i : order) {
+        const uint32_t nseg = (uint32_t)((pl.lengths[i] + seg_len - 1) / seg_len);
+        for (uint32_t g = 0; g < pl.groups.size(); g++)
+            for (uint32_t k = 0; k < nseg; k++) items.push_back(SegItem{(uint32_t)i, g, k, 0});
+    }
+    const size_t n_items = items.size();
+    if (n_items > (size_t)INT32_MAX) {
+        set_error("too many segment work items");
+        return MAGUS_EINVAL;
+    }
+    // change entries after each segment's first event: in the pair's own log when it holds
+    // the whole trace, else in scratch (only the first log_cap of a segment can be kept)
+    const bool has_log = o.log_entries && o.log_cap > 0;
+    const uint64_t seg_cap = has_log ? std::min<uint64_t>(seg_len, o.log_cap) : 0;
+    std::vector<uint64_t> scratch_base(std::max(n_traces, 1), 0);
+    uint64_t scratch_entries = 0;
+    for (int i = 0; i < n_traces && has_log; i++) {
+        if (pl.lengths[i] <= o.log_cap) {
+            scratch_base[i] = kInPlace;
+        } else {
+            scratch_base[i] = scratch_entries;
+            scratch_entries += (pl.lengths[i] + seg_len - 1) / seg_len * (uint64_t)n_pols * seg_cap;
+        }
+    }
+    // plan workspace: policies | groups | items | offsets | lengths | segment bases | scratch bases
+    const size_t sz_pol = align_up(pl.pols.size() * sizeof(DevPolicy), 256);
+    const size_t sz_grp = align_up(std::max<size_t>(pl.groups.size(), 1) * sizeof(PolicyGroup), 256);
+    const size_t sz_items = align_up(std::max<size_t>(n_items, 1) * sizeof(SegItem), 256);
+    const size_t sz_off = align_up(std::max<size_t>(n_traces, 1) * 8, 256);
+    const size_t sz_lit = align_up(std::max<size_t>(pl.lit.size(), 1) * 4, 256);
+    const size_t sz_lad = align_up(std::max<size_t>(pl.lad.size(), 1) * sizeof(LadderItem), 256);
+    const size_t off_lad = sz_pol + sz_grp + sz_items + 4 * sz_off + sz_lit;
+    const size_t total = off_lad + sz_lad;
+    // device buffers: summaries | tails | change-log scratch
+    const uint64_t n_pairs = (uint64_t)n_traces * n_pols;
+    const size_t sz_sum = align_up(std::max<uint64_t>(total_segs * n_pols, 1) * sizeof(SegSummary), 256);
+    const size_t sz_tail = align_up(std::max<uint64_t>(n_pairs, 1) * sizeof(SegTail), 256);
+    const size_t sz_log = align_up(scratch_entries * 4, 256);
+    const size_t seg_need = sz_sum + sz_tail + sz_log;
+    // the tile kernel needs none of the segment buffers: take it when they do not fit
+    if (std::max(total, h->ws_size) + h->scratch_size + std::max(seg_need, h->seg_size) > h->budget) return kUseTile;
+    int rc = ensure_ws(h, &h->ws, &h->ws_size, total);
+    if (rc) return rc;
+    rc = ensure_ws(h, &h->segbuf, &h->seg_size, seg_need);
+    if (rc) return rc;
+    const int slot = h->pin_next;
+    h->pin_next ^= 1;
+    rc = ensure_pin(h, slot, total);
+    if (rc) return rc;
+    char *pin = (char *)h->pin[slot];
+    memcpy(pin, pl.pols.data(), pl.pols.size() * sizeof(DevPolicy));
+    memcpy(pin + sz_pol, pl.groups.data(), pl.groups.size() * sizeof(PolicyGroup));
+    if (n_items) memcpy(pin + sz_pol + sz_grp, items.data(), n_items * sizeof(SegItem));
+    if (n_traces) {
+        memcpy(pin + sz_pol + sz_grp + sz_items, pl.offsets.data(), n_traces * 8);
+        memcpy(pin + sz_pol + sz_grp + sz_items + sz_off, pl.lengths.data(), n_traces * 8);
+        memcpy(pin + sz_pol + sz_grp + sz_items + 2 * sz_off, seg_base.data(), n_traces * 8);
+        memcpy(pin + sz_pol + sz_grp + sz_items + 3 * sz_off, scratch_base.data(), n_traces * 8);
+    }
+    if (!pl.lit.empty()) memcpy(pin + sz_pol + sz_grp + sz_items + 4 * sz_off, pl.lit.data(), pl.lit.size() * 4);
+    if (!pl.lad.empty()) memcpy(pin + off_lad, pl.lad.data(), pl.lad.size() * sizeof(LadderItem));
+    if (h->ws_ev_pending) CK(cudaStreamWaitEvent(stream, h->ws_ev, 0), "cudaStreamWaitEvent");
+    char *ws = (char *)h->ws;
+    CK(cudaMemcpyAsync(ws, pin, total, cudaMemcpyHostToDevice, stream), "cudaMemcpyAsync(plan)");
+    CK(cudaEventRecord(h->pin_ev[slot], stream), "cudaEventRecord");
+    h->pin_pending[slot] = true;
+    CK(cudaMemsetAsync(h->queue, 0, sizeof(unsigned int), stream), "cudaMemsetAsync");
+
+    SegParams p;
+    memset(&p, 0, sizeof(p));
+    p.traces = traces;
+    p.pols = (const DevPolicy *)ws;
+    p.n_pols = n_pols;
+    p.groups = (const PolicyGroup *)(ws + sz_pol);
+    p.items = (const SegItem *)(ws + sz_pol + sz_grp);
+    p.n_items = (int32_t)n_items;
+    p.offsets = (const uint64_t *)(ws + sz_pol + sz_grp + sz_items);
+    p.lengths = (const uint64_t *)(ws + sz_pol + sz_grp + sz_items + sz_off);
+    p.seg_base = (const uint64_t *)(ws + sz_pol + sz_grp + sz_items + 2 * sz_off);
+    p.seg_len = (uint32_t)seg_len;
+    p.queue = h->queue;
+    p.status = h->status;
+    p.model = h->dm;
+    p.summ = (SegSummary *)h->segbuf;
+    p.tails = (SegTail *)((char *)h->segbuf + sz_sum);
+    p.scratch_base = has_log ? (const uint64_t *)(ws + sz_pol + sz_grp + sz_items + 3 * sz_off) : nullptr;
+    p.scratch_log = scratch_entries ? (uint32_t *)((char *)h->segbuf + sz_sum + sz_tail) : nullptr;
+    p.seg_cap = seg_cap;
+    p.log = has_log ? o.log_entries : nullptr;
+    p.log_cap = has_log ? o.log_cap : 0;
+    p.state = o.state;
+    CUtensorMap tmap;
+    memset(&tmap, 0, sizeof(tmap));
+    if (n_items) {
+        uint64_t total_elems = 0;
+        for (int i = 0; i < n_traces; i++)
+            total_elems += (pl.lengths[i] + kTraceAlign - 1) / kTraceAlign * kTraceAlign;
+        std::string err;
+        rc = make_trace_tmap(traces, total_elems, 32, &tmap, &err);
+        if (rc) { set_error(err); return rc; }
+    }
+    const int per_sm = seg_max_ctas_per_sm(pl.gp);
+    if (per_sm <= 0) {
+        set_error("segment kernel does not fit on this device");
+        return MAGUS_ECUDA;
+    }
+    const size_t warps = (size_t)h->sms * per_sm * seg_warps_per_cta();
+    const int grid = (int)std::max<size_t>(1, std::min<size_t>((n_items + seg_warps_per_cta() - 1) / seg_warps_per_cta(),
+                                                               warps / seg_warps_per_cta()));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (ms_out) {
+        CK(cudaEventCreate(&e0), "cudaEventCreate");
+        CK(cudaEventCreate(&e1), "cudaEventCreate");
+        CK(cudaEventRecord(e0, stream), "cudaEventRecord");
+    }
+    size_t slot_k;
+    rc = kev_slot(h, &slot_k);
+    if (rc) return rc;
+    // event m follows the main kernel: the segment kernel, else the first one launched
+    bool m_done = false;
+    auto mark = [&]() -> int {
+        if (!m_done) CK(cudaEventRecord(h->k_ev[slot_k].m, stream), "cudaEventRecord");
+        m_done = true;
+        return MAGUS_OK;
+    };
+    CK(cudaEventRecord(h->k_ev[slot_k].a, stream), "cudaEventRecord");
+    if (n_items) {
+        CK(launch_replay_seg(pl.gp, p, tmap, grid, stream), "segment kernel launch");
+        if ((rc = mark())) return rc;
+    }
+    const bool any_tp = std::count(pl.tp.begin(), pl.tp.end(), (char)1) > 0;
+    if (n_pairs && any_tp) {
+        CK(launch_combine(p, (int64_t)n_pairs, o.energy, o.edp, o.time, o.n_changes, o.change_hash, o.n_hf, stream),
+           "combine kernel launch");
+        if ((rc = mark())) return rc;
+    }
+    const bool has_lad = !pl.lad.empty();
+    if (has_lad) {
+        rc = launch_ladder_part(h, pl, traces, o, p.pols, p.offsets, p.lengths, (const LadderItem *)(ws + off_lad),
+                                stream);
+        if (rc || (rc = mark())) return rc;
+    }
+    const bool has_lit = !pl.lit.empty() && n_traces > 0;
+    if (has_lit) {
+        rc = launch_literal_part(h, pl, traces, o, p.pols, p.offsets, p.lengths,
+                                 (const int32_t *)(ws + sz_pol + sz_grp + sz_items + 4 * sz_off), stream);
+        if (rc || (rc = mark())) return rc;
+    }
+    if ((rc = mark())) return rc;
+    CK(cudaEventRecord(h->k_ev[slot_k].b, stream), "cudaEventRecord");
+    h->k_ev[slot_k].kernels = (n_items ? 1 : 0) + ((n_pairs && any_tp) ? 1 : 0) + (has_lad ? 1 : 0) + (has_lit ? 1 : 0);
+    if (h->k_used < h->k_ev.size()) h->k_used++;
+    if (ms_out) {
+        CK(cudaEventRecord(e1, stream), "cudaEventRecord");
+        CK(cudaEventSynchronize(e1), "cudaEventSynchronize");
+        CK(cudaEventElapsedTime(ms_out, e0, e1), "cudaEventElapsedTime");
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+    }
+    CK(cudaEventRecord(h->ws_ev, stream), "cudaEventRecord");
+    h->ws_ev_pending = true;
+    return MAGUS_OK;
+}
+
+}  // namespace host
+}  // namespace magus

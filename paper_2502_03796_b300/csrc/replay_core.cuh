@@ -109,6 +109,7 @@ __device__ __forceinline__ void predict_exact(uint32_t a, uint32_t b, const DevP
         up = der > P.inc;
         dn = der < P.dec;
     }
+    dn = dn && !up;   // Alg. 1 tests +1 first: with inc < dec both can hold
 }
 
 // Alg. 1 for one row, exact for any deltas (the fallback of the fast path below).
@@ -211,7 +212,7 @@ __device__ __forceinline__ RowPred row_predict(uint32_t base, int lane, const De
     r.fast = ok;
     if (!ok) row_predict_general(base, lane, P, M, r.UP, r.DN, r.S0, r.SM);
     r.UP &= pmask;
-    r.DN &= pmask;
+    r.DN &= pmask & ~r.UP;   // Alg. 1 tests +1 first: with inc < dec both comparisons can hold
     r.S0 &= vmask;
     r.SM &= vmask;
     return r;

@@ -262,6 +262,23 @@ def test_brute_force_tiny_traces(model):
     assert cases > 20000
 
 
+def test_brute_force_inverted_thresholds(model):
+    """inc below dec: a derivative between them satisfies both comparisons of Alg. 1, which
+    tests +1 first.  Exact-rational restatement on every trace of length <= 6."""
+    alphabet = [0, 10_000_000, 30_000_000, 100_000_000]
+    for n in range(1, 7):
+        for tr in itertools.product(alphabet, repeat=n):
+            d = np.array(tr, dtype=np.uint32)
+            for W, L, th in [(1, 2, 1.5), (2, 3, 0.6), (3, 4, 1.0)]:
+                pol = dict(inc_threshold=-1.0, dec_threshold=2.0, direv_length=W, tune_window=L,
+                           high_freq_threshold=th, step_mode=0)
+                r = oracle.replay(d, pol, model, detail=True)
+                levels, log, n_hf = naive_exact(tr, W, L, -1.0, 2.0, th, model)
+                assert r["level_log"].tolist() == levels
+                assert list(zip(r["log_t"].tolist(), r["log_level"].tolist())) == log
+                assert r["n_hf"] == n_hf
+
+
 def test_brute_force_closed_loop(model):
     """Closed loop on every trace of length <= 6 over an alphabet whose larger demands
     exceed the bottom capacity (66.7 GB/s) but not the top one (200 GB/s), jump and

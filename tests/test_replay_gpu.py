@@ -45,6 +45,7 @@ def edge_policies():
         dict(base, direv_length=7, tune_window=33, inc_threshold=3.3, dec_threshold=-1.25,
              high_freq_threshold=0.3),
         dict(base, inc_threshold=-1.0, dec_threshold=-2.0),                      # negative inc
+        dict(base, inc_threshold=-2.0, dec_threshold=3.0, direv_length=9),       # inc < dec: +1 first
         dict(base, pin_level=17),                                                # static maximum
         dict(base, direv_length=7, high_freq_threshold=0.0, pin_level=1),        # static minimum
     ]
