@@ -51,3 +51,84 @@ def test_random_policies_and_lengths(seed):
                 assert_pair(out, p, r, cap=cap, tag=f"seed {seed} seg {seg} policy {pols[p % len(pols)]}")
     finally:
         rp.close()
+
+
+@pytest.mark.parametrize("seed", [11, 12, 13, 14])
+def test_random_split_replay_with_state(seed):
+    """Random cuts of random traces replayed piece by piece with carried state, policies of
+    every mode that can resume (the closed loop starts fresh only): concatenated logs and
+    summed energies equal the oracle's whole-trace replay."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2502_03796_b300 import magus
+    import oracle
+    from gpu_util import REL_TOL
+    rng = np.random.default_rng(seed)
+    model = tracegen.default_model()
+    K = len(model["f_ghz"])
+    n = int(rng.integers(2000, 30_000))
+    full = tracegen.make_traces(np.array([n], dtype=np.uint64), seed=seed, mean_phase=float(rng.uniform(3, 60))).trace(0)
+    pols = []
+    while len(pols) < 6:
+        p = random_policy(rng, K)
+        if not p["step_mode"] & 2:
+            pols.append(p)
+    cuts = sorted(set([0, n] + rng.integers(1, n, size=int(rng.integers(1, 8))).tolist()))
+    state = torch.zeros(len(pols) * magus.STATE_BYTES, dtype=torch.uint8, device="cuda")
+    E = np.zeros(len(pols))
+    logs = [[] for _ in pols]
+    rp = magus.Replay(model)
+    try:
+        rp.set_segments(int(rng.choice([-1, 1024])))
+        for a, b in zip(cuts[:-1], cuts[1:]):
+            ts = tracegen.single_trace_set(full[a:b])
+            cap = b - a
+            out = to_numpy(rp.run(to_device(ts), ts.lengths, pols, log_capacity=cap, state=state))
+            for c in range(len(pols)):
+                E[c] += out["energy_j"][c]
+                logs[c].append(out["log"][c * cap:c * cap + int(out["n_changes"][c])])
+        assert rp.status() == 0
+    finally:
+        rp.close()
+    for c, pol in enumerate(pols):
+        ref = oracle.replay(full, pol, model)
+        ent = np.concatenate(logs[c]).astype(np.uint32)
+        assert np.array_equal((ent >> 5).astype(np.uint64), ref["log_t"]), (seed, pol, cuts)
+        assert np.array_equal((ent & 31).astype(np.uint8), ref["log_level"]), (seed, pol, cuts)
+        assert abs(E[c] - ref["energy_j"]) <= REL_TOL * ref["energy_j"], (seed, pol)
+
+
+@pytest.mark.parametrize("seed", [21, 22])
+def test_random_serving_streams(seed):
+    """A serving handle with a random jump-mode policy: random request sizes on a few
+    streams, every result against the oracle's split replay."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2502_03796_b300 import magus
+    import oracle
+    from gpu_util import REL_TOL
+    rng = np.random.default_rng(seed)
+    model = tracegen.default_model()
+    K = len(model["f_ghz"])
+    pol = random_policy(rng, K)
+    pol["step_mode"] = 0
+    if pol["pin_level"] not in (0, 1, K):
+        pol["pin_level"] = 0
+    ts = tracegen.make_traces(np.full(5, 7000, dtype=np.uint64), seed=seed, mean_phase=float(rng.uniform(3, 60)))
+    sv = magus.Serve(model, pol, 5)
+    try:
+        for s in range(5):
+            t, st = 0, oracle.new_state()
+            ids = []
+            while t < 7000:
+                k = int(min(7000 - t, np.exp(rng.uniform(0, np.log(4096)))))
+                ids.append((sv.submit(s, ts.trace(s)[t:t + k]), oracle.replay(ts.trace(s)[t:t + k], pol, model, state=st)))
+                t += k
+            sv.drain()
+            for rid, ref in ids:
+                r = sv.poll(rid)
+                assert r["n_changes"] == ref["n_changes"] and r["change_hash"] == ref["change_hash"], (seed, pol)
+                assert r["n_hf"] == ref["n_hf"]
+                assert abs(r["energy_j"] - ref["energy_j"]) <= REL_TOL * max(ref["energy_j"], 1e-300)
+    finally:
+        sv.close()
