@@ -56,7 +56,8 @@ constexpr int kMaxGroup = 4;
 struct PolicyGroup {
     int32_t count;                 // 1..kMaxGroup
     int32_t member[kMaxGroup];     // policy indices (unused slots repeat member[0])
-    int32_t pad[3];
+    int32_t same_L;                // every member has the same Alg. 2 list length
+    int32_t pad[2];
 };
 
 struct TpParams {

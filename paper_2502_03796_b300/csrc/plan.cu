@@ -147,6 +147,8 @@ void form_groups(const std::vector<DevPolicy> &pols, int gp, std::vector<PolicyG
         while (j < order.size() && g.count < gp && (g.count == 0 || same(order[i], order[j])))
             g.member[g.count++] = order[j++];
         for (int m = g.count; m < kMaxGroup; m++) g.member[m] = g.member[0];
+        g.same_L = 1;
+        for (int m = 1; m < g.count; m++) g.same_L &= pols[g.member[m]].L == pols[g.member[0]].L ? 1 : 0;
         out->push_back(g);
         i = j;
     }

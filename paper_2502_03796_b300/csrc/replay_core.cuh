@@ -245,6 +245,34 @@ __device__ __forceinline__ uint32_t hf_row(uint64_t H, uint32_t FL, int L, int k
     return HF;
 }
 
+// Algorithm 2 for several policies sharing L (a policy group of the sweep): the sliding
+// counts are formed once -- byte b of w[p] holds the flag count of the window ending at
+// round 8b + p (0..64) -- and each policy only compares them with its own kmin.
+__device__ __forceinline__ void hf_counts(uint64_t H, uint32_t FL, int L, uint32_t (&w)[8]) {
+    const int s = 64 - L;
+    const uint32_t LV = s == 0 ? (uint32_t)H : (uint32_t)((H >> s) | ((uint64_t)FL << (64 - s)));
+    const uint32_t c0 = __popcll(H >> s);
+    const uint32_t d0 = __popc(FL & 0xffu) - __popc(LV & 0xffu);
+    const uint32_t d1 = __popc(FL & 0xff00u) - __popc(LV & 0xff00u);
+    const uint32_t d2 = __popc(FL & 0xff0000u) - __popc(LV & 0xff0000u);
+    const uint32_t c1 = c0 + d0, c2 = c1 + d1, c3 = c2 + d2;
+    uint32_t e4 = c0 | (c1 << 8) | (c2 << 16) | (c3 << 24);
+#pragma unroll
+    for (int p = 0; p < 8; p++) {
+        e4 = e4 + ((FL >> p) & 0x01010101u) - ((LV >> p) & 0x01010101u);
+        w[p] = e4;
+    }
+}
+// bit p of the result: count of the window ending at round p >= kmin (byte + 128 - kmin
+// sets bit 7 exactly then; counts <= 64 and kmin <= 65 keep every byte in 0..192)
+__device__ __forceinline__ uint32_t hf_from_counts(const uint32_t (&w)[8], int kmin) {
+    const uint32_t bias = (uint32_t)(128 - kmin) * 0x01010101u;
+    uint32_t HF = 0;
+#pragma unroll
+    for (int p = 0; p < 8; p++) HF = (HF >> 1) | ((w[p] + bias) & 0x80808080u);
+    return HF;
+}
+
 // Flag history before each lane's row: lanes 0 and 1 take the 64 flags before the first
 // row (tailH), the others their two predecessor rows.
 __device__ __forceinline__ uint64_t row_history(uint32_t FL, uint64_t tailH, int lane) {

@@ -228,13 +228,25 @@ __global__ void __launch_bounds__(TG * CW * 32) replay_tp_kernel(const TpParams 
             const uint64_t tailH = (g == 0) ? sh.hist[cw][c & 1] : sh.xf[cw][g > 0 ? g - 1 : 0];
             const uint64_t H = core::row_history(FL, tailH, lane);
 
+            // Algorithm 2's sliding counts once for a group whose members share L
+            uint32_t hw[GP > 1 ? 8 : 1];
+            const bool shared_counts = GP > 1 && cnt > 1 && G.same_L;
+            if constexpr (GP > 1) {
+                if (shared_counts) core::hf_counts(H, FL, Lm[0] & 0xff, hw);
+            }
             // members one after another (not unrolled: unrolling four members doubles the
             // registers and halves the resident CTAs, measured slower)
 #pragma unroll 1
             for (int m = 0; m < (GP == 1 ? 1 : cnt); m++) {
                 // ------------------------------------------------------------ phase B
                 const uint32_t act = (Lm[m] & 0x100) ? 0u : FULL;
-                const uint32_t HF = core::hf_row(H, FL, Lm[m] & 0xff, Km[m]) & vmask & act;
+                uint32_t HFr;
+                if constexpr (GP > 1) {
+                    HFr = shared_counts ? core::hf_from_counts(hw, Km[m]) : core::hf_row(H, FL, Lm[m] & 0xff, Km[m]);
+                } else {
+                    HFr = core::hf_row(H, FL, Lm[m] & 0xff, Km[m]);
+                }
+                const uint32_t HF = HFr & vmask & act;
                 const uint32_t SETM = (HF | UP) & act;
                 const uint32_t SET0 = DN & ~HF & act;
                 const uint32_t EV = SETM | SET0;
