@@ -372,6 +372,11 @@ def run_other(args, world, rank, local) -> int:
                               traffic=None, kernel_ms=k_avg, main_kernel_ms=k_main / max(k_n, 1),
                               alg_bytes_per_launch=alg_bytes),
                 gpu_launches=k_kernels, clocks=clk)
+    if args.no_plain:
+        if rank == 0:
+            print(json.dumps(line), flush=True)
+        rp.close()
+        return 0
     # one launch per trace (time-parallel kernel) on a sample of traces
     k = min(256, ts.n_traces)
     per_ms = 0.0
