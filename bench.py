@@ -58,9 +58,9 @@ def measured_peaks() -> dict:
     return dict(hbm_gbs=6400.0, source="fallback")
 
 
-def ncu_traffic(key: str) -> float | None:
-    """Per-launch DRAM bytes of the batched replay from the committed ncu summary, if it was
-    taken on the current kernel source."""
+def ncu_record(key: str) -> dict | None:
+    """The committed ncu figures of a kernel (profiles/traffic.json), if they were taken on the
+    current kernel sources."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
@@ -69,7 +69,13 @@ def ncu_traffic(key: str) -> float | None:
     e = d.get(key)
     if not e or e.get("kernel_sha") != kernel_sha():
         return None
-    return float(e["dram_bytes_per_launch"])
+    return e
+
+
+def ncu_traffic(key: str) -> float | None:
+    """Per-launch DRAM bytes of the batched replay from the committed ncu summary."""
+    e = ncu_record(key)
+    return float(e["dram_bytes_per_launch"]) if e else None
 
 
 class _Nvml:
@@ -508,6 +514,16 @@ def main() -> int:
                     kernel=("replay_seg_kernel<1> + combine_kernel" if seg_path else "replay_tp_kernel<8,1>"),
                     kernel_ms=k_avg_ms, main_kernel_ms=k_main_ms / max(k_n, 1),
                     alg_bytes_per_launch=alg_bytes, frac_of_nominal_8tbs=achieved / 8000.0)
+    # the pipe that actually bounds the kernel: integer ALU lane-operations per interval
+    # (ncu, committed with the kernel-source hash) against 148 SMs x 4 partitions x 16 lanes
+    # x the SM clock sampled during the timed region
+    rec = ncu_record("replay_tp_batched") if not seg_path else None
+    if rec and rec.get("alu_lane_ops_per_interval") and clk.get("sm_mhz"):
+        alu_ach = rec["alu_lane_ops_per_interval"] * samples_per_step / (k_main_ms / max(k_n, 1) * 1e-3)
+        alu_peak = 148 * 4 * 16 * clk["sm_mhz"] * 1e6
+        roofline["alu"] = dict(achieved=alu_ach, peak=alu_peak, unit="lane-ops/s", frac=alu_ach / alu_peak,
+                               ops_per_interval=rec["alu_lane_ops_per_interval"],
+                               peak_source="derived: 148 SMs x 64 integer lanes per cycle x sampled SM clock")
 
     line = dict(metric=METRIC, value=value, unit="samples/s", n_gpus=world, steps=args.steps,
                 warmup=args.warmup, ms_per_step=ms / args.steps, higher_is_better=True, scaling="weak",
