@@ -264,6 +264,12 @@ int magus_packed_size(const uint64_t *lengths, int32_t n_traces, uint64_t *offse
  * c / L >= high_freq_threshold (L + 1 if none). */
 int magus_policy_bounds(const magus_policy_t *policy, const magus_model_t *model, int64_t out[4]);
 
+/* FP64 decision thresholds the literal kernel derives for one policy (diagnostics and
+ * tests).  With d = x_t - x_{t-W} the FP64 throughput difference, Algorithm 1's
+ * RN(d / W) > inc holds exactly when d > out[0], and RN(d / W) < dec exactly when
+ * d <= out[1] (+-infinity when never / always). */
+int magus_policy_fp64_thresholds(const magus_policy_t *policy, const magus_model_t *model, double out[2]);
+
 const char *magus_last_error(void);
 const char *magus_version(void);
 

@@ -239,6 +239,20 @@ int magus_policy_bounds(const magus_policy_t *policy, const magus_model_t *model
     return MAGUS_OK;
 }
 
+int magus_policy_fp64_thresholds(const magus_policy_t *policy, const magus_model_t *model, double out[2]) {
+    if (!policy || !model || !out) { set_error("NULL argument"); return MAGUS_EINVAL; }
+    std::string err;
+    DevModel dm;
+    int rc = derive_model(*model, &dm, &err);
+    if (rc) { set_error(err); return rc; }
+    DevPolicy dp;
+    rc = derive_policy(*policy, *model, &dp, &err);
+    if (rc) { set_error(err); return rc; }
+    out[0] = dp.up_last;
+    out[1] = dp.dn_last;
+    return MAGUS_OK;
+}
+
 int magus_replay_open(magus_replay_t **out, const magus_model_t *model, int device, size_t mem_budget) {
     if (!out || !model) { set_error("NULL argument"); return MAGUS_EINVAL; }
     *out = nullptr;

@@ -27,6 +27,10 @@ struct alignas(16) DevPolicy {
     double th;             // Alg. 2 threshold (the plain kernel evaluates it literally)
     int32_t pin;           // 0: controlled; k > 0: static baseline at ladder index k - 1
     int32_t pad;
+    // Alg. 1 on the FP64 difference d = x_t - x_{t-W} without the division: RN(d / W) > inc
+    // exactly when d > up_last, RN(d / W) < dec exactly when d <= dn_last (RN(d / W) is
+    // monotone in d; both found on the host over the ordered doubles)
+    double up_last, dn_last;
 };
 
 // Ladder / energy model as the kernels use it.

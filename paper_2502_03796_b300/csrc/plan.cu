@@ -29,6 +29,35 @@ const char *last_error_cstr() { return g_last_error.c_str(); }
 
 static const long double kReach = 8589934592.0L;  // 2^33 > any |m| = |a - b| < 2^32
 
+// Doubles in order as integers (-0 and +0 share 0) and back.
+static int64_t dkey(double x) {
+    uint64_t b;
+    memcpy(&b, &x, 8);
+    return (b >> 63) ? -(int64_t)(b & 0x7fffffffffffffffull) : (int64_t)b;
+}
+static double dval(int64_t k) {
+    const uint64_t b = k >= 0 ? (uint64_t)k : ((uint64_t)(-k) | 0x8000000000000000ull);
+    double x;
+    memcpy(&x, &b, 8);
+    return x;
+}
+// The largest finite d with pred(d) true, for pred true on a prefix of the finite doubles;
+// -inf when it holds for none, +inf when for all.
+template <class Pred>
+static double last_true(Pred pred) {
+    const double lo_d = -1.7976931348623157e308, hi_d = 1.7976931348623157e308;
+    if (!pred(lo_d)) return -INFINITY;
+    if (pred(hi_d)) return INFINITY;
+    int64_t lo = dkey(lo_d), hi = dkey(hi_d);   // pred(lo) true, pred(hi) false
+    // the span of the keys exceeds INT64_MAX: step in unsigned arithmetic
+    while ((uint64_t)hi - (uint64_t)lo > 1u) {
+        const int64_t mid = (int64_t)((uint64_t)lo + ((uint64_t)hi - (uint64_t)lo) / 2u);
+        if (pred(dval(mid))) lo = mid;
+        else hi = mid;
+    }
+    return dval(lo);
+}
+
 int derive_model(const magus_model_t &m, DevModel *out, std::string *err) {
     if (m.n_levels < 2 || m.n_levels > MAGUS_MAX_LEVELS) { *err = "n_levels must be 2..32"; return MAGUS_EINVAL; }
     if (!m.f_ghz) { *err = "f_ghz is NULL"; return MAGUS_EINVAL; }
@@ -106,6 +135,9 @@ int derive_policy(const magus_policy_t &p, const magus_model_t &m, DevPolicy *ou
     };
     crossing(p.inc_threshold, &d.up_mid, &d.up_lo, &d.up_w);
     crossing(p.dec_threshold, &d.dn_mid, &d.dn_lo, &d.dn_w);
+    const double Wd = (double)p.direv_length, inc = p.inc_threshold, dec = p.dec_threshold;
+    d.up_last = last_true([&](double x) { return !(x / Wd > inc); });
+    d.dn_last = last_true([&](double x) { return x / Wd < dec; });
     // Alg. 2: freq = sum / len >= threshold, sum in 0..L
     d.kmin = d.L + 1;
     for (int c = 0; c <= d.L; c++) {

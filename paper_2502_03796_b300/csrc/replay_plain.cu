@@ -40,6 +40,13 @@ struct LitOut {
 // One pair, rounds in order.  st (optional): carried state, read at the start and written
 // at the end (the FIFO of throughputs is rebuilt from the last deltas; a closed loop would
 // also need the levels of those intervals, so it only starts from a fresh state).
+// kDirect: the plain form -- every expression evaluated as written (divisions included).
+// Otherwise the same decisions without divisions on the round-to-round chain: Alg. 1
+// compares the FP64 difference with thresholds equivalent to RN(d / W) > inc and < dec,
+// Alg. 2 compares the flag count with kmin, and the energy is charged as integer counts and
+// stretched-delta sums per level (E and T formed once, within 1e-15 relative of the
+// sequential FP64 sums).
+template <bool kDirect>
 __device__ void replay_pair_literal(const uint32_t *trace, uint64_t n, const DevPolicy &P, const DevModel &M,
                                     int64_t pair, const LitOut &o, magus_state_t *st) {
     const int W = P.W, L = P.L, K = M.K;
@@ -73,14 +80,33 @@ __device__ void replay_pair_literal(const uint32_t *trace, uint64_t n, const Dev
     if (pinned) level = P.pin - 1;
     double E = 0.0, T = 0.0;
     uint64_t nch = 0, hash = 0, nhf = 0;
+    // integer energy per level (kDirect == false): counts of unstretched intervals and sums
+    // of stretched deltas, flushed per run of constant level
+    uint64_t lv_n[kDirect ? 1 : MAGUS_MAX_LEVELS], lv_s[kDirect ? 1 : MAGUS_MAX_LEVELS];
+    uint64_t run_n = 0, run_s = 0;
+    uint32_t thr_cur = 0;
+    if (!kDirect) {
+        for (int k = 0; k < K; k++) lv_n[k] = lv_s[k] = 0;
+        thr_cur = M.thr[level];
+    }
+    double x_next = n ? __ddiv_rn(__dmul_rn(M.bpc, (double)trace[0]), M.q) : 0.0;
     for (uint64_t t = 0; t < n; t++) {
-        const double x = __ddiv_rn(__dmul_rn(M.bpc, (double)trace[t]), M.q);
+        const uint32_t delta = trace[t];
+        const double x = kDirect ? __ddiv_rn(__dmul_rn(M.bpc, (double)delta), M.q) : x_next;
+        // the next round's throughput does not depend on this round's decision
+        if (!kDirect && t + 1 < n) x_next = __ddiv_rn(__dmul_rn(M.bpc, (double)trace[t + 1]), M.q);
         // energy model: interval t at `level`
-        double s = __ddiv_rn(x, M.cap[level]);
-        if (s < 1.0) s = 1.0;
-        const double tau = __dmul_rn(M.dt, s);
-        T = __dadd_rn(T, tau);
-        E = __dadd_rn(E, __dmul_rn(M.pw[level], tau));
+        if (kDirect) {
+            double s = __ddiv_rn(x, M.cap[level]);
+            if (s < 1.0) s = 1.0;
+            const double tau = __dmul_rn(M.dt, s);
+            T = __dadd_rn(T, tau);
+            E = __dadd_rn(E, __dmul_rn(M.pw[level], tau));
+        } else {
+            const bool stretched = delta > thr_cur;
+            run_n += stretched ? 0u : 1u;
+            run_s += stretched ? delta : 0u;
+        }
         if (o.level_log) o.level_log[t] = (uint8_t)level;
         // Alg. 1: FIFO of W+1 throughputs
         if (ls_len == W + 1) {
@@ -96,14 +122,20 @@ __device__ void replay_pair_literal(const uint32_t *trace, uint64_t n, const Dev
         double der = __longlong_as_double(0x7ff8000000000000ll);
         if (ls_len == W + 1) {
             const int newest = ls_head == 0 ? W : ls_head - 1;
-            der = __ddiv_rn(__dsub_rn(ls[newest], ls[ls_head]), (double)W);
-            pred = der > P.inc ? 1 : (der < P.dec ? -1 : 0);
+            const double d = __dsub_rn(ls[newest], ls[ls_head]);
+            if (kDirect) {
+                der = __ddiv_rn(d, (double)W);
+                pred = der > P.inc ? 1 : (der < P.dec ? -1 : 0);
+            } else {
+                pred = d > P.up_last ? 1 : (d <= P.dn_last ? -1 : 0);
+            }
         }
         if (o.deriv_log) o.deriv_log[t] = der;
         // Alg. 2: FIFO of L flags, zero-filled
         tune = (tune << 1) | (pred != 0 ? 1ull : 0ull);
-        const double freq = __ddiv_rn((double)__popcll(tune & tmask), (double)L);
-        const bool hf = !pinned && freq >= P.th;
+        bool hf;
+        if (kDirect) hf = !pinned && __ddiv_rn((double)__popcll(tune & tmask), (double)L) >= P.th;
+        else hf = !pinned && __popcll(tune & tmask) >= P.kmin;
         nhf += hf ? 1 : 0;
         int next;
         if (pinned) next = level;
@@ -116,8 +148,23 @@ __device__ void replay_pair_literal(const uint32_t *trace, uint64_t n, const Dev
             if (o.log && nch < o.log_cap) o.log[nch] = (uint32_t)(when << 5) | (uint32_t)next;
             nch++;
             hash += mix64_plain((when << 8) | (uint64_t)next);
+            if (!kDirect) {
+                lv_n[level] += run_n;
+                lv_s[level] += run_s;
+                run_n = run_s = 0;
+                thr_cur = M.thr[next];
+            }
         }
         level = next;
+    }
+    if (!kDirect) {
+        lv_n[level] += run_n;
+        lv_s[level] += run_s;
+        for (int k = 0; k < K; k++) {
+            const double tk = M.dt * (double)lv_n[k] + M.ak[k] * (double)lv_s[k];
+            T += tk;
+            E += M.pw[k] * tk;
+        }
     }
     o.energy[pair] = E;
     o.edp[pair] = __dmul_rn(E, T);
@@ -155,7 +202,7 @@ __global__ void replay_plain_kernel(const PlainParams p) {
     o.level_log = p.level_log;
     o.deriv_log = p.deriv_log;
     o.status = nullptr;
-    replay_pair_literal(p.trace, p.n, P, p.model, pair, o, nullptr);
+    replay_pair_literal<true>(p.trace, p.n, P, p.model, pair, o, nullptr);
 }
 
 __global__ void replay_literal_kernel(const LiteralParams p) {
@@ -177,8 +224,8 @@ __global__ void replay_literal_kernel(const LiteralParams p) {
     o.level_log = nullptr;
     o.deriv_log = nullptr;
     o.status = p.status;
-    replay_pair_literal(p.traces + p.offsets[trace], p.lengths[trace], P, p.model, pair, o,
-                        p.state ? p.state + pair : nullptr);
+    replay_pair_literal<false>(p.traces + p.offsets[trace], p.lengths[trace], P, p.model, pair, o,
+                               p.state ? p.state + pair : nullptr);
 }
 
 }  // namespace

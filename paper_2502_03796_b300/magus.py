@@ -86,6 +86,7 @@ SIGNATURES = {
     "magus_replay_run_static": ([ctypes.POINTER(Model), P, P, _I32, P, _I32, P, P, P, P, P, P], ctypes.c_int),
     "magus_packed_size": ([P, _I32, P, P], ctypes.c_int),
     "magus_policy_bounds": ([ctypes.POINTER(Policy), ctypes.POINTER(Model), P], ctypes.c_int),
+    "magus_policy_fp64_thresholds": ([ctypes.POINTER(Policy), ctypes.POINTER(Model), P], ctypes.c_int),
     "magus_last_error": ([], ctypes.c_char_p),
     "magus_version": ([], ctypes.c_char_p),
     "magus_serve_open": ([P, ctypes.POINTER(Model), ctypes.POINTER(Policy), _I32, _SZ, ctypes.c_int, _I32, _I64],
@@ -162,6 +163,16 @@ def policy_bounds(policy: Dict, model: Dict) -> np.ndarray:
     out = np.zeros(4, dtype=np.int64)
     check(lib().magus_policy_bounds(ctypes.byref(pol), ctypes.byref(mh.m), out.ctypes.data))
     return out
+
+
+def policy_fp64_thresholds(policy: Dict, model: Dict):
+    """magus_policy_fp64_thresholds: (up_last, dn_last) -- +1 iff d > up_last, -1 iff
+    d <= dn_last, with d the FP64 throughput difference over W intervals."""
+    mh = ModelHolder(model)
+    pol = make_policy(policy)
+    out = np.zeros(2, dtype=np.float64)
+    check(lib().magus_policy_fp64_thresholds(ctypes.byref(pol), ctypes.byref(mh.m), out.ctypes.data))
+    return float(out[0]), float(out[1])
 
 
 def _ptr(t) -> Optional[int]:

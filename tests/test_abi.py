@@ -125,3 +125,29 @@ def test_policy_field_validation(mg):
         with pytest.raises(mg.MagusError):
             mg.policy_bounds(dict(tracegen.default_policy(), **bad), model)
         assert word in mg.lib().magus_last_error()
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_fp64_thresholds_reproduce_algorithm_1(mg, seed):
+    """The literal kernel's division-free test of Algorithm 1: d > up_last exactly when
+    RN(d / W) > inc, d <= dn_last exactly when RN(d / W) < dec -- checked with numpy's IEEE
+    division on the thresholds' neighbours and on random differences."""
+    rng = np.random.default_rng(seed)
+    model = tracegen.default_model()
+    for _ in range(40):
+        W = int(rng.integers(1, 65))
+        inc = float(rng.choice([rng.uniform(-50, 50), np.inf, -np.inf, 0.0]))
+        dec = float(rng.choice([rng.uniform(-50, 50), np.inf, -np.inf, 0.0]))
+        pol = dict(tracegen.default_policy(), direv_length=W, inc_threshold=inc, dec_threshold=dec)
+        up, dn = mg.policy_fp64_thresholds(pol, model)
+        Wd = np.float64(W)
+        probes = [up, dn] + rng.uniform(-200 * W, 200 * W, size=400).tolist()
+        for t in (up, dn):
+            if np.isfinite(t):
+                probes += [np.nextafter(t, np.inf), np.nextafter(t, -np.inf)]
+        for d in probes:
+            d = np.float64(d)
+            if not np.isfinite(d):
+                continue
+            assert (d / Wd > inc) == (d > up), (W, inc, d, up)
+            assert (d / Wd < dec) == (d <= dn), (W, dec, d, dn)
