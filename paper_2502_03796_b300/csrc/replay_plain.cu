@@ -240,8 +240,8 @@ cudaError_t launch_replay_plain(const PlainParams &p, cudaStream_t stream) {
 cudaError_t launch_replay_literal(const LiteralParams &p, cudaStream_t stream) {
     const int64_t threads = (int64_t)p.n_traces * p.n_lit;
     if (threads <= 0) return cudaSuccess;
-    // few threads per SM: small blocks spread the pairs over every SM
-    const int block = 64;
+    // one latency-bound chain per thread: one warp per block spreads the pairs over all SMs
+    const int block = 32;
     replay_literal_kernel<<<(unsigned)((threads + block - 1) / block), block, 0, stream>>>(p);
     return cudaGetLastError();
 }
