@@ -472,6 +472,36 @@ def test_run_host_matches_device(rp):
         assert np.array_equal(np.asarray(host[k]).view(dev[k].dtype), dev[k]), k
 
 
+def test_run_host_mixed_modes(rp):
+    """Host-buffer replay routes every mode the same way as the device call."""
+    ts = tracegen.batched(24, 9_000, seed=5)
+    pols = [tracegen.default_policy()] + literal_policies()
+    dev = to_numpy(rp.run(to_device(ts), ts.lengths, pols, log_capacity=3000))
+    host = rp.run_host(ts.data, ts.lengths, pols, log_capacity=3000)
+    for k in ("energy_j", "edp_js", "time_s", "n_changes", "change_hash", "n_hf", "log"):
+        assert np.array_equal(np.asarray(host[k]).view(dev[k].dtype), dev[k]), k
+
+
+def test_segment_buffers_over_budget_fall_back_to_tiles(mg):
+    """Asked for the segment kernel with a log scratch larger than the handle's budget, the
+    call runs the tile kernel instead (one kernel per replay) with the same results."""
+    model = tracegen.default_model()
+    ts = tracegen.batched(64, 60_000, seed=9)
+    pols = [tracegen.default_policy()]
+    cap = 20_000                            # < n: scratch of 4 segments x 16,384 x 4 B per pair
+    small = mg.Replay(model, mem_budget=8 << 20)
+    try:
+        small.set_segments(16384)
+        out = to_numpy(small.run(to_device(ts), ts.lengths, pols, log_capacity=cap))
+        tot, main, runs, kernels = small.kernel_time(detail=True)
+        assert small.status() == 0 and runs == 1 and kernels == 1
+    finally:
+        small.close()
+    ref = oracle_pairs(ts, pols, model, pairs=range(0, 64, 7))
+    for p, r in ref.items():
+        assert_pair(out, p, r, cap=cap, tag="budget fallback")
+
+
 def test_sweep_grid_scaled(rp):
     ts = tracegen.sweep(n_traces=6, n=40_000, seed=0)
     pols = tracegen.sweep_policies()
