@@ -579,9 +579,21 @@ def main() -> int:
         for _ in range(ksteps):
             rp.run_host(host_tr, ts.lengths, [policy], out=hout)
         edt = time.perf_counter() - t0
+        # the bound of this path: the host-to-device link, measured with one plain pinned
+        # copy of the same bytes outside the timed loop
+        dst = torch.empty(ts.data.nbytes // 4, dtype=torch.int32, device=dev)
+        dst.copy_(pinned, non_blocking=True)
+        torch.cuda.synchronize(dev)
+        t1 = time.perf_counter()
+        dst.copy_(pinned, non_blocking=True)
+        torch.cuda.synchronize(dev)
+        link_gbs = ts.data.nbytes / (time.perf_counter() - t1) / 1e9
+        del dst
+        h2d_gbs = ts.data.nbytes * ksteps / edt / 1e9
         line["e2e"] = dict(value=samples_per_step * ksteps / edt, unit="samples/s",
                            h2d_bytes_per_step=int(ts.data.nbytes), d2h_bytes_per_step=48 * n_pairs,
-                           steps=ksteps, api="magus_replay_run_host")
+                           steps=ksteps, api="magus_replay_run_host",
+                           h2d_gbs=h2d_gbs, link_gbs=link_gbs, link_frac=h2d_gbs / link_gbs)
         rp.kernel_time()
 
     if rank == 0 and not args.no_savings:
