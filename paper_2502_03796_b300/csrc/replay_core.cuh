@@ -20,8 +20,6 @@ namespace core {
 constexpr uint32_t FULL = 0xffffffffu;
 constexpr int32_t kFastLimit = 1 << 30;   // fast path: every delta below 2^30
 
-__device__ __forceinline__ uint32_t rotl(uint32_t x, int s) { return __funnelshift_l(x, x, s); }
-__device__ __forceinline__ uint32_t rotr(uint32_t x, int s) { return __funnelshift_r(x, x, s); }
 
 // SplitMix64 output function (Steele, Lea, Flood 2014): hashes change-log entries.
 __device__ __forceinline__ uint64_t mix64(uint64_t z) {

@@ -279,13 +279,29 @@ __global__ void __launch_bounds__(TG * CW * 32) replay_tp_kernel(const TpParams 
 
                 // ------------------------------------------------------------ phase C
                 const MemberCarry cr = sh.carry[cw][m][c & 1];
+                // level entering this sub-block and the chunk's changes before it
                 uint32_t wcin = cr.level;
-                uint64_t before = 0;   // changes of earlier sub-blocks of this chunk
-                for (int gg = 0; gg < g; gg++) {
-                    const uint32_t sv = sh.xs[cw][m][gg];
-                    if (sv & 1u) {
-                        before += (sv >> 3) + ((((sv >> 2) & 1u) != wcin) ? 1u : 0u);
-                        wcin = (sv >> 1) & 1u;
+                uint64_t before = 0;
+                if constexpr (TG >= 4) {
+                    // lane i holds sub-block i's summary: the last earlier sub-block with an
+                    // event sets the level (a ballot); each earlier sub-block adds its own
+                    // changes plus one if its first event flips the level it entered with.
+                    // Branch-free, so the warps of a chunk reach the next barrier together.
+                    const uint32_t sv_i = lane < TG ? sh.xs[cw][m][lane] : 0u;
+                    const uint32_t hasb = __ballot_sync(FULL, sv_i & 1u), exb = __ballot_sync(FULL, (sv_i >> 1) & 1u);
+                    const uint32_t prior_i = hasb & lanemask_lt;
+                    const uint32_t lin_i = prior_i ? (exb >> (31 - __clz(prior_i))) & 1u : cr.level;
+                    const uint32_t add_i = (sv_i & 1u) ? (sv_i >> 3) + ((((sv_i >> 2) & 1u) != lin_i) ? 1u : 0u) : 0u;
+                    before = __reduce_add_sync(FULL, lane < g ? add_i : 0u);
+                    const uint32_t prior_g = hasb & ((1u << g) - 1u);
+                    if (prior_g) wcin = (exb >> (31 - __clz(prior_g))) & 1u;
+                } else {
+                    for (int gg = 0; gg < g; gg++) {
+                        const uint32_t sv = sh.xs[cw][m][gg];
+                        if (sv & 1u) {
+                            before += (sv >> 3) + ((((sv >> 2) & 1u) != wcin) ? 1u : 0u);
+                            wcin = (sv >> 1) & 1u;
+                        }
                     }
                 }
                 const uint32_t cin = prior ? cin_prior : wcin;

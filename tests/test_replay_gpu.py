@@ -463,13 +463,23 @@ def test_empty_inputs(rp):
     assert out["energy_j"].numel() == 0
 
 
+def same_outputs(host, dev, cap):
+    """run_host against run: every output, the log up to each pair's change count (slots
+    past it are unspecified)."""
+    for k in ("energy_j", "edp_js", "time_s", "n_changes", "change_hash", "n_hf"):
+        assert np.array_equal(np.asarray(host[k]).view(dev[k].dtype), dev[k]), k
+    hl = np.asarray(host["log"]).view(np.uint32)
+    for p, k in enumerate(dev["n_changes"]):
+        k = min(int(k), cap)
+        assert np.array_equal(hl[p * cap:p * cap + k], dev["log"][p * cap:p * cap + k]), ("log", p)
+
+
 def test_run_host_matches_device(rp):
     ts = tracegen.batched(64, 10_000, seed=2)
     pols = tracegen.sweep_policies()[:5]
     dev = to_numpy(rp.run(to_device(ts), ts.lengths, pols, log_capacity=2000))
     host = rp.run_host(ts.data, ts.lengths, pols, log_capacity=2000)
-    for k in ("energy_j", "edp_js", "time_s", "n_changes", "change_hash", "n_hf", "log"):
-        assert np.array_equal(np.asarray(host[k]).view(dev[k].dtype), dev[k]), k
+    same_outputs(host, dev, 2000)
 
 
 def test_run_host_mixed_modes(rp):
@@ -478,8 +488,7 @@ def test_run_host_mixed_modes(rp):
     pols = [tracegen.default_policy()] + literal_policies()
     dev = to_numpy(rp.run(to_device(ts), ts.lengths, pols, log_capacity=3000))
     host = rp.run_host(ts.data, ts.lengths, pols, log_capacity=3000)
-    for k in ("energy_j", "edp_js", "time_s", "n_changes", "change_hash", "n_hf", "log"):
-        assert np.array_equal(np.asarray(host[k]).view(dev[k].dtype), dev[k]), k
+    same_outputs(host, dev, 3000)
 
 
 def test_segment_buffers_over_budget_fall_back_to_tiles(mg):
