@@ -206,7 +206,14 @@ __global__ void __launch_bounds__(TG * CW * 32) replay_tp_kernel(const TpParams 
                 const uint32_t prev = stage_base(s ^ 1) + (uint32_t)(CH_ROWS - 2) * 128u;
                 for (int k = lane; k < HALO; k += 32) core::sts32(sbase - 256u + 4u * k, core::lds32(prev + 4u * k));
             }
-            __syncthreads();
+            if constexpr (CW == 1) {
+                // only warp 0 reads rows -2, -1 (the other warps' preceding rows lie inside the
+                // stage), and it copied them itself; every warp left the previous stage at the
+                // barrier above, so the next copy may overwrite it once warp 0's reads are done
+                __syncwarp();
+            } else {
+                __syncthreads();   // the first warp of every policy slot reads the halo
+            }
             if (tid == 0 && c + 1 < nchunks) issue(c + 1, sq + 1);
             if (!active) continue;
 
