@@ -37,6 +37,7 @@ namespace magus {
 namespace {
 
 using tma::mbar_init;
+using tma::mbar_arrive;
 using tma::fence_mbar_init;
 using tma::mbar_expect_tx;
 using tma::mbar_wait_bounded;
@@ -59,7 +60,8 @@ struct MemberCarry {
 
 template <int TG, int CW, int GP>
 struct Shared {
-    uint64_t bar[2];
+    uint64_t bar[2];                  // stage s holds its chunk (copy complete)
+    uint64_t empty[2];                // stage s is free again (every warp done with it; one slot)
     uint64_t xf[CW][TG];              // flags of the last 64 rounds of each sub-block
     uint64_t hist[CW][2];             // flags of the 64 rounds before the chunk (by parity)
     uint32_t xs[CW][GP][TG];          // sub-block summary: has | exit<<1 | first<<2 | nch<<3
@@ -106,6 +108,8 @@ __global__ void __launch_bounds__(TG * CW * 32) replay_tp_kernel(const TpParams 
     if (tid == 0) {
         mbar_init(&sh.bar[0], 1);
         mbar_init(&sh.bar[1], 1);
+        mbar_init(&sh.empty[0], TG);
+        mbar_init(&sh.empty[1], TG);
         fence_mbar_init();
         sh.abort = 0;
     }
@@ -188,33 +192,64 @@ __global__ void __launch_bounds__(TG * CW * 32) replay_tp_kernel(const TpParams 
             const uint32_t sq = seq + c;
             const int s = (int)(sq & 1);
             const uint32_t sbase = stage_base(s);
-            if (tid == 0) {
-                if (!mbar_wait_bounded(&sh.bar[s], (sq >> 1) & 1)) {
-                    atomicCAS(p.status, 0, MAGUS_ETIMEDOUT);
-                    sh.abort = 1;
-                } else {
-                    pend[s] = -1;
-                }
-            }
-            __syncthreads();
-            if (sh.abort) break;
-            // every thread observes the completed phase (acquire of the bulk-copy data)
-            if (tid != 0) (void)mbar_wait_bounded(&sh.bar[s], (sq >> 1) & 1);
-            if (c > 0 && warp == 0) {
-                // the previous chunk's last two rows become rows -2, -1 (same swizzle phase:
-                // CH_ROWS is a multiple of 8)
-                const uint32_t prev = stage_base(s ^ 1) + (uint32_t)(CH_ROWS - 2) * 128u;
-                for (int k = lane; k < HALO; k += 32) core::sts32(sbase - 256u + 4u * k, core::lds32(prev + 4u * k));
-            }
             if constexpr (CW == 1) {
-                // only warp 0 reads rows -2, -1 (the other warps' preceding rows lie inside the
-                // stage), and it copied them itself; every warp left the previous stage at the
-                // barrier above, so the next copy may overwrite it once warp 0's reads are done
-                __syncwarp();
+                // One policy slot: no CTA barrier per chunk.  Every warp waits for its stage
+                // itself; a stage is refilled once all TG warps have released it (empty
+                // barrier), so a warp that finishes a chunk early starts the next one.  A
+                // bounded wait that gives up marks the CTA aborted; later waits are skipped
+                // and the chunk loop runs to the end of the item, where the CTA stops.
+                if (!*(volatile int *)&sh.abort) {
+                    if (mbar_wait_bounded(&sh.bar[s], (sq >> 1) & 1)) {
+                        if (tid == 0) pend[s] = -1;
+                    } else {
+                        atomicCAS(p.status, 0, MAGUS_ETIMEDOUT);
+                        sh.abort = 1;
+                    }
+                }
+                if (warp == 0) {
+                    if (c > 0) {
+                        // the previous chunk's last two rows become rows -2, -1 (same swizzle
+                        // phase: CH_ROWS is a multiple of 8); only warp 0 reads them
+                        const uint32_t prev = stage_base(s ^ 1) + (uint32_t)(CH_ROWS - 2) * 128u;
+                        for (int k = lane; k < HALO; k += 32)
+                            core::sts32(sbase - 256u + 4u * k, core::lds32(prev + 4u * k));
+                    }
+                    __syncwarp();
+                    if (lane == 0 && c + 1 < nchunks && !*(volatile int *)&sh.abort) {
+                        // stage s ^ 1 last held chunk sq - 1: wait until every warp released it
+                        bool free = true;
+                        if (sq >= 1) free = mbar_wait_bounded(&sh.empty[s ^ 1], ((sq - 1) >> 1) & 1);
+                        if (free) {
+                            issue(c + 1, sq + 1);
+                        } else {
+                            atomicCAS(p.status, 0, MAGUS_ETIMEDOUT);
+                            sh.abort = 1;
+                        }
+                    }
+                }
             } else {
+                if (tid == 0) {
+                    if (!mbar_wait_bounded(&sh.bar[s], (sq >> 1) & 1)) {
+                        atomicCAS(p.status, 0, MAGUS_ETIMEDOUT);
+                        sh.abort = 1;
+                    } else {
+                        pend[s] = -1;
+                    }
+                }
+                __syncthreads();
+                if (sh.abort) break;
+                // every thread observes the completed phase (acquire of the bulk-copy data)
+                if (tid != 0) (void)mbar_wait_bounded(&sh.bar[s], (sq >> 1) & 1);
+                if (c > 0 && warp == 0) {
+                    // the previous chunk's last two rows become rows -2, -1 (same swizzle
+                    // phase: CH_ROWS is a multiple of 8)
+                    const uint32_t prev = stage_base(s ^ 1) + (uint32_t)(CH_ROWS - 2) * 128u;
+                    for (int k = lane; k < HALO; k += 32)
+                        core::sts32(sbase - 256u + 4u * k, core::lds32(prev + 4u * k));
+                }
                 __syncthreads();   // the first warp of every policy slot reads the halo
+                if (tid == 0 && c + 1 < nchunks) issue(c + 1, sq + 1);
             }
-            if (tid == 0 && c + 1 < nchunks) issue(c + 1, sq + 1);
             if (!active) continue;
 
             // ---------------------------------------------------------------- phase A
@@ -350,7 +385,13 @@ __global__ void __launch_bounds__(TG * CW * 32) replay_tp_kernel(const TpParams 
                     core::read_hist(sub, 32 * lane + pl, so.hist);
                 }
             }
+            if constexpr (CW == 1) {
+                // this warp is done with the chunk's stage
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&sh.empty[s]);
+            }
         }
+        if constexpr (CW == 1) __syncthreads();   // every warp sees the same abort flag
         if (sh.abort) break;
         seq += nchunks;
 
