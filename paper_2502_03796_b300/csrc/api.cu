@@ -52,6 +52,7 @@ int ensure_ws(magus_replay *h, void **buf, size_t *size, size_t need) {
         return MAGUS_ENOMEM;
     }
     if (h->ws_ev_pending) CK(cudaEventSynchronize(h->ws_ev), "cudaEventSynchronize");
+    if (buf == &h->ws) h->ws_plan_valid = false;
     if (*buf) CK(cudaFree(*buf), "cudaFree");
     *buf = nullptr;
     *size = 0;
@@ -166,6 +167,7 @@ int plain_impl(magus_replay *h, const uint32_t *traces, const uint64_t *lengths,
         if (rc) return rc;
         memcpy(h->pin[slot], pols.data(), sz);
         if (h->ws_ev_pending) CK(cudaStreamWaitEvent(s, h->ws_ev, 0), "cudaStreamWaitEvent");
+        h->ws_plan_valid = false;
         CK(cudaMemcpyAsync(h->ws, h->pin[slot], sz, cudaMemcpyHostToDevice, s), "cudaMemcpyAsync");
         CK(cudaEventRecord(h->pin_ev[slot], s), "cudaEventRecord");
         h->pin_pending[slot] = true;

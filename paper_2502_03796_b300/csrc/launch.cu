@@ -242,11 +242,16 @@ int launch_plan(magus_replay *h, const Plan &pl, const uint32_t *traces, const O
     }
     if (!pl.lit.empty()) memcpy(pin + sz_pol + sz_grp + sz_items + 2 * sz_off, pl.lit.data(), pl.lit.size() * 4);
     if (!pl.lad.empty()) memcpy(pin + off_lad, pl.lad.data(), pl.lad.size() * sizeof(LadderItem));
-    if (h->ws_ev_pending) CK(cudaStreamWaitEvent(stream, h->ws_ev, 0), "cudaStreamWaitEvent");
     char *ws = (char *)h->ws;
-    CK(cudaMemcpyAsync(ws, pin, total, cudaMemcpyHostToDevice, stream), "cudaMemcpyAsync(plan)");
-    CK(cudaEventRecord(h->pin_ev[slot], stream), "cudaEventRecord");
-    h->pin_pending[slot] = true;
+    const bool same_plan = h->ws_plan_valid && h->ws_plan.size() == total && !memcmp(h->ws_plan.data(), pin, total);
+    if (!same_plan) {
+        if (h->ws_ev_pending) CK(cudaStreamWaitEvent(stream, h->ws_ev, 0), "cudaStreamWaitEvent");
+        CK(cudaMemcpyAsync(ws, pin, total, cudaMemcpyHostToDevice, stream), "cudaMemcpyAsync(plan)");
+        CK(cudaEventRecord(h->pin_ev[slot], stream), "cudaEventRecord");
+        h->pin_pending[slot] = true;
+        h->ws_plan.assign(pin, pin + total);
+        h->ws_plan_valid = true;
+    }
     CK(cudaMemsetAsync(h->queue, 0, sizeof(unsigned int), stream), "cudaMemsetAsync");
 
     TpParams p;
@@ -420,6 +425,7 @@ int launch_seg_plan(magus_replay *h, const Plan &pl, const uint32_t *traces, con
     if (!pl.lad.empty()) memcpy(pin + off_lad, pl.lad.data(), pl.lad.size() * sizeof(LadderItem));
     if (h->ws_ev_pending) CK(cudaStreamWaitEvent(stream, h->ws_ev, 0), "cudaStreamWaitEvent");
     char *ws = (char *)h->ws;
+    h->ws_plan_valid = false;
     CK(cudaMemcpyAsync(ws, pin, total, cudaMemcpyHostToDevice, stream), "cudaMemcpyAsync(plan)");
     CK(cudaEventRecord(h->pin_ev[slot], stream), "cudaEventRecord");
     h->pin_pending[slot] = true;

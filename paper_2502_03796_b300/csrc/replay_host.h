@@ -26,6 +26,10 @@ struct magus_replay {
     size_t ws_size = 0;
     cudaEvent_t ws_ev = nullptr;      // last use of the workspace
     bool ws_ev_pending = false;
+    // the tile-kernel plan now in the workspace (a repeated call with the same plan skips
+    // the upload and with it the wait for the previous launch)
+    std::vector<char> ws_plan;
+    bool ws_plan_valid = false;
     // pinned staging ring for plan uploads
     void *pin[2] = {nullptr, nullptr};
     size_t pin_size[2] = {0, 0};
