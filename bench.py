@@ -332,7 +332,9 @@ def run_other(args, world, rank, local) -> int:
         ts = tracegen.batched(n_traces=args.traces, seed=rank, first_id=rank * args.traces)
         mode = 1 if args.workload == "ladder" else 2
         pols = [dict(tracegen.default_policy(), step_mode=mode)]
-        desc = (f"batched replay, {'one rung per decision (ladder kernel)' if mode == 1 else 'closed loop (literal kernel)'}: "
+        kern = "ladder kernel" if mode == 1 else ("literal kernel" if args.closed.startswith("-1") else
+                                                  "segmented closed-loop kernels")
+        desc = (f"batched replay, {'one rung per decision' if mode == 1 else 'closed loop'} ({kern}): "
                 f"{args.traces} traces x 100000 intervals (phase mean 40), 1 policy")
     elif args.workload == "long":
         ts = tracegen.batched(n_traces=16, n=4_000_000, seed=rank, first_id=rank * 16)
@@ -356,6 +358,8 @@ def run_other(args, world, rank, local) -> int:
     if args.tile:
         rp.set_tile(*[int(x) for x in args.tile.split(",")])
     rp.set_segments(args.segments)
+    if args.closed:
+        rp.set_closed(*[int(x) for x in args.closed.split(",")])
     if args.workload in ("sweep", "uneven") and not args.tile and args.segments < 0:
         tuned, tms = rp.autotune(d_tr, ts.lengths, pols, stream=stream)
     rp.kernel_time()
@@ -379,6 +383,9 @@ def run_other(args, world, rank, local) -> int:
                               traffic=None, kernel_ms=k_avg, main_kernel_ms=k_main / max(k_n, 1),
                               alg_bytes_per_launch=alg_bytes),
                 gpu_launches=k_kernels, clocks=clk)
+    if args.workload == "closed":
+        segs, second, final = rp.closed_stats()
+        line["config"]["closed_replay"] = dict(segments=segs, second_replays=second, final_pass_replays=final)
     # many policies per byte read: the integer ALU pipe bounds these launches; report that
     # roofline (ncu lane-operations per (interval, policy), committed with the source hash,
     # against 148 SMs x 64 integer lanes per cycle at the sampled SM clock)
@@ -451,6 +458,8 @@ def main() -> int:
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--tile", default="", help="time_groups,policy_slots (default: automatic)")
+    ap.add_argument("--closed", default="",
+                    help="closed loop: seg_rounds[,burn_rounds] (default automatic; -1: literal kernel)")
     ap.add_argument("--segments", type=int, default=-1,
                     help="-1 automatic, 0 tile kernel, >0 segment kernel with this many rounds per segment")
     ap.add_argument("--traces", type=int, default=N_TRACES, help="traces per GPU (profiling runs use fewer)")

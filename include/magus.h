@@ -135,10 +135,13 @@ int magus_replay_open(magus_replay_t **h, const magus_model_t *model, int device
 
 /* Replay n_traces x n_configs (trace, policy) pairs (rounds above).  Policies in the open-loop
  * jump mode (step_mode 0, pin_level 0, 1 or n_levels) run on the time-parallel kernels (tile
- * or segment kernel); the others (one rung per decision, closed loop, a pin inside the
- * ladder) run in the same call on the literal kernel, one thread per pair.  With io_state a
- * closed-loop policy needs a fresh state (n_seen 0; else EINVAL through
- * magus_replay_status): its throughput FIFO would need past levels.
+ * or segment kernel), the one-rung mode (step_mode 1, pin_level 0) on the ladder kernel, the
+ * closed loop in jump mode (step_mode 2, pin_level 0) on the segmented closed-loop kernels
+ * (magus_replay_set_closed); the others (closed loop one rung per decision, a pin inside
+ * the ladder or under a closed loop) run in the same call on the literal kernel, one
+ * thread per pair.  With io_state a closed-loop policy needs a fresh state (n_seen 0; else
+ * EINVAL through magus_replay_status): its throughput FIFO would need past levels; in jump
+ * mode its carried level must be 0 or n_levels - 1.
  *   traces     device, packed layout; base address 16-byte aligned
  *   lengths    host [n_traces] intervals per trace (0 allowed)
  *   configs    host [n_configs], 1 <= n_configs <= 4096
@@ -207,6 +210,21 @@ int magus_replay_set_tile(magus_replay_t *h, int32_t time_groups, int32_t policy
  * otherwise. */
 int magus_replay_set_segments(magus_replay_t *h, int32_t seg_rounds);
 
+/* Closed loop in jump mode (step_mode 2, pin_level 0): replayed time-parallel.  Every
+ * (trace, policy, segment of seg_rounds rounds) is replayed on its own from a guessed state
+ * burn_rounds earlier; a segment whose guess did not reach the state its predecessor ended
+ * in is replayed again, and a final pass per pair takes the replays that started from the
+ * true state (results identical to the sequential replay whatever the guesses).
+ * seg_rounds: 0 automatic (about four waves of threads, 1,024 .. 65,536), > 0 a multiple of
+ * 64 up to 2^24, -1 the literal kernel (one thread per pair); burn_rounds: -1 automatic
+ * (seg_rounds / 4), else a multiple of 64 up to 2^24.  EINVAL otherwise. */
+int magus_replay_set_closed(magus_replay_t *h, int32_t seg_rounds, int32_t burn_rounds);
+
+/* Work of the last call's time-parallel closed-loop replay (host, 3 values): segments
+ * replayed, second replays, replays in the final pass (0, 0, 0 when it did not run).  Waits
+ * for the handle's outstanding launches. */
+int magus_replay_closed_stats(magus_replay_t *h, uint64_t *out3);
+
 /* Autotuner: time every supported tile shape (time_groups x policy_slots x group size 1 or
  * 4) of the tile kernel and the segment kernel (segments of 8,192 / 16,384 / 32,768 rounds,
  * group size 1 or 4) on the given (device, packed) workload and keep the fastest for later
@@ -269,6 +287,19 @@ int magus_policy_bounds(const magus_policy_t *policy, const magus_model_t *model
  * RN(d / W) > inc holds exactly when d > out[0], and RN(d / W) < dec exactly when
  * d <= out[1] (+-infinity when never / always). */
 int magus_policy_fp64_thresholds(const magus_policy_t *policy, const magus_model_t *model, double out[2]);
+
+/* Closed-loop decision thresholds the segmented closed-loop kernels derive for one policy
+ * (diagnostics and tests).  For level l = 0 (bottom) and 1 (top of the ladder), with
+ * x(delta) = bytes_per_count * delta / (dt * 1e9) in FP64 and C_l the capacity there:
+ *   out[0 + l]  largest delta with x(delta) <= C_l (a throughput is capped above it);
+ *   out[2 + l]  Algorithm 1 gives +1 for obs_t = C_l, obs_{t-W} = x(b) exactly when b < out[2 + l];
+ *   out[4 + l]  ... gives -1 there exactly when b >= out[4 + l];
+ *   out[6 + l]  +1 for obs_t = x(a), obs_{t-W} = C_l exactly when a >= out[6 + l];
+ *   out[8 + l]  -1 there exactly when a < out[8 + l];
+ *   out[10]     both capped (levels la, lb): bit 2 la + lb set when +1, bit 4 + 2 la + lb
+ *               when -1 (before Algorithm 1's preference of +1).
+ * Thresholds range over 0 .. 2^32. */
+int magus_policy_closed_thresholds(const magus_policy_t *policy, const magus_model_t *model, int64_t out[11]);
 
 const char *magus_last_error(void);
 const char *magus_version(void);

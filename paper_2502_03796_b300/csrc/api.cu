@@ -45,7 +45,7 @@ size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 int ensure_ws(magus_replay *h, void **buf, size_t *size, size_t need) {
     if (need <= *size) return MAGUS_OK;
     size_t want = std::max(need, *size * 2);
-    size_t other = h->ws_size + h->scratch_size + h->seg_size - *size;
+    size_t other = h->ws_size + h->scratch_size + h->seg_size + h->cls_size - *size;
     if (want + other > h->budget) want = need;
     if (want + other > h->budget) {
         set_error("device workspace of " + std::to_string(need) + " bytes exceeds the handle's memory budget");
@@ -255,6 +255,28 @@ int magus_policy_fp64_thresholds(const magus_policy_t *policy, const magus_model
     return MAGUS_OK;
 }
 
+int magus_policy_closed_thresholds(const magus_policy_t *policy, const magus_model_t *model, int64_t out[11]) {
+    if (!policy || !model || !out) { set_error("NULL argument"); return MAGUS_EINVAL; }
+    std::string err;
+    DevModel dm;
+    int rc = derive_model(*model, &dm, &err);
+    if (rc) { set_error(err); return rc; }
+    DevPolicy dp;
+    rc = derive_policy(*policy, *model, &dp, &err);
+    if (rc) { set_error(err); return rc; }
+    ClosedThr c;
+    derive_closed(dp, dm, &c);
+    for (int l = 0; l < 2; l++) {
+        out[0 + l] = c.cthr[l];
+        out[2 + l] = c.bu[l];
+        out[4 + l] = c.bd[l];
+        out[6 + l] = c.au[l];
+        out[8 + l] = c.ad[l];
+    }
+    out[10] = c.cc;
+    return MAGUS_OK;
+}
+
 int magus_replay_open(magus_replay_t **out, const magus_model_t *model, int device, size_t mem_budget) {
     if (!out || !model) { set_error("NULL argument"); return MAGUS_EINVAL; }
     *out = nullptr;
@@ -309,6 +331,7 @@ int magus_replay_close(magus_replay_t *h) {
     if (h->ws) cudaFree(h->ws);
     if (h->scratch) cudaFree(h->scratch);
     if (h->segbuf) cudaFree(h->segbuf);
+    if (h->clsbuf) cudaFree(h->clsbuf);
     if (h->status) cudaFree(h->status);
     if (h->ws_ev) cudaEventDestroy(h->ws_ev);
     delete h;
@@ -337,6 +360,34 @@ int magus_replay_set_segments(magus_replay_t *h, int32_t seg_rounds) {
         return MAGUS_EINVAL;
     }
     h->seg_rounds = seg_rounds;
+    return MAGUS_OK;
+}
+
+int magus_replay_set_closed(magus_replay_t *h, int32_t seg_rounds, int32_t burn_rounds) {
+    if (!h) { set_error("NULL handle"); return MAGUS_EINVAL; }
+    if (seg_rounds < -1 || (seg_rounds > 0 && (seg_rounds % 64 != 0 || seg_rounds > (1 << 24)))) {
+        set_error("closed-loop segment rounds must be -1 (literal kernel), 0 (automatic) or a multiple of 64 up to 2^24");
+        return MAGUS_EINVAL;
+    }
+    if (burn_rounds < -1 || (burn_rounds >= 0 && (burn_rounds % 64 != 0 || burn_rounds > (1 << 24)))) {
+        set_error("burn-in rounds must be -1 (automatic) or a multiple of 64 up to 2^24");
+        return MAGUS_EINVAL;
+    }
+    h->cls_seg = seg_rounds;
+    h->cls_burn = burn_rounds;
+    return MAGUS_OK;
+}
+
+int magus_replay_closed_stats(magus_replay_t *h, uint64_t *out3) {
+    if (!h || !out3) { set_error("NULL argument"); return MAGUS_EINVAL; }
+    out3[0] = out3[1] = out3[2] = 0;
+    if (!h->cls_stats) return MAGUS_OK;
+    if (h->ws_ev_pending) CK(cudaEventSynchronize(h->ws_ev), "cudaEventSynchronize");
+    unsigned long long st[2] = {0, 0};
+    CK(cudaMemcpy(st, h->cls_stats, sizeof(st), cudaMemcpyDeviceToHost), "cudaMemcpy(closed stats)");
+    out3[0] = h->cls_items;
+    out3[1] = st[0];
+    out3[2] = st[1];
     return MAGUS_OK;
 }
 

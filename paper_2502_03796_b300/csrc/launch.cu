@@ -1,6 +1,7 @@
 // launch.cu - planning (kernel choice, policy routing, work items) and the launches of the
 // replay kernels: tile or segment kernel for the jump mode, ladder kernel for the one-rung
-// mode, literal kernel for the rest.
+// mode, the segmented closed-loop kernels for the closed loop in jump mode, literal kernel
+// for the rest.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -96,11 +97,21 @@ int build_plan(magus_replay *h, const uint64_t *lengths, int32_t n_traces, const
     pl->tp.resize(pl->pols.size());
     pl->lit.clear();
     std::vector<int32_t> lad_pols;
+    pl->cls.clear();
+    pl->cthr.clear();
     for (size_t i = 0; i < pl->pols.size(); i++) {
         pl->tp[i] = tp_policy(pl->pols[i], h->model.n_levels) ? 1 : 0;
         if (pl->tp[i]) continue;
-        if (ladder_policy(pl->pols[i])) lad_pols.push_back((int32_t)i);
-        else pl->lit.push_back((int32_t)i);
+        if (ladder_policy(pl->pols[i])) {
+            lad_pols.push_back((int32_t)i);
+        } else if (closed_policy(pl->pols[i])) {
+            pl->cls.push_back((int32_t)i);
+            ClosedThr c;
+            derive_closed(pl->pols[i], h->dm, &c);
+            pl->cthr.push_back(c);
+        } else {
+            pl->lit.push_back((int32_t)i);
+        }
     }
     form_groups(pl->pols, gp, &pl->groups, &pl->tp);
     pl->offsets.resize(n_traces);
@@ -137,7 +148,7 @@ int build_plan(magus_replay *h, const uint64_t *lengths, int32_t n_traces, const
 // one launch (replay_plain.cu).  d_*: the plan as uploaded to the workspace.
 int launch_literal_part(magus_replay *h, const Plan &pl, const uint32_t *traces, const Outs &o,
                         const DevPolicy *d_pols, const uint64_t *d_off, const uint64_t *d_len, const int32_t *d_lit,
-                        cudaStream_t stream) {
+                        int32_t n_lit, cudaStream_t stream) {
     LiteralParams lp;
     memset(&lp, 0, sizeof(lp));
     lp.traces = traces;
@@ -147,7 +158,7 @@ int launch_literal_part(magus_replay *h, const Plan &pl, const uint32_t *traces,
     lp.n_pols = (int32_t)pl.pols.size();
     lp.pols = d_pols;
     lp.lit = d_lit;
-    lp.n_lit = (int32_t)pl.lit.size();
+    lp.n_lit = n_lit;
     lp.model = h->dm;
     lp.energy = o.energy;
     lp.edp = o.edp;
@@ -302,7 +313,8 @@ int launch_plan(magus_replay *h, const Plan &pl, const uint32_t *traces, const O
     }
     const bool has_lit = !pl.lit.empty() && !pl.lengths.empty();
     const bool has_lad = !pl.lad.empty();
-    if (n_items || has_lit || has_lad) {
+    const bool has_cls = !pl.cls.empty() && !pl.lengths.empty();
+    if (n_items || has_lit || has_lad || has_cls) {
         size_t slot_k;
         rc = kev_slot(h, &slot_k);
         if (rc) return rc;
@@ -325,11 +337,17 @@ int launch_plan(magus_replay *h, const Plan &pl, const uint32_t *traces, const O
         }
         if (has_lit) {
             rc = launch_literal_part(h, pl, traces, o, p.pols, p.offsets, p.lengths,
-                                     (const int32_t *)(ws + sz_pol + sz_grp + sz_items + 2 * sz_off), stream);
+                                     (const int32_t *)(ws + sz_pol + sz_grp + sz_items + 2 * sz_off),
+                                     (int32_t)pl.lit.size(), stream);
+            if (rc || (rc = mark())) return rc;
+        }
+        int cls_kernels = 0;
+        if (has_cls) {
+            rc = launch_closed_part(h, pl, traces, o, p.pols, p.offsets, p.lengths, stream, &cls_kernels);
             if (rc || (rc = mark())) return rc;
         }
         CK(cudaEventRecord(h->k_ev[slot_k].b, stream), "cudaEventRecord");
-        h->k_ev[slot_k].kernels = (n_items ? 1 : 0) + (has_lad ? 1 : 0) + (has_lit ? 1 : 0);
+        h->k_ev[slot_k].kernels = (n_items ? 1 : 0) + (has_lad ? 1 : 0) + (has_lit ? 1 : 0) + cls_kernels;
         if (h->k_used < h->k_ev.size()) h->k_used++;
     }
     if (ms_out) {
@@ -402,7 +420,8 @@ int launch_seg_plan(magus_replay *h, const Plan &pl, const uint32_t *traces, con
     const size_t sz_log = align_up(scratch_entries * 4, 256);
     const size_t seg_need = sz_sum + sz_tail + sz_log;
     // the tile kernel needs none of the segment buffers: take it when they do not fit
-    if (std::max(total, h->ws_size) + h->scratch_size + std::max(seg_need, h->seg_size) > h->budget) return kUseTile;
+    if (std::max(total, h->ws_size) + h->scratch_size + h->cls_size + std::max(seg_need, h->seg_size) > h->budget)
+        return kUseTile;
     int rc = ensure_ws(h, &h->ws, &h->ws_size, total);
     if (rc) return rc;
     rc = ensure_ws(h, &h->segbuf, &h->seg_size, seg_need);
@@ -508,12 +527,19 @@ int launch_seg_plan(magus_replay *h, const Plan &pl, const uint32_t *traces, con
     const bool has_lit = !pl.lit.empty() && n_traces > 0;
     if (has_lit) {
         rc = launch_literal_part(h, pl, traces, o, p.pols, p.offsets, p.lengths,
-                                 (const int32_t *)(ws + sz_pol + sz_grp + sz_items + 4 * sz_off), stream);
+                                 (const int32_t *)(ws + sz_pol + sz_grp + sz_items + 4 * sz_off),
+                                 (int32_t)pl.lit.size(), stream);
+        if (rc || (rc = mark())) return rc;
+    }
+    int cls_kernels = 0;
+    if (!pl.cls.empty() && n_traces > 0) {
+        rc = launch_closed_part(h, pl, traces, o, p.pols, p.offsets, p.lengths, stream, &cls_kernels);
         if (rc || (rc = mark())) return rc;
     }
     if ((rc = mark())) return rc;
     CK(cudaEventRecord(h->k_ev[slot_k].b, stream), "cudaEventRecord");
-    h->k_ev[slot_k].kernels = (n_items ? 1 : 0) + ((n_pairs && any_tp) ? 1 : 0) + (has_lad ? 1 : 0) + (has_lit ? 1 : 0);
+    h->k_ev[slot_k].kernels = (n_items ? 1 : 0) + ((n_pairs && any_tp) ? 1 : 0) + (has_lad ? 1 : 0) + (has_lit ? 1 : 0) +
+                              cls_kernels;
     if (h->k_used < h->k_ev.size()) h->k_used++;
     if (ms_out) {
         CK(cudaEventRecord(e1, stream), "cudaEventRecord");
@@ -524,6 +550,108 @@ int launch_seg_plan(magus_replay *h, const Plan &pl, const uint32_t *traces, con
     }
     CK(cudaEventRecord(h->ws_ev, stream), "cudaEventRecord");
     h->ws_ev_pending = true;
+    return MAGUS_OK;
+}
+
+// Closed-loop jump-mode policies (replay_closed.cu): every (trace, policy, time segment)
+// replayed on its own thread from a guessed state, segments whose guess was wrong replayed
+// again, then one thread per pair walks its segments in order.  The literal kernel takes
+// them instead when the segmented replay is switched off or its buffers exceed the budget.
+int launch_closed_part(magus_replay *h, const Plan &pl, const uint32_t *traces, const Outs &o, const DevPolicy *d_pols,
+                       const uint64_t *d_off, const uint64_t *d_len, cudaStream_t stream, int *kernels) {
+    const int n_traces = (int)pl.lengths.size();
+    const int n_cls = (int)pl.cls.size();
+    h->cls_items = 0;
+    h->cls_stats = nullptr;
+    if (n_cls == 0 || n_traces == 0) return MAGUS_OK;
+    // segment length: about four waves of threads (8 CTAs of 128 per SM) over all pairs'
+    // rounds, 1,024 .. 65,536; burn-in a quarter of it
+    uint64_t total_rounds = 0;
+    for (uint64_t n : pl.lengths) total_rounds += n;
+    total_rounds *= (uint64_t)n_cls;
+    const uint64_t resident = (uint64_t)h->sms * 8 * closed_threads_per_cta();
+    uint64_t S = h->cls_seg > 0 ? (uint64_t)h->cls_seg
+                                : std::min<uint64_t>(65536, std::max<uint64_t>(1024, align_up(total_rounds / (4 * resident), 64)));
+    const uint64_t G = h->cls_burn >= 0 ? (uint64_t)h->cls_burn : S / 4;
+    int wmax = 1;
+    for (int32_t c : pl.cls) wmax = std::max(wmax, pl.pols[c].W);
+    uint32_t ring = 1;
+    while ((int)ring < wmax) ring <<= 1;
+    std::vector<uint64_t> ibase(n_traces + 1);
+    uint64_t items = 0;
+    for (int i = 0; i < n_traces; i++) {
+        ibase[i] = items;
+        items += (pl.lengths[i] + S - 1) / S * (uint64_t)n_cls;
+    }
+    ibase[n_traces] = items;
+    const bool logging = o.log_entries && o.log_cap > 0;
+    const uint64_t scr_cap = logging ? std::min<uint64_t>(S, std::max<uint64_t>(64, S / 8)) : 0;
+    // buffer: policies | thresholds | item bases | counters | replay slots | entry scratch
+    const size_t sz_cls = align_up((size_t)n_cls * 4, 256);
+    const size_t sz_thr = align_up((size_t)n_cls * sizeof(ClosedThr), 256);
+    const size_t sz_ib = align_up((size_t)(n_traces + 1) * 8, 256);
+    const size_t plan_bytes = sz_cls + sz_thr + sz_ib;
+    const size_t sz_st = 256;
+    const size_t sz_slot = align_up((size_t)(2 * items) * sizeof(ClosedSlot), 256);
+    const size_t sz_scr = align_up((size_t)(2 * items * scr_cap) * 4, 256);
+    const size_t need = plan_bytes + sz_st + sz_slot + sz_scr;
+    const bool segmented = h->cls_seg >= 0 && items <= (uint64_t)INT32_MAX * closed_threads_per_cta() &&
+                           h->ws_size + h->scratch_size + h->seg_size + std::max(need, h->cls_size) <= h->budget;
+    int rc = ensure_ws(h, &h->clsbuf, &h->cls_size, segmented ? need : sz_cls);
+    if (rc) return rc;
+    char *buf = (char *)h->clsbuf;
+    std::vector<char> blob(segmented ? plan_bytes : sz_cls, 0);
+    memcpy(blob.data(), pl.cls.data(), (size_t)n_cls * 4);
+    if (segmented) {
+        memcpy(blob.data() + sz_cls, pl.cthr.data(), (size_t)n_cls * sizeof(ClosedThr));
+        memcpy(blob.data() + sz_cls + sz_thr, ibase.data(), (size_t)(n_traces + 1) * 8);
+    }
+    // the previous call's kernels may still read the buffer
+    if (h->ws_ev_pending) CK(cudaStreamWaitEvent(stream, h->ws_ev, 0), "cudaStreamWaitEvent");
+    CK(cudaMemcpyAsync(buf, blob.data(), blob.size(), cudaMemcpyHostToDevice, stream), "cudaMemcpyAsync(closed plan)");
+    if (!segmented) {
+        rc = launch_literal_part(h, pl, traces, o, d_pols, d_off, d_len, (const int32_t *)buf, n_cls, stream);
+        if (rc) return rc;
+        *kernels += 1;
+        return MAGUS_OK;
+    }
+    unsigned long long *stats = (unsigned long long *)(buf + plan_bytes);
+    CK(cudaMemsetAsync(stats, 0, 2 * sizeof(unsigned long long), stream), "cudaMemsetAsync");
+    ClosedParams cp;
+    memset(&cp, 0, sizeof(cp));
+    cp.traces = traces;
+    cp.offsets = d_off;
+    cp.lengths = d_len;
+    cp.n_traces = n_traces;
+    cp.n_pols = (int32_t)pl.pols.size();
+    cp.pols = d_pols;
+    cp.cls = (const int32_t *)buf;
+    cp.thr = (const ClosedThr *)(buf + sz_cls);
+    cp.n_cls = n_cls;
+    cp.ring = ring;
+    cp.ibase = (const uint64_t *)(buf + sz_cls + sz_thr);
+    cp.n_items = items;
+    cp.seg_len = (uint32_t)S;
+    cp.burn = (uint32_t)G;
+    cp.model = h->dm;
+    cp.slots = (ClosedSlot *)(buf + plan_bytes + sz_st);
+    cp.scratch = scr_cap ? (uint32_t *)(buf + plan_bytes + sz_st + sz_slot) : nullptr;
+    cp.scr_cap = scr_cap;
+    cp.energy = o.energy;
+    cp.edp = o.edp;
+    cp.time = o.time;
+    cp.log_entries = o.log_entries;
+    cp.log_cap = o.log_cap;
+    cp.n_changes = o.n_changes;
+    cp.change_hash = o.change_hash;
+    cp.n_hf = o.n_hf;
+    cp.state = o.state;
+    cp.status = h->status;
+    cp.stats = stats;
+    CK(launch_replay_closed(cp, stream), "closed-loop kernel launch");
+    *kernels += items ? 3 : 1;
+    h->cls_items = items;
+    h->cls_stats = stats;
     return MAGUS_OK;
 }
 

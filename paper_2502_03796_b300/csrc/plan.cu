@@ -147,6 +147,51 @@ int derive_policy(const magus_policy_t &p, const magus_model_t &m, DevPolicy *ou
     return MAGUS_OK;
 }
 
+// Closed loop: x(delta) exactly as the oracle and the kernels evaluate it, and the smallest
+// v in [0, 2^32] with pred(v) for pred false on a prefix of 0 .. 2^32 - 1 and true after it
+// (2^32 when it holds for none).
+static double xval(const DevModel &m, uint32_t delta) { return (m.bpc * (double)delta) / m.q; }
+template <class Pred>
+static int64_t first_true_u32(Pred pred) {
+    int64_t lo = -1, hi = (int64_t)1 << 32;
+    while (hi - lo > 1) {
+        const int64_t mid = lo + (hi - lo) / 2;
+        if (pred((uint32_t)mid)) hi = mid;
+        else lo = mid;
+    }
+    return hi;
+}
+
+// Alg. 1 in the closed loop when a throughput in its window is capped (Sec. 3.1; the
+// monitor reads min(x, C) at the level in effect).  x is non-decreasing in delta and each
+// FP64 difference below is monotone in the free delta, so every decision is a threshold on
+// that delta; the decision itself is the division-free test on d (up_last / dn_last).
+void derive_closed(const DevPolicy &P, const DevModel &M, ClosedThr *out) {
+    ClosedThr c;
+    memset(&c, 0, sizeof(c));
+    const int lvl[2] = {0, M.K - 1};
+    auto up_of = [&](double d) { return d > P.up_last; };
+    auto dn_of = [&](double d) { return d <= P.dn_last; };
+    for (int l = 0; l < 2; l++) {
+        const double C = M.cap[lvl[l]];
+        const int64_t f = first_true_u32([&](uint32_t v) { return xval(M, v) > C; });
+        c.cthr[l] = (uint32_t)(f - 1);   // C > 0 = x(0), so f >= 1
+        // a capped: d = C - x(b), non-increasing in b
+        c.bu[l] = first_true_u32([&](uint32_t b) { return !up_of(C - xval(M, b)); });
+        c.bd[l] = first_true_u32([&](uint32_t b) { return dn_of(C - xval(M, b)); });
+        // b capped: d = x(a) - C, non-decreasing in a
+        c.au[l] = first_true_u32([&](uint32_t a) { return up_of(xval(M, a) - C); });
+        c.ad[l] = first_true_u32([&](uint32_t a) { return !dn_of(xval(M, a) - C); });
+    }
+    for (int la = 0; la < 2; la++)
+        for (int lb = 0; lb < 2; lb++) {
+            const double d = M.cap[lvl[la]] - M.cap[lvl[lb]];
+            if (up_of(d)) c.cc |= 1u << (2 * la + lb);
+            if (dn_of(d)) c.cc |= 1u << (4 + 2 * la + lb);
+        }
+    *out = c;
+}
+
 // Group policies whose Alg. 1 parameters coincide (same W, inc, dec: identical predictions),
 // at most gp members per group, keeping the policies' order within each group.
 void form_groups(const std::vector<DevPolicy> &pols, int gp, std::vector<PolicyGroup> *out,

@@ -55,6 +55,14 @@ struct magus_replay {
     size_t seg_size = 0;
     // policies -> {time_groups, policy_slots, group size, segment rounds (0: tile kernel)}
     std::map<int, std::array<int, 4>> tuned;
+    // closed loop: segment and burn-in rounds (0: automatic; segment -1: literal kernel),
+    // its buffer (plan, replay slots, change-entry scratch, counters) and the last call's
+    // item count
+    int cls_seg = 0, cls_burn = -1;
+    void *clsbuf = nullptr;
+    size_t cls_size = 0;
+    unsigned long long *cls_stats = nullptr;   // device counters of the last closed-loop call
+    uint64_t cls_items = 0;
 };
 
 namespace magus {
@@ -78,6 +86,8 @@ struct Plan {
     std::vector<DevPolicy> pols;
     std::vector<char> tp;              // per policy: replayed by the time-parallel kernels
     std::vector<int32_t> lit;          // policies for the literal kernel
+    std::vector<int32_t> cls;          // closed-loop jump-mode policies (replay_closed.cu)
+    std::vector<ClosedThr> cthr;       // their capped-throughput thresholds
     std::vector<LadderItem> lad;       // (trace, one-rung policy) items, longest traces first
     std::vector<PolicyGroup> groups;
     std::vector<WorkItem> items;
@@ -105,6 +115,10 @@ int build_plan(magus_replay *h, const uint64_t *lengths, int32_t n_traces, const
                int32_t n_configs, int tg, int cw, int gp, int seg, Plan *pl);
 int launch_plan(magus_replay *h, const Plan &pl, const uint32_t *traces, const Outs &o, cudaStream_t stream,
                 float *ms_out = nullptr);
+// The closed-loop jump-mode policies of a plan (time-parallel, or the literal kernel when
+// its buffers exceed the budget); adds the kernels it launched to *kernels.
+int launch_closed_part(magus_replay *h, const Plan &pl, const uint32_t *traces, const Outs &o, const DevPolicy *d_pols,
+                       const uint64_t *d_off, const uint64_t *d_len, cudaStream_t stream, int *kernels);
 
 }  // namespace host
 }  // namespace magus

@@ -79,6 +79,8 @@ SIGNATURES = {
     "magus_replay_status": ([P, P], ctypes.c_int),
     "magus_replay_set_tile": ([P, _I32, _I32], ctypes.c_int),
     "magus_replay_set_segments": ([P, _I32], ctypes.c_int),
+    "magus_replay_set_closed": ([P, _I32, _I32], ctypes.c_int),
+    "magus_replay_closed_stats": ([P, P], ctypes.c_int),
     "magus_replay_kernel_time": ([P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                                   ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
     "magus_replay_autotune": ([P, P, P, _I32, P, _I32, P, P, P], ctypes.c_int),
@@ -87,6 +89,7 @@ SIGNATURES = {
     "magus_packed_size": ([P, _I32, P, P], ctypes.c_int),
     "magus_policy_bounds": ([ctypes.POINTER(Policy), ctypes.POINTER(Model), P], ctypes.c_int),
     "magus_policy_fp64_thresholds": ([ctypes.POINTER(Policy), ctypes.POINTER(Model), P], ctypes.c_int),
+    "magus_policy_closed_thresholds": ([ctypes.POINTER(Policy), ctypes.POINTER(Model), P], ctypes.c_int),
     "magus_last_error": ([], ctypes.c_char_p),
     "magus_version": ([], ctypes.c_char_p),
     "magus_serve_open": ([P, ctypes.POINTER(Model), ctypes.POINTER(Policy), _I32, _SZ, ctypes.c_int, _I32, _I64],
@@ -173,6 +176,15 @@ def policy_fp64_thresholds(policy: Dict, model: Dict):
     out = np.zeros(2, dtype=np.float64)
     check(lib().magus_policy_fp64_thresholds(ctypes.byref(pol), ctypes.byref(mh.m), out.ctypes.data))
     return float(out[0]), float(out[1])
+
+
+def policy_closed_thresholds(policy: Dict, model: Dict) -> np.ndarray:
+    """magus_policy_closed_thresholds: 11 int64 (capped-throughput thresholds per level)."""
+    mh = ModelHolder(model)
+    pol = make_policy(policy)
+    out = np.zeros(11, dtype=np.int64)
+    check(lib().magus_policy_closed_thresholds(ctypes.byref(pol), ctypes.byref(mh.m), out.ctypes.data))
+    return out
 
 
 def _ptr(t) -> Optional[int]:
@@ -326,6 +338,17 @@ class Replay:
     def set_segments(self, seg_rounds: int):
         """-1 automatic, 0 tile kernel, > 0 segment kernel with that many rounds per segment."""
         check(lib().magus_replay_set_segments(self.h, seg_rounds))
+
+    def set_closed(self, seg_rounds: int = 0, burn_rounds: int = -1):
+        """Closed loop in jump mode: 0 automatic segments, > 0 rounds per segment (multiple
+        of 64), -1 the literal kernel; burn_rounds -1 automatic."""
+        check(lib().magus_replay_set_closed(self.h, seg_rounds, burn_rounds))
+
+    def closed_stats(self):
+        """(segments replayed, second replays, final-pass replays) of the last call."""
+        out = (ctypes.c_uint64 * 3)()
+        check(lib().magus_replay_closed_stats(self.h, out))
+        return tuple(int(v) for v in out)
 
     def set_tile(self, time_groups: int, policy_slots: int):
         check(lib().magus_replay_set_tile(self.h, time_groups, policy_slots))

@@ -151,3 +151,48 @@ def test_fp64_thresholds_reproduce_algorithm_1(mg, seed):
                 continue
             assert (d / Wd > inc) == (d > up), (W, inc, d, up)
             assert (d / Wd < dec) == (d <= dn), (W, dec, d, dn)
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_closed_thresholds_reproduce_algorithm_1(mg, seed):
+    """The closed loop's integer tests: a throughput is capped (obs = C) exactly when its
+    delta exceeds out[l], and with one throughput capped Algorithm 1's outcome is a
+    threshold on the other delta -- checked against numpy's IEEE evaluation of
+    x = bpc * delta / q, d = obs_t - obs_{t-W}, d / W > inc and d / W < dec on the
+    thresholds' neighbours and on random deltas; both capped against the constant."""
+    rng = np.random.default_rng(seed)
+    model = tracegen.default_model()
+    bpc, q = np.float64(model["bytes_per_count"]), np.float64(model["dt_s"] * 1e9)
+    caps = [np.float64(model["bw_ref_gbs"] * (f / model["f_ref_ghz"])) for f in (model["f_ghz"][0], model["f_ghz"][-1])]
+
+    def x(v):
+        return (bpc * np.float64(v)) / q
+
+    for _ in range(30):
+        W = int(rng.integers(1, 65))
+        inc = float(rng.choice([rng.uniform(-50, 50), np.inf, -np.inf, 0.0]))
+        dec = float(rng.choice([rng.uniform(-50, 50), np.inf, -np.inf, 0.0]))
+        pol = dict(tracegen.default_policy(), direv_length=W, inc_threshold=inc, dec_threshold=dec, step_mode=2)
+        t = mg.policy_closed_thresholds(pol, model)
+        Wd = np.float64(W)
+        up = lambda d: bool(d / Wd > inc)
+        dn = lambda d: bool(d / Wd < dec)
+        for l, C in enumerate(caps):
+            c = int(t[l])
+            assert x(c) <= C and (c == 2**32 - 1 or x(c + 1) > C)
+            probes = rng.integers(0, 2**32, size=200).tolist()
+            for k in (2, 4, 6, 8):
+                v = int(t[k + l])
+                probes += [v - 2, v - 1, v, v + 1]
+            for v in probes:
+                if not 0 <= v < 2**32:
+                    continue
+                assert up(C - x(v)) == (v < t[2 + l]), (pol, l, v)
+                assert dn(C - x(v)) == (v >= t[4 + l]), (pol, l, v)
+                assert up(x(v) - C) == (v >= t[6 + l]), (pol, l, v)
+                assert dn(x(v) - C) == (v < t[8 + l]), (pol, l, v)
+        for la in range(2):
+            for lb in range(2):
+                d = caps[la] - caps[lb]
+                assert bool((int(t[10]) >> (2 * la + lb)) & 1) == up(d)
+                assert bool((int(t[10]) >> (4 + 2 * la + lb)) & 1) == dn(d)

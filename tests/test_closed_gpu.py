@@ -1,0 +1,170 @@
+"""GPU parity of the closed loop in jump mode (step_mode 2) on the segmented kernels.
+
+Every (trace, policy, segment) is replayed from a guessed state; segments whose guess was
+wrong are replayed again and a final pass per pair keeps only replays that started from the
+true state.  These tests make the guesses fail on purpose (short segments, no burn-in),
+overflow the per-segment change-entry scratch, and check every pair against the oracle:
+decision logs, counts and hashes bit-exact, energy / time / EDP within 1e-9 relative.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+import oracle
+import tracegen
+from gpu_util import REL_TOL, assert_pair, oracle_pairs, to_device, to_numpy
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mg():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2502_03796_b300 import magus
+    magus.lib()
+    return magus
+
+
+@pytest.fixture()
+def rp(mg):
+    r = mg.Replay(tracegen.default_model())
+    yield r
+    r.close()
+
+
+def closed_policies():
+    base = dict(tracegen.default_policy(), step_mode=2)
+    return [
+        base,
+        dict(base, direv_length=1, tune_window=1, high_freq_threshold=1.0),        # hf <=> flag
+        dict(base, direv_length=64, tune_window=64, inc_threshold=0.5, dec_threshold=-0.5),
+        dict(base, inc_threshold=-1.0, dec_threshold=2.0),                         # +1 and -1 overlap
+        dict(base, inc_threshold=np.inf, dec_threshold=-np.inf),                   # never predicts
+        dict(base, high_freq_threshold=0.1),                                       # mostly locked high
+        dict(base, direv_length=7, tune_window=33, inc_threshold=2.0, dec_threshold=-2.0,
+             high_freq_threshold=0.5),
+    ]
+
+
+def ragged():
+    lengths = np.array([0, 1, 5, 63, 64, 65, 300, 1000, 4097, 20_000, 33_333], dtype=np.uint64)
+    return tracegen.make_traces(lengths, seed=23, mean_phase=20.0)
+
+
+@pytest.mark.parametrize("seg,burn", [(0, -1), (256, 64), (512, 0), (64, 0), (-1, -1)])
+def test_closed_loop_matches_oracle(rp, seg, burn):
+    """Ragged lengths, edge policies, open-loop and literal-path policies in the same call,
+    full and short logs; segments down to 64 rounds with no burn-in (most guesses wrong)."""
+    ts = ragged()
+    model = tracegen.default_model()
+    base = tracegen.default_policy()
+    pols = closed_policies() + [base, dict(base, step_mode=3, direv_length=3)]
+    ref = oracle_pairs(ts, pols, model)
+    rp.set_closed(seg, burn)
+    for cap in (40_000, 7):
+        out = to_numpy(rp.run(to_device(ts), ts.lengths, pols, log_capacity=cap))
+        assert rp.status() == 0
+        for p, r in ref.items():
+            assert_pair(out, p, r, cap=cap, tag=f"closed seg={seg} burn={burn} cap={cap}")
+    items, second, final = rp.closed_stats()
+    n_cls = len(closed_policies())
+    if seg > 0:
+        assert items == sum((int(n) + seg - 1) // seg for n in ts.lengths) * n_cls
+        if burn == 0:
+            assert second > 0   # guesses failed and were replayed again
+    if seg < 0:
+        assert items == 0
+
+
+def test_closed_loop_entry_scratch_overflow(rp):
+    """More change entries in a segment than its scratch holds: the final pass replays those
+    segments straight into the log."""
+    ts = tracegen.make_traces(np.array([6000, 9001], dtype=np.uint64), seed=5, mean_phase=2.0)
+    model = tracegen.default_model()
+    pols = [dict(tracegen.default_policy(), step_mode=2, inc_threshold=0.2, dec_threshold=-0.2,
+                 direv_length=1, high_freq_threshold=1.5)]
+    ref = oracle_pairs(ts, pols, model)
+    assert max(r["n_changes"] for r in ref.values()) > 2000   # > 64 per 256-round segment
+    rp.set_closed(256, 0)
+    out = to_numpy(rp.run(to_device(ts), ts.lengths, pols, log_capacity=20_000))
+    assert rp.status() == 0
+    for p, r in ref.items():
+        assert_pair(out, p, r, cap=20_000, tag="scratch overflow")
+    items, second, final = rp.closed_stats()
+    assert final > 0
+
+
+def oracle_state(level, flags64, L):
+    """The oracle's state before round 0 with the given level and the flags of rounds
+    -L .. -1 taken from the carried 64-bit flag word (bit 63 newest)."""
+    st = oracle.new_state()
+    st.level = level
+    for i in range(L):   # oldest first: element L-1 is round -1 (bit 63)
+        st.uncore_tune_ls[i] = (flags64 >> (64 - L + i)) & 1
+    return st
+
+
+def test_closed_loop_carried_state(rp, mg):
+    """A fresh carried state (no rounds seen) with the top level and a flag history: the
+    segmented path matches the oracle started from the same state, and its written state
+    equals the literal kernel's byte for byte.  A level inside the ladder is invalid in
+    jump mode, and a state that has seen rounds is refused (closed loop)."""
+    model = tracegen.default_model()
+    K = len(model["f_ghz"])
+    ts = tracegen.make_traces(np.array([3000, 70, 12_345], dtype=np.uint64), seed=8, mean_phase=15.0)
+    pols = [dict(tracegen.default_policy(), step_mode=2), dict(tracegen.default_policy(), step_mode=2, tune_window=5)]
+    flags = 0xA5F00F0F12345678
+    n_pairs = ts.n_traces * len(pols)
+
+    def fresh_states():
+        st = np.zeros(n_pairs * mg.STATE_BYTES, dtype=np.uint8)
+        v = st.view(np.uint64).reshape(n_pairs, -1)
+        v[:, 1] = flags
+        st.view(np.uint32).reshape(n_pairs, -1)[:, 4] = K - 1
+        return torch.from_numpy(st).cuda()
+
+    written = []
+    for seg in (256, -1):
+        rp.set_closed(seg, 0)
+        state = fresh_states()
+        out = to_numpy(rp.run(to_device(ts), ts.lengths, pols, log_capacity=20_000, state=state))
+        assert rp.status() == 0
+        for p in range(n_pairs):
+            i, c = divmod(p, len(pols))
+            r = oracle.replay(ts.trace(i), pols[c], model, state=oracle_state(K - 1, flags, pols[c]["tune_window"]))
+            assert_pair(out, p, r, cap=20_000, tag=f"carried state seg={seg}")
+        written.append(state.cpu().numpy())
+    assert np.array_equal(written[0], written[1])
+
+    rp.set_closed(256, 0)
+    bad = fresh_states()
+    bad.view(torch.int32)[4] = 3   # pair 0: a level inside the ladder
+    rp.run(to_device(ts), ts.lengths, pols, state=bad)
+    assert rp.status() == mg.EINVAL
+    seen = fresh_states()
+    seen.view(torch.int64)[0] = 10  # pair 0 has seen rounds
+    rp.run(to_device(ts), ts.lengths, pols, state=seen)
+    assert rp.status() == mg.EINVAL
+    assert rp.status() == 0
+
+
+def test_closed_loop_batched_full_size_sampled(mg):
+    """The closed-loop benchmark workload (4,096 traces x 100,000 intervals, one policy) in
+    the launch configuration the benchmark uses: sampled pairs against the oracle."""
+    ts = tracegen.batched(4096, 100_000)
+    model = tracegen.default_model()
+    pols = [dict(tracegen.default_policy(), step_mode=2)]
+    rp = mg.Replay(model, mem_budget=8 << 30)
+    try:
+        out = to_numpy(rp.run(to_device(ts), ts.lengths, pols, log_capacity=0))
+        assert rp.status() == 0
+        items, second, final = rp.closed_stats()
+        assert items > 4096
+    finally:
+        rp.close()
+    for p in (0, 1, 2047, 4095):
+        r = oracle.replay(ts.trace(p), pols[0], model, log_cap=0)
+        assert_pair(out, p, r, tag="closed batched sampled")
