@@ -564,19 +564,65 @@ int launch_closed_part(magus_replay *h, const Plan &pl, const uint32_t *traces, 
     h->cls_items = 0;
     h->cls_stats = nullptr;
     if (n_cls == 0 || n_traces == 0) return MAGUS_OK;
-    // segment length: about four waves of threads (8 CTAs of 128 per SM) over all pairs'
-    // rounds, 1,024 .. 65,536; burn-in a quarter of it
-    uint64_t total_rounds = 0;
-    for (uint64_t n : pl.lengths) total_rounds += n;
-    total_rounds *= (uint64_t)n_cls;
-    const uint64_t resident = (uint64_t)h->sms * 8 * closed_threads_per_cta();
-    uint64_t S = h->cls_seg > 0 ? (uint64_t)h->cls_seg
-                                : std::min<uint64_t>(65536, std::max<uint64_t>(1024, align_up(total_rounds / (4 * resident), 64)));
-    const uint64_t G = h->cls_burn >= 0 ? (uint64_t)h->cls_burn : S / 4;
     int wmax = 1;
     for (int32_t c : pl.cls) wmax = std::max(wmax, pl.pols[c].W);
     uint32_t ring = 1;
     while ((int)ring < wmax) ring <<= 1;
+    // Every thread replays one segment (plus its burn-in) one round after another, so a
+    // launch lasts about (waves of threads) x (segment + burn-in rounds).  Automatic choice:
+    // for each wave count w, the shortest segment whose items fit w waves of resident
+    // threads, burn-in min(512, S / 2); keep the cheapest (cached per workload).
+    auto burn_of = [&](uint64_t S) -> uint64_t {
+        return h->cls_burn >= 0 ? (uint64_t)h->cls_burn : std::min<uint64_t>(512, S / 2 / 64 * 64);
+    };
+    uint64_t S = (uint64_t)h->cls_seg, G = 0;
+    if (h->cls_seg > 0) {
+        G = burn_of(S);
+    } else {
+        uint64_t key = 1469598103934665603ull ^ ((uint64_t)n_cls << 32) ^ ring ^ ((uint64_t)h->cls_burn << 48);
+        uint64_t longest = 0;
+        for (uint64_t n : pl.lengths) {
+            key = (key ^ n) * 1099511628211ull;
+            longest = std::max(longest, n);
+        }
+        if (key == h->cls_key && h->cls_auto_seg) {
+            S = h->cls_auto_seg;
+            G = h->cls_auto_burn;
+        } else {
+            const int ctas = closed_max_ctas_per_sm(ring);
+            const uint64_t resident = (uint64_t)h->sms * std::max(ctas, 1) * closed_threads_per_cta();
+            auto items_of = [&](uint64_t L) {
+                uint64_t it = 0;
+                for (uint64_t n : pl.lengths) it += (n + L - 1) / L;
+                return it * (uint64_t)n_cls;
+            };
+            const uint64_t top = std::max<uint64_t>(64, align_up(longest, 64));
+            double best = 1e300;
+            for (uint64_t w = 1; w <= 64; w++) {
+                // shortest multiple of 64 with items_of(L) <= w * resident (non-increasing in L)
+                if (items_of(top) > w * resident) continue;
+                uint64_t lo = 0, hi = top / 64;   // items_of(64 * hi) fits
+                while (hi - lo > 1) {
+                    const uint64_t mid = (lo + hi) / 2;
+                    if (items_of(64 * mid) <= w * resident) hi = mid;
+                    else lo = mid;
+                }
+                const uint64_t L = 64 * hi;
+                const double cost = (double)((items_of(L) + resident - 1) / resident) * (double)(L + burn_of(L));
+                if (cost < best) {
+                    best = cost;
+                    S = L;
+                }
+                if (L <= 1024) break;
+            }
+            if (S == 0) S = top;   // more than 64 waves even with whole traces
+            S = std::min<uint64_t>(S, (uint64_t)1 << 24);
+            G = burn_of(S);
+            h->cls_key = key;
+            h->cls_auto_seg = S;
+            h->cls_auto_burn = G;
+        }
+    }
     std::vector<uint64_t> ibase(n_traces + 1);
     uint64_t items = 0;
     for (int i = 0; i < n_traces; i++) {

@@ -291,6 +291,7 @@ struct ClosedParams {
 __host__ __device__ inline bool closed_policy(const DevPolicy &d) { return d.step_mode == 2 && d.pin == 0; }
 void derive_closed(const DevPolicy &pol, const DevModel &m, ClosedThr *out);
 int closed_threads_per_cta();
+int closed_max_ctas_per_sm(uint32_t ring);   // resident CTAs of the first-replay kernel
 cudaError_t launch_replay_closed(const ClosedParams &p, cudaStream_t stream);
 
 // Host planning (plan.cu).

@@ -18,7 +18,9 @@
 //           takes a replay whose start state equals the state reached so far, replays the
 //           segment once more where neither does, and adds up charges and change entries.
 // The final walk makes the result exact whatever the guesses; the guesses only decide how
-// much is replayed twice.
+// much is replayed twice.  A second replay runs in lockstep with a repeat of the first one
+// and stops once their states agree: from there on the first replay's charges and entries
+// stand, so a wrong guess costs the rounds until the two trajectories meet, not a segment.
 //
 // Alg. 1 runs on integers: a throughput is capped exactly when its delta exceeds a
 // per-level threshold, each case with one capped throughput is a threshold on the other
@@ -81,76 +83,14 @@ __device__ __forceinline__ void prefill(const uint32_t *tr, uint64_t t0, const R
     for (uint64_t t = h0; t < t0; t++) ring.at(t) = __ldg(tr + t);
 }
 
-// Rounds [t0, t1) of one pair's trace from state s (t0 a multiple of 4; the packed layout
-// pads every trace to a multiple of 32 deltas, so the 16-byte loads stay inside it).
-// kCount: charge the rounds, count flags and changes, emit change entries.
-template <bool kCount, class Emit>
-__device__ __forceinline__ void run_rounds(const uint32_t *tr, uint64_t t0, uint64_t t1, CState &s, CAcc &acc,
-                                           const DevPolicy &P, const ClosedThr &C, const DevModel &M,
-                                           const Ring &ring, Emit emit) {
-    const int W = P.W;
-    const uint64_t lmask = low_mask(P.L);
-    const uint32_t topK = (uint32_t)(M.K - 1);
-#pragma unroll 1
-    for (uint64_t tq = t0; tq < t1; tq += 4) {
-        const uint4 v4 = __ldg(reinterpret_cast<const uint4 *>(tr + tq));
-        const uint32_t vv[4] = {v4.x, v4.y, v4.z, v4.w};
-#pragma unroll
-        for (int j = 0; j < 4; j++) {
-            const uint64_t t = tq + (uint64_t)j;
-            if (t >= t1) break;
-            const uint32_t a = vv[j];
-            const uint32_t b = ring.at(t - (uint64_t)W);   // read before round t's slot is reused
-            ring.at(t) = a;
-            const uint32_t lv = s.lv;
-            const uint32_t lb = (uint32_t)(s.lvh >> (W - 1)) & 1u;   // level of round t - W
-            // Alg. 1 on obs_t = min(x_t, C(lv)) and obs_{t-W} = min(x_{t-W}, C(lb))
-            bool up = false, dn = false;
-            if (t >= (uint64_t)W) {
-                const bool ca = a > (lv ? C.cthr[1] : C.cthr[0]);
-                const bool cb = b > (lb ? C.cthr[1] : C.cthr[0]);
-                if (!ca && !cb) {
-                    core::predict_exact(a, b, P, M, up, dn);
-                } else if (ca && cb) {
-                    const uint32_t k = 2u * lv + lb;
-                    up = (C.cc >> k) & 1u;
-                    dn = (C.cc >> (4u + k)) & 1u;
-                } else if (ca) {
-                    up = (int64_t)b < (lv ? C.bu[1] : C.bu[0]);
-                    dn = (int64_t)b >= (lv ? C.bd[1] : C.bd[0]);
-                } else {
-                    up = (int64_t)a >= (lb ? C.au[1] : C.au[0]);
-                    dn = (int64_t)a < (lb ? C.ad[1] : C.ad[0]);
-                }
-                dn = dn && !up;   // Alg. 1 tests +1 first
-            }
-            // Alg. 2: the flag enters the list, then the share of flagged rounds is tested
-            s.fl = (s.fl << 1) | ((up || dn) ? 1ull : 0ull);
-            const bool hf = __popcll(s.fl & lmask) >= P.kmin;
-            const uint32_t next = (hf || up) ? 1u : (dn ? 0u : lv);
-            if (kCount) {
-                // energy model: round t at level lv, stretched when the demand exceeds C(lv)
-                const bool se = a > (lv ? M.thrM : M.thr0);
-                if (lv) {
-                    acc.nm += se ? 0u : 1u;
-                    acc.sm += se ? a : 0u;
-                } else {
-                    acc.n0 += se ? 0u : 1u;
-                    acc.s0 += se ? a : 0u;
-                }
-                acc.nhf += hf ? 1u : 0u;
-                if (next != lv) {
-                    const uint64_t when = t + 1;   // the new level governs the next round
-                    const uint32_t lvl = next ? topK : 0u;
-                    emit((uint32_t)(when << 5) | lvl, acc.nch);
-                    acc.nch++;
-                    acc.hash += core::mix64((when << 8) | lvl);
-                }
-            }
-            s.lvh = (s.lvh << 1) | lv;
-            s.lv = next;
-        }
-    }
+// Alg. 1 for two uncapped throughputs inside the rounding band around a threshold: the FP64
+// evaluation in the oracle's order (rare; kept out of the round loop).  Bit 0: +1, bit 1: -1.
+static __device__ __noinline__ uint32_t predict_band(uint32_t a, uint32_t b, const DevPolicy *Pg, double bpc,
+                                                      double q) {
+    const double xa = __ddiv_rn(__dmul_rn(bpc, (double)a), q);
+    const double xb = __ddiv_rn(__dmul_rn(bpc, (double)b), q);
+    const double der = __ddiv_rn(__dsub_rn(xa, xb), (double)Pg->W);
+    return (der > Pg->inc ? 1u : 0u) | (der < Pg->dec ? 2u : 0u);
 }
 
 struct NoEmit {
@@ -163,6 +103,148 @@ struct BufEmit {
         if (buf && i < cap) buf[i] = e;
     }
 };
+
+// One replay of a pair over consecutive rounds: its state, its charges (energy per run of
+// constant level: count of unstretched rounds, sum of stretched deltas) and change entries.
+struct Replay {
+    CState s;
+    CAcc acc;
+    uint32_t run_n;
+    unsigned long long run_s;
+
+    __device__ __forceinline__ void start(const CState &st) {
+        s = st;
+        acc = CAcc{};
+        run_n = 0;
+        run_s = 0;
+    }
+    __device__ __forceinline__ void flush() {
+        if (s.lv) {
+            acc.nm += run_n;
+            acc.sm += run_s;
+        } else {
+            acc.n0 += run_n;
+            acc.s0 += run_s;
+        }
+        run_n = 0;
+        run_s = 0;
+    }
+    // Round t = t0 + j with a = delta_t, b = delta_{t-W}.  kCount: charge it, count its flag
+    // and change, emit its entry.
+    template <bool kCount, class Emit>
+    __device__ __forceinline__ void step(uint32_t a, uint32_t b, uint32_t j, uint64_t t0, uint32_t warm,
+                                         const DevPolicy &P, const DevPolicy *Pg, const ClosedThr &C,
+                                         const DevModel &M, uint64_t lmask, Emit emit) {
+        const uint32_t lv = s.lv;
+        const uint32_t lb = (uint32_t)(s.lvh >> (P.W - 1)) & 1u;   // level of round t - W
+        // Alg. 1 on obs_t = min(x_t, C(lv)) and obs_{t-W} = min(x_{t-W}, C(lb)); every case
+        // evaluated, one selected
+        const bool ca = a > (lv ? C.cthr[1] : C.cthr[0]);
+        const bool cb = b > (lb ? C.cthr[1] : C.cthr[0]);
+        const int64_t m = (int64_t)a - (int64_t)b;
+        const uint32_t k = 2u * lv + lb;
+        const bool up_b = ca ? ((C.cc >> k) & 1u) != 0 : (int64_t)a >= (lb ? C.au[1] : C.au[0]);
+        const bool dn_b = ca ? ((C.cc >> (4u + k)) & 1u) != 0 : (int64_t)a < (lb ? C.ad[1] : C.ad[0]);
+        const bool up_n = ca ? (int64_t)b < (lv ? C.bu[1] : C.bu[0]) : m > P.up_mid;
+        const bool dn_n = ca ? (int64_t)b >= (lv ? C.bd[1] : C.bd[0]) : m < P.dn_mid;
+        bool up = cb ? up_b : up_n, dn = cb ? dn_b : dn_n;
+        const uint32_t m32 = a - b;
+        if (!(ca | cb) && ((m32 - P.up_lo) <= P.up_w || (m32 - P.dn_lo) <= P.dn_w)) {
+            const uint32_t r = predict_band(a, b, Pg, M.bpc, M.q);
+            up = (r & 1u) != 0;
+            dn = (r & 2u) != 0;
+        }
+        if (j < warm) up = dn = false;
+        dn = dn && !up;   // Alg. 1 tests +1 first
+        // Alg. 2: the flag enters the list, then the share of flagged rounds is tested
+        s.fl = (s.fl << 1) | ((up || dn) ? 1ull : 0ull);
+        const bool hf = __popcll(s.fl & lmask) >= P.kmin;
+        const uint32_t next = (hf || up) ? 1u : (dn ? 0u : lv);
+        if (kCount) {
+            // energy model: the round at level lv, stretched when the demand exceeds C(lv)
+            const bool se = a > (lv ? M.thrM : M.thr0);
+            run_n += se ? 0u : 1u;
+            run_s += se ? a : 0u;
+            acc.nhf += hf ? 1u : 0u;
+        }
+        s.lvh = (s.lvh << 1) | lv;
+        if (next != lv) {
+            if (kCount) {
+                flush();
+                const uint64_t when = t0 + j + 1;   // the new level governs the next round
+                const uint32_t lvl = next ? (uint32_t)(M.K - 1) : 0u;
+                emit((uint32_t)(when << 5) | lvl, acc.nch);
+                acc.nch++;
+                acc.hash += core::mix64((when << 8) | lvl);
+            }
+            s.lv = next;
+        }
+    }
+};
+
+// Rounds [t0, t1) of one pair's trace (t0 a multiple of 4, t1 - t0 < 2^32; the packed layout
+// pads every trace to a multiple of 32 deltas, so the 16-byte loads stay inside it).  The
+// ring holds the deltas before t0.
+template <bool kCount, class Emit>
+__device__ __forceinline__ void run_rounds(const uint32_t *tr, uint64_t t0, uint64_t t1, Replay &x,
+                                           const DevPolicy *Pg, const ClosedThr &C, const DevModel &M,
+                                           const Ring &ring, Emit emit) {
+    const DevPolicy P = *Pg;
+    const uint64_t lmask = low_mask(P.L);
+    const uint32_t W = (uint32_t)P.W;
+    const uint32_t nr = (uint32_t)(t1 - t0);
+    const uint32_t warm = t0 < W ? (uint32_t)(W - t0) : 0u;   // rounds before the FIFO holds W + 1
+    auto round = [&](uint32_t a, uint32_t j) {
+        const uint32_t b = ring.at(t0 + j - W);   // read before round t's slot is reused (W may equal R)
+        ring.at(t0 + j) = a;
+        x.step<kCount>(a, b, j, t0, warm, P, Pg, C, M, lmask, emit);
+    };
+    uint32_t j = 0;
+#pragma unroll 1
+    for (; j + 4u <= nr; j += 4u) {
+        const uint4 v = __ldg(reinterpret_cast<const uint4 *>(tr + t0 + j));
+        round(v.x, j);
+        round(v.y, j + 1u);
+        round(v.z, j + 2u);
+        round(v.w, j + 3u);
+    }
+#pragma unroll 1
+    for (; j < nr; j++) round(__ldg(tr + t0 + j), j);
+    if (kCount) x.flush();
+}
+
+// Rounds [t0, t1) replayed twice in lockstep: x (charged, entries emitted) and y (charged,
+// no entries: it repeats an earlier replay) until their states agree, checked every 8
+// rounds -- the level, the levels of the last W rounds and all 64 flags (the carried state
+// written at a trace's end holds 64).  Returns the rounds run (both replays then hold the
+// state after them, runs flushed); t1 - t0 when they never agreed.
+template <class Emit>
+__device__ __forceinline__ uint32_t run_until_same(const uint32_t *tr, uint64_t t0, uint64_t t1, Replay &x, Replay &y,
+                                                   const DevPolicy *Pg, const ClosedThr &C, const DevModel &M,
+                                                   const Ring &ring, Emit emit) {
+    const DevPolicy P = *Pg;
+    const uint64_t lmask = low_mask(P.L), wmask = low_mask(P.W);
+    const uint32_t W = (uint32_t)P.W;
+    const uint32_t nr = (uint32_t)(t1 - t0);
+    const uint32_t warm = t0 < W ? (uint32_t)(W - t0) : 0u;
+    uint32_t j = 0;
+#pragma unroll 1
+    while (j < nr) {
+        const uint32_t je = min(nr, j + 8u);
+#pragma unroll 1
+        for (; j < je; j++) {
+            const uint32_t a = __ldg(tr + t0 + j);
+            const uint32_t b = ring.at(t0 + j - W);
+            ring.at(t0 + j) = a;
+            x.step<true>(a, b, j, t0, warm, P, Pg, C, M, lmask, emit);
+            y.step<true>(a, b, j, t0, warm, P, Pg, C, M, lmask, NoEmit{});
+        }
+        if (same_state(x.s, y.s, wmask, ~0ull)) break;
+    }
+    x.flush();
+    y.flush();
+    return j;
+}
 
 struct ItemPos {
     int trace, ci;
@@ -203,15 +285,30 @@ __device__ __forceinline__ void store_slot(ClosedSlot &o, const CState &in, cons
     o.ok = ok;
 }
 
-// pass 1 (first replay of every segment) and pass 2 (second replay where pass 1 started
-// from a state other than its predecessor's end state)
-__global__ void __launch_bounds__(kThreads, 5) closed_pass_kernel(const ClosedParams p, int pass) {
+__device__ __forceinline__ CAcc acc_add_diff(const CAcc &x, const ClosedSlot &r, const CAcc &y) {
+    CAcc o;
+    o.n0 = x.n0 + (r.n0 - y.n0);
+    o.nm = x.nm + (r.nm - y.nm);
+    o.nhf = x.nhf + (r.nhf - y.nhf);
+    o.nch = x.nch + (r.nch - y.nch);
+    o.s0 = x.s0 + (r.s0 - y.s0);
+    o.sm = x.sm + (r.sm - y.sm);
+    o.hash = x.hash + (r.hash - y.hash);
+    return o;
+}
+
+// Pass 1: the first replay of every segment.  Pass 2: a second replay where pass 1 started
+// from a state other than its predecessor's end state.  Separate kernels, so that the
+// lockstep replay of pass 2 does not raise the register count of pass 1.
+template <int kPass>
+__device__ __forceinline__ void closed_pass(const ClosedParams &p) {
+    constexpr int pass = kPass;
     extern __shared__ uint32_t ring_s[];
     const uint64_t item = (uint64_t)blockIdx.x * kThreads + threadIdx.x;
     if (item >= p.n_items) return;
     const ItemPos q = locate(p, item);
     const int pol = p.cls[q.ci];
-    const DevPolicy P = p.pols[pol];
+    const DevPolicy *Pg = p.pols + pol;
     const ClosedThr C = p.thr[q.ci];
     const DevModel &M = p.model;
     const int64_t pair = (int64_t)q.trace * p.n_pols + pol;
@@ -220,43 +317,74 @@ __global__ void __launch_bounds__(kThreads, 5) closed_pass_kernel(const ClosedPa
     const uint64_t s0 = q.k * p.seg_len, s1 = min(n, s0 + p.seg_len);
     ClosedSlot &out = p.slots[(uint64_t)(pass - 1) * p.n_items + item];
     const Ring ring{ring_s + threadIdx.x, p.ring - 1u};
-    CState st;
-    uint32_t ok = 1u;
-    if (pass == 1) {
+    uint32_t *scr = p.scratch ? p.scratch + ((uint64_t)(pass - 1) * p.n_items + item) * p.scr_cap : nullptr;
+    const BufEmit em{scr, p.scr_cap};
+    Replay x;
+    if constexpr (pass == 1) {
+        uint32_t ok = 1u;
         const uint64_t t0 = s0 > p.burn ? s0 - p.burn : 0;
         if (t0 == 0) {
-            st = initial_state(p, pair);
+            x.start(initial_state(p, pair));
             ok |= 2u;   // started from the true state
         } else {
-            st = CState{0u, 0ull, 0ull};
+            x.start(CState{0u, 0ull, 0ull});
         }
         prefill(tr, t0, ring);
-        CAcc none{};
-        run_rounds<false>(tr, t0, s0, st, none, P, C, M, ring, NoEmit{});
+        run_rounds<false>(tr, t0, s0, x, Pg, C, M, ring, NoEmit{});
+        const CState in = x.s;
+        x.start(in);
+        run_rounds<true>(tr, s0, s1, x, Pg, C, M, ring, em);
+        if (scr && x.acc.nch > p.scr_cap) ok |= 4u;   // entries lost: not reused with a log
+        store_slot(out, in, x.s, x.acc, ok);
+        return;
     } else {
-        if (q.k == 0) {
-            out.ok = 0;
-            return;
-        }
-        const ClosedSlot &prev = p.slots[item - 1];   // segment k - 1, pass 1
-        const ClosedSlot &mine = p.slots[item];
-        const CState e{prev.lv_out, prev.lvh_out, prev.fl_out};
-        const CState u{mine.lv_in, mine.lvh_in, mine.fl_in};
-        if ((mine.ok & 2u) || same_state(e, u, low_mask(P.W), low_mask(P.L))) {
-            out.ok = 0;
-            return;
-        }
-        st = e;
-        prefill(tr, s0, ring);
-        atomicAdd(&p.stats[0], 1ull);
+    if (q.k == 0) {
+        out.ok = 0;
+        return;
     }
-    const CState in = st;
-    CAcc acc{};
-    BufEmit em{p.scratch ? p.scratch + ((uint64_t)(pass - 1) * p.n_items + item) * p.scr_cap : nullptr, p.scr_cap};
-    run_rounds<true>(tr, s0, s1, st, acc, P, C, M, ring, em);
-    if (p.scratch && acc.nch > p.scr_cap) ok |= 4u;   // entries lost: the final pass replays it
-    store_slot(out, in, st, acc, ok);
+    const ClosedSlot &prev = p.slots[item - 1];   // segment k - 1, pass 1
+    const ClosedSlot &mine = p.slots[item];
+    const CState e{prev.lv_out, prev.lvh_out, prev.fl_out};
+    const CState u{mine.lv_in, mine.lvh_in, mine.fl_in};
+    if ((mine.ok & 2u) || same_state(e, u, low_mask(Pg->W), low_mask(Pg->L))) {
+        out.ok = 0;
+        return;
+    }
+    atomicAdd(&p.stats[0], 1ull);
+    prefill(tr, s0, ring);
+    x.start(e);
+    CAcc acc;
+    CState end;
+    if (scr && (mine.ok & 4u)) {
+        // the first replay's entries are incomplete: no shortcut
+        run_rounds<true>(tr, s0, s1, x, Pg, C, M, ring, em);
+        acc = x.acc;
+        end = x.s;
+    } else {
+        Replay y;
+        y.start(u);
+        const uint32_t r = run_until_same(tr, s0, s1, x, y, Pg, C, M, ring, em);
+        if (r < (uint32_t)(s1 - s0)) {
+            // from round s0 + r on the first replay stands: its charges, entries, end state
+            acc = acc_add_diff(x.acc, mine, y.acc);
+            end = CState{mine.lv_out, mine.lvh_out, mine.fl_out};
+            if (scr) {
+                const uint32_t *src = p.scratch + item * p.scr_cap;
+                for (uint32_t i = y.acc.nch; i < mine.nch; i++) {
+                    const uint64_t d = (uint64_t)x.acc.nch + (i - y.acc.nch);
+                    if (d < p.scr_cap) scr[d] = src[i];
+                }
+            }
+        } else {
+            acc = x.acc;
+            end = x.s;
+        }
+    }
+    store_slot(out, e, end, acc, 1u | ((scr && acc.nch > p.scr_cap) ? 4u : 0u));
+    }
 }
+__global__ void __launch_bounds__(kThreads, 5) closed_first_kernel(const ClosedParams p) { closed_pass<1>(p); }
+__global__ void __launch_bounds__(kThreads) closed_second_kernel(const ClosedParams p) { closed_pass<2>(p); }
 
 // Final pass: one thread per (trace, closed-loop policy) pair.
 __global__ void __launch_bounds__(kThreads) closed_final_kernel(const ClosedParams p) {
@@ -270,61 +398,89 @@ __global__ void __launch_bounds__(kThreads) closed_final_kernel(const ClosedPara
         atomicCAS(p.status, 0, MAGUS_EINVAL);
         return;
     }
-    const DevPolicy P = p.pols[pol];
+    const DevPolicy *Pg = p.pols + pol;
     const ClosedThr C = p.thr[ci];
     const DevModel &M = p.model;
     const uint32_t *tr = p.traces + p.offsets[trace];
     const uint64_t n = p.lengths[trace];
     const uint64_t nseg = (n + p.seg_len - 1) / p.seg_len;
     const uint64_t item0 = p.ibase[trace] + (uint64_t)ci * nseg;
-    const uint64_t wmask = low_mask(P.W), lmask = low_mask(P.L);
+    const uint64_t wmask = low_mask(Pg->W), lmask = low_mask(Pg->L);
     const bool logging = p.log_entries && p.log_cap > 0;
     uint32_t *lg = logging ? p.log_entries + (uint64_t)pair * p.log_cap : nullptr;
     const Ring ring{ring_s + threadIdx.x, p.ring - 1u};
     CState E = initial_state(p, pair);
     uint64_t N0 = 0, NM = 0, NHF = 0, NCH = 0;
     unsigned long long S0 = 0, SM = 0, HS = 0;
+    auto add = [&](const CAcc &a) {
+        N0 += a.n0;
+        NM += a.nm;
+        NHF += a.nhf;
+        NCH += a.nch;
+        S0 += a.s0;
+        SM += a.sm;
+        HS += a.hash;
+    };
+    // copy entries [i0, i1) of a replay's scratch to the log after the NCH entries so far
+    auto copy = [&](uint64_t which, uint64_t item, uint32_t i0, uint32_t i1, uint64_t at) {
+        const uint32_t *src = p.scratch + (which * p.n_items + item) * p.scr_cap;
+        for (uint32_t i = i0; i < i1 && at + (i - i0) < p.log_cap; i++) lg[at + (i - i0)] = src[i];
+    };
     for (uint64_t k = 0; k < nseg; k++) {
         const uint64_t item = item0 + k;
+        const uint64_t s0 = k * p.seg_len, s1 = min(n, s0 + p.seg_len);
+        // a replay's end state holds 64 flags of its own: after fewer rounds than that, the
+        // last segment must have started with all 64 flags right for the written state
+        const uint64_t fmask = (k + 1 == nseg && s1 - s0 < 64 && p.state) ? ~0ull : lmask;
         const ClosedSlot *pick = nullptr;
         uint64_t which = 0;
         for (uint64_t w = 0; w < 2 && !pick; w++) {
             const ClosedSlot &c = p.slots[w * p.n_items + item];
             if (!(c.ok & 1u) || (logging && (c.ok & 4u))) continue;
             const CState u{c.lv_in, c.lvh_in, c.fl_in};
-            if ((c.ok & 2u) || same_state(E, u, wmask, lmask)) {
+            if ((c.ok & 2u) || same_state(E, u, wmask, fmask)) {
                 pick = &c;
                 which = w;
             }
         }
         if (pick) {
-            if (logging) {
-                const uint32_t *src = p.scratch + (which * p.n_items + item) * p.scr_cap;
-                for (uint32_t j = 0; j < pick->nch && NCH + j < p.log_cap; j++) lg[NCH + j] = src[j];
-            }
-            N0 += pick->n0;
-            NM += pick->nm;
-            NHF += pick->nhf;
-            NCH += pick->nch;
-            S0 += pick->s0;
-            SM += pick->sm;
-            HS += pick->hash;
+            if (logging) copy(which, item, 0, pick->nch, NCH);
+            CAcc a;
+            a.n0 = pick->n0;
+            a.nm = pick->nm;
+            a.nhf = pick->nhf;
+            a.nch = pick->nch;
+            a.s0 = pick->s0;
+            a.sm = pick->sm;
+            a.hash = pick->hash;
+            add(a);
             E = CState{pick->lv_out, pick->lvh_out, pick->fl_out};
+            continue;
+        }
+        // neither replay started from the state reached here: replay the segment now,
+        // alongside a repeat of the first replay until the two agree
+        atomicAdd(&p.stats[1], 1ull);
+        const ClosedSlot &first = p.slots[item];
+        prefill(tr, s0, ring);
+        const BufEmit em{lg ? lg + NCH : nullptr, NCH < p.log_cap ? p.log_cap - NCH : 0};
+        Replay x;
+        x.start(E);
+        if (logging && (first.ok & 4u)) {
+            run_rounds<true>(tr, s0, s1, x, Pg, C, M, ring, em);
+            add(x.acc);
+            E = x.s;
+            continue;
+        }
+        Replay y;
+        y.start(CState{first.lv_in, first.lvh_in, first.fl_in});
+        const uint32_t r = run_until_same(tr, s0, s1, x, y, Pg, C, M, ring, em);
+        if (r < (uint32_t)(s1 - s0)) {
+            if (logging) copy(0, item, y.acc.nch, first.nch, NCH + x.acc.nch);
+            add(acc_add_diff(x.acc, first, y.acc));
+            E = CState{first.lv_out, first.lvh_out, first.fl_out};
         } else {
-            // neither replay started from the state reached here: replay the segment now
-            const uint64_t s0 = k * p.seg_len, s1 = min(n, s0 + p.seg_len);
-            prefill(tr, s0, ring);
-            CAcc acc{};
-            BufEmit em{lg ? lg + NCH : nullptr, NCH < p.log_cap ? p.log_cap - NCH : 0};
-            run_rounds<true>(tr, s0, s1, E, acc, P, C, M, ring, em);
-            N0 += acc.n0;
-            NM += acc.nm;
-            NHF += acc.nhf;
-            NCH += acc.nch;
-            S0 += acc.s0;
-            SM += acc.sm;
-            HS += acc.hash;
-            atomicAdd(&p.stats[1], 1ull);
+            add(x.acc);
+            E = x.s;
         }
     }
     double En, T;
@@ -353,14 +509,24 @@ __global__ void __launch_bounds__(kThreads) closed_final_kernel(const ClosedPara
 
 int closed_threads_per_cta() { return kThreads; }
 
+int closed_max_ctas_per_sm(uint32_t ring) {
+    int blocks = 0;
+    const size_t smem = (size_t)ring * kThreads * sizeof(uint32_t);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, closed_first_kernel, kThreads, smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return blocks;
+}
+
 cudaError_t launch_replay_closed(const ClosedParams &p, cudaStream_t stream) {
     const size_t smem = (size_t)p.ring * kThreads * sizeof(uint32_t);
     if (p.n_items) {
         const uint64_t grid = (p.n_items + kThreads - 1) / kThreads;
-        closed_pass_kernel<<<(unsigned)grid, kThreads, smem, stream>>>(p, 1);
+        closed_first_kernel<<<(unsigned)grid, kThreads, smem, stream>>>(p);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
-        closed_pass_kernel<<<(unsigned)grid, kThreads, smem, stream>>>(p, 2);
+        closed_second_kernel<<<(unsigned)grid, kThreads, smem, stream>>>(p);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }

@@ -59,6 +59,8 @@ struct magus_replay {
     // its buffer (plan, replay slots, change-entry scratch, counters) and the last call's
     // item count
     int cls_seg = 0, cls_burn = -1;
+    uint64_t cls_key = 0;                      // workload of the cached automatic choice
+    uint64_t cls_auto_seg = 0, cls_auto_burn = 0;
     void *clsbuf = nullptr;
     size_t cls_size = 0;
     unsigned long long *cls_stats = nullptr;   // device counters of the last closed-loop call
