@@ -41,9 +41,14 @@ KERNEL_SOURCES = ["paper_2502_03796_b300/csrc/replay_tp.cu", "paper_2502_03796_b
                   "paper_2502_03796_b300/csrc/tma.cuh"]
 
 
-def kernel_sha() -> str:
+# the closed-loop kernels (their records: keys starting with "replay_closed")
+CLOSED_SOURCES = ["paper_2502_03796_b300/csrc/replay_closed.cu", "paper_2502_03796_b300/csrc/replay_closed.h",
+                  "paper_2502_03796_b300/csrc/replay_core.cuh", "paper_2502_03796_b300/csrc/magus_internal.h"]
+
+
+def kernel_sha(sources=None) -> str:
     h = hashlib.sha256()
-    for f in KERNEL_SOURCES:
+    for f in sources or KERNEL_SOURCES:
         with open(os.path.join(ROOT, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -67,7 +72,8 @@ def ncu_record(key: str) -> dict | None:
     with open(p) as f:
         d = json.load(f)
     e = d.get(key)
-    if not e or e.get("kernel_sha") != kernel_sha():
+    srcs = CLOSED_SOURCES if key.startswith("replay_closed") else KERNEL_SOURCES
+    if not e or e.get("kernel_sha") != kernel_sha(srcs):
         return None
     return e
 

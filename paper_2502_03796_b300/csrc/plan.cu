@@ -18,7 +18,7 @@
 #include <string>
 #include <vector>
 
-#include "magus_internal.h"
+#include "replay_closed.h"
 
 namespace magus {
 

@@ -30,7 +30,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-#include "magus_internal.h"
+#include "replay_closed.h"
 #include "replay_core.cuh"
 
 namespace magus {

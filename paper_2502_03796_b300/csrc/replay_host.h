@@ -8,7 +8,7 @@
 #include <string>
 #include <vector>
 
-#include "magus_internal.h"
+#include "replay_closed.h"
 
 // The replay handle (magus_replay_t of the C ABI).
 struct magus_replay {
