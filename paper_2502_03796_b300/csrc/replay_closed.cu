@@ -106,17 +106,42 @@ struct BufEmit {
 
 // One replay of a pair over consecutive rounds: its state, its charges (energy per run of
 // constant level: count of unstretched rounds, sum of stretched deltas) and change entries.
+// The thresholds of the level in effect (lv) and of the level W rounds back (lb) are kept
+// in registers and reloaded when that level changes; the flag count of Alg. 2's window is
+// kept up to date instead of recounted.
 struct Replay {
     CState s;
     CAcc acc;
     uint32_t run_n;
     unsigned long long run_s;
+    uint32_t capa, cc, thr;   // level lv: capped above capa; both capped: bit lb +1, 4 + lb -1
+    int64_t bu, bd;           // a capped, b not: +1 iff b < bu, -1 iff b >= bd
+    uint32_t lbp, capb;       // level lb (as last loaded): capped above capb
+    int64_t au, ad;           // b capped, a not: +1 iff a >= au, -1 iff a < ad
+    uint32_t cnt;             // flags among the last L rounds
 
-    __device__ __forceinline__ void start(const CState &st) {
+    __device__ __forceinline__ void load_a(const ClosedThr *Cg, const DevModel &M) {
+        capa = __ldg(&Cg->cthr[s.lv]);
+        bu = __ldg(&Cg->bu[s.lv]);
+        bd = __ldg(&Cg->bd[s.lv]);
+        cc = __ldg(&Cg->cc) >> (2u * s.lv);
+        thr = s.lv ? M.thrM : M.thr0;
+    }
+    __device__ __forceinline__ void load_b(const ClosedThr *Cg) {
+        capb = __ldg(&Cg->cthr[lbp]);
+        au = __ldg(&Cg->au[lbp]);
+        ad = __ldg(&Cg->ad[lbp]);
+    }
+    __device__ __forceinline__ void start(const CState &st, const DevPolicy &P, const ClosedThr *Cg,
+                                          const DevModel &M) {
         s = st;
         acc = CAcc{};
         run_n = 0;
         run_s = 0;
+        load_a(Cg, M);
+        lbp = (uint32_t)(s.lvh >> (P.W - 1)) & 1u;
+        load_b(Cg);
+        cnt = (uint32_t)__popcll(s.fl & low_mask(P.L));
     }
     __device__ __forceinline__ void flush() {
         if (s.lv) {
@@ -130,23 +155,25 @@ struct Replay {
         run_s = 0;
     }
     // Round t = t0 + j with a = delta_t, b = delta_{t-W}.  kCount: charge it, count its flag
-    // and change, emit its entry.
-    template <bool kCount, class Emit>
+    // and change, emit its entry.  kWarm: rounds j < warm come before the FIFO holds W + 1.
+    template <bool kCount, bool kWarm, class Emit>
     __device__ __forceinline__ void step(uint32_t a, uint32_t b, uint32_t j, uint64_t t0, uint32_t warm,
-                                         const DevPolicy &P, const DevPolicy *Pg, const ClosedThr &C,
-                                         const DevModel &M, uint64_t lmask, Emit emit) {
+                                         const DevPolicy &P, const DevPolicy *Pg, const ClosedThr *Cg,
+                                         const DevModel &M, Emit emit) {
         const uint32_t lv = s.lv;
         const uint32_t lb = (uint32_t)(s.lvh >> (P.W - 1)) & 1u;   // level of round t - W
+        if (lb != lbp) {
+            lbp = lb;
+            load_b(Cg);
+        }
         // Alg. 1 on obs_t = min(x_t, C(lv)) and obs_{t-W} = min(x_{t-W}, C(lb)); every case
         // evaluated, one selected
-        const bool ca = a > (lv ? C.cthr[1] : C.cthr[0]);
-        const bool cb = b > (lb ? C.cthr[1] : C.cthr[0]);
+        const bool ca = a > capa, cb = b > capb;
         const int64_t m = (int64_t)a - (int64_t)b;
-        const uint32_t k = 2u * lv + lb;
-        const bool up_b = ca ? ((C.cc >> k) & 1u) != 0 : (int64_t)a >= (lb ? C.au[1] : C.au[0]);
-        const bool dn_b = ca ? ((C.cc >> (4u + k)) & 1u) != 0 : (int64_t)a < (lb ? C.ad[1] : C.ad[0]);
-        const bool up_n = ca ? (int64_t)b < (lv ? C.bu[1] : C.bu[0]) : m > P.up_mid;
-        const bool dn_n = ca ? (int64_t)b >= (lv ? C.bd[1] : C.bd[0]) : m < P.dn_mid;
+        const bool up_b = ca ? ((cc >> lb) & 1u) != 0 : (int64_t)a >= au;
+        const bool dn_b = ca ? ((cc >> (4u + lb)) & 1u) != 0 : (int64_t)a < ad;
+        const bool up_n = ca ? (int64_t)b < bu : m > P.up_mid;
+        const bool dn_n = ca ? (int64_t)b >= bd : m < P.dn_mid;
         bool up = cb ? up_b : up_n, dn = cb ? dn_b : dn_n;
         const uint32_t m32 = a - b;
         if (!(ca | cb) && ((m32 - P.up_lo) <= P.up_w || (m32 - P.dn_lo) <= P.dn_w)) {
@@ -154,15 +181,19 @@ struct Replay {
             up = (r & 1u) != 0;
             dn = (r & 2u) != 0;
         }
-        if (j < warm) up = dn = false;
+        if (kWarm && j < warm) up = dn = false;
         dn = dn && !up;   // Alg. 1 tests +1 first
-        // Alg. 2: the flag enters the list, then the share of flagged rounds is tested
-        s.fl = (s.fl << 1) | ((up || dn) ? 1ull : 0ull);
-        const bool hf = __popcll(s.fl & lmask) >= P.kmin;
+        // Alg. 2: the flag enters the list (the one L rounds back leaves it), then the share
+        // of flagged rounds is tested
+        const uint32_t f = (up || dn) ? 1u : 0u;
+        const uint32_t gone = (uint32_t)(s.fl >> (P.L - 1)) & 1u;
+        s.fl = (s.fl << 1) | f;
+        cnt = cnt + f - gone;
+        const bool hf = (int)cnt >= P.kmin;
         const uint32_t next = (hf || up) ? 1u : (dn ? 0u : lv);
         if (kCount) {
             // energy model: the round at level lv, stretched when the demand exceeds C(lv)
-            const bool se = a > (lv ? M.thrM : M.thr0);
+            const bool se = a > thr;
             run_n += se ? 0u : 1u;
             run_s += se ? a : 0u;
             acc.nhf += hf ? 1u : 0u;
@@ -178,28 +209,37 @@ struct Replay {
                 acc.hash += core::mix64((when << 8) | lvl);
             }
             s.lv = next;
+            load_a(Cg, M);
         }
     }
 };
 
 // Rounds [t0, t1) of one pair's trace (t0 a multiple of 4, t1 - t0 < 2^32; the packed layout
 // pads every trace to a multiple of 32 deltas, so the 16-byte loads stay inside it).  The
-// ring holds the deltas before t0.
+// ring holds the deltas before t0; x has been started.
 template <bool kCount, class Emit>
 __device__ __forceinline__ void run_rounds(const uint32_t *tr, uint64_t t0, uint64_t t1, Replay &x,
-                                           const DevPolicy *Pg, const ClosedThr &C, const DevModel &M,
+                                           const DevPolicy *Pg, const ClosedThr *Cg, const DevModel &M,
                                            const Ring &ring, Emit emit) {
     const DevPolicy P = *Pg;
-    const uint64_t lmask = low_mask(P.L);
     const uint32_t W = (uint32_t)P.W;
     const uint32_t nr = (uint32_t)(t1 - t0);
     const uint32_t warm = t0 < W ? (uint32_t)(W - t0) : 0u;   // rounds before the FIFO holds W + 1
-    auto round = [&](uint32_t a, uint32_t j) {
-        const uint32_t b = ring.at(t0 + j - W);   // read before round t's slot is reused (W may equal R)
-        ring.at(t0 + j) = a;
-        x.step<kCount>(a, b, j, t0, warm, P, Pg, C, M, lmask, emit);
-    };
     uint32_t j = 0;
+    // the rounds before the FIFO fills (a trace's first W), to a multiple of 4
+    const uint32_t jw = min(nr, (warm + 3u) & ~3u);
+#pragma unroll 1
+    for (; j < jw; j++) {
+        const uint32_t a = __ldg(tr + t0 + j);
+        const uint32_t b = ring.at(t0 + j - W);
+        ring.at(t0 + j) = a;
+        x.step<kCount, true>(a, b, j, t0, warm, P, Pg, Cg, M, emit);
+    }
+    auto round = [&](uint32_t a, uint32_t jj) {
+        const uint32_t b = ring.at(t0 + jj - W);   // read before round t's slot is reused (W may equal R)
+        ring.at(t0 + jj) = a;
+        x.step<kCount, false>(a, b, jj, t0, 0u, P, Pg, Cg, M, emit);
+    };
 #pragma unroll 1
     for (; j + 4u <= nr; j += 4u) {
         const uint4 v = __ldg(reinterpret_cast<const uint4 *>(tr + t0 + j));
@@ -217,13 +257,13 @@ __device__ __forceinline__ void run_rounds(const uint32_t *tr, uint64_t t0, uint
 // no entries: it repeats an earlier replay) until their states agree, checked every 8
 // rounds -- the level, the levels of the last W rounds and all 64 flags (the carried state
 // written at a trace's end holds 64).  Returns the rounds run (both replays then hold the
-// state after them, runs flushed); t1 - t0 when they never agreed.
+// state after them, runs flushed); t1 - t0 when they never agreed.  Both have been started.
 template <class Emit>
 __device__ __forceinline__ uint32_t run_until_same(const uint32_t *tr, uint64_t t0, uint64_t t1, Replay &x, Replay &y,
-                                                   const DevPolicy *Pg, const ClosedThr &C, const DevModel &M,
+                                                   const DevPolicy *Pg, const ClosedThr *Cg, const DevModel &M,
                                                    const Ring &ring, Emit emit) {
     const DevPolicy P = *Pg;
-    const uint64_t lmask = low_mask(P.L), wmask = low_mask(P.W);
+    const uint64_t wmask = low_mask(P.W);
     const uint32_t W = (uint32_t)P.W;
     const uint32_t nr = (uint32_t)(t1 - t0);
     const uint32_t warm = t0 < W ? (uint32_t)(W - t0) : 0u;
@@ -236,8 +276,8 @@ __device__ __forceinline__ uint32_t run_until_same(const uint32_t *tr, uint64_t 
             const uint32_t a = __ldg(tr + t0 + j);
             const uint32_t b = ring.at(t0 + j - W);
             ring.at(t0 + j) = a;
-            x.step<true>(a, b, j, t0, warm, P, Pg, C, M, lmask, emit);
-            y.step<true>(a, b, j, t0, warm, P, Pg, C, M, lmask, NoEmit{});
+            x.step<true, true>(a, b, j, t0, warm, P, Pg, Cg, M, emit);
+            y.step<true, true>(a, b, j, t0, warm, P, Pg, Cg, M, NoEmit{});
         }
         if (same_state(x.s, y.s, wmask, ~0ull)) break;
     }
@@ -309,7 +349,7 @@ __device__ __forceinline__ void closed_pass(const ClosedParams &p) {
     const ItemPos q = locate(p, item);
     const int pol = p.cls[q.ci];
     const DevPolicy *Pg = p.pols + pol;
-    const ClosedThr C = p.thr[q.ci];
+    const ClosedThr *C = p.thr + q.ci;
     const DevModel &M = p.model;
     const int64_t pair = (int64_t)q.trace * p.n_pols + pol;
     const uint32_t *tr = p.traces + p.offsets[q.trace];
@@ -324,15 +364,15 @@ __device__ __forceinline__ void closed_pass(const ClosedParams &p) {
         uint32_t ok = 1u;
         const uint64_t t0 = s0 > p.burn ? s0 - p.burn : 0;
         if (t0 == 0) {
-            x.start(initial_state(p, pair));
+            x.start(initial_state(p, pair), *Pg, C, M);
             ok |= 2u;   // started from the true state
         } else {
-            x.start(CState{0u, 0ull, 0ull});
+            x.start(CState{0u, 0ull, 0ull}, *Pg, C, M);
         }
         prefill(tr, t0, ring);
         run_rounds<false>(tr, t0, s0, x, Pg, C, M, ring, NoEmit{});
         const CState in = x.s;
-        x.start(in);
+        x.start(in, *Pg, C, M);
         run_rounds<true>(tr, s0, s1, x, Pg, C, M, ring, em);
         if (scr && x.acc.nch > p.scr_cap) ok |= 4u;   // entries lost: not reused with a log
         store_slot(out, in, x.s, x.acc, ok);
@@ -352,7 +392,7 @@ __device__ __forceinline__ void closed_pass(const ClosedParams &p) {
     }
     atomicAdd(&p.stats[0], 1ull);
     prefill(tr, s0, ring);
-    x.start(e);
+    x.start(e, *Pg, C, M);
     CAcc acc;
     CState end;
     if (scr && (mine.ok & 4u)) {
@@ -362,7 +402,7 @@ __device__ __forceinline__ void closed_pass(const ClosedParams &p) {
         end = x.s;
     } else {
         Replay y;
-        y.start(u);
+        y.start(u, *Pg, C, M);
         const uint32_t r = run_until_same(tr, s0, s1, x, y, Pg, C, M, ring, em);
         if (r < (uint32_t)(s1 - s0)) {
             // from round s0 + r on the first replay stands: its charges, entries, end state
@@ -399,7 +439,7 @@ __global__ void __launch_bounds__(kThreads) closed_final_kernel(const ClosedPara
         return;
     }
     const DevPolicy *Pg = p.pols + pol;
-    const ClosedThr C = p.thr[ci];
+    const ClosedThr *C = p.thr + ci;
     const DevModel &M = p.model;
     const uint32_t *tr = p.traces + p.offsets[trace];
     const uint64_t n = p.lengths[trace];
@@ -464,7 +504,7 @@ __global__ void __launch_bounds__(kThreads) closed_final_kernel(const ClosedPara
         prefill(tr, s0, ring);
         const BufEmit em{lg ? lg + NCH : nullptr, NCH < p.log_cap ? p.log_cap - NCH : 0};
         Replay x;
-        x.start(E);
+        x.start(E, *Pg, C, M);
         if (logging && (first.ok & 4u)) {
             run_rounds<true>(tr, s0, s1, x, Pg, C, M, ring, em);
             add(x.acc);
@@ -472,7 +512,7 @@ __global__ void __launch_bounds__(kThreads) closed_final_kernel(const ClosedPara
             continue;
         }
         Replay y;
-        y.start(CState{first.lv_in, first.lvh_in, first.fl_in});
+        y.start(CState{first.lv_in, first.lvh_in, first.fl_in}, *Pg, C, M);
         const uint32_t r = run_until_same(tr, s0, s1, x, y, Pg, C, M, ring, em);
         if (r < (uint32_t)(s1 - s0)) {
             if (logging) copy(0, item, y.acc.nch, first.nch, NCH + x.acc.nch);
