@@ -98,7 +98,7 @@ struct NoEmit {
 };
 struct BufEmit {
     uint32_t *buf;
-    uint64_t cap;
+    uint32_t cap;
     __device__ __forceinline__ void operator()(uint32_t e, uint32_t i) const {
         if (buf && i < cap) buf[i] = e;
     }
@@ -358,7 +358,7 @@ __device__ __forceinline__ void closed_pass(const ClosedParams &p) {
     ClosedSlot &out = p.slots[(uint64_t)(pass - 1) * p.n_items + item];
     const Ring ring{ring_s + threadIdx.x, p.ring - 1u};
     uint32_t *scr = p.scratch ? p.scratch + ((uint64_t)(pass - 1) * p.n_items + item) * p.scr_cap : nullptr;
-    const BufEmit em{scr, p.scr_cap};
+    const BufEmit em{scr, (uint32_t)p.scr_cap};   // scr_cap <= segment rounds < 2^32
     Replay x;
     if constexpr (pass == 1) {
         uint32_t ok = 1u;
@@ -371,11 +371,14 @@ __device__ __forceinline__ void closed_pass(const ClosedParams &p) {
         }
         prefill(tr, t0, ring);
         run_rounds<false>(tr, t0, s0, x, Pg, C, M, ring, NoEmit{});
-        const CState in = x.s;
-        x.start(in, *Pg, C, M);
+        // the start state goes out now (fewer live registers through the segment)
+        out.lv_in = x.s.lv;
+        out.lvh_in = x.s.lvh;
+        out.fl_in = x.s.fl;
+        x.start(x.s, *Pg, C, M);
         run_rounds<true>(tr, s0, s1, x, Pg, C, M, ring, em);
         if (scr && x.acc.nch > p.scr_cap) ok |= 4u;   // entries lost: not reused with a log
-        store_slot(out, in, x.s, x.acc, ok);
+        store_slot(out, CState{out.lv_in, out.lvh_in, out.fl_in}, x.s, x.acc, ok);
         return;
     } else {
     if (q.k == 0) {
@@ -502,7 +505,8 @@ __global__ void __launch_bounds__(kThreads) closed_final_kernel(const ClosedPara
         atomicAdd(&p.stats[1], 1ull);
         const ClosedSlot &first = p.slots[item];
         prefill(tr, s0, ring);
-        const BufEmit em{lg ? lg + NCH : nullptr, NCH < p.log_cap ? p.log_cap - NCH : 0};
+        const BufEmit em{lg ? lg + NCH : nullptr,
+                         NCH < p.log_cap ? (uint32_t)min(p.log_cap - NCH, (uint64_t)0xffffffffull) : 0u};
         Replay x;
         x.start(E, *Pg, C, M);
         if (logging && (first.ok & 4u)) {
