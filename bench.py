@@ -395,7 +395,13 @@ def run_other(args, world, rank, local) -> int:
     # many policies per byte read: the integer ALU pipe bounds these launches; report that
     # roofline (ncu lane-operations per (interval, policy), committed with the source hash,
     # against 148 SMs x 64 integer lanes per cycle at the sampled SM clock)
-    rec = ncu_record(f"replay_tp_{args.workload}")
+    # (the closed loop: one thread per segment replays its rounds in order, integer ALU work;
+    # its record holds for the benchmark's 4,096 traces, whose automatic segments fix the
+    # share of burn-in rounds)
+    if args.workload == "closed":
+        rec = ncu_record("replay_closed_batched") if ts.n_traces == N_TRACES else None
+    else:
+        rec = ncu_record(f"replay_tp_{args.workload}")
     if rec and rec.get("alu_lane_ops_per_pair_interval") and clk.get("sm_mhz"):
         alu_ach = rec["alu_lane_ops_per_pair_interval"] * pair_steps / (k_avg * 1e-3)
         alu_peak = 148 * 4 * 16 * clk["sm_mhz"] * 1e6
