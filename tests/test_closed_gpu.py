@@ -6,14 +6,13 @@ true state.  These tests make the guesses fail on purpose (short segments, no bu
 overflow the per-segment change-entry scratch, and check every pair against the oracle:
 decision logs, counts and hashes bit-exact, energy / time / EDP within 1e-9 relative.
 """
-import ctypes
 
 import numpy as np
 import pytest
 
 import oracle
 import tracegen
-from gpu_util import REL_TOL, assert_pair, oracle_pairs, to_device, to_numpy
+from gpu_util import assert_pair, oracle_pairs, to_device, to_numpy
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -168,3 +167,34 @@ def test_closed_loop_batched_full_size_sampled(mg):
     for p in (0, 1, 2047, 4095):
         r = oracle.replay(ts.trace(p), pols[0], model, log_cap=0)
         assert_pair(out, p, r, tag="closed batched sampled")
+
+
+@pytest.mark.parametrize("seed", [31, 32, 33, 34])
+def test_closed_loop_random(mg, seed):
+    """Random closed-loop policies (windows, lists, thresholds including infinities and
+    inc < dec), random lengths and phase means, random segment / burn-in lengths and log
+    capacities: every pair against the oracle."""
+    from test_fuzz_gpu import random_policy
+    rng = np.random.default_rng(seed)
+    model = tracegen.default_model()
+    K = len(model["f_ghz"])
+    lengths = rng.integers(0, 60_000, size=7).astype(np.uint64)
+    ts = tracegen.make_traces(lengths, seed=seed, mean_phase=float(rng.uniform(2, 80)))
+    pols = []
+    while len(pols) < 6:
+        p = random_policy(rng, K)
+        p["step_mode"], p["pin_level"] = 2, 0
+        pols.append(p)
+    ref = oracle_pairs(ts, pols, model)
+    rp = mg.Replay(model)
+    try:
+        for _ in range(2):
+            seg, burn = [(64, 0), (128, 64), (256, 0), (512, 128), (0, -1)][int(rng.integers(0, 5))]
+            cap = int(rng.choice([0, 13, 60_000]))
+            rp.set_closed(seg, burn)
+            out = to_numpy(rp.run(to_device(ts), ts.lengths, pols, log_capacity=cap))
+            assert rp.status() == 0
+            for p, r in ref.items():
+                assert_pair(out, p, r, cap=cap, tag=f"seed {seed} seg {seg} burn {burn} policy {pols[p % len(pols)]}")
+    finally:
+        rp.close()
