@@ -390,8 +390,9 @@ def run_other(args, world, rank, local) -> int:
                               alg_bytes_per_launch=alg_bytes),
                 gpu_launches=k_kernels, clocks=clk)
     if args.workload == "closed":
-        segs, second, final = rp.closed_stats()
-        line["config"]["closed_replay"] = dict(segments=segs, second_replays=second, final_pass_replays=final)
+        segs, second, final, logged = rp.closed_stats()
+        line["config"]["closed_replay"] = dict(segments=segs, second_replays=second, final_pass_replays=final,
+                                               log_pass_replays=logged)
     # many policies per byte read: the integer ALU pipe bounds these launches; report that
     # roofline (ncu lane-operations per (interval, policy), committed with the source hash,
     # against 148 SMs x 64 integer lanes per cycle at the sampled SM clock)

@@ -214,16 +214,19 @@ int magus_replay_set_segments(magus_replay_t *h, int32_t seg_rounds);
  * (trace, policy, segment of seg_rounds rounds) is replayed on its own from a guessed state
  * burn_rounds earlier; a segment whose guess did not reach the state its predecessor ended
  * in is replayed again, and a final pass per pair takes the replays that started from the
- * true state (results identical to the sequential replay whatever the guesses).
+ * true state (results identical to the sequential replay whatever the guesses); with a
+ * change log, segments with more entries than their scratch holds are replayed once more
+ * to write them.
  * seg_rounds: 0 automatic (about four waves of threads, 1,024 .. 65,536), > 0 a multiple of
  * 64 up to 2^24, -1 the literal kernel (one thread per pair); burn_rounds: -1 automatic
  * (seg_rounds / 4), else a multiple of 64 up to 2^24.  EINVAL otherwise. */
 int magus_replay_set_closed(magus_replay_t *h, int32_t seg_rounds, int32_t burn_rounds);
 
-/* Work of the last call's time-parallel closed-loop replay (host, 3 values): segments
- * replayed, second replays, replays in the final pass (0, 0, 0 when it did not run).  Waits
- * for the handle's outstanding launches. */
-int magus_replay_closed_stats(magus_replay_t *h, uint64_t *out3);
+/* Work of the last call's time-parallel closed-loop replay (host, 4 values): segments
+ * replayed, second replays, replays in the final pass, replays in the log pass (segments
+ * whose change entries overflowed their scratch); all 0 when it did not run.  Waits for the
+ * handle's outstanding launches. */
+int magus_replay_closed_stats(magus_replay_t *h, uint64_t *out4);
 
 /* Autotuner: time every supported tile shape (time_groups x policy_slots x group size 1 or
  * 4) of the tile kernel and the segment kernel (segments of 8,192 / 16,384 / 32,768 rounds,

@@ -378,16 +378,17 @@ int magus_replay_set_closed(magus_replay_t *h, int32_t seg_rounds, int32_t burn_
     return MAGUS_OK;
 }
 
-int magus_replay_closed_stats(magus_replay_t *h, uint64_t *out3) {
-    if (!h || !out3) { set_error("NULL argument"); return MAGUS_EINVAL; }
-    out3[0] = out3[1] = out3[2] = 0;
+int magus_replay_closed_stats(magus_replay_t *h, uint64_t *out4) {
+    if (!h || !out4) { set_error("NULL argument"); return MAGUS_EINVAL; }
+    out4[0] = out4[1] = out4[2] = out4[3] = 0;
     if (!h->cls_stats) return MAGUS_OK;
     if (h->ws_ev_pending) CK(cudaEventSynchronize(h->ws_ev), "cudaEventSynchronize");
-    unsigned long long st[2] = {0, 0};
+    unsigned long long st[3] = {0, 0, 0};
     CK(cudaMemcpy(st, h->cls_stats, sizeof(st), cudaMemcpyDeviceToHost), "cudaMemcpy(closed stats)");
-    out3[0] = h->cls_items;
-    out3[1] = st[0];
-    out3[2] = st[1];
+    out4[0] = h->cls_items;
+    out4[1] = st[0];
+    out4[2] = st[1];
+    out4[3] = st[2];
     return MAGUS_OK;
 }
 

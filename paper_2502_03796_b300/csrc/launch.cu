@@ -631,18 +631,25 @@ int launch_closed_part(magus_replay *h, const Plan &pl, const uint32_t *traces, 
     }
     ibase[n_traces] = items;
     const bool logging = o.log_entries && o.log_cap > 0;
-    const uint64_t scr_cap = logging ? std::min<uint64_t>(S, std::max<uint64_t>(64, S / 8)) : 0;
-    // buffer: policies | thresholds | item bases | counters | replay slots | entry scratch
+    // buffer: policies | thresholds | item bases | counters | replay slots | log-pass jobs |
+    // entry scratch (per replay; a replay with more entries leaves them to the log pass, so
+    // the scratch shrinks to what the budget holds)
     const size_t sz_cls = align_up((size_t)n_cls * 4, 256);
     const size_t sz_thr = align_up((size_t)n_cls * sizeof(ClosedThr), 256);
     const size_t sz_ib = align_up((size_t)(n_traces + 1) * 8, 256);
     const size_t plan_bytes = sz_cls + sz_thr + sz_ib;
     const size_t sz_st = 256;
     const size_t sz_slot = align_up((size_t)(2 * items) * sizeof(ClosedSlot), 256);
-    const size_t sz_scr = align_up((size_t)(2 * items * scr_cap) * 4, 256);
-    const size_t need = plan_bytes + sz_st + sz_slot + sz_scr;
+    const size_t sz_job = logging ? align_up((size_t)items * sizeof(ClosedJob), 256) : 0;
+    const size_t others = h->ws_size + h->scratch_size + h->seg_size;
+    uint64_t scr_cap = logging ? std::min<uint64_t>(S, std::max<uint64_t>(64, S / 8)) : 0;
+    auto need_of = [&](uint64_t cap) {
+        return plan_bytes + sz_st + sz_slot + sz_job + align_up((size_t)(2 * items * cap) * 4, 256);
+    };
+    while (scr_cap > 0 && others + std::max(need_of(scr_cap), h->cls_size) > h->budget) scr_cap /= 2;
+    const size_t need = need_of(scr_cap);
     const bool segmented = h->cls_seg >= 0 && items <= (uint64_t)INT32_MAX * closed_threads_per_cta() &&
-                           h->ws_size + h->scratch_size + h->seg_size + std::max(need, h->cls_size) <= h->budget;
+                           others + std::max(need, h->cls_size) <= h->budget;
     int rc = ensure_ws(h, &h->clsbuf, &h->cls_size, segmented ? need : sz_cls);
     if (rc) return rc;
     char *buf = (char *)h->clsbuf;
@@ -662,7 +669,9 @@ int launch_closed_part(magus_replay *h, const Plan &pl, const uint32_t *traces, 
         return MAGUS_OK;
     }
     unsigned long long *stats = (unsigned long long *)(buf + plan_bytes);
-    CK(cudaMemsetAsync(stats, 0, 2 * sizeof(unsigned long long), stream), "cudaMemsetAsync");
+    CK(cudaMemsetAsync(stats, 0, 3 * sizeof(unsigned long long), stream), "cudaMemsetAsync");
+    // no stale log-pass jobs (the final pass sets those of every pair it completes)
+    if (logging) CK(cudaMemsetAsync(buf + plan_bytes + sz_st + sz_slot, 0, sz_job, stream), "cudaMemsetAsync");
     ClosedParams cp;
     memset(&cp, 0, sizeof(cp));
     cp.traces = traces;
@@ -681,7 +690,8 @@ int launch_closed_part(magus_replay *h, const Plan &pl, const uint32_t *traces, 
     cp.burn = (uint32_t)G;
     cp.model = h->dm;
     cp.slots = (ClosedSlot *)(buf + plan_bytes + sz_st);
-    cp.scratch = scr_cap ? (uint32_t *)(buf + plan_bytes + sz_st + sz_slot) : nullptr;
+    cp.jobs = logging ? (ClosedJob *)(buf + plan_bytes + sz_st + sz_slot) : nullptr;
+    cp.scratch = scr_cap ? (uint32_t *)(buf + plan_bytes + sz_st + sz_slot + sz_job) : nullptr;
     cp.scr_cap = scr_cap;
     cp.energy = o.energy;
     cp.edp = o.edp;
@@ -695,7 +705,7 @@ int launch_closed_part(magus_replay *h, const Plan &pl, const uint32_t *traces, 
     cp.status = h->status;
     cp.stats = stats;
     CK(launch_replay_closed(cp, stream), "closed-loop kernel launch");
-    *kernels += items ? 3 : 1;
+    *kernels += (items ? 3 : 1) + ((items && logging) ? 1 : 0);
     h->cls_items = items;
     h->cls_stats = stats;
     return MAGUS_OK;

@@ -17,6 +17,8 @@
 //   final   one thread per pair walks its segments in order from the true initial state,
 //           takes a replay whose start state equals the state reached so far, replays the
 //           segment once more where neither does, and adds up charges and change entries.
+//   log     with a change log, segments whose entries overflowed their replay's scratch are
+//           replayed once more from their true start state, writing straight to the log.
 // The final walk makes the result exact whatever the guesses; the guesses only decide how
 // much is replayed twice.  A second replay runs in lockstep with a repeat of the first one
 // and stops once their states agree: from there on the first replay's charges and entries
@@ -357,6 +359,7 @@ __device__ __forceinline__ void closed_pass(const ClosedParams &p) {
     const uint64_t s0 = q.k * p.seg_len, s1 = min(n, s0 + p.seg_len);
     ClosedSlot &out = p.slots[(uint64_t)(pass - 1) * p.n_items + item];
     const Ring ring{ring_s + threadIdx.x, p.ring - 1u};
+    const bool logging = p.log_entries && p.log_cap > 0;
     uint32_t *scr = p.scratch ? p.scratch + ((uint64_t)(pass - 1) * p.n_items + item) * p.scr_cap : nullptr;
     const BufEmit em{scr, (uint32_t)p.scr_cap};   // scr_cap <= segment rounds < 2^32
     Replay x;
@@ -377,7 +380,7 @@ __device__ __forceinline__ void closed_pass(const ClosedParams &p) {
         out.fl_in = x.s.fl;
         x.start(x.s, *Pg, C, M);
         run_rounds<true>(tr, s0, s1, x, Pg, C, M, ring, em);
-        if (scr && x.acc.nch > p.scr_cap) ok |= 4u;   // entries lost: not reused with a log
+        if (logging && x.acc.nch > p.scr_cap) ok |= 4u;   // entries lost: the log pass writes them
         store_slot(out, CState{out.lv_in, out.lvh_in, out.fl_in}, x.s, x.acc, ok);
         return;
     } else {
@@ -398,32 +401,28 @@ __device__ __forceinline__ void closed_pass(const ClosedParams &p) {
     x.start(e, *Pg, C, M);
     CAcc acc;
     CState end;
-    if (scr && (mine.ok & 4u)) {
-        // the first replay's entries are incomplete: no shortcut
-        run_rounds<true>(tr, s0, s1, x, Pg, C, M, ring, em);
+    bool lost = false;   // entries incomplete
+    Replay y;
+    y.start(u, *Pg, C, M);
+    const uint32_t r = run_until_same(tr, s0, s1, x, y, Pg, C, M, ring, em);
+    if (r < (uint32_t)(s1 - s0)) {
+        // from round s0 + r on the first replay stands: its charges, entries, end state
+        acc = acc_add_diff(x.acc, mine, y.acc);
+        end = CState{mine.lv_out, mine.lvh_out, mine.fl_out};
+        lost = (mine.ok & 4u) != 0;
+        if (scr && !lost) {
+            const uint32_t *src = p.scratch + item * p.scr_cap;
+            for (uint32_t i = y.acc.nch; i < mine.nch; i++) {
+                const uint64_t d = (uint64_t)x.acc.nch + (i - y.acc.nch);
+                if (d < p.scr_cap) scr[d] = src[i];
+            }
+        }
+    } else {
         acc = x.acc;
         end = x.s;
-    } else {
-        Replay y;
-        y.start(u, *Pg, C, M);
-        const uint32_t r = run_until_same(tr, s0, s1, x, y, Pg, C, M, ring, em);
-        if (r < (uint32_t)(s1 - s0)) {
-            // from round s0 + r on the first replay stands: its charges, entries, end state
-            acc = acc_add_diff(x.acc, mine, y.acc);
-            end = CState{mine.lv_out, mine.lvh_out, mine.fl_out};
-            if (scr) {
-                const uint32_t *src = p.scratch + item * p.scr_cap;
-                for (uint32_t i = y.acc.nch; i < mine.nch; i++) {
-                    const uint64_t d = (uint64_t)x.acc.nch + (i - y.acc.nch);
-                    if (d < p.scr_cap) scr[d] = src[i];
-                }
-            }
-        } else {
-            acc = x.acc;
-            end = x.s;
-        }
     }
-    store_slot(out, e, end, acc, 1u | ((scr && acc.nch > p.scr_cap) ? 4u : 0u));
+    lost = lost || acc.nch > p.scr_cap;
+    store_slot(out, e, end, acc, 1u | ((logging && lost) ? 4u : 0u));
     }
 }
 __global__ void __launch_bounds__(kThreads, 5) closed_first_kernel(const ClosedParams p) { closed_pass<1>(p); }
@@ -479,15 +478,28 @@ __global__ void __launch_bounds__(kThreads) closed_final_kernel(const ClosedPara
         uint64_t which = 0;
         for (uint64_t w = 0; w < 2 && !pick; w++) {
             const ClosedSlot &c = p.slots[w * p.n_items + item];
-            if (!(c.ok & 1u) || (logging && (c.ok & 4u))) continue;
+            if (!(c.ok & 1u)) continue;
             const CState u{c.lv_in, c.lvh_in, c.fl_in};
             if ((c.ok & 2u) || same_state(E, u, wmask, fmask)) {
                 pick = &c;
                 which = w;
             }
         }
+        // with a log: the segment's entries come from a replay's scratch, else (it overflowed)
+        // from the log pass, replaying the segment from the state reached here
+        if (logging) {
+            ClosedJob &jb = p.jobs[item];
+            jb.on = 0;
+            if (pick ? (pick->ok & 4u) != 0 : (p.slots[item].ok & 4u) != 0) {
+                jb.lvh = E.lvh;
+                jb.fl = E.fl;
+                jb.lv = E.lv;
+                jb.off = NCH;
+                jb.on = 1;
+            }
+        }
         if (pick) {
-            if (logging) copy(which, item, 0, pick->nch, NCH);
+            if (logging && !(pick->ok & 4u)) copy(which, item, 0, pick->nch, NCH);
             CAcc a;
             a.n0 = pick->n0;
             a.nm = pick->nm;
@@ -509,20 +521,16 @@ __global__ void __launch_bounds__(kThreads) closed_final_kernel(const ClosedPara
                          NCH < p.log_cap ? (uint32_t)min(p.log_cap - NCH, (uint64_t)0xffffffffull) : 0u};
         Replay x;
         x.start(E, *Pg, C, M);
-        if (logging && (first.ok & 4u)) {
-            run_rounds<true>(tr, s0, s1, x, Pg, C, M, ring, em);
-            add(x.acc);
-            E = x.s;
-            continue;
-        }
         Replay y;
         y.start(CState{first.lv_in, first.lvh_in, first.fl_in}, *Pg, C, M);
         const uint32_t r = run_until_same(tr, s0, s1, x, y, Pg, C, M, ring, em);
         if (r < (uint32_t)(s1 - s0)) {
-            if (logging) copy(0, item, y.acc.nch, first.nch, NCH + x.acc.nch);
+            // (entries of an overflowed first replay: the log pass writes the segment)
+            if (logging && !(first.ok & 4u)) copy(0, item, y.acc.nch, first.nch, NCH + x.acc.nch);
             add(acc_add_diff(x.acc, first, y.acc));
             E = CState{first.lv_out, first.lvh_out, first.fl_out};
         } else {
+            if (logging) p.jobs[item].on = 0;   // every entry went straight to the log
             add(x.acc);
             E = x.s;
         }
@@ -547,6 +555,32 @@ __global__ void __launch_bounds__(kThreads) closed_final_kernel(const ClosedPara
             so.hist[k] = idx >= 0 ? tr[idx] : so.hist[64 + idx];
         }
     }
+}
+
+// Log pass: the segments the final pass marked, replayed from their true start state with
+// their entries written straight to the pair's log.
+__global__ void __launch_bounds__(kThreads) closed_log_kernel(const ClosedParams p) {
+    extern __shared__ uint32_t ring_s[];
+    const uint64_t item = (uint64_t)blockIdx.x * kThreads + threadIdx.x;
+    if (item >= p.n_items || !p.jobs[item].on) return;
+    const ClosedJob jb = p.jobs[item];
+    const ItemPos q = locate(p, item);
+    const int pol = p.cls[q.ci];
+    const DevPolicy *Pg = p.pols + pol;
+    const ClosedThr *C = p.thr + q.ci;
+    const int64_t pair = (int64_t)q.trace * p.n_pols + pol;
+    const uint32_t *tr = p.traces + p.offsets[q.trace];
+    const uint64_t n = p.lengths[q.trace];
+    const uint64_t s0 = q.k * p.seg_len, s1 = min(n, s0 + p.seg_len);
+    if (jb.off >= p.log_cap) return;
+    atomicAdd(&p.stats[2], 1ull);
+    const Ring ring{ring_s + threadIdx.x, p.ring - 1u};
+    prefill(tr, s0, ring);
+    Replay x;
+    x.start(CState{jb.lv, jb.lvh, jb.fl}, *Pg, C, p.model);
+    const BufEmit em{p.log_entries + (uint64_t)pair * p.log_cap + jb.off,
+                     (uint32_t)min(p.log_cap - jb.off, (uint64_t)0xffffffffull)};
+    run_rounds<true>(tr, s0, s1, x, Pg, C, p.model, ring, em);
 }
 
 }  // namespace
@@ -577,6 +611,11 @@ cudaError_t launch_replay_closed(const ClosedParams &p, cudaStream_t stream) {
     const int64_t pairs = (int64_t)p.n_traces * p.n_cls;
     if (pairs > 0) {
         closed_final_kernel<<<(unsigned)((pairs + kThreads - 1) / kThreads), kThreads, smem, stream>>>(p);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    if (p.n_items && p.jobs && p.log_entries && p.log_cap > 0) {
+        closed_log_kernel<<<(unsigned)((p.n_items + kThreads - 1) / kThreads), kThreads, smem, stream>>>(p);
         return cudaGetLastError();
     }
     return cudaSuccess;

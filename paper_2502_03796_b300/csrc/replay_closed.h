@@ -30,6 +30,15 @@ struct ClosedSlot {
     uint32_t pad;
 };
 
+// A segment whose change entries the final pass could not take from a replay's scratch (it
+// overflowed): replayed once more by the log pass from its true start state, writing its
+// entries to the pair's log from entry `off` on.
+struct ClosedJob {
+    uint64_t lvh, fl;   // state at the segment start
+    uint64_t off;       // index of its first entry in the pair's log
+    uint32_t lv, on;    // level bit; on: replay it
+};
+
 struct ClosedParams {
     const uint32_t *traces;
     const uint64_t *offsets;
@@ -49,13 +58,14 @@ struct ClosedParams {
     ClosedSlot *slots;           // [2][n_items]: first replay, second replay
     uint32_t *scratch;           // [2][n_items][scr_cap] change entries, or NULL
     uint64_t scr_cap;
+    ClosedJob *jobs;             // [n_items], with a log: segments for the log pass
     double *energy, *edp, *time;
     uint32_t *log_entries;
     uint64_t log_cap;
     uint64_t *n_changes, *change_hash, *n_hf;
     magus_state_t *state;
     int *status;
-    unsigned long long *stats;   // [2]: second replays, replays in the final pass
+    unsigned long long *stats;   // [3]: second replays, replays in the final pass, in the log pass
 };
 __host__ __device__ inline bool closed_policy(const DevPolicy &d) { return d.step_mode == 2 && d.pin == 0; }
 void derive_closed(const DevPolicy &pol, const DevModel &m, ClosedThr *out);

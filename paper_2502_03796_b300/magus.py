@@ -345,8 +345,9 @@ class Replay:
         check(lib().magus_replay_set_closed(self.h, seg_rounds, burn_rounds))
 
     def closed_stats(self):
-        """(segments replayed, second replays, final-pass replays) of the last call."""
-        out = (ctypes.c_uint64 * 3)()
+        """(segments replayed, second replays, final-pass replays, log-pass replays) of the
+        last call."""
+        out = (ctypes.c_uint64 * 4)()
         check(lib().magus_replay_closed_stats(self.h, out))
         return tuple(int(v) for v in out)
 

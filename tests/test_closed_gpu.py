@@ -68,7 +68,7 @@ def test_closed_loop_matches_oracle(rp, seg, burn):
         assert rp.status() == 0
         for p, r in ref.items():
             assert_pair(out, p, r, cap=cap, tag=f"closed seg={seg} burn={burn} cap={cap}")
-    items, second, final = rp.closed_stats()
+    items, second, final, logged = rp.closed_stats()
     n_cls = len(closed_policies())
     if seg > 0:
         assert items == sum((int(n) + seg - 1) // seg for n in ts.lengths) * n_cls
@@ -79,7 +79,7 @@ def test_closed_loop_matches_oracle(rp, seg, burn):
 
 
 def test_closed_loop_entry_scratch_overflow(rp):
-    """More change entries in a segment than its scratch holds: the final pass replays those
+    """More change entries in a segment than its scratch holds: the log pass replays those
     segments straight into the log."""
     ts = tracegen.make_traces(np.array([6000, 9001], dtype=np.uint64), seed=5, mean_phase=2.0)
     model = tracegen.default_model()
@@ -92,8 +92,8 @@ def test_closed_loop_entry_scratch_overflow(rp):
     assert rp.status() == 0
     for p, r in ref.items():
         assert_pair(out, p, r, cap=20_000, tag="scratch overflow")
-    items, second, final = rp.closed_stats()
-    assert final > 0
+    items, second, final, logged = rp.closed_stats()
+    assert logged > 0
 
 
 def oracle_state(level, flags64, L):
@@ -160,8 +160,8 @@ def test_closed_loop_batched_full_size_sampled(mg):
     try:
         out = to_numpy(rp.run(to_device(ts), ts.lengths, pols, log_capacity=0))
         assert rp.status() == 0
-        items, second, final = rp.closed_stats()
-        assert items > 4096
+        items, second, final, logged = rp.closed_stats()
+        assert items > 4096 and logged == 0
     finally:
         rp.close()
     for p in (0, 1, 2047, 4095):
