@@ -334,13 +334,14 @@ def run_other(args, world, rank, local) -> int:
         ts = tracegen.sweep(first_id=rank * 1024)
         pols = tracegen.sweep_policies()
         desc = "policy sweep: 1024 traces x 200000 intervals (bursty mean 10 / long mean 500 regimes), 256 policies"
-    elif args.workload in ("ladder", "closed"):
+    elif args.workload in ("ladder", "closed", "closed_ladder"):
         ts = tracegen.batched(n_traces=args.traces, seed=rank, first_id=rank * args.traces)
-        mode = 1 if args.workload == "ladder" else 2
+        mode = {"ladder": 1, "closed": 2, "closed_ladder": 3}[args.workload]
         pols = [dict(tracegen.default_policy(), step_mode=mode)]
         kern = "ladder kernel" if mode == 1 else ("literal kernel" if args.closed.startswith("-1") else
                                                   "segmented closed-loop kernels")
-        desc = (f"batched replay, {'one rung per decision' if mode == 1 else 'closed loop'} ({kern}): "
+        what = {1: "one rung per decision", 2: "closed loop", 3: "closed loop, one rung per decision"}[mode]
+        desc = (f"batched replay, {what} ({kern}): "
                 f"{args.traces} traces x 100000 intervals (phase mean 40), 1 policy")
     elif args.workload == "long":
         ts = tracegen.batched(n_traces=16, n=4_000_000, seed=rank, first_id=rank * 16)
@@ -389,7 +390,7 @@ def run_other(args, world, rank, local) -> int:
                               traffic=None, kernel_ms=k_avg, main_kernel_ms=k_main / max(k_n, 1),
                               alg_bytes_per_launch=alg_bytes),
                 gpu_launches=k_kernels, clocks=clk)
-    if args.workload == "closed":
+    if args.workload in ("closed", "closed_ladder"):
         segs, second, final, logged = rp.closed_stats()
         line["config"]["closed_replay"] = dict(segments=segs, second_replays=second, final_pass_replays=final,
                                                log_pass_replays=logged)
@@ -399,8 +400,9 @@ def run_other(args, world, rank, local) -> int:
     # (the closed loop: one thread per segment replays its rounds in order, integer ALU work;
     # its record holds for the benchmark's 4,096 traces, whose automatic segments fix the
     # share of burn-in rounds)
-    if args.workload == "closed":
-        rec = ncu_record("replay_closed_batched") if ts.n_traces == N_TRACES else None
+    if args.workload in ("closed", "closed_ladder"):
+        key = "replay_closed_batched" if args.workload == "closed" else "replay_closed_ladder_batched"
+        rec = ncu_record(key) if ts.n_traces == N_TRACES else None
     else:
         rec = ncu_record(f"replay_tp_{args.workload}")
     if rec and rec.get("alu_lane_ops_per_pair_interval") and clk.get("sm_mhz"):
@@ -478,7 +480,8 @@ def main() -> int:
     ap.add_argument("--traces", type=int, default=N_TRACES, help="traces per GPU (profiling runs use fewer)")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-savings", action="store_true")
-    ap.add_argument("--workload", default="batched", choices=["batched", "sweep", "uneven", "single", "long", "ladder", "closed"],
+    ap.add_argument("--workload", default="batched",
+                    choices=["batched", "sweep", "uneven", "single", "long", "ladder", "closed", "closed_ladder"],
                     help="batched (default, the headline line); sweep / uneven / single print their own line")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)

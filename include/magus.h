@@ -136,12 +136,12 @@ int magus_replay_open(magus_replay_t **h, const magus_model_t *model, int device
 /* Replay n_traces x n_configs (trace, policy) pairs (rounds above).  Policies in the open-loop
  * jump mode (step_mode 0, pin_level 0, 1 or n_levels) run on the time-parallel kernels (tile
  * or segment kernel), the one-rung mode (step_mode 1, pin_level 0) on the ladder kernel, the
- * closed loop in jump mode (step_mode 2, pin_level 0) on the segmented closed-loop kernels
- * (magus_replay_set_closed); the others (closed loop one rung per decision, a pin inside
- * the ladder or under a closed loop) run in the same call on the literal kernel, one
- * thread per pair.  With io_state a closed-loop policy needs a fresh state (n_seen 0; else
- * EINVAL through magus_replay_status): its throughput FIFO would need past levels; in jump
- * mode its carried level must be 0 or n_levels - 1.
+ * closed loop (step_mode 2 or 3, pin_level 0) on the segmented closed-loop kernels
+ * (magus_replay_set_closed); the others (a pin inside the ladder or under a closed loop)
+ * run in the same call on the literal kernel, one thread per pair.  With io_state a
+ * closed-loop policy needs a fresh state (n_seen 0; else EINVAL through
+ * magus_replay_status): its throughput FIFO would need past levels; in jump mode its
+ * carried level must be 0 or n_levels - 1.
  *   traces     device, packed layout; base address 16-byte aligned
  *   lengths    host [n_traces] intervals per trace (0 allowed)
  *   configs    host [n_configs], 1 <= n_configs <= 4096
@@ -210,7 +210,7 @@ int magus_replay_set_tile(magus_replay_t *h, int32_t time_groups, int32_t policy
  * otherwise. */
 int magus_replay_set_segments(magus_replay_t *h, int32_t seg_rounds);
 
-/* Closed loop in jump mode (step_mode 2, pin_level 0): replayed time-parallel.  Every
+/* Closed loop (step_mode 2 or 3, pin_level 0): replayed time-parallel.  Every
  * (trace, policy, segment of seg_rounds rounds) is replayed on its own from a guessed state
  * burn_rounds earlier; a segment whose guess did not reach the state its predecessor ended
  * in is replayed again, and a final pass per pair takes the replays that started from the

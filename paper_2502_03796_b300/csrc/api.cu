@@ -45,7 +45,7 @@ size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 int ensure_ws(magus_replay *h, void **buf, size_t *size, size_t need) {
     if (need <= *size) return MAGUS_OK;
     size_t want = std::max(need, *size * 2);
-    size_t other = h->ws_size + h->scratch_size + h->seg_size + h->cls_size - *size;
+    size_t other = h->ws_size + h->scratch_size + h->seg_size + h->cls_size[0] + h->cls_size[1] - *size;
     if (want + other > h->budget) want = need;
     if (want + other > h->budget) {
         set_error("device workspace of " + std::to_string(need) + " bytes exceeds the handle's memory budget");
@@ -265,15 +265,19 @@ int magus_policy_closed_thresholds(const magus_policy_t *policy, const magus_mod
     rc = derive_policy(*policy, *model, &dp, &err);
     if (rc) { set_error(err); return rc; }
     ClosedThr c;
-    derive_closed(dp, dm, &c);
+    derive_closed(dp, dm, false, &c);
+    out[10] = 0;
     for (int l = 0; l < 2; l++) {
         out[0 + l] = c.cthr[l];
         out[2 + l] = c.bu[l];
         out[4 + l] = c.bd[l];
         out[6 + l] = c.au[l];
         out[8 + l] = c.ad[l];
+        for (int lb = 0; lb < 2; lb++) {
+            if ((c.ccu[l] >> lb) & 1u) out[10] |= 1 << (2 * l + lb);
+            if ((c.ccd[l] >> lb) & 1u) out[10] |= 1 << (4 + 2 * l + lb);
+        }
     }
-    out[10] = c.cc;
     return MAGUS_OK;
 }
 
@@ -331,7 +335,8 @@ int magus_replay_close(magus_replay_t *h) {
     if (h->ws) cudaFree(h->ws);
     if (h->scratch) cudaFree(h->scratch);
     if (h->segbuf) cudaFree(h->segbuf);
-    if (h->clsbuf) cudaFree(h->clsbuf);
+    for (int m = 0; m < 2; m++)
+        if (h->clsbuf[m]) cudaFree(h->clsbuf[m]);
     if (h->status) cudaFree(h->status);
     if (h->ws_ev) cudaEventDestroy(h->ws_ev);
     delete h;
@@ -381,14 +386,16 @@ int magus_replay_set_closed(magus_replay_t *h, int32_t seg_rounds, int32_t burn_
 int magus_replay_closed_stats(magus_replay_t *h, uint64_t *out4) {
     if (!h || !out4) { set_error("NULL argument"); return MAGUS_EINVAL; }
     out4[0] = out4[1] = out4[2] = out4[3] = 0;
-    if (!h->cls_stats) return MAGUS_OK;
-    if (h->ws_ev_pending) CK(cudaEventSynchronize(h->ws_ev), "cudaEventSynchronize");
-    unsigned long long st[3] = {0, 0, 0};
-    CK(cudaMemcpy(st, h->cls_stats, sizeof(st), cudaMemcpyDeviceToHost), "cudaMemcpy(closed stats)");
-    out4[0] = h->cls_items;
-    out4[1] = st[0];
-    out4[2] = st[1];
-    out4[3] = st[2];
+    for (int m = 0; m < 2; m++) {
+        if (!h->cls_stats[m]) continue;
+        if (h->ws_ev_pending) CK(cudaEventSynchronize(h->ws_ev), "cudaEventSynchronize");
+        unsigned long long st[3] = {0, 0, 0};
+        CK(cudaMemcpy(st, h->cls_stats[m], sizeof(st), cudaMemcpyDeviceToHost), "cudaMemcpy(closed stats)");
+        out4[0] += h->cls_items[m];
+        out4[1] += st[0];
+        out4[2] += st[1];
+        out4[3] += st[2];
+    }
     return MAGUS_OK;
 }
 

@@ -107,7 +107,7 @@ int build_plan(magus_replay *h, const uint64_t *lengths, int32_t n_traces, const
         } else if (closed_policy(pl->pols[i])) {
             pl->cls.push_back((int32_t)i);
             ClosedThr c;
-            derive_closed(pl->pols[i], h->dm, &c);
+            derive_closed(pl->pols[i], h->dm, pl->pols[i].step_mode == 3, &c);
             pl->cthr.push_back(c);
         } else {
             pl->lit.push_back((int32_t)i);
@@ -420,7 +420,8 @@ int launch_seg_plan(magus_replay *h, const Plan &pl, const uint32_t *traces, con
     const size_t sz_log = align_up(scratch_entries * 4, 256);
     const size_t seg_need = sz_sum + sz_tail + sz_log;
     // the tile kernel needs none of the segment buffers: take it when they do not fit
-    if (std::max(total, h->ws_size) + h->scratch_size + h->cls_size + std::max(seg_need, h->seg_size) > h->budget)
+    if (std::max(total, h->ws_size) + h->scratch_size + h->cls_size[0] + h->cls_size[1] + std::max(seg_need, h->seg_size) >
+        h->budget)
         return kUseTile;
     int rc = ensure_ws(h, &h->ws, &h->ws_size, total);
     if (rc) return rc;
@@ -557,23 +558,27 @@ int launch_seg_plan(magus_replay *h, const Plan &pl, const uint32_t *traces, con
 // replayed on its own thread from a guessed state, segments whose guess was wrong replayed
 // again, then one thread per pair walks its segments in order.  The literal kernel takes
 // them instead when the segmented replay is switched off or its buffers exceed the budget.
-int launch_closed_part(magus_replay *h, const Plan &pl, const uint32_t *traces, const Outs &o, const DevPolicy *d_pols,
-                       const uint64_t *d_off, const uint64_t *d_len, cudaStream_t stream, int *kernels) {
+static int launch_closed_mode(magus_replay *h, const Plan &pl, int mode, const std::vector<int32_t> &cls,
+                              const std::vector<ClosedThr> &cthr, const uint32_t *traces, const Outs &o,
+                              const DevPolicy *d_pols, const uint64_t *d_off, const uint64_t *d_len,
+                              cudaStream_t stream, int *kernels) {
     const int n_traces = (int)pl.lengths.size();
-    const int n_cls = (int)pl.cls.size();
-    h->cls_items = 0;
-    h->cls_stats = nullptr;
-    if (n_cls == 0 || n_traces == 0) return MAGUS_OK;
+    const int n_cls = (int)cls.size();
+    const bool ladder = mode == 1;
     int wmax = 1;
-    for (int32_t c : pl.cls) wmax = std::max(wmax, pl.pols[c].W);
+    for (int32_t c : cls) wmax = std::max(wmax, pl.pols[c].W);
     uint32_t ring = 1;
     while ((int)ring < wmax) ring <<= 1;
     // Every thread replays one segment (plus its burn-in) one round after another, so a
     // launch lasts about (waves of threads) x (segment + burn-in rounds).  Automatic choice:
     // for each wave count w, the shortest segment whose items fit w waves of resident
-    // threads, burn-in min(512, S / 2); keep the cheapest (cached per workload).
+    // threads, burn-in min(512, S / 2) in jump mode and min(2048, S / 2) with one rung per
+    // decision (a guessed rung takes longer to meet the true one: 512 rounds left 15 % of
+    // the 4,096 x 100,000 segments to a second replay, 2,048 rounds 0.01 %); keep the
+    // cheapest (cached per workload).
     auto burn_of = [&](uint64_t S) -> uint64_t {
-        return h->cls_burn >= 0 ? (uint64_t)h->cls_burn : std::min<uint64_t>(512, S / 2 / 64 * 64);
+        return h->cls_burn >= 0 ? (uint64_t)h->cls_burn
+                                : std::min<uint64_t>(ladder ? 2048 : 512, S / 2 / 64 * 64);
     };
     uint64_t S = (uint64_t)h->cls_seg, G = 0;
     if (h->cls_seg > 0) {
@@ -585,11 +590,11 @@ int launch_closed_part(magus_replay *h, const Plan &pl, const uint32_t *traces, 
             key = (key ^ n) * 1099511628211ull;
             longest = std::max(longest, n);
         }
-        if (key == h->cls_key && h->cls_auto_seg) {
-            S = h->cls_auto_seg;
-            G = h->cls_auto_burn;
+        if (key == h->cls_key[mode] && h->cls_auto_seg[mode]) {
+            S = h->cls_auto_seg[mode];
+            G = h->cls_auto_burn[mode];
         } else {
-            const int ctas = closed_max_ctas_per_sm(ring);
+            const int ctas = closed_max_ctas_per_sm(ring, ladder);
             const uint64_t resident = (uint64_t)h->sms * std::max(ctas, 1) * closed_threads_per_cta();
             auto items_of = [&](uint64_t L) {
                 uint64_t it = 0;
@@ -618,9 +623,9 @@ int launch_closed_part(magus_replay *h, const Plan &pl, const uint32_t *traces, 
             if (S == 0) S = top;   // more than 64 waves even with whole traces
             S = std::min<uint64_t>(S, (uint64_t)1 << 24);
             G = burn_of(S);
-            h->cls_key = key;
-            h->cls_auto_seg = S;
-            h->cls_auto_burn = G;
+            h->cls_key[mode] = key;
+            h->cls_auto_seg[mode] = S;
+            h->cls_auto_burn[mode] = G;
         }
     }
     std::vector<uint64_t> ibase(n_traces + 1);
@@ -631,32 +636,33 @@ int launch_closed_part(magus_replay *h, const Plan &pl, const uint32_t *traces, 
     }
     ibase[n_traces] = items;
     const bool logging = o.log_entries && o.log_cap > 0;
-    // buffer: policies | thresholds | item bases | counters | replay slots | log-pass jobs |
-    // entry scratch (per replay; a replay with more entries leaves them to the log pass, so
-    // the scratch shrinks to what the budget holds)
+    // buffer: policies | thresholds | item bases | counters | replay slots | rung histories
+    // (one-rung mode) | log-pass jobs | entry scratch (per replay; a replay with more entries
+    // leaves them to the log pass, so the scratch shrinks to what the budget holds)
     const size_t sz_cls = align_up((size_t)n_cls * 4, 256);
     const size_t sz_thr = align_up((size_t)n_cls * sizeof(ClosedThr), 256);
     const size_t sz_ib = align_up((size_t)(n_traces + 1) * 8, 256);
     const size_t plan_bytes = sz_cls + sz_thr + sz_ib;
     const size_t sz_st = 256;
     const size_t sz_slot = align_up((size_t)(2 * items) * sizeof(ClosedSlot), 256);
+    const size_t sz_hist = ladder ? align_up((size_t)(4 * items) * MAGUS_MAX_WINDOW, 256) : 0;
     const size_t sz_job = logging ? align_up((size_t)items * sizeof(ClosedJob), 256) : 0;
-    const size_t others = h->ws_size + h->scratch_size + h->seg_size;
+    const size_t others = h->ws_size + h->scratch_size + h->seg_size + h->cls_size[1 - mode];
     uint64_t scr_cap = logging ? std::min<uint64_t>(S, std::max<uint64_t>(64, S / 8)) : 0;
     auto need_of = [&](uint64_t cap) {
-        return plan_bytes + sz_st + sz_slot + sz_job + align_up((size_t)(2 * items * cap) * 4, 256);
+        return plan_bytes + sz_st + sz_slot + sz_hist + sz_job + align_up((size_t)(2 * items * cap) * 4, 256);
     };
-    while (scr_cap > 0 && others + std::max(need_of(scr_cap), h->cls_size) > h->budget) scr_cap /= 2;
+    while (scr_cap > 0 && others + std::max(need_of(scr_cap), h->cls_size[mode]) > h->budget) scr_cap /= 2;
     const size_t need = need_of(scr_cap);
     const bool segmented = h->cls_seg >= 0 && items <= (uint64_t)INT32_MAX * closed_threads_per_cta() &&
-                           others + std::max(need, h->cls_size) <= h->budget;
-    int rc = ensure_ws(h, &h->clsbuf, &h->cls_size, segmented ? need : sz_cls);
+                           others + std::max(need, h->cls_size[mode]) <= h->budget;
+    int rc = ensure_ws(h, &h->clsbuf[mode], &h->cls_size[mode], segmented ? need : sz_cls);
     if (rc) return rc;
-    char *buf = (char *)h->clsbuf;
+    char *buf = (char *)h->clsbuf[mode];
     std::vector<char> blob(segmented ? plan_bytes : sz_cls, 0);
-    memcpy(blob.data(), pl.cls.data(), (size_t)n_cls * 4);
+    memcpy(blob.data(), cls.data(), (size_t)n_cls * 4);
     if (segmented) {
-        memcpy(blob.data() + sz_cls, pl.cthr.data(), (size_t)n_cls * sizeof(ClosedThr));
+        memcpy(blob.data() + sz_cls, cthr.data(), (size_t)n_cls * sizeof(ClosedThr));
         memcpy(blob.data() + sz_cls + sz_thr, ibase.data(), (size_t)(n_traces + 1) * 8);
     }
     // the previous call's kernels may still read the buffer
@@ -671,7 +677,7 @@ int launch_closed_part(magus_replay *h, const Plan &pl, const uint32_t *traces, 
     unsigned long long *stats = (unsigned long long *)(buf + plan_bytes);
     CK(cudaMemsetAsync(stats, 0, 3 * sizeof(unsigned long long), stream), "cudaMemsetAsync");
     // no stale log-pass jobs (the final pass sets those of every pair it completes)
-    if (logging) CK(cudaMemsetAsync(buf + plan_bytes + sz_st + sz_slot, 0, sz_job, stream), "cudaMemsetAsync");
+    if (logging) CK(cudaMemsetAsync(buf + plan_bytes + sz_st + sz_slot + sz_hist, 0, sz_job, stream), "cudaMemsetAsync");
     ClosedParams cp;
     memset(&cp, 0, sizeof(cp));
     cp.traces = traces;
@@ -690,8 +696,9 @@ int launch_closed_part(magus_replay *h, const Plan &pl, const uint32_t *traces, 
     cp.burn = (uint32_t)G;
     cp.model = h->dm;
     cp.slots = (ClosedSlot *)(buf + plan_bytes + sz_st);
-    cp.jobs = logging ? (ClosedJob *)(buf + plan_bytes + sz_st + sz_slot) : nullptr;
-    cp.scratch = scr_cap ? (uint32_t *)(buf + plan_bytes + sz_st + sz_slot + sz_job) : nullptr;
+    cp.lhist = ladder ? (uint8_t *)(buf + plan_bytes + sz_st + sz_slot) : nullptr;
+    cp.jobs = logging ? (ClosedJob *)(buf + plan_bytes + sz_st + sz_slot + sz_hist) : nullptr;
+    cp.scratch = scr_cap ? (uint32_t *)(buf + plan_bytes + sz_st + sz_slot + sz_hist + sz_job) : nullptr;
     cp.scr_cap = scr_cap;
     cp.energy = o.energy;
     cp.edp = o.edp;
@@ -704,10 +711,34 @@ int launch_closed_part(magus_replay *h, const Plan &pl, const uint32_t *traces, 
     cp.state = o.state;
     cp.status = h->status;
     cp.stats = stats;
-    CK(launch_replay_closed(cp, stream), "closed-loop kernel launch");
+    CK(launch_replay_closed(cp, ladder, stream), "closed-loop kernel launch");
     *kernels += (items ? 3 : 1) + ((items && logging) ? 1 : 0);
-    h->cls_items = items;
-    h->cls_stats = stats;
+    h->cls_items[mode] = items;
+    h->cls_stats[mode] = stats;
+    return MAGUS_OK;
+}
+
+// The closed-loop policies of a plan, jump mode and one rung per decision in turn (their own
+// kernels and buffers).
+int launch_closed_part(magus_replay *h, const Plan &pl, const uint32_t *traces, const Outs &o, const DevPolicy *d_pols,
+                       const uint64_t *d_off, const uint64_t *d_len, cudaStream_t stream, int *kernels) {
+    for (int mode = 0; mode < 2; mode++) {
+        h->cls_items[mode] = 0;
+        h->cls_stats[mode] = nullptr;
+    }
+    if (pl.cls.empty() || pl.lengths.empty()) return MAGUS_OK;
+    for (int mode = 0; mode < 2; mode++) {
+        std::vector<int32_t> cls;
+        std::vector<ClosedThr> cthr;
+        for (size_t i = 0; i < pl.cls.size(); i++)
+            if ((pl.pols[pl.cls[i]].step_mode == 3) == (mode == 1)) {
+                cls.push_back(pl.cls[i]);
+                cthr.push_back(pl.cthr[i]);
+            }
+        if (cls.empty()) continue;
+        const int rc = launch_closed_mode(h, pl, mode, cls, cthr, traces, o, d_pols, d_off, d_len, stream, kernels);
+        if (rc) return rc;
+    }
     return MAGUS_OK;
 }
 

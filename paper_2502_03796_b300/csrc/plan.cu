@@ -166,14 +166,15 @@ static int64_t first_true_u32(Pred pred) {
 // monitor reads min(x, C) at the level in effect).  x is non-decreasing in delta and each
 // FP64 difference below is monotone in the free delta, so every decision is a threshold on
 // that delta; the decision itself is the division-free test on d (up_last / dn_last).
-void derive_closed(const DevPolicy &P, const DevModel &M, ClosedThr *out) {
+void derive_closed(const DevPolicy &P, const DevModel &M, bool ladder, ClosedThr *out) {
     ClosedThr c;
     memset(&c, 0, sizeof(c));
-    const int lvl[2] = {0, M.K - 1};
+    const int n = ladder ? M.K : 2;
+    auto level = [&](int l) { return ladder ? l : (l ? M.K - 1 : 0); };
     auto up_of = [&](double d) { return d > P.up_last; };
     auto dn_of = [&](double d) { return d <= P.dn_last; };
-    for (int l = 0; l < 2; l++) {
-        const double C = M.cap[lvl[l]];
+    for (int l = 0; l < n; l++) {
+        const double C = M.cap[level(l)];
         const int64_t f = first_true_u32([&](uint32_t v) { return xval(M, v) > C; });
         c.cthr[l] = (uint32_t)(f - 1);   // C > 0 = x(0), so f >= 1
         // a capped: d = C - x(b), non-increasing in b
@@ -183,11 +184,11 @@ void derive_closed(const DevPolicy &P, const DevModel &M, ClosedThr *out) {
         c.au[l] = first_true_u32([&](uint32_t a) { return up_of(xval(M, a) - C); });
         c.ad[l] = first_true_u32([&](uint32_t a) { return !dn_of(xval(M, a) - C); });
     }
-    for (int la = 0; la < 2; la++)
-        for (int lb = 0; lb < 2; lb++) {
-            const double d = M.cap[lvl[la]] - M.cap[lvl[lb]];
-            if (up_of(d)) c.cc |= 1u << (2 * la + lb);
-            if (dn_of(d)) c.cc |= 1u << (4 + 2 * la + lb);
+    for (int la = 0; la < n; la++)
+        for (int lb = 0; lb < n; lb++) {
+            const double d = M.cap[level(la)] - M.cap[level(lb)];
+            if (up_of(d)) c.ccu[la] |= 1u << lb;
+            if (dn_of(d)) c.ccd[la] |= 1u << lb;
         }
     *out = c;
 }

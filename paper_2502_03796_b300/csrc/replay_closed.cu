@@ -1,4 +1,4 @@
-// replay_closed.cu - time-parallel replay of the closed loop in jump mode.
+// replay_closed.cu - time-parallel replay of the closed loop, jump and one-rung modes.
 //
 // In the closed loop the monitor reads what the uncore at the level in effect delivers,
 // min(demand, capacity) (Sec. 3 monitor, Sec. 6.3 on the throttled minimum frequency), so a
@@ -28,7 +28,10 @@
 // per-level threshold, each case with one capped throughput is a threshold on the other
 // delta and both capped is a constant (host-derived with the oracle's FP64 expressions,
 // plan.cu); two uncapped throughputs take the open-loop test with its FP64 evaluation
-// inside the rounding band.  Energy is charged as integer counts and sums per level.
+// inside the rounding band.  Jump mode (kL = false) keeps the level as a bit and the levels
+// of the last 64 rounds in a word, and charges energy as integer counts and sums at the two
+// levels; one rung per decision (kL = true) keeps the rung and a shared-memory ring of past
+// rungs, and charges energy in FP64 per run of constant rung.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -41,48 +44,78 @@ namespace {
 constexpr int kThreads = 128;
 
 struct CState {
-    uint32_t lv;     // 0 bottom, 1 top
-    uint64_t lvh;    // bit j: level bit of round t-1-j
+    uint32_t lv;     // jump: 0 bottom / 1 top; one-rung: the rung
+    uint64_t lvh;    // jump: bit j = level bit of round t-1-j (one-rung: in the ring)
     uint64_t fl;     // bit j: flag of round t-1-j
 };
 
 struct CAcc {
     uint32_t n0, nm, nhf, nch;
     unsigned long long s0, sm, hash;
+    double e, t;     // one-rung mode: energy and time
 };
 
+__device__ __forceinline__ uint64_t low_mask(int k) { return k >= 64 ? ~0ull : ((1ull << k) - 1ull); }
 __device__ __forceinline__ bool same_state(const CState &x, const CState &y, uint64_t wmask, uint64_t lmask) {
     return x.lv == y.lv && ((x.lvh ^ y.lvh) & wmask) == 0 && ((x.fl ^ y.fl) & lmask) == 0;
 }
-__device__ __forceinline__ uint64_t low_mask(int k) { return k >= 64 ? ~0ull : ((1ull << k) - 1ull); }
+__device__ __forceinline__ bool same_hist(const uint8_t *a, const uint8_t *b, int W) {
+    for (int j = 0; j < W; j++)
+        if (a[j] != b[j]) return false;
+    return true;
+}
 
 // The pair's state before round 0: fresh, or the carried one (which must not have seen a
-// round: the throughput FIFO would need the levels behind it).  A carried level other than
-// the bottom or the top is invalid in jump mode.
+// round: the throughput FIFO would need the levels behind it).  Jump mode: a carried level
+// other than the bottom or the top is invalid; one-rung mode: any rung of the ladder.
+template <bool kL>
 __device__ CState initial_state(const ClosedParams &p, int64_t pair) {
     CState s{0u, 0ull, 0ull};
     if (p.state) {
         const magus_state_t &st = p.state[pair];
         if (st.n_seen > 0) atomicCAS(p.status, 0, MAGUS_EINVAL);
         const uint32_t top = (uint32_t)(p.model.K - 1);
-        if (st.level != 0 && st.level != top) atomicCAS(p.status, 0, MAGUS_EINVAL);
-        s.lv = st.level == top ? 1u : 0u;
+        if (kL) {
+            if (st.level > top) atomicCAS(p.status, 0, MAGUS_EINVAL);
+            s.lv = st.level > top ? 0u : st.level;
+        } else {
+            if (st.level != 0 && st.level != top) atomicCAS(p.status, 0, MAGUS_EINVAL);
+            s.lv = st.level == top ? 1u : 0u;
+        }
         s.fl = __brevll(st.flags);
     }
     return s;
 }
 
-// Per-thread ring of the last R deltas in shared memory, slot-major ([slot][thread]): the
-// lanes of a warp always touch distinct banks.
+// Per-thread rings in shared memory, slot-major ([slot][thread]) so that the lanes of a warp
+// always touch distinct banks (bytes of a word for the rung rings): the last R deltas, and
+// in one-rung mode the rungs of the last R rounds of one or two replays.
 struct Ring {
-    uint32_t *col;     // this thread's column
+    uint32_t *col;     // this thread's delta column
     uint32_t mask;     // R - 1
     __device__ __forceinline__ uint32_t &at(uint64_t t) const { return col[((uint32_t)t & mask) * kThreads]; }
 };
+struct LRing {
+    uint8_t *col;      // this thread's rung column (NULL in jump mode)
+    uint32_t mask;
+    __device__ __forceinline__ uint8_t &at(uint64_t t) const { return col[((uint32_t)t & mask) * kThreads]; }
+};
+__device__ __forceinline__ Ring delta_ring(uint32_t *smem, uint32_t R) { return Ring{smem + threadIdx.x, R - 1u}; }
+__device__ __forceinline__ LRing rung_ring(uint32_t *smem, uint32_t R, int which) {
+    return LRing{reinterpret_cast<uint8_t *>(smem + (size_t)R * kThreads) + (size_t)which * R * kThreads + threadIdx.x,
+                 R - 1u};
+}
 
 __device__ __forceinline__ void prefill(const uint32_t *tr, uint64_t t0, const Ring &ring) {
     const uint64_t h0 = t0 > ring.mask ? t0 - ring.mask - 1 : 0;
     for (uint64_t t = h0; t < t0; t++) ring.at(t) = __ldg(tr + t);
+}
+// rungs of the W rounds before t0 (newest first) into / out of a ring (NULL: all bottom)
+__device__ __forceinline__ void hist_to_ring(const LRing &r, uint64_t t0, const uint8_t *h, int W) {
+    for (int j = 0; j < W; j++) r.at(t0 - 1 - (uint64_t)j) = h ? h[j] : (uint8_t)0;
+}
+__device__ __forceinline__ void ring_to_hist(const LRing &r, uint64_t t1, uint8_t *h, int W) {
+    for (int j = 0; j < W; j++) h[j] = r.at(t1 - 1 - (uint64_t)j);
 }
 
 // Alg. 1 for two uncapped throughputs inside the rounding band around a threshold: the FP64
@@ -111,42 +144,53 @@ struct BufEmit {
 // The thresholds of the level in effect (lv) and of the level W rounds back (lb) are kept
 // in registers and reloaded when that level changes; the flag count of Alg. 2's window is
 // kept up to date instead of recounted.
+template <bool kL>
 struct Replay {
     CState s;
     CAcc acc;
     uint32_t run_n;
     unsigned long long run_s;
-    uint32_t capa, cc, thr;   // level lv: capped above capa; both capped: bit lb +1, 4 + lb -1
-    int64_t bu, bd;           // a capped, b not: +1 iff b < bu, -1 iff b >= bd
-    uint32_t lbp, capb;       // level lb (as last loaded): capped above capb
-    int64_t au, ad;           // b capped, a not: +1 iff a >= au, -1 iff a < ad
-    uint32_t cnt;             // flags among the last L rounds
+    uint32_t capa, ccu, ccd, thr;   // level lv: capped above capa; both capped: bit lb +1 / -1
+    int64_t bu, bd;                 // a capped, b not: +1 iff b < bu, -1 iff b >= bd
+    uint32_t lbp, capb;             // level lb (as last loaded): capped above capb
+    int64_t au, ad;                 // b capped, a not: +1 iff a >= au, -1 iff a < ad
+    uint32_t cnt;                   // flags among the last L rounds
+    LRing lr;                       // one-rung mode: this replay's rungs
 
     __device__ __forceinline__ void load_a(const ClosedThr *Cg, const DevModel &M) {
         capa = __ldg(&Cg->cthr[s.lv]);
         bu = __ldg(&Cg->bu[s.lv]);
         bd = __ldg(&Cg->bd[s.lv]);
-        cc = __ldg(&Cg->cc) >> (2u * s.lv);
-        thr = s.lv ? M.thrM : M.thr0;
+        ccu = __ldg(&Cg->ccu[s.lv]);
+        ccd = __ldg(&Cg->ccd[s.lv]);
+        thr = kL ? M.thr[s.lv] : (s.lv ? M.thrM : M.thr0);
     }
     __device__ __forceinline__ void load_b(const ClosedThr *Cg) {
         capb = __ldg(&Cg->cthr[lbp]);
         au = __ldg(&Cg->au[lbp]);
         ad = __ldg(&Cg->ad[lbp]);
     }
-    __device__ __forceinline__ void start(const CState &st, const DevPolicy &P, const ClosedThr *Cg,
+    __device__ __forceinline__ uint32_t level_back(uint64_t t, uint32_t W) const {
+        return kL ? (uint32_t)lr.at(t - W) : ((uint32_t)(s.lvh >> (W - 1u)) & 1u);
+    }
+    // state at round t0 (one-rung mode: its rungs already in lr)
+    __device__ __forceinline__ void start(const CState &st, uint64_t t0, const DevPolicy &P, const ClosedThr *Cg,
                                           const DevModel &M) {
         s = st;
         acc = CAcc{};
         run_n = 0;
         run_s = 0;
         load_a(Cg, M);
-        lbp = (uint32_t)(s.lvh >> (P.W - 1)) & 1u;
+        lbp = level_back(t0, (uint32_t)P.W);
         load_b(Cg);
         cnt = (uint32_t)__popcll(s.fl & low_mask(P.L));
     }
-    __device__ __forceinline__ void flush() {
-        if (s.lv) {
+    __device__ __forceinline__ void flush(const DevModel &M) {
+        if (kL) {
+            const double tk = M.dt * (double)run_n + M.ak[s.lv] * (double)run_s;
+            acc.t += tk;
+            acc.e += M.pw[s.lv] * tk;
+        } else if (s.lv) {
             acc.nm += run_n;
             acc.sm += run_s;
         } else {
@@ -158,12 +202,14 @@ struct Replay {
     }
     // Round t = t0 + j with a = delta_t, b = delta_{t-W}.  kCount: charge it, count its flag
     // and change, emit its entry.  kWarm: rounds j < warm come before the FIFO holds W + 1.
+    // Returns the level of round t - W (for the lockstep comparison).
     template <bool kCount, bool kWarm, class Emit>
-    __device__ __forceinline__ void step(uint32_t a, uint32_t b, uint32_t j, uint64_t t0, uint32_t warm,
-                                         const DevPolicy &P, const DevPolicy *Pg, const ClosedThr *Cg,
-                                         const DevModel &M, Emit emit) {
+    __device__ __forceinline__ uint32_t step(uint32_t a, uint32_t b, uint32_t j, uint64_t t0, uint32_t warm,
+                                             const DevPolicy &P, const DevPolicy *Pg, const ClosedThr *Cg,
+                                             const DevModel &M, Emit emit) {
+        const uint64_t t = t0 + j;
         const uint32_t lv = s.lv;
-        const uint32_t lb = (uint32_t)(s.lvh >> (P.W - 1)) & 1u;   // level of round t - W
+        const uint32_t lb = level_back(t, (uint32_t)P.W);   // level of round t - W
         if (lb != lbp) {
             lbp = lb;
             load_b(Cg);
@@ -172,8 +218,8 @@ struct Replay {
         // evaluated, one selected
         const bool ca = a > capa, cb = b > capb;
         const int64_t m = (int64_t)a - (int64_t)b;
-        const bool up_b = ca ? ((cc >> lb) & 1u) != 0 : (int64_t)a >= au;
-        const bool dn_b = ca ? ((cc >> (4u + lb)) & 1u) != 0 : (int64_t)a < ad;
+        const bool up_b = ca ? ((ccu >> lb) & 1u) != 0 : (int64_t)a >= au;
+        const bool dn_b = ca ? ((ccd >> lb) & 1u) != 0 : (int64_t)a < ad;
         const bool up_n = ca ? (int64_t)b < bu : m > P.up_mid;
         const bool dn_n = ca ? (int64_t)b >= bd : m < P.dn_mid;
         bool up = cb ? up_b : up_n, dn = cb ? dn_b : dn_n;
@@ -192,7 +238,14 @@ struct Replay {
         s.fl = (s.fl << 1) | f;
         cnt = cnt + f - gone;
         const bool hf = (int)cnt >= P.kmin;
-        const uint32_t next = (hf || up) ? 1u : (dn ? 0u : lv);
+        uint32_t next;
+        if (kL) {
+            // one rung per decision; the high-frequency state goes to the top (Sec. 3.2)
+            const uint32_t top = (uint32_t)(M.K - 1);
+            next = hf ? top : (up ? (lv < top ? lv + 1u : top) : (dn ? (lv > 0 ? lv - 1u : 0u) : lv));
+        } else {
+            next = (hf || up) ? 1u : (dn ? 0u : lv);
+        }
         if (kCount) {
             // energy model: the round at level lv, stretched when the demand exceeds C(lv)
             const bool se = a > thr;
@@ -200,12 +253,13 @@ struct Replay {
             run_s += se ? a : 0u;
             acc.nhf += hf ? 1u : 0u;
         }
-        s.lvh = (s.lvh << 1) | lv;
+        if (kL) lr.at(t) = (uint8_t)lv;
+        else s.lvh = (s.lvh << 1) | lv;
         if (next != lv) {
             if (kCount) {
-                flush();
-                const uint64_t when = t0 + j + 1;   // the new level governs the next round
-                const uint32_t lvl = next ? (uint32_t)(M.K - 1) : 0u;
+                flush(M);
+                const uint64_t when = t + 1;   // the new level governs the next round
+                const uint32_t lvl = kL ? next : (next ? (uint32_t)(M.K - 1) : 0u);
                 emit((uint32_t)(when << 5) | lvl, acc.nch);
                 acc.nch++;
                 acc.hash += core::mix64((when << 8) | lvl);
@@ -213,14 +267,15 @@ struct Replay {
             s.lv = next;
             load_a(Cg, M);
         }
+        return lb;
     }
 };
 
 // Rounds [t0, t1) of one pair's trace (t0 a multiple of 4, t1 - t0 < 2^32; the packed layout
 // pads every trace to a multiple of 32 deltas, so the 16-byte loads stay inside it).  The
-// ring holds the deltas before t0; x has been started.
-template <bool kCount, class Emit>
-__device__ __forceinline__ void run_rounds(const uint32_t *tr, uint64_t t0, uint64_t t1, Replay &x,
+// delta ring holds the deltas before t0; x has been started.
+template <bool kL, bool kCount, class Emit>
+__device__ __forceinline__ void run_rounds(const uint32_t *tr, uint64_t t0, uint64_t t1, Replay<kL> &x,
                                            const DevPolicy *Pg, const ClosedThr *Cg, const DevModel &M,
                                            const Ring &ring, Emit emit) {
     const DevPolicy P = *Pg;
@@ -235,12 +290,12 @@ __device__ __forceinline__ void run_rounds(const uint32_t *tr, uint64_t t0, uint
         const uint32_t a = __ldg(tr + t0 + j);
         const uint32_t b = ring.at(t0 + j - W);
         ring.at(t0 + j) = a;
-        x.step<kCount, true>(a, b, j, t0, warm, P, Pg, Cg, M, emit);
+        x.template step<kCount, true>(a, b, j, t0, warm, P, Pg, Cg, M, emit);
     }
     auto round = [&](uint32_t a, uint32_t jj) {
         const uint32_t b = ring.at(t0 + jj - W);   // read before round t's slot is reused (W may equal R)
         ring.at(t0 + jj) = a;
-        x.step<kCount, false>(a, b, jj, t0, 0u, P, Pg, Cg, M, emit);
+        x.template step<kCount, false>(a, b, jj, t0, 0u, P, Pg, Cg, M, emit);
     };
 #pragma unroll 1
     for (; j + 4u <= nr; j += 4u) {
@@ -252,7 +307,7 @@ __device__ __forceinline__ void run_rounds(const uint32_t *tr, uint64_t t0, uint
     }
 #pragma unroll 1
     for (; j < nr; j++) round(__ldg(tr + t0 + j), j);
-    if (kCount) x.flush();
+    if (kCount) x.flush(M);
 }
 
 // Rounds [t0, t1) replayed twice in lockstep: x (charged, entries emitted) and y (charged,
@@ -260,15 +315,19 @@ __device__ __forceinline__ void run_rounds(const uint32_t *tr, uint64_t t0, uint
 // rounds -- the level, the levels of the last W rounds and all 64 flags (the carried state
 // written at a trace's end holds 64).  Returns the rounds run (both replays then hold the
 // state after them, runs flushed); t1 - t0 when they never agreed.  Both have been started.
-template <class Emit>
-__device__ __forceinline__ uint32_t run_until_same(const uint32_t *tr, uint64_t t0, uint64_t t1, Replay &x, Replay &y,
-                                                   const DevPolicy *Pg, const ClosedThr *Cg, const DevModel &M,
-                                                   const Ring &ring, Emit emit) {
+template <bool kL, class Emit>
+__device__ __forceinline__ uint32_t run_until_same(const uint32_t *tr, uint64_t t0, uint64_t t1, Replay<kL> &x,
+                                                   Replay<kL> &y, const DevPolicy *Pg, const ClosedThr *Cg,
+                                                   const DevModel &M, const Ring &ring, Emit emit) {
     const DevPolicy P = *Pg;
     const uint64_t wmask = low_mask(P.W);
     const uint32_t W = (uint32_t)P.W;
     const uint32_t nr = (uint32_t)(t1 - t0);
     const uint32_t warm = t0 < W ? (uint32_t)(W - t0) : 0u;
+    // one-rung mode: rungs that differ among the last W rounds of the two replays
+    int diff = 0;
+    if (kL)
+        for (uint32_t i = 1; i <= W; i++) diff += x.lr.at(t0 - i) != y.lr.at(t0 - i) ? 1 : 0;
     uint32_t j = 0;
 #pragma unroll 1
     while (j < nr) {
@@ -278,13 +337,15 @@ __device__ __forceinline__ uint32_t run_until_same(const uint32_t *tr, uint64_t 
             const uint32_t a = __ldg(tr + t0 + j);
             const uint32_t b = ring.at(t0 + j - W);
             ring.at(t0 + j) = a;
-            x.step<true, true>(a, b, j, t0, warm, P, Pg, Cg, M, emit);
-            y.step<true, true>(a, b, j, t0, warm, P, Pg, Cg, M, NoEmit{});
+            const uint32_t xl = x.s.lv, yl = y.s.lv;
+            const uint32_t xb = x.template step<true, true>(a, b, j, t0, warm, P, Pg, Cg, M, emit);
+            const uint32_t yb = y.template step<true, true>(a, b, j, t0, warm, P, Pg, Cg, M, NoEmit{});
+            if (kL) diff += (xl != yl ? 1 : 0) - (xb != yb ? 1 : 0);
         }
-        if (same_state(x.s, y.s, wmask, ~0ull)) break;
+        if (kL ? (x.s.lv == y.s.lv && x.s.fl == y.s.fl && diff == 0) : same_state(x.s, y.s, wmask, ~0ull)) break;
     }
-    x.flush();
-    y.flush();
+    x.flush(M);
+    y.flush(M);
     return j;
 }
 
@@ -308,25 +369,47 @@ __device__ ItemPos locate(const ClosedParams &p, uint64_t item) {
     return q;
 }
 
-__device__ __forceinline__ void store_slot(ClosedSlot &o, const CState &in, const CState &out, const CAcc &acc,
-                                           uint32_t ok) {
+// rung histories of a slot (one-rung mode): io 0 at its start, 1 at its end
+__device__ __forceinline__ uint8_t *slot_hist(const ClosedParams &p, uint64_t which, uint64_t item, int io) {
+    return p.lhist + ((which * p.n_items + item) * 2 + (uint64_t)io) * MAGUS_MAX_WINDOW;
+}
+
+__device__ __forceinline__ void store_counts(ClosedSlot &o, const CAcc &acc) {
     o.s0 = acc.s0;
     o.sm = acc.sm;
     o.hash = acc.hash;
-    o.lvh_in = in.lvh;
-    o.fl_in = in.fl;
-    o.lvh_out = out.lvh;
-    o.fl_out = out.fl;
+    o.e = acc.e;
+    o.t = acc.t;
     o.n0 = acc.n0;
     o.nm = acc.nm;
     o.nhf = acc.nhf;
     o.nch = acc.nch;
+}
+__device__ __forceinline__ void store_in(ClosedSlot &o, const CState &in) {
     o.lv_in = in.lv;
+    o.lvh_in = in.lvh;
+    o.fl_in = in.fl;
+}
+__device__ __forceinline__ void store_out(ClosedSlot &o, const CState &out, uint32_t ok) {
     o.lv_out = out.lv;
+    o.lvh_out = out.lvh;
+    o.fl_out = out.fl;
     o.pad = 0;
     o.ok = ok;
 }
-
+__device__ __forceinline__ CAcc slot_acc(const ClosedSlot &r) {
+    CAcc a;
+    a.n0 = r.n0;
+    a.nm = r.nm;
+    a.nhf = r.nhf;
+    a.nch = r.nch;
+    a.s0 = r.s0;
+    a.sm = r.sm;
+    a.hash = r.hash;
+    a.e = r.e;
+    a.t = r.t;
+    return a;
+}
 __device__ __forceinline__ CAcc acc_add_diff(const CAcc &x, const ClosedSlot &r, const CAcc &y) {
     CAcc o;
     o.n0 = x.n0 + (r.n0 - y.n0);
@@ -336,15 +419,16 @@ __device__ __forceinline__ CAcc acc_add_diff(const CAcc &x, const ClosedSlot &r,
     o.s0 = x.s0 + (r.s0 - y.s0);
     o.sm = x.sm + (r.sm - y.sm);
     o.hash = x.hash + (r.hash - y.hash);
+    o.e = x.e + (r.e - y.e);
+    o.t = x.t + (r.t - y.t);
     return o;
 }
 
 // Pass 1: the first replay of every segment.  Pass 2: a second replay where pass 1 started
 // from a state other than its predecessor's end state.  Separate kernels, so that the
 // lockstep replay of pass 2 does not raise the register count of pass 1.
-template <int kPass>
+template <bool kL, int kPass>
 __device__ __forceinline__ void closed_pass(const ClosedParams &p) {
-    constexpr int pass = kPass;
     extern __shared__ uint32_t ring_s[];
     const uint64_t item = (uint64_t)blockIdx.x * kThreads + threadIdx.x;
     if (item >= p.n_items) return;
@@ -353,82 +437,113 @@ __device__ __forceinline__ void closed_pass(const ClosedParams &p) {
     const DevPolicy *Pg = p.pols + pol;
     const ClosedThr *C = p.thr + q.ci;
     const DevModel &M = p.model;
+    const int W = Pg->W;
     const int64_t pair = (int64_t)q.trace * p.n_pols + pol;
     const uint32_t *tr = p.traces + p.offsets[q.trace];
     const uint64_t n = p.lengths[q.trace];
     const uint64_t s0 = q.k * p.seg_len, s1 = min(n, s0 + p.seg_len);
-    ClosedSlot &out = p.slots[(uint64_t)(pass - 1) * p.n_items + item];
-    const Ring ring{ring_s + threadIdx.x, p.ring - 1u};
+    ClosedSlot &out = p.slots[(uint64_t)(kPass - 1) * p.n_items + item];
+    const Ring ring = delta_ring(ring_s, p.ring);
     const bool logging = p.log_entries && p.log_cap > 0;
-    uint32_t *scr = p.scratch ? p.scratch + ((uint64_t)(pass - 1) * p.n_items + item) * p.scr_cap : nullptr;
+    uint32_t *scr = p.scratch ? p.scratch + ((uint64_t)(kPass - 1) * p.n_items + item) * p.scr_cap : nullptr;
     const BufEmit em{scr, (uint32_t)p.scr_cap};   // scr_cap <= segment rounds < 2^32
-    Replay x;
-    if constexpr (pass == 1) {
+    Replay<kL> x;
+    x.lr = kL ? rung_ring(ring_s, p.ring, 0) : LRing{nullptr, 0u};
+    if constexpr (kPass == 1) {
         uint32_t ok = 1u;
         const uint64_t t0 = s0 > p.burn ? s0 - p.burn : 0;
+        CState st{0u, 0ull, 0ull};
         if (t0 == 0) {
-            x.start(initial_state(p, pair), *Pg, C, M);
+            st = initial_state<kL>(p, pair);
             ok |= 2u;   // started from the true state
-        } else {
-            x.start(CState{0u, 0ull, 0ull}, *Pg, C, M);
         }
         prefill(tr, t0, ring);
-        run_rounds<false>(tr, t0, s0, x, Pg, C, M, ring, NoEmit{});
+        if (kL) hist_to_ring(x.lr, t0, nullptr, W);
+        x.start(st, t0, *Pg, C, M);
+        run_rounds<kL, false>(tr, t0, s0, x, Pg, C, M, ring, NoEmit{});
         // the start state goes out now (fewer live registers through the segment)
-        out.lv_in = x.s.lv;
-        out.lvh_in = x.s.lvh;
-        out.fl_in = x.s.fl;
-        x.start(x.s, *Pg, C, M);
-        run_rounds<true>(tr, s0, s1, x, Pg, C, M, ring, em);
+        store_in(out, x.s);
+        if (kL) ring_to_hist(x.lr, s0, slot_hist(p, 0, item, 0), W);
+        x.start(x.s, s0, *Pg, C, M);
+        run_rounds<kL, true>(tr, s0, s1, x, Pg, C, M, ring, em);
         if (logging && x.acc.nch > p.scr_cap) ok |= 4u;   // entries lost: the log pass writes them
-        store_slot(out, CState{out.lv_in, out.lvh_in, out.fl_in}, x.s, x.acc, ok);
-        return;
+        store_counts(out, x.acc);
+        if (kL) ring_to_hist(x.lr, s1, slot_hist(p, 0, item, 1), W);
+        store_out(out, x.s, ok);
     } else {
-    if (q.k == 0) {
-        out.ok = 0;
-        return;
-    }
-    const ClosedSlot &prev = p.slots[item - 1];   // segment k - 1, pass 1
-    const ClosedSlot &mine = p.slots[item];
-    const CState e{prev.lv_out, prev.lvh_out, prev.fl_out};
-    const CState u{mine.lv_in, mine.lvh_in, mine.fl_in};
-    if ((mine.ok & 2u) || same_state(e, u, low_mask(Pg->W), low_mask(Pg->L))) {
-        out.ok = 0;
-        return;
-    }
-    atomicAdd(&p.stats[0], 1ull);
-    prefill(tr, s0, ring);
-    x.start(e, *Pg, C, M);
-    CAcc acc;
-    CState end;
-    bool lost = false;   // entries incomplete
-    Replay y;
-    y.start(u, *Pg, C, M);
-    const uint32_t r = run_until_same(tr, s0, s1, x, y, Pg, C, M, ring, em);
-    if (r < (uint32_t)(s1 - s0)) {
-        // from round s0 + r on the first replay stands: its charges, entries, end state
-        acc = acc_add_diff(x.acc, mine, y.acc);
-        end = CState{mine.lv_out, mine.lvh_out, mine.fl_out};
-        lost = (mine.ok & 4u) != 0;
-        if (scr && !lost) {
-            const uint32_t *src = p.scratch + item * p.scr_cap;
-            for (uint32_t i = y.acc.nch; i < mine.nch; i++) {
-                const uint64_t d = (uint64_t)x.acc.nch + (i - y.acc.nch);
-                if (d < p.scr_cap) scr[d] = src[i];
+        if (q.k == 0) {
+            out.ok = 0;
+            return;
+        }
+        const ClosedSlot &prev = p.slots[item - 1];   // segment k - 1, pass 1
+        const ClosedSlot &mine = p.slots[item];
+        const CState e{prev.lv_out, prev.lvh_out, prev.fl_out};
+        const CState u{mine.lv_in, mine.lvh_in, mine.fl_in};
+        const uint8_t *eh = kL ? slot_hist(p, 0, item - 1, 1) : nullptr;
+        const uint8_t *uh = kL ? slot_hist(p, 0, item, 0) : nullptr;
+        if ((mine.ok & 2u) ||
+            (same_state(e, u, low_mask(W), low_mask(Pg->L)) && (!kL || same_hist(eh, uh, W)))) {
+            out.ok = 0;
+            return;
+        }
+        atomicAdd(&p.stats[0], 1ull);
+        prefill(tr, s0, ring);
+        Replay<kL> y;
+        y.lr = kL ? rung_ring(ring_s, p.ring, 1) : LRing{nullptr, 0u};
+        if (kL) {
+            hist_to_ring(x.lr, s0, eh, W);
+            hist_to_ring(y.lr, s0, uh, W);
+        }
+        x.start(e, s0, *Pg, C, M);
+        y.start(u, s0, *Pg, C, M);
+        CAcc acc;
+        CState end;
+        bool lost = false;   // entries incomplete
+        const uint32_t r = run_until_same(tr, s0, s1, x, y, Pg, C, M, ring, em);
+        const bool met = r < (uint32_t)(s1 - s0);
+        if (met) {
+            // from round s0 + r on the first replay stands: its charges, entries, end state
+            acc = acc_add_diff(x.acc, mine, y.acc);
+            end = CState{mine.lv_out, mine.lvh_out, mine.fl_out};
+            lost = (mine.ok & 4u) != 0;
+            if (scr && !lost) {
+                const uint32_t *src = p.scratch + item * p.scr_cap;
+                for (uint32_t i = y.acc.nch; i < mine.nch; i++) {
+                    const uint64_t d = (uint64_t)x.acc.nch + (i - y.acc.nch);
+                    if (d < p.scr_cap) scr[d] = src[i];
+                }
+            }
+        } else {
+            acc = x.acc;
+            end = x.s;
+        }
+        lost = lost || acc.nch > p.scr_cap;
+        store_in(out, e);
+        store_counts(out, acc);
+        if (kL) {
+            uint8_t *ih = slot_hist(p, 1, item, 0), *oh = slot_hist(p, 1, item, 1);
+            for (int i = 0; i < W; i++) ih[i] = eh[i];
+            if (met) {
+                const uint8_t *mh = slot_hist(p, 0, item, 1);
+                for (int i = 0; i < W; i++) oh[i] = mh[i];
+            } else {
+                ring_to_hist(x.lr, s1, oh, W);
             }
         }
-    } else {
-        acc = x.acc;
-        end = x.s;
-    }
-    lost = lost || acc.nch > p.scr_cap;
-    store_slot(out, e, end, acc, 1u | ((logging && lost) ? 4u : 0u));
+        store_out(out, end, 1u | ((logging && lost) ? 4u : 0u));
     }
 }
-__global__ void __launch_bounds__(kThreads, 5) closed_first_kernel(const ClosedParams p) { closed_pass<1>(p); }
-__global__ void __launch_bounds__(kThreads) closed_second_kernel(const ClosedParams p) { closed_pass<2>(p); }
+template <bool kL>
+__global__ void __launch_bounds__(kThreads, 5) closed_first_kernel(const ClosedParams p) {
+    closed_pass<kL, 1>(p);
+}
+template <bool kL>
+__global__ void __launch_bounds__(kThreads) closed_second_kernel(const ClosedParams p) {
+    closed_pass<kL, 2>(p);
+}
 
 // Final pass: one thread per (trace, closed-loop policy) pair.
+template <bool kL>
 __global__ void __launch_bounds__(kThreads) closed_final_kernel(const ClosedParams p) {
     extern __shared__ uint32_t ring_s[];
     const int64_t id = (int64_t)blockIdx.x * kThreads + threadIdx.x;
@@ -443,17 +558,22 @@ __global__ void __launch_bounds__(kThreads) closed_final_kernel(const ClosedPara
     const DevPolicy *Pg = p.pols + pol;
     const ClosedThr *C = p.thr + ci;
     const DevModel &M = p.model;
+    const int W = Pg->W;
     const uint32_t *tr = p.traces + p.offsets[trace];
     const uint64_t n = p.lengths[trace];
     const uint64_t nseg = (n + p.seg_len - 1) / p.seg_len;
     const uint64_t item0 = p.ibase[trace] + (uint64_t)ci * nseg;
-    const uint64_t wmask = low_mask(Pg->W), lmask = low_mask(Pg->L);
+    const uint64_t wmask = low_mask(W), lmask = low_mask(Pg->L);
     const bool logging = p.log_entries && p.log_cap > 0;
     uint32_t *lg = logging ? p.log_entries + (uint64_t)pair * p.log_cap : nullptr;
-    const Ring ring{ring_s + threadIdx.x, p.ring - 1u};
-    CState E = initial_state(p, pair);
+    const Ring ring = delta_ring(ring_s, p.ring);
+    CState E = initial_state<kL>(p, pair);
+    uint8_t Eh[kL ? MAGUS_MAX_WINDOW : 1];   // one-rung mode: rungs of the W rounds before
+    if (kL)
+        for (int i = 0; i < W; i++) Eh[i] = 0;
     uint64_t N0 = 0, NM = 0, NHF = 0, NCH = 0;
     unsigned long long S0 = 0, SM = 0, HS = 0;
+    double ET = 0.0, TT = 0.0;
     auto add = [&](const CAcc &a) {
         N0 += a.n0;
         NM += a.nm;
@@ -462,11 +582,16 @@ __global__ void __launch_bounds__(kThreads) closed_final_kernel(const ClosedPara
         S0 += a.s0;
         SM += a.sm;
         HS += a.hash;
+        ET += a.e;
+        TT += a.t;
     };
-    // copy entries [i0, i1) of a replay's scratch to the log after the NCH entries so far
+    // copy entries [i0, i1) of a replay's scratch to the log at entry `at`
     auto copy = [&](uint64_t which, uint64_t item, uint32_t i0, uint32_t i1, uint64_t at) {
         const uint32_t *src = p.scratch + (which * p.n_items + item) * p.scr_cap;
         for (uint32_t i = i0; i < i1 && at + (i - i0) < p.log_cap; i++) lg[at + (i - i0)] = src[i];
+    };
+    auto take_hist = [&](const uint8_t *h) {
+        for (int i = 0; i < W; i++) Eh[i] = h[i];
     };
     for (uint64_t k = 0; k < nseg; k++) {
         const uint64_t item = item0 + k;
@@ -480,7 +605,8 @@ __global__ void __launch_bounds__(kThreads) closed_final_kernel(const ClosedPara
             const ClosedSlot &c = p.slots[w * p.n_items + item];
             if (!(c.ok & 1u)) continue;
             const CState u{c.lv_in, c.lvh_in, c.fl_in};
-            if ((c.ok & 2u) || same_state(E, u, wmask, fmask)) {
+            if ((c.ok & 2u) ||
+                (same_state(E, u, wmask, fmask) && (!kL || same_hist(Eh, slot_hist(p, w, item, 0), W)))) {
                 pick = &c;
                 which = w;
             }
@@ -495,21 +621,16 @@ __global__ void __launch_bounds__(kThreads) closed_final_kernel(const ClosedPara
                 jb.fl = E.fl;
                 jb.lv = E.lv;
                 jb.off = NCH;
+                if (kL)
+                    for (int i = 0; i < W; i++) jb.hist[i] = Eh[i];
                 jb.on = 1;
             }
         }
         if (pick) {
             if (logging && !(pick->ok & 4u)) copy(which, item, 0, pick->nch, NCH);
-            CAcc a;
-            a.n0 = pick->n0;
-            a.nm = pick->nm;
-            a.nhf = pick->nhf;
-            a.nch = pick->nch;
-            a.s0 = pick->s0;
-            a.sm = pick->sm;
-            a.hash = pick->hash;
-            add(a);
+            add(slot_acc(*pick));
             E = CState{pick->lv_out, pick->lvh_out, pick->fl_out};
+            if (kL) take_hist(slot_hist(p, which, item, 1));
             continue;
         }
         // neither replay started from the state reached here: replay the segment now,
@@ -519,24 +640,36 @@ __global__ void __launch_bounds__(kThreads) closed_final_kernel(const ClosedPara
         prefill(tr, s0, ring);
         const BufEmit em{lg ? lg + NCH : nullptr,
                          NCH < p.log_cap ? (uint32_t)min(p.log_cap - NCH, (uint64_t)0xffffffffull) : 0u};
-        Replay x;
-        x.start(E, *Pg, C, M);
-        Replay y;
-        y.start(CState{first.lv_in, first.lvh_in, first.fl_in}, *Pg, C, M);
+        Replay<kL> x, y;
+        x.lr = kL ? rung_ring(ring_s, p.ring, 0) : LRing{nullptr, 0u};
+        y.lr = kL ? rung_ring(ring_s, p.ring, 1) : LRing{nullptr, 0u};
+        if (kL) {
+            hist_to_ring(x.lr, s0, Eh, W);
+            hist_to_ring(y.lr, s0, slot_hist(p, 0, item, 0), W);
+        }
+        x.start(E, s0, *Pg, C, M);
+        y.start(CState{first.lv_in, first.lvh_in, first.fl_in}, s0, *Pg, C, M);
         const uint32_t r = run_until_same(tr, s0, s1, x, y, Pg, C, M, ring, em);
         if (r < (uint32_t)(s1 - s0)) {
             // (entries of an overflowed first replay: the log pass writes the segment)
             if (logging && !(first.ok & 4u)) copy(0, item, y.acc.nch, first.nch, NCH + x.acc.nch);
             add(acc_add_diff(x.acc, first, y.acc));
             E = CState{first.lv_out, first.lvh_out, first.fl_out};
+            if (kL) take_hist(slot_hist(p, 0, item, 1));
         } else {
             if (logging) p.jobs[item].on = 0;   // every entry went straight to the log
             add(x.acc);
             E = x.s;
+            if (kL) ring_to_hist(x.lr, s1, Eh, W);
         }
     }
     double En, T;
-    core::totals(M, N0, NM, S0, SM, &En, &T);
+    if (kL) {
+        En = ET;
+        T = TT;
+    } else {
+        core::totals(M, N0, NM, S0, SM, &En, &T);
+    }
     p.energy[pair] = En;
     p.edp[pair] = En * T;
     if (p.time) p.time[pair] = T;
@@ -546,7 +679,7 @@ __global__ void __launch_bounds__(kThreads) closed_final_kernel(const ClosedPara
     if (p.state && n > 0) {
         magus_state_t &so = p.state[pair];
         so.n_seen = n;
-        so.level = E.lv ? (uint32_t)(M.K - 1) : 0u;
+        so.level = kL ? E.lv : (E.lv ? (uint32_t)(M.K - 1) : 0u);
         so.flags = __brevll(E.fl);
         // last 64 deltas (earlier carried ones first when the trace is shorter); hist[n + k]
         // is read before it could be overwritten (n >= 1)
@@ -559,11 +692,12 @@ __global__ void __launch_bounds__(kThreads) closed_final_kernel(const ClosedPara
 
 // Log pass: the segments the final pass marked, replayed from their true start state with
 // their entries written straight to the pair's log.
+template <bool kL>
 __global__ void __launch_bounds__(kThreads) closed_log_kernel(const ClosedParams p) {
     extern __shared__ uint32_t ring_s[];
     const uint64_t item = (uint64_t)blockIdx.x * kThreads + threadIdx.x;
     if (item >= p.n_items || !p.jobs[item].on) return;
-    const ClosedJob jb = p.jobs[item];
+    const ClosedJob &jb = p.jobs[item];
     const ItemPos q = locate(p, item);
     const int pol = p.cls[q.ci];
     const DevPolicy *Pg = p.pols + pol;
@@ -574,51 +708,71 @@ __global__ void __launch_bounds__(kThreads) closed_log_kernel(const ClosedParams
     const uint64_t s0 = q.k * p.seg_len, s1 = min(n, s0 + p.seg_len);
     if (jb.off >= p.log_cap) return;
     atomicAdd(&p.stats[2], 1ull);
-    const Ring ring{ring_s + threadIdx.x, p.ring - 1u};
+    const Ring ring = delta_ring(ring_s, p.ring);
     prefill(tr, s0, ring);
-    Replay x;
-    x.start(CState{jb.lv, jb.lvh, jb.fl}, *Pg, C, p.model);
+    Replay<kL> x;
+    x.lr = kL ? rung_ring(ring_s, p.ring, 0) : LRing{nullptr, 0u};
+    if (kL) hist_to_ring(x.lr, s0, jb.hist, Pg->W);
+    x.start(CState{jb.lv, jb.lvh, jb.fl}, s0, *Pg, C, p.model);
     const BufEmit em{p.log_entries + (uint64_t)pair * p.log_cap + jb.off,
                      (uint32_t)min(p.log_cap - jb.off, (uint64_t)0xffffffffull)};
-    run_rounds<true>(tr, s0, s1, x, Pg, C, p.model, ring, em);
+    run_rounds<kL, true>(tr, s0, s1, x, Pg, C, p.model, ring, em);
 }
 
-}  // namespace
+template <bool kL>
+size_t smem_of(uint32_t ring) {
+    return (size_t)ring * kThreads * (sizeof(uint32_t) + (kL ? 2u : 0u));   // deltas (+ two rung rings)
+}
 
-int closed_threads_per_cta() { return kThreads; }
+template <bool kL>
+cudaError_t launch_t(const ClosedParams &p, cudaStream_t stream) {
+    const size_t smem = smem_of<kL>(p.ring);
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(closed_first_kernel<kL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) ||
+        (e = cudaFuncSetAttribute(closed_second_kernel<kL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) ||
+        (e = cudaFuncSetAttribute(closed_final_kernel<kL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) ||
+        (e = cudaFuncSetAttribute(closed_log_kernel<kL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)))
+        return e;
+    if (p.n_items) {
+        const uint64_t grid = (p.n_items + kThreads - 1) / kThreads;
+        closed_first_kernel<kL><<<(unsigned)grid, kThreads, smem, stream>>>(p);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        closed_second_kernel<kL><<<(unsigned)grid, kThreads, smem, stream>>>(p);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    const int64_t pairs = (int64_t)p.n_traces * p.n_cls;
+    if (pairs > 0) {
+        closed_final_kernel<kL><<<(unsigned)((pairs + kThreads - 1) / kThreads), kThreads, smem, stream>>>(p);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    if (p.n_items && p.jobs && p.log_entries && p.log_cap > 0) {
+        closed_log_kernel<kL><<<(unsigned)((p.n_items + kThreads - 1) / kThreads), kThreads, smem, stream>>>(p);
+        return cudaGetLastError();
+    }
+    return cudaSuccess;
+}
 
-int closed_max_ctas_per_sm(uint32_t ring) {
+template <bool kL>
+int max_ctas_t(uint32_t ring) {
     int blocks = 0;
-    const size_t smem = (size_t)ring * kThreads * sizeof(uint32_t);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, closed_first_kernel, kThreads, smem) != cudaSuccess) {
+    const size_t smem = smem_of<kL>(ring);
+    if (cudaFuncSetAttribute(closed_first_kernel<kL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+            cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, closed_first_kernel<kL>, kThreads, smem) != cudaSuccess) {
         cudaGetLastError();
         return 0;
     }
     return blocks;
 }
 
-cudaError_t launch_replay_closed(const ClosedParams &p, cudaStream_t stream) {
-    const size_t smem = (size_t)p.ring * kThreads * sizeof(uint32_t);
-    if (p.n_items) {
-        const uint64_t grid = (p.n_items + kThreads - 1) / kThreads;
-        closed_first_kernel<<<(unsigned)grid, kThreads, smem, stream>>>(p);
-        cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
-        closed_second_kernel<<<(unsigned)grid, kThreads, smem, stream>>>(p);
-        e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
-    }
-    const int64_t pairs = (int64_t)p.n_traces * p.n_cls;
-    if (pairs > 0) {
-        closed_final_kernel<<<(unsigned)((pairs + kThreads - 1) / kThreads), kThreads, smem, stream>>>(p);
-        cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
-    }
-    if (p.n_items && p.jobs && p.log_entries && p.log_cap > 0) {
-        closed_log_kernel<<<(unsigned)((p.n_items + kThreads - 1) / kThreads), kThreads, smem, stream>>>(p);
-        return cudaGetLastError();
-    }
-    return cudaSuccess;
+}  // namespace
+
+int closed_threads_per_cta() { return kThreads; }
+
+int closed_max_ctas_per_sm(uint32_t ring, bool ladder) { return ladder ? max_ctas_t<true>(ring) : max_ctas_t<false>(ring); }
+
+cudaError_t launch_replay_closed(const ClosedParams &p, bool ladder, cudaStream_t stream) {
+    return ladder ? launch_t<true>(p, stream) : launch_t<false>(p, stream);
 }
 
 }  // namespace magus

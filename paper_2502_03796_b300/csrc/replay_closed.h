@@ -1,32 +1,37 @@
-// replay_closed.h - the time-parallel closed loop in jump mode (replay_closed.cu): its
-// per-policy thresholds, per-segment replay records, launch parameters and host entry points.
+// replay_closed.h - the time-parallel closed loop (replay_closed.cu), jump and one-rung
+// modes: per-policy thresholds, per-segment replay records, launch parameters and host
+// entry points.
 #pragma once
 #include "magus_internal.h"
 
 namespace magus {
 
-// Closed-loop jump mode: the monitor reads obs = min(x, C(level)).  Levels are the bottom or
-// the top of the ladder (l = 0 / 1 below).  With a = delta_t, b = delta_{t-W}, a throughput is
-// capped exactly when its delta exceeds cthr[level]; Alg. 1's decision is then a threshold
-// test on the other delta (both capped: a constant), all found on the host by bisection
-// with the FP64 expressions the oracle evaluates (plan.cu).
+// Closed loop: the monitor reads obs = min(x, C(level in effect)).  With a = delta_t and
+// b = delta_{t-W}, a throughput is capped exactly when its delta exceeds cthr[level]; Alg. 1's
+// decision is then a threshold test on the other delta (both capped: a constant), all found
+// on the host by bisection with the FP64 expressions the oracle evaluates (plan.cu).
+// Level index l: jump mode 0 = bottom, 1 = top of the ladder; one-rung mode the rung itself.
 struct ClosedThr {
-    int64_t bu[2], bd[2];  // a capped at level l, b not: +1 iff b < bu[l]; -1 iff b >= bd[l]
-    int64_t au[2], ad[2];  // b capped at level l, a not: +1 iff a >= au[l]; -1 iff a < ad[l]
-    uint32_t cthr[2];      // delta > cthr[l] <=> x(delta) > C(level l), exactly
-    uint32_t cc;           // both capped (levels la, lb): bit 2 la + lb: +1; bit 4 + 2 la + lb: -1
-    uint32_t pad;
+    int64_t bu[MAGUS_MAX_LEVELS];   // a capped at level l, b not: +1 iff b < bu[l]
+    int64_t bd[MAGUS_MAX_LEVELS];   //                              -1 iff b >= bd[l]
+    int64_t au[MAGUS_MAX_LEVELS];   // b capped at level l, a not: +1 iff a >= au[l]
+    int64_t ad[MAGUS_MAX_LEVELS];   //                              -1 iff a < ad[l]
+    uint32_t cthr[MAGUS_MAX_LEVELS];  // delta > cthr[l] <=> x(delta) > C(level l), exactly
+    uint32_t ccu[MAGUS_MAX_LEVELS];   // both capped, a at la, b at lb: bit lb of ccu[la]: +1
+    uint32_t ccd[MAGUS_MAX_LEVELS];   //                                 bit lb of ccd[la]: -1
 };
 
 // One replay of one time segment of one pair: the state it started from, what it charged
-// and logged, the state it ended in.
+// and logged, the state it ended in.  One-rung mode keeps the levels of the last W rounds in
+// a separate byte array per slot (newest first) and charges energy in FP64 (e, t).
 struct ClosedSlot {
-    unsigned long long s0, sm, hash;  // stretched sums at bottom / top, hash of its change entries
-    uint64_t lvh_in, fl_in;           // levels (bit j: round start-1-j) and flags at its start
+    unsigned long long s0, sm, hash;  // jump: stretched sums at bottom / top; hash of its entries
+    uint64_t lvh_in, fl_in;           // jump: levels (bit j: round start-1-j); flags at its start
     uint64_t lvh_out, fl_out;         // the same after its last round
-    uint32_t n0, nm, nhf, nch;        // unstretched rounds at bottom / top, hf rounds, changes
-    uint32_t lv_in, lv_out;           // level bit at the start / after the last round
-    uint32_t ok;                      // bit 0 replayed, bit 1 exact start, bit 2 log overflow
+    double e, t;                      // one-rung mode: energy and time charged
+    uint32_t n0, nm, nhf, nch;        // jump: unstretched rounds at bottom / top; hf rounds; changes
+    uint32_t lv_in, lv_out;           // level (jump: bit, one-rung: rung) at the start / at the end
+    uint32_t ok;                      // bit 0 replayed, bit 1 exact start, bit 2 entries lost
     uint32_t pad;
 };
 
@@ -34,9 +39,10 @@ struct ClosedSlot {
 // overflowed): replayed once more by the log pass from its true start state, writing its
 // entries to the pair's log from entry `off` on.
 struct ClosedJob {
-    uint64_t lvh, fl;   // state at the segment start
+    uint64_t lvh, fl;   // state at the segment start (jump: level bits)
     uint64_t off;       // index of its first entry in the pair's log
-    uint32_t lv, on;    // level bit; on: replay it
+    uint32_t lv, on;    // level; on: replay it
+    uint8_t hist[MAGUS_MAX_WINDOW];   // one-rung mode: levels of the W rounds before, newest first
 };
 
 struct ClosedParams {
@@ -56,6 +62,7 @@ struct ClosedParams {
     uint32_t burn;               // rounds replayed before a segment from a guessed state
     DevModel model;
     ClosedSlot *slots;           // [2][n_items]: first replay, second replay
+    uint8_t *lhist;              // one-rung mode: [2][n_items][2][64] level histories (start, end)
     uint32_t *scratch;           // [2][n_items][scr_cap] change entries, or NULL
     uint64_t scr_cap;
     ClosedJob *jobs;             // [n_items], with a log: segments for the log pass
@@ -67,10 +74,14 @@ struct ClosedParams {
     int *status;
     unsigned long long *stats;   // [3]: second replays, replays in the final pass, in the log pass
 };
-__host__ __device__ inline bool closed_policy(const DevPolicy &d) { return d.step_mode == 2 && d.pin == 0; }
-void derive_closed(const DevPolicy &pol, const DevModel &m, ClosedThr *out);
+// Closed loop, not pinned: jump mode (step_mode 2) or one rung per decision (step_mode 3).
+__host__ __device__ inline bool closed_policy(const DevPolicy &d) {
+    return (d.step_mode == 2 || d.step_mode == 3) && d.pin == 0;
+}
+// ladder: levels 0 .. K-1 (one-rung mode), else bottom and top (jump mode).
+void derive_closed(const DevPolicy &pol, const DevModel &m, bool ladder, ClosedThr *out);
 int closed_threads_per_cta();
-int closed_max_ctas_per_sm(uint32_t ring);   // resident CTAs of the first-replay kernel
-cudaError_t launch_replay_closed(const ClosedParams &p, cudaStream_t stream);
+int closed_max_ctas_per_sm(uint32_t ring, bool ladder);   // resident CTAs of the first-replay kernel
+cudaError_t launch_replay_closed(const ClosedParams &p, bool ladder, cudaStream_t stream);
 
 }  // namespace magus

@@ -55,16 +55,16 @@ struct magus_replay {
     size_t seg_size = 0;
     // policies -> {time_groups, policy_slots, group size, segment rounds (0: tile kernel)}
     std::map<int, std::array<int, 4>> tuned;
-    // closed loop: segment and burn-in rounds (0: automatic; segment -1: literal kernel),
-    // its buffer (plan, replay slots, change-entry scratch, counters) and the last call's
-    // item count
+    // closed loop: segment and burn-in rounds (0: automatic; segment -1: literal kernel);
+    // per mode (jump, one rung per decision): the buffer (plan, replay slots, change-entry
+    // scratch, counters), the cached automatic choice and the last call's item count
     int cls_seg = 0, cls_burn = -1;
-    uint64_t cls_key = 0;                      // workload of the cached automatic choice
-    uint64_t cls_auto_seg = 0, cls_auto_burn = 0;
-    void *clsbuf = nullptr;
-    size_t cls_size = 0;
-    unsigned long long *cls_stats = nullptr;   // device counters of the last closed-loop call
-    uint64_t cls_items = 0;
+    uint64_t cls_key[2] = {0, 0};              // workload of the cached automatic choice
+    uint64_t cls_auto_seg[2] = {0, 0}, cls_auto_burn[2] = {0, 0};
+    void *clsbuf[2] = {nullptr, nullptr};
+    size_t cls_size[2] = {0, 0};
+    unsigned long long *cls_stats[2] = {nullptr, nullptr};   // device counters of the last call
+    uint64_t cls_items[2] = {0, 0};
 };
 
 namespace magus {
@@ -88,7 +88,7 @@ struct Plan {
     std::vector<DevPolicy> pols;
     std::vector<char> tp;              // per policy: replayed by the time-parallel kernels
     std::vector<int32_t> lit;          // policies for the literal kernel
-    std::vector<int32_t> cls;          // closed-loop jump-mode policies (replay_closed.cu)
+    std::vector<int32_t> cls;          // closed-loop policies (replay_closed.cu)
     std::vector<ClosedThr> cthr;       // their capped-throughput thresholds
     std::vector<LadderItem> lad;       // (trace, one-rung policy) items, longest traces first
     std::vector<PolicyGroup> groups;

@@ -1,4 +1,5 @@
-"""GPU parity of the closed loop in jump mode (step_mode 2) on the segmented kernels.
+"""GPU parity of the closed loop (step_mode 2: jump mode, 3: one rung per decision) on the
+segmented kernels.
 
 Every (trace, policy, segment) is replayed from a guessed state; segments whose guess was
 wrong are replayed again and a final pass per pair keeps only replays that started from the
@@ -34,8 +35,8 @@ def rp(mg):
     r.close()
 
 
-def closed_policies():
-    base = dict(tracegen.default_policy(), step_mode=2)
+def closed_policies(step_mode=2):
+    base = dict(tracegen.default_policy(), step_mode=step_mode)
     return [
         base,
         dict(base, direv_length=1, tune_window=1, high_freq_threshold=1.0),        # hf <=> flag
@@ -55,12 +56,13 @@ def ragged():
 
 @pytest.mark.parametrize("seg,burn", [(0, -1), (256, 64), (512, 0), (64, 0), (-1, -1)])
 def test_closed_loop_matches_oracle(rp, seg, burn):
-    """Ragged lengths, edge policies, open-loop and literal-path policies in the same call,
-    full and short logs; segments down to 64 rounds with no burn-in (most guesses wrong)."""
+    """Ragged lengths, edge policies of both step modes, open-loop and literal-path policies
+    in the same call, full and short logs; segments down to 64 rounds with no burn-in (most
+    guesses wrong)."""
     ts = ragged()
     model = tracegen.default_model()
     base = tracegen.default_policy()
-    pols = closed_policies() + [base, dict(base, step_mode=3, direv_length=3)]
+    pols = closed_policies(2) + closed_policies(3)[:5] + [base, dict(base, step_mode=3, pin_level=5)]
     ref = oracle_pairs(ts, pols, model)
     rp.set_closed(seg, burn)
     for cap in (40_000, 7):
@@ -69,7 +71,7 @@ def test_closed_loop_matches_oracle(rp, seg, burn):
         for p, r in ref.items():
             assert_pair(out, p, r, cap=cap, tag=f"closed seg={seg} burn={burn} cap={cap}")
     items, second, final, logged = rp.closed_stats()
-    n_cls = len(closed_policies())
+    n_cls = len(closed_policies(2)) + 5
     if seg > 0:
         assert items == sum((int(n) + seg - 1) // seg for n in ts.lengths) * n_cls
         if burn == 0:
@@ -171,9 +173,9 @@ def test_closed_loop_batched_full_size_sampled(mg):
 
 @pytest.mark.parametrize("seed", [31, 32, 33, 34])
 def test_closed_loop_random(mg, seed):
-    """Random closed-loop policies (windows, lists, thresholds including infinities and
-    inc < dec), random lengths and phase means, random segment / burn-in lengths and log
-    capacities: every pair against the oracle."""
+    """Random closed-loop policies of both step modes (windows, lists, thresholds including
+    infinities and inc < dec), random lengths and phase means, random segment / burn-in
+    lengths and log capacities: every pair against the oracle."""
     from test_fuzz_gpu import random_policy
     rng = np.random.default_rng(seed)
     model = tracegen.default_model()
@@ -183,7 +185,7 @@ def test_closed_loop_random(mg, seed):
     pols = []
     while len(pols) < 6:
         p = random_policy(rng, K)
-        p["step_mode"], p["pin_level"] = 2, 0
+        p["step_mode"], p["pin_level"] = int(rng.choice([2, 3])), 0
         pols.append(p)
     ref = oracle_pairs(ts, pols, model)
     rp = mg.Replay(model)
@@ -196,5 +198,45 @@ def test_closed_loop_random(mg, seed):
             assert rp.status() == 0
             for p, r in ref.items():
                 assert_pair(out, p, r, cap=cap, tag=f"seed {seed} seg {seg} burn {burn} policy {pols[p % len(pols)]}")
+    finally:
+        rp.close()
+
+
+@pytest.mark.parametrize("n_levels", [2, 5, 32])
+def test_closed_loop_one_rung(mg, n_levels):
+    """One rung per decision in the closed loop on ladders of 2, 5 and 32 rungs (2 rungs: the
+    jump mode's outcome), a carried inner rung and flag history, short segments with no
+    burn-in; every pair and the written state against the oracle and the literal kernel."""
+    model = dict(tracegen.default_model(), f_ghz=[0.8 + 1.6 * k / (n_levels - 1) for k in range(n_levels)])
+    ts = tracegen.make_traces(np.array([0, 3, 700, 5000, 21_111], dtype=np.uint64), seed=41, mean_phase=12.0)
+    pols = closed_policies(3)
+    ref = oracle_pairs(ts, pols, model)
+    rp = mg.Replay(model)
+    try:
+        for seg, burn in ((128, 0), (0, -1)):
+            rp.set_closed(seg, burn)
+            out = to_numpy(rp.run(to_device(ts), ts.lengths, pols, log_capacity=25_000))
+            assert rp.status() == 0
+            for p, r in ref.items():
+                assert_pair(out, p, r, cap=25_000, tag=f"one rung K={n_levels} seg={seg}")
+        # carried state: an inner rung and a flag history (no rounds seen)
+        n_pairs = ts.n_traces * len(pols)
+        rung, flags = n_levels // 2, 0x0F0F00FF12345678
+        written = []
+        for seg in (128, -1):
+            st = np.zeros(n_pairs * mg.STATE_BYTES, dtype=np.uint8)
+            st.view(np.uint64).reshape(n_pairs, -1)[:, 1] = flags
+            st.view(np.uint32).reshape(n_pairs, -1)[:, 4] = rung
+            state = torch.from_numpy(st).cuda()
+            rp.set_closed(seg, 0)
+            out = to_numpy(rp.run(to_device(ts), ts.lengths, pols, log_capacity=25_000, state=state))
+            assert rp.status() == 0
+            for p in range(n_pairs):
+                i, c = divmod(p, len(pols))
+                r = oracle.replay(ts.trace(i), pols[c], model,
+                                  state=oracle_state(rung, flags, pols[c]["tune_window"]))
+                assert_pair(out, p, r, cap=25_000, tag=f"one rung state K={n_levels} seg={seg}")
+            written.append(state.cpu().numpy())
+        assert np.array_equal(written[0], written[1])
     finally:
         rp.close()
