@@ -594,7 +594,7 @@ static int launch_closed_mode(magus_replay *h, const Plan &pl, int mode, const s
             S = h->cls_auto_seg[mode];
             G = h->cls_auto_burn[mode];
         } else {
-            const int ctas = closed_max_ctas_per_sm(ring, ladder);
+            const int ctas = closed_max_ctas_per_sm(ring, ladder, h->dm.K);
             const uint64_t resident = (uint64_t)h->sms * std::max(ctas, 1) * closed_threads_per_cta();
             auto items_of = [&](uint64_t L) {
                 uint64_t it = 0;

@@ -31,7 +31,8 @@
 // inside the rounding band.  Jump mode (kL = false) keeps the level as a bit and the levels
 // of the last 64 rounds in a word, and charges energy as integer counts and sums at the two
 // levels; one rung per decision (kL = true) keeps the rung and a shared-memory ring of past
-// rungs, and charges energy in FP64 per run of constant rung.
+// rungs, and charges energy as integer counts and sums per rung in shared memory (FP64 once
+// per segment: B300's FP64 pipe is too narrow for a charge at every rung change).
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -100,10 +101,15 @@ struct LRing {
     uint32_t mask;
     __device__ __forceinline__ uint8_t &at(uint64_t t) const { return col[((uint32_t)t & mask) * kThreads]; }
 };
+// Shared memory of the one-rung kernels: delta ring [R][threads] u32 | per replay: sums of
+// stretched deltas per rung [K][threads] u64 | counts of unstretched rounds [K][threads]
+// u32 | rung ring [R][threads] u8 (8-byte multiples throughout).
 __device__ __forceinline__ Ring delta_ring(uint32_t *smem, uint32_t R) { return Ring{smem + threadIdx.x, R - 1u}; }
-__device__ __forceinline__ LRing rung_ring(uint32_t *smem, uint32_t R, int which) {
-    return LRing{reinterpret_cast<uint8_t *>(smem + (size_t)R * kThreads) + (size_t)which * R * kThreads + threadIdx.x,
-                 R - 1u};
+__host__ __device__ constexpr size_t rung_block_bytes(uint32_t R, int K) {
+    return (size_t)K * kThreads * (sizeof(uint64_t) + sizeof(uint32_t)) + (size_t)R * kThreads;
+}
+__device__ __forceinline__ unsigned char *rung_block(uint32_t *smem, uint32_t R, int K, int which) {
+    return reinterpret_cast<unsigned char *>(smem + (size_t)R * kThreads) + (size_t)which * rung_block_bytes(R, K);
 }
 
 __device__ __forceinline__ void prefill(const uint32_t *tr, uint64_t t0, const Ring &ring) {
@@ -156,6 +162,22 @@ struct Replay {
     int64_t au, ad;                 // b capped, a not: +1 iff a >= au, -1 iff a < ad
     uint32_t cnt;                   // flags among the last L rounds
     LRing lr;                       // one-rung mode: this replay's rungs
+    unsigned long long *rs;         // one-rung mode: stretched-delta sum per rung (stride kThreads)
+    uint32_t *rn;                   //                unstretched rounds per rung
+
+    // one-rung mode: rings and accumulators of replay `which` of this thread
+    __device__ __forceinline__ void bind(uint32_t *smem, uint32_t R, int K, int which) {
+        if (kL) {
+            unsigned char *b = rung_block(smem, R, K, which);
+            rs = reinterpret_cast<unsigned long long *>(b) + threadIdx.x;
+            rn = reinterpret_cast<uint32_t *>(b + (size_t)K * kThreads * 8) + threadIdx.x;
+            lr = LRing{b + (size_t)K * kThreads * 12 + threadIdx.x, R - 1u};
+        } else {
+            rs = nullptr;
+            rn = nullptr;
+            lr = LRing{nullptr, 0u};
+        }
+    }
 
     __device__ __forceinline__ void load_a(const ClosedThr *Cg, const DevModel &M) {
         capa = __ldg(&Cg->cthr[s.lv]);
@@ -184,12 +206,16 @@ struct Replay {
         lbp = level_back(t0, (uint32_t)P.W);
         load_b(Cg);
         cnt = (uint32_t)__popcll(s.fl & low_mask(P.L));
+        if (kL)
+            for (int k = 0; k < M.K; k++) {
+                rs[k * kThreads] = 0;
+                rn[k * kThreads] = 0;
+            }
     }
     __device__ __forceinline__ void flush(const DevModel &M) {
         if (kL) {
-            const double tk = M.dt * (double)run_n + M.ak[s.lv] * (double)run_s;
-            acc.t += tk;
-            acc.e += M.pw[s.lv] * tk;
+            rn[s.lv * kThreads] += run_n;
+            rs[s.lv * kThreads] += run_s;
         } else if (s.lv) {
             acc.nm += run_n;
             acc.sm += run_s;
@@ -200,16 +226,27 @@ struct Replay {
         run_n = 0;
         run_s = 0;
     }
-    // Round t = t0 + j with a = delta_t, b = delta_{t-W}.  kCount: charge it, count its flag
-    // and change, emit its entry.  kWarm: rounds j < warm come before the FIFO holds W + 1.
-    // Returns the level of round t - W (for the lockstep comparison).
+    // one-rung mode: energy and time from the per-rung counts (after the last flush)
+    __device__ __forceinline__ void finish(const DevModel &M) {
+        if (!kL) return;
+        double e = 0.0, t = 0.0;
+        for (int k = 0; k < M.K; k++) {
+            const double tk = M.dt * (double)rn[k * kThreads] + M.ak[k] * (double)rs[k * kThreads];
+            t += tk;
+            e += M.pw[k] * tk;
+        }
+        acc.e = e;
+        acc.t = t;
+    }
+    // Round t = t0 + j with a = delta_t, b = delta_{t-W} and lb the level of round t - W.
+    // kCount: charge it, count its flag and change, emit its entry.  kWarm: rounds j < warm
+    // come before the FIFO holds W + 1.
     template <bool kCount, bool kWarm, class Emit>
-    __device__ __forceinline__ uint32_t step(uint32_t a, uint32_t b, uint32_t j, uint64_t t0, uint32_t warm,
-                                             const DevPolicy &P, const DevPolicy *Pg, const ClosedThr *Cg,
-                                             const DevModel &M, Emit emit) {
+    __device__ __forceinline__ void step(uint32_t a, uint32_t b, uint32_t lb, uint32_t j, uint64_t t0, uint32_t warm,
+                                         const DevPolicy &P, const DevPolicy *Pg, const ClosedThr *Cg,
+                                         const DevModel &M, Emit emit) {
         const uint64_t t = t0 + j;
         const uint32_t lv = s.lv;
-        const uint32_t lb = level_back(t, (uint32_t)P.W);   // level of round t - W
         if (lb != lbp) {
             lbp = lb;
             load_b(Cg);
@@ -267,7 +304,6 @@ struct Replay {
             s.lv = next;
             load_a(Cg, M);
         }
-        return lb;
     }
 };
 
@@ -283,6 +319,16 @@ __device__ __forceinline__ void run_rounds(const uint32_t *tr, uint64_t t0, uint
     const uint32_t nr = (uint32_t)(t1 - t0);
     const uint32_t warm = t0 < W ? (uint32_t)(W - t0) : 0u;   // rounds before the FIFO holds W + 1
     uint32_t j = 0;
+    // one-rung mode: the rung of round t - W is fetched a round ahead (for W = 1 it is the
+    // rung in effect now; otherwise its ring slot was written rounds before and is not the
+    // one this round writes), off the round's dependency chain
+    uint32_t lbn = kL ? x.level_back(t0, W) : 0u;
+    auto lb_of = [&](uint32_t jj) -> uint32_t {
+        if (!kL) return x.level_back(t0 + jj, W);
+        const uint32_t lb = lbn;
+        lbn = W == 1u ? x.s.lv : (uint32_t)x.lr.at(t0 + jj + 1u - W);
+        return lb;
+    };
     // the rounds before the FIFO fills (a trace's first W), to a multiple of 4
     const uint32_t jw = min(nr, (warm + 3u) & ~3u);
 #pragma unroll 1
@@ -290,12 +336,14 @@ __device__ __forceinline__ void run_rounds(const uint32_t *tr, uint64_t t0, uint
         const uint32_t a = __ldg(tr + t0 + j);
         const uint32_t b = ring.at(t0 + j - W);
         ring.at(t0 + j) = a;
-        x.template step<kCount, true>(a, b, j, t0, warm, P, Pg, Cg, M, emit);
+        const uint32_t lb = lb_of(j);
+        x.template step<kCount, true>(a, b, lb, j, t0, warm, P, Pg, Cg, M, emit);
     }
     auto round = [&](uint32_t a, uint32_t jj) {
         const uint32_t b = ring.at(t0 + jj - W);   // read before round t's slot is reused (W may equal R)
         ring.at(t0 + jj) = a;
-        x.template step<kCount, false>(a, b, jj, t0, 0u, P, Pg, Cg, M, emit);
+        const uint32_t lb = lb_of(jj);
+        x.template step<kCount, false>(a, b, lb, jj, t0, 0u, P, Pg, Cg, M, emit);
     };
 #pragma unroll 1
     for (; j + 4u <= nr; j += 4u) {
@@ -307,7 +355,10 @@ __device__ __forceinline__ void run_rounds(const uint32_t *tr, uint64_t t0, uint
     }
 #pragma unroll 1
     for (; j < nr; j++) round(__ldg(tr + t0 + j), j);
-    if (kCount) x.flush(M);
+    if (kCount) {
+        x.flush(M);
+        x.finish(M);
+    }
 }
 
 // Rounds [t0, t1) replayed twice in lockstep: x (charged, entries emitted) and y (charged,
@@ -338,14 +389,17 @@ __device__ __forceinline__ uint32_t run_until_same(const uint32_t *tr, uint64_t 
             const uint32_t b = ring.at(t0 + j - W);
             ring.at(t0 + j) = a;
             const uint32_t xl = x.s.lv, yl = y.s.lv;
-            const uint32_t xb = x.template step<true, true>(a, b, j, t0, warm, P, Pg, Cg, M, emit);
-            const uint32_t yb = y.template step<true, true>(a, b, j, t0, warm, P, Pg, Cg, M, NoEmit{});
+            const uint32_t xb = x.level_back(t0 + j, W), yb = y.level_back(t0 + j, W);
+            x.template step<true, true>(a, b, xb, j, t0, warm, P, Pg, Cg, M, emit);
+            y.template step<true, true>(a, b, yb, j, t0, warm, P, Pg, Cg, M, NoEmit{});
             if (kL) diff += (xl != yl ? 1 : 0) - (xb != yb ? 1 : 0);
         }
         if (kL ? (x.s.lv == y.s.lv && x.s.fl == y.s.fl && diff == 0) : same_state(x.s, y.s, wmask, ~0ull)) break;
     }
     x.flush(M);
     y.flush(M);
+    x.finish(M);
+    y.finish(M);
     return j;
 }
 
@@ -448,7 +502,7 @@ __device__ __forceinline__ void closed_pass(const ClosedParams &p) {
     uint32_t *scr = p.scratch ? p.scratch + ((uint64_t)(kPass - 1) * p.n_items + item) * p.scr_cap : nullptr;
     const BufEmit em{scr, (uint32_t)p.scr_cap};   // scr_cap <= segment rounds < 2^32
     Replay<kL> x;
-    x.lr = kL ? rung_ring(ring_s, p.ring, 0) : LRing{nullptr, 0u};
+    x.bind(ring_s, p.ring, p.model.K, 0);
     if constexpr (kPass == 1) {
         uint32_t ok = 1u;
         const uint64_t t0 = s0 > p.burn ? s0 - p.burn : 0;
@@ -489,7 +543,7 @@ __device__ __forceinline__ void closed_pass(const ClosedParams &p) {
         atomicAdd(&p.stats[0], 1ull);
         prefill(tr, s0, ring);
         Replay<kL> y;
-        y.lr = kL ? rung_ring(ring_s, p.ring, 1) : LRing{nullptr, 0u};
+        y.bind(ring_s, p.ring, p.model.K, 1);
         if (kL) {
             hist_to_ring(x.lr, s0, eh, W);
             hist_to_ring(y.lr, s0, uh, W);
@@ -641,8 +695,8 @@ __global__ void __launch_bounds__(kThreads) closed_final_kernel(const ClosedPara
         const BufEmit em{lg ? lg + NCH : nullptr,
                          NCH < p.log_cap ? (uint32_t)min(p.log_cap - NCH, (uint64_t)0xffffffffull) : 0u};
         Replay<kL> x, y;
-        x.lr = kL ? rung_ring(ring_s, p.ring, 0) : LRing{nullptr, 0u};
-        y.lr = kL ? rung_ring(ring_s, p.ring, 1) : LRing{nullptr, 0u};
+        x.bind(ring_s, p.ring, p.model.K, 0);
+        y.bind(ring_s, p.ring, p.model.K, 1);
         if (kL) {
             hist_to_ring(x.lr, s0, Eh, W);
             hist_to_ring(y.lr, s0, slot_hist(p, 0, item, 0), W);
@@ -711,7 +765,7 @@ __global__ void __launch_bounds__(kThreads) closed_log_kernel(const ClosedParams
     const Ring ring = delta_ring(ring_s, p.ring);
     prefill(tr, s0, ring);
     Replay<kL> x;
-    x.lr = kL ? rung_ring(ring_s, p.ring, 0) : LRing{nullptr, 0u};
+    x.bind(ring_s, p.ring, p.model.K, 0);
     if (kL) hist_to_ring(x.lr, s0, jb.hist, Pg->W);
     x.start(CState{jb.lv, jb.lvh, jb.fl}, s0, *Pg, C, p.model);
     const BufEmit em{p.log_entries + (uint64_t)pair * p.log_cap + jb.off,
@@ -719,43 +773,45 @@ __global__ void __launch_bounds__(kThreads) closed_log_kernel(const ClosedParams
     run_rounds<kL, true>(tr, s0, s1, x, Pg, C, p.model, ring, em);
 }
 
+// shared memory: the delta ring, and in one-rung mode the rung block of each replay a
+// thread runs (one in the first and log kernels, two in the lockstep kernels)
 template <bool kL>
-size_t smem_of(uint32_t ring) {
-    return (size_t)ring * kThreads * (sizeof(uint32_t) + (kL ? 2u : 0u));   // deltas (+ two rung rings)
+size_t smem_of(uint32_t ring, int replays, int K) {
+    return (size_t)ring * kThreads * sizeof(uint32_t) + (kL ? (size_t)replays * rung_block_bytes(ring, K) : 0);
 }
 
 template <bool kL>
 cudaError_t launch_t(const ClosedParams &p, cudaStream_t stream) {
-    const size_t smem = smem_of<kL>(p.ring);
+    const size_t sm1 = smem_of<kL>(p.ring, 1, p.model.K), sm2 = smem_of<kL>(p.ring, 2, p.model.K);
     cudaError_t e;
-    if ((e = cudaFuncSetAttribute(closed_first_kernel<kL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) ||
-        (e = cudaFuncSetAttribute(closed_second_kernel<kL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) ||
-        (e = cudaFuncSetAttribute(closed_final_kernel<kL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) ||
-        (e = cudaFuncSetAttribute(closed_log_kernel<kL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)))
+    if ((e = cudaFuncSetAttribute(closed_first_kernel<kL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1)) ||
+        (e = cudaFuncSetAttribute(closed_second_kernel<kL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2)) ||
+        (e = cudaFuncSetAttribute(closed_final_kernel<kL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2)) ||
+        (e = cudaFuncSetAttribute(closed_log_kernel<kL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1)))
         return e;
     if (p.n_items) {
         const uint64_t grid = (p.n_items + kThreads - 1) / kThreads;
-        closed_first_kernel<kL><<<(unsigned)grid, kThreads, smem, stream>>>(p);
+        closed_first_kernel<kL><<<(unsigned)grid, kThreads, sm1, stream>>>(p);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        closed_second_kernel<kL><<<(unsigned)grid, kThreads, smem, stream>>>(p);
+        closed_second_kernel<kL><<<(unsigned)grid, kThreads, sm2, stream>>>(p);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     const int64_t pairs = (int64_t)p.n_traces * p.n_cls;
     if (pairs > 0) {
-        closed_final_kernel<kL><<<(unsigned)((pairs + kThreads - 1) / kThreads), kThreads, smem, stream>>>(p);
+        closed_final_kernel<kL><<<(unsigned)((pairs + kThreads - 1) / kThreads), kThreads, sm2, stream>>>(p);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     if (p.n_items && p.jobs && p.log_entries && p.log_cap > 0) {
-        closed_log_kernel<kL><<<(unsigned)((p.n_items + kThreads - 1) / kThreads), kThreads, smem, stream>>>(p);
+        closed_log_kernel<kL><<<(unsigned)((p.n_items + kThreads - 1) / kThreads), kThreads, sm1, stream>>>(p);
         return cudaGetLastError();
     }
     return cudaSuccess;
 }
 
 template <bool kL>
-int max_ctas_t(uint32_t ring) {
+int max_ctas_t(uint32_t ring, int K) {
     int blocks = 0;
-    const size_t smem = smem_of<kL>(ring);
+    const size_t smem = smem_of<kL>(ring, 1, K);
     if (cudaFuncSetAttribute(closed_first_kernel<kL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
             cudaSuccess ||
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, closed_first_kernel<kL>, kThreads, smem) != cudaSuccess) {
@@ -769,7 +825,9 @@ int max_ctas_t(uint32_t ring) {
 
 int closed_threads_per_cta() { return kThreads; }
 
-int closed_max_ctas_per_sm(uint32_t ring, bool ladder) { return ladder ? max_ctas_t<true>(ring) : max_ctas_t<false>(ring); }
+int closed_max_ctas_per_sm(uint32_t ring, bool ladder, int n_levels) {
+    return ladder ? max_ctas_t<true>(ring, n_levels) : max_ctas_t<false>(ring, n_levels);
+}
 
 cudaError_t launch_replay_closed(const ClosedParams &p, bool ladder, cudaStream_t stream) {
     return ladder ? launch_t<true>(p, stream) : launch_t<false>(p, stream);

@@ -23,7 +23,8 @@ struct ClosedThr {
 
 // One replay of one time segment of one pair: the state it started from, what it charged
 // and logged, the state it ended in.  One-rung mode keeps the levels of the last W rounds in
-// a separate byte array per slot (newest first) and charges energy in FP64 (e, t).
+// a separate byte array per slot (newest first) and its energy and time as FP64 totals
+// (e, t), formed once per segment from integer per-rung counts and sums.
 struct ClosedSlot {
     unsigned long long s0, sm, hash;  // jump: stretched sums at bottom / top; hash of its entries
     uint64_t lvh_in, fl_in;           // jump: levels (bit j: round start-1-j); flags at its start
@@ -81,7 +82,7 @@ __host__ __device__ inline bool closed_policy(const DevPolicy &d) {
 // ladder: levels 0 .. K-1 (one-rung mode), else bottom and top (jump mode).
 void derive_closed(const DevPolicy &pol, const DevModel &m, bool ladder, ClosedThr *out);
 int closed_threads_per_cta();
-int closed_max_ctas_per_sm(uint32_t ring, bool ladder);   // resident CTAs of the first-replay kernel
+int closed_max_ctas_per_sm(uint32_t ring, bool ladder, int n_levels);   // resident CTAs, first-replay kernel
 cudaError_t launch_replay_closed(const ClosedParams &p, bool ladder, cudaStream_t stream);
 
 }  // namespace magus
