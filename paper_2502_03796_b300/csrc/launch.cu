@@ -1,7 +1,7 @@
 // launch.cu - planning (kernel choice, policy routing, work items) and the launches of the
 // replay kernels: tile or segment kernel for the jump mode, ladder kernel for the one-rung
-// mode, the segmented closed-loop kernels for the closed loop in jump mode, literal kernel
-// for the rest.
+// mode, the segmented closed-loop kernels for the closed loop (both step modes), literal
+// kernel for the rest.
 #include <cuda_runtime.h>
 
 #include <algorithm>

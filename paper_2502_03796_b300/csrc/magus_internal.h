@@ -202,8 +202,9 @@ struct LiteralParams {
 cudaError_t launch_replay_literal(const LiteralParams &p, cudaStream_t stream);
 
 // Policies the time-parallel kernels replay: open-loop jump mode, pinned (if at all) to a
-// ladder bound.  The ladder kernel takes the open-loop one-rung mode; the literal kernel
-// the rest.
+// ladder bound.  The ladder kernel takes the open-loop one-rung mode, the segmented
+// closed-loop kernels the closed loop (replay_closed.h), the literal kernel the rest (pins
+// inside the ladder in jump mode, pins in the other modes).
 __host__ __device__ inline bool tp_policy(const DevPolicy &d, int n_levels) {
     return d.step_mode == 0 && (d.pin == 0 || d.pin == 1 || d.pin == n_levels);
 }

@@ -11,8 +11,9 @@
 //     time-parallel kernel is measured against and the source of per-interval detail
 //     (level and derivative logs);
 //   * replay_literal_kernel: one launch over all traces for the policies the time-parallel
-//     kernels do not replay (one rung per decision, closed loop, a pin inside the ladder),
-//     with carried state.
+//     kernels do not replay (pins inside the ladder in jump mode, pins in the other modes;
+//     the closed loop when its segmented replay is switched off or over budget), with
+//     carried state.
 #include <cuda_runtime.h>
 #include <stdint.h>
 

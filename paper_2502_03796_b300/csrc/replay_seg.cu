@@ -323,7 +323,7 @@ __global__ void __launch_bounds__(256) combine_kernel(const SegParams p, int64_t
     const int64_t pair = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
     if (pair >= n_pairs) return;
     const int64_t trace = pair / p.n_pols, pol = pair % p.n_pols;
-    if (!tp_policy(p.pols[pol], p.model.K)) return;   // replayed by the literal kernel
+    if (!tp_policy(p.pols[pol], p.model.K)) return;   // replayed by another kernel
     const uint64_t n = p.lengths[trace];
     const uint64_t nseg = (n + p.seg_len - 1) / p.seg_len;
     const uint32_t topK = (uint32_t)(p.model.K - 1);
