@@ -240,3 +240,47 @@ def test_closed_loop_one_rung(mg, n_levels):
         assert np.array_equal(written[0], written[1])
     finally:
         rp.close()
+
+
+@pytest.mark.parametrize("step_mode", [2, 3])
+def test_closed_loop_threshold_edges(mg, step_mode):
+    """Traces built around the closed loop's decision points -- deltas at and next to the
+    capping thresholds of the bottom and top levels, at and next to the capped-case
+    thresholds of Algorithm 1, zero and 2^32 - 1 -- in random order and as steps, so that
+    capped and uncapped throughputs meet at every boundary: every pair against the oracle."""
+    model = tracegen.default_model()
+    rng = np.random.default_rng(7 + step_mode)
+    pols = [dict(tracegen.default_policy(), step_mode=step_mode),
+            dict(tracegen.default_policy(), step_mode=step_mode, direv_length=2, inc_threshold=1.0,
+                 dec_threshold=-1.0, high_freq_threshold=0.9),
+            dict(tracegen.default_policy(), step_mode=step_mode, direv_length=9, inc_threshold=40.0,
+                 dec_threshold=-60.0, tune_window=3)]
+    vals = {0, 1, 2**32 - 1, 2**32 - 2}
+    for p in pols:
+        t = [int(v) for v in mg.policy_closed_thresholds(p, model)]
+        for v in t[:10]:
+            for d in (-2, -1, 0, 1, 2):
+                if 0 <= v + d < 2**32:
+                    vals.add(v + d)
+    # every rung's capacity in deltas (the one-rung mode caps at inner rungs too)
+    q = model["dt_s"] * 1e9
+    for f in model["f_ghz"]:
+        c = int(model["bw_ref_gbs"] * (f / model["f_ref_ghz"]) * q / model["bytes_per_count"])
+        vals.update(v for v in range(c - 2, c + 3) if 0 <= v < 2**32)
+    vals = np.array(sorted(vals), dtype=np.uint64)
+    pieces = [rng.choice(vals, size=3000)]                        # random order
+    for v in vals:                                                # steps: runs of one value
+        pieces.append(np.full(int(rng.integers(1, 12)), v, dtype=np.uint64))
+    data = np.concatenate(pieces).astype(np.uint32)
+    ts = tracegen.single_trace_set(data)
+    ref = oracle_pairs(ts, pols, model)
+    rp = mg.Replay(model)
+    try:
+        for seg, burn in ((64, 0), (0, -1), (-1, -1)):
+            rp.set_closed(seg, burn)
+            out = to_numpy(rp.run(to_device(ts), ts.lengths, pols, log_capacity=len(data)))
+            assert rp.status() == 0
+            for p, r in ref.items():
+                assert_pair(out, p, r, cap=len(data), tag=f"edges mode {step_mode} seg={seg}")
+    finally:
+        rp.close()
