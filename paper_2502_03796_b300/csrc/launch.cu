@@ -106,9 +106,16 @@ int build_plan(magus_replay *h, const uint64_t *lengths, int32_t n_traces, const
             lad_pols.push_back((int32_t)i);
         } else if (closed_policy(pl->pols[i])) {
             pl->cls.push_back((int32_t)i);
-            ClosedThr c;
-            derive_closed(pl->pols[i], h->dm, pl->pols[i].step_mode == 3, &c);
-            pl->cthr.push_back(c);
+            // thresholds per rung take a few thousand FP64 bisection steps: kept per policy
+            std::string key(reinterpret_cast<const char *>(&pl->pols[i]), sizeof(DevPolicy));
+            auto it = h->cthr_cache.find(key);
+            if (it == h->cthr_cache.end()) {
+                if (h->cthr_cache.size() >= 16384) h->cthr_cache.clear();
+                ClosedThr c;
+                derive_closed(pl->pols[i], h->dm, pl->pols[i].step_mode == 3, &c);
+                it = h->cthr_cache.emplace(key, c).first;
+            }
+            pl->cthr.push_back(it->second);
         } else {
             pl->lit.push_back((int32_t)i);
         }

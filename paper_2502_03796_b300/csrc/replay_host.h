@@ -6,6 +6,7 @@
 #include <array>
 #include <map>
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 #include "replay_closed.h"
@@ -65,6 +66,7 @@ struct magus_replay {
     size_t cls_size[2] = {0, 0};
     unsigned long long *cls_stats[2] = {nullptr, nullptr};   // device counters of the last call
     uint64_t cls_items[2] = {0, 0};
+    std::unordered_map<std::string, magus::ClosedThr> cthr_cache;   // derived policy bytes -> thresholds
 };
 
 namespace magus {
