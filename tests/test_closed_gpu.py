@@ -284,3 +284,27 @@ def test_closed_loop_threshold_edges(mg, step_mode):
                 assert_pair(out, p, r, cap=len(data), tag=f"edges mode {step_mode} seg={seg}")
     finally:
         rp.close()
+
+
+def test_closed_loop_with_autotune_and_host_buffers(mg):
+    """Closed-loop policies of both modes next to open-loop ones through the autotuner (which
+    times the tile shapes with the closed-loop kernels in the same calls) and through the
+    host-buffer entry point (traces streamed in batches): every pair against the oracle."""
+    model = tracegen.default_model()
+    ts = tracegen.make_traces(np.array([7000, 300, 12_345, 64, 2048], dtype=np.uint64), seed=61, mean_phase=18.0)
+    base = tracegen.default_policy()
+    pols = [base, dict(base, step_mode=2), dict(base, step_mode=3), dict(base, direv_length=3),
+            dict(base, step_mode=2, tune_window=20, high_freq_threshold=0.3)]
+    ref = oracle_pairs(ts, pols, model)
+    rp = mg.Replay(model)
+    try:
+        rp.autotune(to_device(ts), ts.lengths, pols)
+        out = to_numpy(rp.run(to_device(ts), ts.lengths, pols, log_capacity=13_000))
+        assert rp.status() == 0
+        for p, r in ref.items():
+            assert_pair(out, p, r, cap=13_000, tag="after autotune")
+        host = rp.run_host(ts.data.view(np.uint32), ts.lengths, pols, log_capacity=13_000)
+        for p, r in ref.items():
+            assert_pair(host, p, r, cap=13_000, tag="host buffers")
+    finally:
+        rp.close()
