@@ -343,6 +343,12 @@ def run_other(args, world, rank, local) -> int:
         what = {1: "one rung per decision", 2: "closed loop", 3: "closed loop, one rung per decision"}[mode]
         desc = (f"batched replay, {what} ({kern}): "
                 f"{args.traces} traces x 100000 intervals (phase mean 40), 1 policy")
+    elif args.workload == "static":
+        ts = tracegen.batched(n_traces=args.traces, seed=rank, first_id=rank * args.traces)
+        K = len(model["f_ghz"])
+        pols = [dict(tracegen.default_policy(), pin_level=k) for k in range(1, K + 1)]
+        desc = (f"static baselines at every rung ({K} pinned policies: the ladder bounds on the tile kernel, the "
+                f"others on the static kernel): {args.traces} traces x 100000 intervals (phase mean 40)")
     elif args.workload == "long":
         ts = tracegen.batched(n_traces=16, n=4_000_000, seed=rank, first_id=rank * 16)
         pols = [tracegen.default_policy()]
@@ -481,7 +487,8 @@ def main() -> int:
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-savings", action="store_true")
     ap.add_argument("--workload", default="batched",
-                    choices=["batched", "sweep", "uneven", "single", "long", "ladder", "closed", "closed_ladder"],
+                    choices=["batched", "sweep", "uneven", "single", "long", "ladder", "closed", "closed_ladder",
+                             "static"],
                     help="batched (default, the headline line); sweep / uneven / single print their own line")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)

@@ -153,9 +153,36 @@ int build_plan(magus_replay *h, const uint64_t *lengths, int32_t n_traces, const
 // Upload the plan through pinned staging and launch the batched kernel on `stream`.
 // The policies the time-parallel kernels do not replay: one thread per pair, all traces in
 // one launch (replay_plain.cu).  d_*: the plan as uploaded to the workspace.
+// Without carried state the pinned ones among them go to the static kernel (one pass over
+// the trace at the pinned rung, replay_static.cu).  Adds the kernels launched to *kernels.
 int launch_literal_part(magus_replay *h, const Plan &pl, const uint32_t *traces, const Outs &o,
                         const DevPolicy *d_pols, const uint64_t *d_off, const uint64_t *d_len, const int32_t *d_lit,
-                        int32_t n_lit, cudaStream_t stream) {
+                        int32_t n_lit, const std::vector<int32_t> &lit, cudaStream_t stream, int *kernels) {
+    const bool split = o.state == nullptr;
+    int n_pinned = 0;
+    for (int32_t c : lit) n_pinned += pl.pols[c].pin > 0 ? 1 : 0;
+    if (split && n_pinned > 0) {
+        StaticParams sp;
+        memset(&sp, 0, sizeof(sp));
+        sp.traces = traces;
+        sp.offsets = d_off;
+        sp.lengths = d_len;
+        sp.n_traces = (int32_t)pl.lengths.size();
+        sp.n_pols = (int32_t)pl.pols.size();
+        sp.pols = d_pols;
+        sp.lit = d_lit;
+        sp.n_lit = n_lit;
+        sp.model = h->dm;
+        sp.energy = o.energy;
+        sp.edp = o.edp;
+        sp.time = o.time;
+        sp.n_changes = o.n_changes;
+        sp.change_hash = o.change_hash;
+        sp.n_hf = o.n_hf;
+        CK(launch_replay_static(sp, stream), "static kernel launch");
+        *kernels += 1;
+        if (n_pinned == (int)lit.size()) return MAGUS_OK;
+    }
     LiteralParams lp;
     memset(&lp, 0, sizeof(lp));
     lp.traces = traces;
@@ -177,7 +204,9 @@ int launch_literal_part(magus_replay *h, const Plan &pl, const uint32_t *traces,
     lp.n_hf = o.n_hf;
     lp.state = o.state;
     lp.status = h->status;
+    lp.skip_pinned = split ? 1 : 0;
     CK(launch_replay_literal(lp, stream), "literal kernel launch");
+    *kernels += 1;
     return MAGUS_OK;
 }
 
@@ -342,10 +371,11 @@ int launch_plan(magus_replay *h, const Plan &pl, const uint32_t *traces, const O
                                     stream);
             if (rc || (rc = mark())) return rc;
         }
+        int lit_kernels = 0;
         if (has_lit) {
             rc = launch_literal_part(h, pl, traces, o, p.pols, p.offsets, p.lengths,
                                      (const int32_t *)(ws + sz_pol + sz_grp + sz_items + 2 * sz_off),
-                                     (int32_t)pl.lit.size(), stream);
+                                     (int32_t)pl.lit.size(), pl.lit, stream, &lit_kernels);
             if (rc || (rc = mark())) return rc;
         }
         int cls_kernels = 0;
@@ -354,7 +384,7 @@ int launch_plan(magus_replay *h, const Plan &pl, const uint32_t *traces, const O
             if (rc || (rc = mark())) return rc;
         }
         CK(cudaEventRecord(h->k_ev[slot_k].b, stream), "cudaEventRecord");
-        h->k_ev[slot_k].kernels = (n_items ? 1 : 0) + (has_lad ? 1 : 0) + (has_lit ? 1 : 0) + cls_kernels;
+        h->k_ev[slot_k].kernels = (n_items ? 1 : 0) + (has_lad ? 1 : 0) + lit_kernels + cls_kernels;
         if (h->k_used < h->k_ev.size()) h->k_used++;
     }
     if (ms_out) {
@@ -533,10 +563,11 @@ int launch_seg_plan(magus_replay *h, const Plan &pl, const uint32_t *traces, con
         if (rc || (rc = mark())) return rc;
     }
     const bool has_lit = !pl.lit.empty() && n_traces > 0;
+    int lit_kernels = 0;
     if (has_lit) {
         rc = launch_literal_part(h, pl, traces, o, p.pols, p.offsets, p.lengths,
                                  (const int32_t *)(ws + sz_pol + sz_grp + sz_items + 4 * sz_off),
-                                 (int32_t)pl.lit.size(), stream);
+                                 (int32_t)pl.lit.size(), pl.lit, stream, &lit_kernels);
         if (rc || (rc = mark())) return rc;
     }
     int cls_kernels = 0;
@@ -546,7 +577,7 @@ int launch_seg_plan(magus_replay *h, const Plan &pl, const uint32_t *traces, con
     }
     if ((rc = mark())) return rc;
     CK(cudaEventRecord(h->k_ev[slot_k].b, stream), "cudaEventRecord");
-    h->k_ev[slot_k].kernels = (n_items ? 1 : 0) + ((n_pairs && any_tp) ? 1 : 0) + (has_lad ? 1 : 0) + (has_lit ? 1 : 0) +
+    h->k_ev[slot_k].kernels = (n_items ? 1 : 0) + ((n_pairs && any_tp) ? 1 : 0) + (has_lad ? 1 : 0) + lit_kernels +
                               cls_kernels;
     if (h->k_used < h->k_ev.size()) h->k_used++;
     if (ms_out) {
@@ -675,12 +706,8 @@ static int launch_closed_mode(magus_replay *h, const Plan &pl, int mode, const s
     // the previous call's kernels may still read the buffer
     if (h->ws_ev_pending) CK(cudaStreamWaitEvent(stream, h->ws_ev, 0), "cudaStreamWaitEvent");
     CK(cudaMemcpyAsync(buf, blob.data(), blob.size(), cudaMemcpyHostToDevice, stream), "cudaMemcpyAsync(closed plan)");
-    if (!segmented) {
-        rc = launch_literal_part(h, pl, traces, o, d_pols, d_off, d_len, (const int32_t *)buf, n_cls, stream);
-        if (rc) return rc;
-        *kernels += 1;
-        return MAGUS_OK;
-    }
+    if (!segmented) return launch_literal_part(h, pl, traces, o, d_pols, d_off, d_len, (const int32_t *)buf, n_cls, cls,
+                                               stream, kernels);
     unsigned long long *stats = (unsigned long long *)(buf + plan_bytes);
     CK(cudaMemsetAsync(stats, 0, 3 * sizeof(unsigned long long), stream), "cudaMemsetAsync");
     // no stale log-pass jobs (the final pass sets those of every pair it completes)

@@ -190,7 +190,7 @@ struct LiteralParams {
     const DevPolicy *pols;
     const int32_t *lit;        // device: policy indices replayed here
     int32_t n_lit;
-    int32_t pad;
+    int32_t skip_pinned;       // pinned policies are left to the static kernel
     DevModel model;
     double *energy, *edp, *time;
     uint32_t *log_entries;
@@ -209,6 +209,26 @@ __host__ __device__ inline bool tp_policy(const DevPolicy &d, int n_levels) {
     return d.step_mode == 0 && (d.pin == 0 || d.pin == 1 || d.pin == n_levels);
 }
 __host__ __device__ inline bool ladder_policy(const DevPolicy &d) { return d.step_mode == 1 && d.pin == 0; }
+// Pinned policies the tile and segment kernels do not take (a pin inside the ladder in jump
+// mode, any pin in the other modes): without carried state, the static kernel.
+__host__ __device__ inline bool static_policy(const DevPolicy &d, int n_levels) {
+    return d.pin > 0 && !tp_policy(d, n_levels);
+}
+struct StaticParams {
+    const uint32_t *traces;
+    const uint64_t *offsets;
+    const uint64_t *lengths;
+    int32_t n_traces;
+    int32_t n_pols;            // pair index = trace * n_pols + policy
+    const DevPolicy *pols;
+    const int32_t *lit;        // device: policy indices; the pinned ones are replayed here
+    int32_t n_lit;
+    int32_t pad;
+    DevModel model;
+    double *energy, *edp, *time;
+    uint64_t *n_changes, *change_hash, *n_hf;
+};
+cudaError_t launch_replay_static(const StaticParams &p, cudaStream_t stream);
 
 // The one-rung (ladder) kernel: one warp per (trace, policy) item.
 struct LadderItem {

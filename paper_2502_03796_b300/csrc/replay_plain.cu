@@ -212,6 +212,7 @@ __global__ void replay_literal_kernel(const LiteralParams p) {
     const int64_t trace = k / p.n_lit;
     const int pol = p.lit[k % p.n_lit];
     const DevPolicy P = p.pols[pol];
+    if (p.skip_pinned && P.pin > 0) return;   // replayed by the static kernel
     const int64_t pair = trace * p.n_pols + pol;
     LitOut o;
     o.energy = p.energy;

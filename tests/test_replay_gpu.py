@@ -552,3 +552,32 @@ def test_full_size_batched_workload(rp):
     np.testing.assert_allclose(out["time_s"], ref["time_s"], rtol=REL_TOL)
     for p, r in oracle_pairs(ts, pol, tracegen.default_model(), pairs=[0, 1, 777, 2048, 4095]).items():
         assert_pair(out, p, r, cap=cap)
+
+
+def test_static_baselines_every_rung_every_mode(rp, mg):
+    """Static baselines (pin_level 1..K) in all four step modes, ragged lengths, in one call:
+    without carried state the pins outside the tile kernel's reach take the static kernel
+    (one pass at the pinned rung), with carried state the literal kernel (which also writes
+    the flag history); both against the oracle, and the kernels launched are counted."""
+    model = tracegen.default_model()
+    K = len(model["f_ghz"])
+    ts = tracegen.make_traces(np.array([0, 1, 33, 1000, 40_001], dtype=np.uint64), seed=19, mean_phase=25.0)
+    base = tracegen.default_policy()
+    pols = [dict(base, step_mode=m, pin_level=k) for m in range(4) for k in (1, 2, 9, K - 1, K)]
+    ref = oracle_pairs(ts, pols, model)
+    rp.set_segments(0)
+    try:
+        rp.kernel_time()
+        out = to_numpy(rp.run(to_device(ts), ts.lengths, pols, log_capacity=50))
+        tot, main, runs, kernels = rp.kernel_time(detail=True)
+    finally:
+        rp.set_segments(-1)
+    assert rp.status() == 0
+    for p, r in ref.items():
+        assert_pair(out, p, r, cap=50, tag="static, no state")
+    assert runs == 1 and kernels == 2   # tile kernel (jump-mode pins at the bounds) + static kernel
+    state = torch.zeros(ts.n_traces * len(pols) * mg.STATE_BYTES, dtype=torch.uint8, device="cuda")
+    out = to_numpy(rp.run(to_device(ts), ts.lengths, pols, log_capacity=50, state=state))
+    assert rp.status() == 0
+    for p, r in ref.items():
+        assert_pair(out, p, r, cap=50, tag="static, with state")
