@@ -139,7 +139,8 @@ int magus_replay_open(magus_replay_t **h, const magus_model_t *model, int device
  * closed loop (step_mode 2 or 3, pin_level 0) on the segmented closed-loop kernels
  * (magus_replay_set_closed); the others (a pin inside the ladder in jump mode, any pin in
  * the other modes) on the static kernel (one pass per trace at the pinned rungs), or with
- * io_state on the literal kernel, one thread per pair.  With io_state a
+ * io_state on the literal kernel, one thread per pair.  Without io_state, when the static
+ * kernel runs, the pins at a ladder bound in jump mode join it.  With io_state a
  * closed-loop policy needs a fresh state (n_seen 0; else EINVAL through
  * magus_replay_status): its throughput FIFO would need past levels; in jump mode its
  * carried level must be 0 or n_levels - 1.

@@ -410,10 +410,11 @@ int magus_replay_run(magus_replay_t *h, const uint32_t *traces, const uint64_t *
         std::vector<DevPolicy> pols;
         rc = check_policies(h, configs, n_configs, &pols);
         if (rc) return rc;
+        route_pins(&pols, h->model.n_levels, io_state != nullptr);
         int tg, cw, gp, seg;
         choose_tile(h, pols, lengths, n_traces, &tg, &cw, &gp, &seg);
         Plan pl;
-        rc = build_plan(h, lengths, n_traces, configs, n_configs, tg, cw, gp, seg, &pl);
+        rc = build_plan(h, lengths, n_traces, configs, n_configs, tg, cw, gp, seg, &pl, io_state != nullptr);
         if (rc) return rc;
         return launch_plan(h, pl, traces, outs_of(log, out_energy, out_edp, out_time, io_state),
                            (cudaStream_t)stream);
@@ -484,6 +485,7 @@ int magus_replay_autotune(magus_replay_t *h, const uint32_t *traces, const uint6
         std::vector<DevPolicy> pols;
         rc = check_policies(h, configs, n_configs, &pols);
         if (rc) return rc;
+        route_pins(&pols, h->model.n_levels, false);
         std::vector<PolicyGroup> g4;
         form_groups(pols, kMaxGroup, &g4);
         for (auto &sh : shapes) {
@@ -570,6 +572,7 @@ int magus_replay_run_host(magus_replay_t *h, const uint32_t *traces, const uint6
         std::vector<DevPolicy> pols;
         rc = check_policies(h, configs, n_configs, &pols);
         if (rc) return rc;
+        route_pins(&pols, h->model.n_levels, false);
         int tg, cw, gp, seg;
         choose_tile(h, pols, lengths, n_traces, &tg, &cw, &gp, &seg);
         const bool has_log = log != nullptr;

@@ -86,10 +86,20 @@ void choose_tile(magus_replay *h, const std::vector<DevPolicy> &pols, const uint
     }
 }
 
+void route_pins(std::vector<DevPolicy> *pols, int n_levels, bool with_state) {
+    if (with_state) return;
+    bool any = false;
+    for (const DevPolicy &d : *pols) any = any || static_policy(d, n_levels);
+    if (!any) return;
+    for (DevPolicy &d : *pols)
+        if (d.pin > 0 && tp_policy(d, n_levels)) d.to_static = 1;
+}
+
 int build_plan(magus_replay *h, const uint64_t *lengths, int32_t n_traces, const magus_policy_t *configs,
-               int32_t n_configs, int tg, int cw, int gp, int seg, Plan *pl) {
+               int32_t n_configs, int tg, int cw, int gp, int seg, Plan *pl, bool with_state) {
     int rc = check_policies(h, configs, n_configs, &pl->pols);
     if (rc) return rc;
+    route_pins(&pl->pols, h->model.n_levels, with_state);
     pl->tg = tg;
     pl->cw = cw;
     pl->gp = gp;

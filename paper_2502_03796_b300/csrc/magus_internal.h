@@ -26,7 +26,7 @@ struct alignas(16) DevPolicy {
     int32_t step_mode;
     double th;             // Alg. 2 threshold (the plain kernel evaluates it literally)
     int32_t pin;           // 0: controlled; k > 0: static baseline at ladder index k - 1
-    int32_t pad;
+    int32_t to_static;     // a pin at a ladder bound sent to the static kernel (set on the host)
     // Alg. 1 on the FP64 difference d = x_t - x_{t-W} without the division: RN(d / W) > inc
     // exactly when d > up_last, RN(d / W) < dec exactly when d <= dn_last (RN(d / W) is
     // monotone in d; both found on the host over the ordered doubles)
@@ -204,13 +204,15 @@ cudaError_t launch_replay_literal(const LiteralParams &p, cudaStream_t stream);
 // Policies the time-parallel kernels replay: open-loop jump mode, pinned (if at all) to a
 // ladder bound.  The ladder kernel takes the open-loop one-rung mode, the segmented
 // closed-loop kernels the closed loop (replay_closed.h), the literal kernel the rest (pins
-// inside the ladder in jump mode, pins in the other modes).
+// inside the ladder in jump mode, pins in the other modes).  A pin at a bound joins the
+// static kernel when that kernel runs anyway (to_static).
 __host__ __device__ inline bool tp_policy(const DevPolicy &d, int n_levels) {
-    return d.step_mode == 0 && (d.pin == 0 || d.pin == 1 || d.pin == n_levels);
+    return d.step_mode == 0 && d.to_static == 0 && (d.pin == 0 || d.pin == 1 || d.pin == n_levels);
 }
 __host__ __device__ inline bool ladder_policy(const DevPolicy &d) { return d.step_mode == 1 && d.pin == 0; }
 // Pinned policies the tile and segment kernels do not take (a pin inside the ladder in jump
-// mode, any pin in the other modes): without carried state, the static kernel.
+// mode, any pin in the other modes, a bound pin marked to_static): without carried state,
+// the static kernel.
 __host__ __device__ inline bool static_policy(const DevPolicy &d, int n_levels) {
     return d.pin > 0 && !tp_policy(d, n_levels);
 }

@@ -113,10 +113,13 @@ size_t align_up(size_t v, size_t a);
 int ensure_ws(magus_replay *h, void **buf, size_t *size, size_t need);
 int ensure_pin(magus_replay *h, int slot, size_t need);
 int check_policies(magus_replay *h, const magus_policy_t *configs, int32_t n_configs, std::vector<DevPolicy> *out);
+// Without carried state, when some pin takes the static kernel, the pins at a ladder bound
+// join it (one pass charges every rung) instead of a replay each on the tile kernel.
+void route_pins(std::vector<DevPolicy> *pols, int n_levels, bool with_state);
 void choose_tile(magus_replay *h, const std::vector<DevPolicy> &pols, const uint64_t *lengths, int n_traces, int *tg,
                  int *cw, int *gp, int *seg);
 int build_plan(magus_replay *h, const uint64_t *lengths, int32_t n_traces, const magus_policy_t *configs,
-               int32_t n_configs, int tg, int cw, int gp, int seg, Plan *pl);
+               int32_t n_configs, int tg, int cw, int gp, int seg, Plan *pl, bool with_state = false);
 int launch_plan(magus_replay *h, const Plan &pl, const uint32_t *traces, const Outs &o, cudaStream_t stream,
                 float *ms_out = nullptr);
 // The closed-loop jump-mode policies of a plan (time-parallel, or the literal kernel when

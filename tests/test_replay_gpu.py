@@ -395,6 +395,43 @@ def test_ladder_kernel_matches_oracle(mg, n_levels):
         h.close()
 
 
+@pytest.mark.parametrize("ladder", ["two", "thirty-two", "close rungs", "saturating", "never stretched"])
+def test_static_kernel_ladders(mg, ladder):
+    """The static kernel's rung lookup on ladders of 2 and 32 rungs, two rungs 1e-7 GHz
+    apart (their thresholds share every cell the lookup table could use: the binary-search
+    variant), capacities whose upper thresholds exceed the 32-bit counter range (never
+    stretched there) and a ladder where no delta is ever stretched: every rung pinned, ragged
+    lengths, against the oracle; one static-kernel launch."""
+    f17 = tracegen.default_model()["f_ghz"]
+    models = {
+        "two": dict(tracegen.default_model(), f_ghz=[0.8, 2.4]),
+        "thirty-two": dict(tracegen.default_model(), f_ghz=[0.8 + 1.6 * k / 31 for k in range(32)]),
+        "close rungs": dict(tracegen.default_model(), f_ghz=[0.8, 0.8000001] + f17[1:]),
+        "saturating": dict(tracegen.default_model(), bw_ref_gbs=4000.0),
+        "never stretched": dict(tracegen.default_model(), bw_ref_gbs=1e6),
+    }
+    model = models[ladder]
+    K = len(model["f_ghz"])
+    ts = tracegen.make_traces(np.array([0, 1, 33, 2047, 2048, 2049, 30_001], dtype=np.uint64), seed=23,
+                              mean_phase=30.0)
+    if ladder == "saturating":
+        ts.data[:] = np.minimum(ts.data.astype(np.uint64) * 16, 0xFFFFFFFF).astype(ts.data.dtype)
+    base = tracegen.default_policy()
+    pols = [dict(base, pin_level=k) for k in range(1, K + 1)] + [dict(base, step_mode=3, pin_level=K // 2 + 1)]
+    ref = oracle_pairs(ts, pols, model)
+    h = mg.Replay(model)
+    try:
+        h.kernel_time()
+        out = to_numpy(h.run(to_device(ts), ts.lengths, pols, log_capacity=8))
+        tot, main, runs, kernels = h.kernel_time(detail=True)
+        assert h.status() == 0
+        for p, r in ref.items():
+            assert_pair(out, p, r, cap=8, tag=f"static, {ladder}")
+        assert runs == 1 and kernels == 1
+    finally:
+        h.close()
+
+
 def test_literal_split_replay_with_state(rp, mg):
     """Ladder mode and an inner pin carry their state across calls (open loop); a closed
     loop can only start from a fresh state (EINVAL otherwise)."""
@@ -575,9 +612,25 @@ def test_static_baselines_every_rung_every_mode(rp, mg):
     assert rp.status() == 0
     for p, r in ref.items():
         assert_pair(out, p, r, cap=50, tag="static, no state")
-    assert runs == 1 and kernels == 2   # tile kernel (jump-mode pins at the bounds) + static kernel
+    assert runs == 1 and kernels == 1   # the static kernel takes every pin, those at the bounds too
     state = torch.zeros(ts.n_traces * len(pols) * mg.STATE_BYTES, dtype=torch.uint8, device="cuda")
     out = to_numpy(rp.run(to_device(ts), ts.lengths, pols, log_capacity=50, state=state))
     assert rp.status() == 0
     for p, r in ref.items():
         assert_pair(out, p, r, cap=50, tag="static, with state")
+    # jump mode, controlled with pins at the bounds: those stay on the tile kernel, and join
+    # the static kernel once an inner pin makes it run
+    for mix, n_k in (([base, dict(base, pin_level=1), dict(base, pin_level=K)], 1),
+                     ([base, dict(base, pin_level=K), dict(base, pin_level=5), dict(base, pin_level=1)], 2)):
+        ref = oracle_pairs(ts, mix, model)
+        rp.set_segments(0)
+        try:
+            rp.kernel_time()
+            out = to_numpy(rp.run(to_device(ts), ts.lengths, mix, log_capacity=50))
+            tot, main, runs, kernels = rp.kernel_time(detail=True)
+        finally:
+            rp.set_segments(-1)
+        assert rp.status() == 0
+        for p, r in ref.items():
+            assert_pair(out, p, r, cap=50, tag=f"mix of {len(mix)}")
+        assert runs == 1 and kernels == n_k
