@@ -46,6 +46,11 @@ CLOSED_SOURCES = ["paper_2502_03796_b300/csrc/replay_closed.cu", "paper_2502_037
                   "paper_2502_03796_b300/csrc/replay_core.cuh", "paper_2502_03796_b300/csrc/magus_internal.h"]
 
 
+# the static-baseline kernel (its records: keys starting with "replay_static")
+STATIC_SOURCES = ["paper_2502_03796_b300/csrc/replay_static.cu", "paper_2502_03796_b300/csrc/replay_static.h",
+                  "paper_2502_03796_b300/csrc/replay_core.cuh", "paper_2502_03796_b300/csrc/magus_internal.h"]
+
+
 def kernel_sha(sources=None) -> str:
     h = hashlib.sha256()
     for f in sources or KERNEL_SOURCES:
@@ -72,7 +77,8 @@ def ncu_record(key: str) -> dict | None:
     with open(p) as f:
         d = json.load(f)
     e = d.get(key)
-    srcs = CLOSED_SOURCES if key.startswith("replay_closed") else KERNEL_SOURCES
+    srcs = (CLOSED_SOURCES if key.startswith("replay_closed") else
+            STATIC_SOURCES if key.startswith("replay_static") else KERNEL_SOURCES)
     if not e or e.get("kernel_sha") != kernel_sha(srcs):
         return None
     return e
@@ -412,6 +418,14 @@ def run_other(args, world, rank, local) -> int:
     if args.workload in ("closed", "closed_ladder"):
         key = "replay_closed_batched" if args.workload == "closed" else "replay_closed_ladder_batched"
         rec = ncu_record(key) if ts.n_traces == N_TRACES else None
+    elif args.workload == "static":
+        # one pass over the traces: the HBM roofline stands; the record gives the DRAM bytes
+        # of one launch on the benchmark's 4,096 traces
+        rec = ncu_record("replay_static_batched") if ts.n_traces == N_TRACES else None
+        if rec:
+            line["roofline"]["traffic"] = rec["dram_bytes_per_launch"]
+            line["roofline"]["kernel"] = "replay_static_kernel"
+        rec = None
     else:
         rec = ncu_record(f"replay_tp_{args.workload}")
     if rec and rec.get("alu_lane_ops_per_pair_interval") and clk.get("sm_mhz"):

@@ -45,7 +45,7 @@ size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 int ensure_ws(magus_replay *h, void **buf, size_t *size, size_t need) {
     if (need <= *size) return MAGUS_OK;
     size_t want = std::max(need, *size * 2);
-    size_t other = h->ws_size + h->scratch_size + h->seg_size + h->cls_size[0] + h->cls_size[1] - *size;
+    size_t other = h->ws_size + h->scratch_size + h->seg_size + h->cls_size[0] + h->cls_size[1] + h->st_size - *size;
     if (want + other > h->budget) want = need;
     if (want + other > h->budget) {
         set_error("device workspace of " + std::to_string(need) + " bytes exceeds the handle's memory budget");
@@ -335,6 +335,7 @@ int magus_replay_close(magus_replay_t *h) {
     if (h->ws) cudaFree(h->ws);
     if (h->scratch) cudaFree(h->scratch);
     if (h->segbuf) cudaFree(h->segbuf);
+    if (h->stbuf) cudaFree(h->stbuf);
     for (int m = 0; m < 2; m++)
         if (h->clsbuf[m]) cudaFree(h->clsbuf[m]);
     if (h->status) cudaFree(h->status);

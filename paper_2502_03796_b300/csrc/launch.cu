@@ -156,6 +156,17 @@ int build_plan(magus_replay *h, const uint64_t *lengths, int32_t n_traces, const
     pl->lad.reserve((size_t)n_traces * lad_pols.size());
     for (int i : order)
         for (int32_t c : lad_pols) pl->lad.push_back(LadderItem{(uint32_t)i, (uint32_t)c});
+    // without carried state the pins among the literal policies take the static kernel
+    pl->sit.clear();
+    bool any_pin = false;
+    for (int32_t c : pl->lit) any_pin = any_pin || pl->pols[c].pin > 0;
+    if (!with_state && any_pin && n_traces > 0) {
+        static_items(pl->lengths, h->sms, h->model.n_levels, &pl->sit);
+        if (pl->sit.size() > (size_t)INT32_MAX) {
+            set_error("too many static-kernel work items");
+            return MAGUS_EINVAL;
+        }
+    }
     return MAGUS_OK;
 }
 
@@ -167,8 +178,9 @@ int build_plan(magus_replay *h, const uint64_t *lengths, int32_t n_traces, const
 // the trace at the pinned rung, replay_static.cu).  Adds the kernels launched to *kernels.
 int launch_literal_part(magus_replay *h, const Plan &pl, const uint32_t *traces, const Outs &o,
                         const DevPolicy *d_pols, const uint64_t *d_off, const uint64_t *d_len, const int32_t *d_lit,
-                        int32_t n_lit, const std::vector<int32_t> &lit, cudaStream_t stream, int *kernels) {
-    const bool split = o.state == nullptr;
+                        int32_t n_lit, const std::vector<int32_t> &lit, const StaticItem *d_sit, cudaStream_t stream,
+                        int *kernels) {
+    const bool split = o.state == nullptr && d_sit != nullptr;
     int n_pinned = 0;
     for (int32_t c : lit) n_pinned += pl.pols[c].pin > 0 ? 1 : 0;
     if (split && n_pinned > 0) {
@@ -189,6 +201,21 @@ int launch_literal_part(magus_replay *h, const Plan &pl, const uint32_t *traces,
         sp.n_changes = o.n_changes;
         sp.change_hash = o.change_hash;
         sp.n_hf = o.n_hf;
+        // a trace split into parts sums them in zeroed per-trace accumulators
+        bool split_traces = false;
+        for (const StaticItem &it : pl.sit) split_traces = split_traces || it.parts > 1;
+        sp.items = d_sit;
+        sp.n_items = (int32_t)pl.sit.size();
+        if (split_traces) {
+            const size_t n_tr = pl.lengths.size();
+            const size_t sz_acc = align_up(n_tr * 2 * (MAGUS_MAX_LEVELS + 1) * sizeof(unsigned long long), 256);
+            const size_t need = sz_acc + n_tr * sizeof(uint32_t);
+            const int rc = ensure_ws(h, &h->stbuf, &h->st_size, need);
+            if (rc) return rc;
+            CK(cudaMemsetAsync(h->stbuf, 0, need, stream), "cudaMemsetAsync");
+            sp.acc = (unsigned long long *)h->stbuf;
+            sp.arrived = (uint32_t *)((char *)h->stbuf + sz_acc);
+        }
         CK(launch_replay_static(sp, stream), "static kernel launch");
         *kernels += 1;
         if (n_pinned == (int)lit.size()) return MAGUS_OK;
@@ -282,7 +309,9 @@ int launch_plan(magus_replay *h, const Plan &pl, const uint32_t *traces, const O
     const size_t sz_lit = align_up(std::max<size_t>(pl.lit.size(), 1) * 4, 256);
     const size_t sz_lad = align_up(std::max<size_t>(pl.lad.size(), 1) * sizeof(LadderItem), 256);
     const size_t off_lad = sz_pol + sz_grp + sz_items + 2 * sz_off + sz_lit;
-    const size_t total = off_lad + sz_lad;
+    const size_t sz_sit = align_up(std::max<size_t>(pl.sit.size(), 1) * sizeof(StaticItem), 256);
+    const size_t off_sit = off_lad + sz_lad;
+    const size_t total = off_sit + sz_sit;
     int rc = ensure_ws(h, &h->ws, &h->ws_size, total);
     if (rc) return rc;
     const int slot = h->pin_next;
@@ -299,6 +328,7 @@ int launch_plan(magus_replay *h, const Plan &pl, const uint32_t *traces, const O
     }
     if (!pl.lit.empty()) memcpy(pin + sz_pol + sz_grp + sz_items + 2 * sz_off, pl.lit.data(), pl.lit.size() * 4);
     if (!pl.lad.empty()) memcpy(pin + off_lad, pl.lad.data(), pl.lad.size() * sizeof(LadderItem));
+    if (!pl.sit.empty()) memcpy(pin + off_sit, pl.sit.data(), pl.sit.size() * sizeof(StaticItem));
     char *ws = (char *)h->ws;
     const bool same_plan = h->ws_plan_valid && h->ws_plan.size() == total && !memcmp(h->ws_plan.data(), pin, total);
     if (!same_plan) {
@@ -385,7 +415,9 @@ int launch_plan(magus_replay *h, const Plan &pl, const uint32_t *traces, const O
         if (has_lit) {
             rc = launch_literal_part(h, pl, traces, o, p.pols, p.offsets, p.lengths,
                                      (const int32_t *)(ws + sz_pol + sz_grp + sz_items + 2 * sz_off),
-                                     (int32_t)pl.lit.size(), pl.lit, stream, &lit_kernels);
+                                     (int32_t)pl.lit.size(), pl.lit,
+                                     pl.sit.empty() ? nullptr : (const StaticItem *)(ws + off_sit), stream,
+                                     &lit_kernels);
             if (rc || (rc = mark())) return rc;
         }
         int cls_kernels = 0;
@@ -459,7 +491,9 @@ int launch_seg_plan(magus_replay *h, const Plan &pl, const uint32_t *traces, con
     const size_t sz_lit = align_up(std::max<size_t>(pl.lit.size(), 1) * 4, 256);
     const size_t sz_lad = align_up(std::max<size_t>(pl.lad.size(), 1) * sizeof(LadderItem), 256);
     const size_t off_lad = sz_pol + sz_grp + sz_items + 4 * sz_off + sz_lit;
-    const size_t total = off_lad + sz_lad;
+    const size_t sz_sit = align_up(std::max<size_t>(pl.sit.size(), 1) * sizeof(StaticItem), 256);
+    const size_t off_sit = off_lad + sz_lad;
+    const size_t total = off_sit + sz_sit;
     // device buffers: summaries | tails | change-log scratch
     const uint64_t n_pairs = (uint64_t)n_traces * n_pols;
     const size_t sz_sum = align_up(std::max<uint64_t>(total_segs * n_pols, 1) * sizeof(SegSummary), 256);
@@ -467,7 +501,8 @@ int launch_seg_plan(magus_replay *h, const Plan &pl, const uint32_t *traces, con
     const size_t sz_log = align_up(scratch_entries * 4, 256);
     const size_t seg_need = sz_sum + sz_tail + sz_log;
     // the tile kernel needs none of the segment buffers: take it when they do not fit
-    if (std::max(total, h->ws_size) + h->scratch_size + h->cls_size[0] + h->cls_size[1] + std::max(seg_need, h->seg_size) >
+    if (std::max(total, h->ws_size) + h->scratch_size + h->cls_size[0] + h->cls_size[1] + h->st_size +
+            std::max(seg_need, h->seg_size) >
         h->budget)
         return kUseTile;
     int rc = ensure_ws(h, &h->ws, &h->ws_size, total);
@@ -490,6 +525,7 @@ int launch_seg_plan(magus_replay *h, const Plan &pl, const uint32_t *traces, con
     }
     if (!pl.lit.empty()) memcpy(pin + sz_pol + sz_grp + sz_items + 4 * sz_off, pl.lit.data(), pl.lit.size() * 4);
     if (!pl.lad.empty()) memcpy(pin + off_lad, pl.lad.data(), pl.lad.size() * sizeof(LadderItem));
+    if (!pl.sit.empty()) memcpy(pin + off_sit, pl.sit.data(), pl.sit.size() * sizeof(StaticItem));
     if (h->ws_ev_pending) CK(cudaStreamWaitEvent(stream, h->ws_ev, 0), "cudaStreamWaitEvent");
     char *ws = (char *)h->ws;
     h->ws_plan_valid = false;
@@ -577,7 +613,8 @@ int launch_seg_plan(magus_replay *h, const Plan &pl, const uint32_t *traces, con
     if (has_lit) {
         rc = launch_literal_part(h, pl, traces, o, p.pols, p.offsets, p.lengths,
                                  (const int32_t *)(ws + sz_pol + sz_grp + sz_items + 4 * sz_off),
-                                 (int32_t)pl.lit.size(), pl.lit, stream, &lit_kernels);
+                                 (int32_t)pl.lit.size(), pl.lit,
+                                 pl.sit.empty() ? nullptr : (const StaticItem *)(ws + off_sit), stream, &lit_kernels);
         if (rc || (rc = mark())) return rc;
     }
     int cls_kernels = 0;
@@ -695,7 +732,7 @@ static int launch_closed_mode(magus_replay *h, const Plan &pl, int mode, const s
     const size_t sz_slot = align_up((size_t)(2 * items) * sizeof(ClosedSlot), 256);
     const size_t sz_hist = ladder ? align_up((size_t)(4 * items) * MAGUS_MAX_WINDOW, 256) : 0;
     const size_t sz_job = logging ? align_up((size_t)items * sizeof(ClosedJob), 256) : 0;
-    const size_t others = h->ws_size + h->scratch_size + h->seg_size + h->cls_size[1 - mode];
+    const size_t others = h->ws_size + h->scratch_size + h->seg_size + h->cls_size[1 - mode] + h->st_size;
     uint64_t scr_cap = logging ? std::min<uint64_t>(S, std::max<uint64_t>(64, S / 8)) : 0;
     auto need_of = [&](uint64_t cap) {
         return plan_bytes + sz_st + sz_slot + sz_hist + sz_job + align_up((size_t)(2 * items * cap) * 4, 256);
@@ -717,7 +754,7 @@ static int launch_closed_mode(magus_replay *h, const Plan &pl, int mode, const s
     if (h->ws_ev_pending) CK(cudaStreamWaitEvent(stream, h->ws_ev, 0), "cudaStreamWaitEvent");
     CK(cudaMemcpyAsync(buf, blob.data(), blob.size(), cudaMemcpyHostToDevice, stream), "cudaMemcpyAsync(closed plan)");
     if (!segmented) return launch_literal_part(h, pl, traces, o, d_pols, d_off, d_len, (const int32_t *)buf, n_cls, cls,
-                                               stream, kernels);
+                                               nullptr, stream, kernels);
     unsigned long long *stats = (unsigned long long *)(buf + plan_bytes);
     CK(cudaMemsetAsync(stats, 0, 3 * sizeof(unsigned long long), stream), "cudaMemsetAsync");
     // no stale log-pass jobs (the final pass sets those of every pair it completes)

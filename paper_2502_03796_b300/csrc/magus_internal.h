@@ -216,21 +216,7 @@ __host__ __device__ inline bool ladder_policy(const DevPolicy &d) { return d.ste
 __host__ __device__ inline bool static_policy(const DevPolicy &d, int n_levels) {
     return d.pin > 0 && !tp_policy(d, n_levels);
 }
-struct StaticParams {
-    const uint32_t *traces;
-    const uint64_t *offsets;
-    const uint64_t *lengths;
-    int32_t n_traces;
-    int32_t n_pols;            // pair index = trace * n_pols + policy
-    const DevPolicy *pols;
-    const int32_t *lit;        // device: policy indices; the pinned ones are replayed here
-    int32_t n_lit;
-    int32_t pad;
-    DevModel model;
-    double *energy, *edp, *time;
-    uint64_t *n_changes, *change_hash, *n_hf;
-};
-cudaError_t launch_replay_static(const StaticParams &p, cudaStream_t stream);
+// The static kernel's parameters and launcher: replay_static.h.
 
 // The one-rung (ladder) kernel: one warp per (trace, policy) item.
 struct LadderItem {

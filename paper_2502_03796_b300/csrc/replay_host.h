@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "replay_closed.h"
+#include "replay_static.h"
 
 // The replay handle (magus_replay_t of the C ABI).
 struct magus_replay {
@@ -54,6 +55,8 @@ struct magus_replay {
     int seg_rounds = -1;              // -1: automatic; 0: tile kernel; > 0: segment kernel
     void *segbuf = nullptr;           // segment summaries, tails, log scratch
     size_t seg_size = 0;
+    void *stbuf = nullptr;            // static kernel: per-trace accumulators of split traces
+    size_t st_size = 0;
     // policies -> {time_groups, policy_slots, group size, segment rounds (0: tile kernel)}
     std::map<int, std::array<int, 4>> tuned;
     // closed loop: segment and burn-in rounds (0: automatic; segment -1: literal kernel);
@@ -92,6 +95,7 @@ struct Plan {
     std::vector<int32_t> lit;          // policies for the literal kernel
     std::vector<int32_t> cls;          // closed-loop policies (replay_closed.cu)
     std::vector<ClosedThr> cthr;       // their capped-throughput thresholds
+    std::vector<StaticItem> sit;       // static-kernel CTAs (pins without carried state), or none
     std::vector<LadderItem> lad;       // (trace, one-rung policy) items, longest traces first
     std::vector<PolicyGroup> groups;
     std::vector<WorkItem> items;

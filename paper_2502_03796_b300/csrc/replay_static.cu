@@ -17,8 +17,10 @@
 // traces, so the columns take every delta (no run kept in registers).
 //
 // The columns pack a sum and a count into one 64-bit word per r (one load and one store per
-// delta); every 4,096 deltas per thread, and at the end, a warp sums each r's words into
-// totals that lane r keeps in registers.
+// delta), exact for up to 4,096 deltas per thread: a CTA charges a part of a trace of at most
+// 256 blocks of 2048 deltas.  Parts are whole blocks, about four waves of CTAs, longest
+// first; a trace in several parts adds each part's totals to its accumulators in global
+// memory, and the part that arrives last charges the rungs.
 //
 // r(a) comes from a table of cells of 2^shift counter units: a cell's word holds the number
 // of thresholds below its start (top 6 bits) and the offset of the one threshold inside it,
@@ -34,8 +36,11 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-#include "magus_internal.h"
+#include <algorithm>
+#include <vector>
+
 #include "replay_core.cuh"
+#include "replay_static.h"
 
 namespace magus {
 namespace {
@@ -45,30 +50,35 @@ constexpr int kThreads = kWarps * 32;
 constexpr int kMaxCells = 512;
 constexpr int kSumBits = 44;    // 2^12 deltas below 2^32 sum below 2^44; their count fits 20 bits
 constexpr unsigned long long kSumMask = (1ull << kSumBits) - 1ull;
-constexpr int kFlush = 4096;    // deltas per thread between flushes of the packed columns
+constexpr uint32_t kMaxPartBlocks = 256;   // 2048-delta blocks per CTA: 4096 deltas per thread
 
 template <bool kCells>
-__global__ void __launch_bounds__(kThreads) replay_static_kernel(const StaticParams p, const uint32_t shift,
+__global__ void __launch_bounds__(kThreads, 10) replay_static_kernel(const StaticParams p, const uint32_t shift,
                                                                   const uint32_t n_cells) {
     // per thread and r = 0 .. K: sum and count of the deltas with r thresholds below them
     extern __shared__ unsigned long long st_s[];
     __shared__ uint32_t thr_s[MAGUS_MAX_LEVELS];   // padded with never-exceeded thresholds
     __shared__ uint32_t cell_s[kCells ? kMaxCells : 1];
-    __shared__ unsigned long long red_n[kWarps][MAGUS_MAX_LEVELS + 1], red_s[kWarps][MAGUS_MAX_LEVELS + 1];
+    __shared__ unsigned long long red_n[MAGUS_MAX_LEVELS + 1], red_s[MAGUS_MAX_LEVELS + 1];   // per r
     __shared__ unsigned long long rung_n[MAGUS_MAX_LEVELS], rung_s[MAGUS_MAX_LEVELS];
+    __shared__ int last_s;
     const DevModel &M = p.model;
     const int K = M.K;
-    const int64_t trace = blockIdx.x;
+    // this CTA's part of a trace: blocks of 2048 deltas [first, first + count)
+    const StaticItem it = p.items[blockIdx.x];
+    const int64_t trace = it.trace;
     const uint32_t *tr = p.traces + p.offsets[trace];
-    const uint64_t n = p.lengths[trace];
+    const uint64_t len = p.lengths[trace];
+    const uint64_t start = (uint64_t)it.first * 2048;
+    const uint64_t n = min(len, start + (uint64_t)it.count * 2048);   // end of the part
     // thread i takes deltas 4i .. 4i+3 of every 512 (the packed layout pads each trace to a
     // multiple of 32 deltas, so whole 16-byte loads stay inside it): the first 2048 deltas'
     // loads are issued before the tables are set up, each next 2048's before a block is charged
     const uint32_t lo4 = 4u * threadIdx.x;
     uint4 v[4];
-    if (n >= 2048) {
+    if (start + 2048 <= n) {
 #pragma unroll
-        for (int u = 0; u < 4; u++) v[u] = __ldg(reinterpret_cast<const uint4 *>(tr + 512u * u + lo4));
+        for (int u = 0; u < 4; u++) v[u] = __ldg(reinterpret_cast<const uint4 *>(tr + start + 512u * u + lo4));
     }
     if (threadIdx.x < MAGUS_MAX_LEVELS) thr_s[threadIdx.x] = threadIdx.x < (unsigned)K ? M.thr[threadIdx.x] : 0xffffffffu;
     if (kCells) {
@@ -87,30 +97,10 @@ __global__ void __launch_bounds__(kThreads) replay_static_kernel(const StaticPar
         }
     }
     // packed per-thread columns, one word per r: bits 0..43 the sum of the deltas, 44..63
-    // their count; at most kFlush deltas per thread between two flushes keep both exact
+    // their count (at most kMaxPartBlocks * 16 deltas per thread keep both exact)
     unsigned long long *pk = st_s + threadIdx.x;
     for (int r = 0; r <= K; r++) pk[r * kThreads] = 0;
     __syncthreads();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    // the warp's totals of r = lane (and r = 32 in lane 0), in registers
-    unsigned long long tot_s = 0, tot_n = 0, tot_s2 = 0, tot_n2 = 0;
-    auto flush = [&]() {
-        for (int r = 0; r <= K; r++) {
-            const unsigned long long w = pk[r * kThreads];
-            pk[r * kThreads] = 0;
-            const unsigned long long ws = core::warp_sum_u64(w & kSumMask);
-            uint32_t wn = (uint32_t)(w >> kSumBits);
-#pragma unroll
-            for (int d = 16; d > 0; d >>= 1) wn += __shfl_xor_sync(0xffffffffu, wn, d);
-            if (r == lane) {
-                tot_s += ws;
-                tot_n += wn;
-            } else if (r == lane + 32) {
-                tot_s2 += ws;
-                tot_n2 += wn;
-            }
-        }
-    };
     auto charge = [&](uint32_t a) {
         int r;
         if (kCells) {
@@ -124,9 +114,9 @@ __global__ void __launch_bounds__(kThreads) replay_static_kernel(const StaticPar
         }
         pk[r * kThreads] += (1ull << kSumBits) | a;
     };
-    uint64_t base = 0;
-    if (n >= 2048) {
-        for (uint32_t blk = 1;; blk++) {
+    uint64_t base = start;
+    if (start + 2048 <= n) {
+        for (;;) {
             const bool more = base + 4096 <= n;
             uint4 w[4];
             if (more) {
@@ -141,13 +131,11 @@ __global__ void __launch_bounds__(kThreads) replay_static_kernel(const StaticPar
                 charge(v[u].w);
             }
             base += 2048;
-            if (blk % (kFlush / 16) == 0) flush();   // 16 deltas per thread and block
             if (!more) break;
 #pragma unroll
             for (int u = 0; u < 4; u++) v[u] = w[u];
         }
     }
-    flush();
     for (; base < n; base += 512) {   // at most 12 deltas per thread
         const uint64_t e = base + lo4;
         if (e >= n) continue;
@@ -157,23 +145,60 @@ __global__ void __launch_bounds__(kThreads) replay_static_kernel(const StaticPar
         for (int j = 0; j < 4; j++)
             if (e + (uint64_t)j < n) charge(vv[j]);
     }
-    flush();
-    // rung k: unstretched deltas have r <= k, stretched ones r > k
-    red_n[warp][lane] = tot_n;
-    red_s[warp][lane] = tot_s;
-    if (lane == 0) {
-        red_n[warp][32] = tot_n2;
-        red_s[warp][32] = tot_s2;
+    __syncthreads();
+    // the columns' totals: four threads per r, 32 columns each (rotated: few bank conflicts)
+    for (int t0 = 0; t0 < 4 * (K + 1); t0 += kThreads) {
+        const int t = t0 + (int)threadIdx.x;
+        const int r = t >> 2, q = t & 3;
+        unsigned long long cs = 0, cn = 0;
+        if (t < 4 * (K + 1)) {
+            const unsigned long long *col = st_s + (size_t)r * kThreads + 32 * q;
+            for (int i = 0; i < 32; i++) {
+                const unsigned long long w = col[(i + r + 8 * q) & 31];
+                cs += w & kSumMask;
+                cn += w >> kSumBits;
+            }
+        }
+        cs += __shfl_xor_sync(0xffffffffu, cs, 1);
+        cs += __shfl_xor_sync(0xffffffffu, cs, 2);
+        cn += __shfl_xor_sync(0xffffffffu, cn, 1);
+        cn += __shfl_xor_sync(0xffffffffu, cn, 2);
+        if (t < 4 * (K + 1) && q == 0) {
+            red_n[r] = cn;
+            red_s[r] = cs;
+        }
     }
     __syncthreads();
+    // the CTA's totals per r; a trace in several parts adds them to its accumulators, and
+    // the part that arrives last charges the rungs from those
+    if (it.parts > 1 && threadIdx.x <= (unsigned)K) {
+        const int r = threadIdx.x;
+        unsigned long long *acc = p.acc + (size_t)trace * 2 * (MAGUS_MAX_LEVELS + 1);
+        atomicAdd(acc + r, red_n[r]);
+        atomicAdd(acc + MAGUS_MAX_LEVELS + 1 + r, red_s[r]);
+    }
+    if (it.parts > 1) {
+        __threadfence();
+        __syncthreads();
+        if (threadIdx.x == 0) last_s = atomicAdd(p.arrived + trace, 1u) == it.parts - 1u;
+        __syncthreads();
+        if (!last_s) return;
+        __threadfence();
+        if (threadIdx.x <= (unsigned)K) {
+            const unsigned long long *acc = p.acc + (size_t)trace * 2 * (MAGUS_MAX_LEVELS + 1);
+            red_n[threadIdx.x] = __ldcg(acc + threadIdx.x);
+            red_s[threadIdx.x] = __ldcg(acc + MAGUS_MAX_LEVELS + 1 + threadIdx.x);
+        }
+    }
+    __syncthreads();
+    // rung k: unstretched deltas have r <= k, stretched ones r > k
     if (threadIdx.x < (unsigned)K) {
         const int k = threadIdx.x;
         unsigned long long N = 0, S = 0;
-        for (int w = 0; w < kWarps; w++)
-            for (int r = 0; r <= K; r++) {
-                if (r <= k) N += red_n[w][r];
-                else S += red_s[w][r];
-            }
+        for (int r = 0; r <= K; r++) {
+            if (r <= k) N += red_n[r];
+            else S += red_s[r];
+        }
         rung_n[k] = N;
         rung_s[k] = S;
     }
@@ -226,20 +251,52 @@ bool choose_cells(const DevModel &m, uint32_t *shift, uint32_t *n_cells) {
     return false;
 }
 
+size_t static_smem(int K) { return (size_t)(K + 1) * kThreads * sizeof(unsigned long long); }
+
 }  // namespace
+
+void static_items(const std::vector<uint64_t> &lengths, int sms, int K, std::vector<StaticItem> *out) {
+    out->clear();
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, replay_static_kernel<true>, kThreads, static_smem(K)) !=
+            cudaSuccess || per_sm < 1) {
+        cudaGetLastError();
+        per_sm = 1;
+    }
+    uint64_t total = 0;
+    for (uint64_t n : lengths) total += n;
+    // deltas per part: about four waves of CTAs, no part under 16 blocks
+    const uint64_t waves = 4ull * (uint64_t)std::max(sms, 1) * (uint64_t)per_sm;
+    const uint64_t target = std::min<uint64_t>(kMaxPartBlocks, std::max<uint64_t>(16, (total / waves + 2047) / 2048));
+    for (size_t t = 0; t < lengths.size(); t++) {
+        const uint64_t blocks = (lengths[t] + 2047) / 2048;
+        uint64_t parts = std::max<uint64_t>(1, (blocks + target - 1) / target);
+        const uint64_t per = (blocks + parts - 1) / parts;
+        parts = per ? (blocks + per - 1) / per : 1;
+        for (uint64_t j = 0; j < parts; j++)
+            out->push_back(StaticItem{(uint32_t)t, (uint32_t)(j * per), (uint32_t)std::min(per, blocks - j * per),
+                                      (uint32_t)parts});
+    }
+    // longest parts first: the last wave holds the short ones
+    std::stable_sort(out->begin(), out->end(),
+                     [](const StaticItem &a, const StaticItem &b) { return a.count > b.count; });
+}
 
 cudaError_t launch_replay_static(const StaticParams &p, cudaStream_t stream) {
     if (p.n_traces <= 0) return cudaSuccess;
-    const size_t smem = (size_t)(p.model.K + 1) * kThreads * sizeof(unsigned long long);
+    const size_t smem = static_smem(p.model.K);
     uint32_t shift = 0, n_cells = 0;
     const bool cells = choose_cells(p.model, &shift, &n_cells);
     cudaError_t e = cells ? cudaFuncSetAttribute(replay_static_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
                           : cudaFuncSetAttribute(replay_static_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
+    if (!p.items) return cudaErrorInvalidValue;
+    const unsigned grid = (unsigned)p.n_items;
+    if (grid == 0) return cudaSuccess;
     if (cells)
-        replay_static_kernel<true><<<(unsigned)p.n_traces, kThreads, smem, stream>>>(p, shift, n_cells);
+        replay_static_kernel<true><<<grid, kThreads, smem, stream>>>(p, shift, n_cells);
     else
-        replay_static_kernel<false><<<(unsigned)p.n_traces, kThreads, smem, stream>>>(p, 0, 1);
+        replay_static_kernel<false><<<grid, kThreads, smem, stream>>>(p, 0, 1);
     return cudaGetLastError();
 }
 

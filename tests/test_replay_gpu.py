@@ -401,7 +401,8 @@ def test_static_kernel_ladders(mg, ladder):
     apart (their thresholds share every cell the lookup table could use: the binary-search
     variant), capacities whose upper thresholds exceed the 32-bit counter range (never
     stretched there) and a ladder where no delta is ever stretched: every rung pinned, ragged
-    lengths, against the oracle; one static-kernel launch."""
+    lengths (the longest trace split over four CTAs), against the oracle; one static-kernel
+    launch."""
     f17 = tracegen.default_model()["f_ghz"]
     models = {
         "two": dict(tracegen.default_model(), f_ghz=[0.8, 2.4]),
@@ -412,7 +413,7 @@ def test_static_kernel_ladders(mg, ladder):
     }
     model = models[ladder]
     K = len(model["f_ghz"])
-    ts = tracegen.make_traces(np.array([0, 1, 33, 2047, 2048, 2049, 30_001], dtype=np.uint64), seed=23,
+    ts = tracegen.make_traces(np.array([0, 1, 33, 2047, 2048, 2049, 30_001, 100_003], dtype=np.uint64), seed=23,
                               mean_phase=30.0)
     if ladder == "saturating":
         ts.data[:] = np.minimum(ts.data.astype(np.uint64) * 16, 0xFFFFFFFF).astype(ts.data.dtype)
