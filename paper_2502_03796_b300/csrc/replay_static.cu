@@ -37,6 +37,7 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <atomic>
 #include <vector>
 
 #include "replay_core.cuh"
@@ -256,30 +257,54 @@ size_t static_smem(int K) { return (size_t)(K + 1) * kThreads * sizeof(unsigned 
 }  // namespace
 
 void static_items(const std::vector<uint64_t> &lengths, int sms, int K, std::vector<StaticItem> *out) {
-    out->clear();
-    int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, replay_static_kernel<true>, kThreads, static_smem(K)) !=
-            cudaSuccess || per_sm < 1) {
-        cudaGetLastError();
-        per_sm = 1;
+    // resident CTAs per SM, per ladder size (the columns grow with K); asked once
+    static std::atomic<int> resident[MAGUS_MAX_LEVELS + 1];
+    int per_sm = K >= 1 && K <= MAGUS_MAX_LEVELS ? resident[K].load(std::memory_order_relaxed) : 0;
+    if (per_sm < 1) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, replay_static_kernel<true>, kThreads,
+                                                          static_smem(K)) != cudaSuccess || per_sm < 1) {
+            cudaGetLastError();
+            per_sm = 1;
+        } else if (K >= 1 && K <= MAGUS_MAX_LEVELS) {
+            resident[K].store(per_sm, std::memory_order_relaxed);
+        }
     }
     uint64_t total = 0;
     for (uint64_t n : lengths) total += n;
     // deltas per part: about four waves of CTAs, no part under 16 blocks
     const uint64_t waves = 4ull * (uint64_t)std::max(sms, 1) * (uint64_t)per_sm;
     const uint64_t target = std::min<uint64_t>(kMaxPartBlocks, std::max<uint64_t>(16, (total / waves + 2047) / 2048));
+    // longest parts first (the last wave holds the short ones): a counting sort on the
+    // block count, trace order within a count
+    std::vector<uint32_t> at(kMaxPartBlocks + 2, 0);
+    size_t n_items = 0;
+    auto split = [&](uint64_t blocks, uint64_t *parts, uint64_t *per) {
+        *parts = std::max<uint64_t>(1, (blocks + target - 1) / target);
+        *per = (blocks + *parts - 1) / *parts;
+        *parts = *per ? (blocks + *per - 1) / *per : 1;
+    };
+    for (uint64_t n : lengths) {
+        const uint64_t blocks = (n + 2047) / 2048;
+        uint64_t parts, per;
+        split(blocks, &parts, &per);
+        for (uint64_t j = 0; j < parts; j++) at[kMaxPartBlocks - std::min(per, blocks - j * per)]++;
+        n_items += parts;
+    }
+    for (uint32_t c = 0, sum = 0; c < at.size(); c++) {   // slot of the first item per count
+        const uint32_t k = at[c];
+        at[c] = sum;
+        sum += k;
+    }
+    out->resize(n_items);
     for (size_t t = 0; t < lengths.size(); t++) {
         const uint64_t blocks = (lengths[t] + 2047) / 2048;
-        uint64_t parts = std::max<uint64_t>(1, (blocks + target - 1) / target);
-        const uint64_t per = (blocks + parts - 1) / parts;
-        parts = per ? (blocks + per - 1) / per : 1;
-        for (uint64_t j = 0; j < parts; j++)
-            out->push_back(StaticItem{(uint32_t)t, (uint32_t)(j * per), (uint32_t)std::min(per, blocks - j * per),
-                                      (uint32_t)parts});
+        uint64_t parts, per;
+        split(blocks, &parts, &per);
+        for (uint64_t j = 0; j < parts; j++) {
+            const uint64_t c = std::min(per, blocks - j * per);
+            (*out)[at[kMaxPartBlocks - c]++] = StaticItem{(uint32_t)t, (uint32_t)(j * per), (uint32_t)c, (uint32_t)parts};
+        }
     }
-    // longest parts first: the last wave holds the short ones
-    std::stable_sort(out->begin(), out->end(),
-                     [](const StaticItem &a, const StaticItem &b) { return a.count > b.count; });
 }
 
 cudaError_t launch_replay_static(const StaticParams &p, cudaStream_t stream) {
