@@ -12,7 +12,8 @@
 // Each warp replays one (trace, policy) pair at a time (items from the device queue,
 // longest traces first), streaming the trace through its own two-stage ring of 32-row TMA
 // boxes.  Energy: per rung, integer counts of unstretched intervals and sums of stretched
-// deltas (shared-memory atomics per run of constant rung), FP64 totals once per pair.
+// deltas (32-bit shared-memory atomics per run of constant rung, folded into 64-bit totals
+// per sub-block), FP64 totals once per pair.
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -37,9 +38,14 @@ constexpr uint32_t kStageBytes = 1024 + SB * 4;   // [block whose last 2 rows ar
 constexpr uint32_t kWarpBytes = 2 * kStageBytes;
 constexpr int kLevels = MAGUS_MAX_LEVELS;
 
+// Per rung, over one sub-block (then folded into 64-bit totals that lane k keeps for rung
+// k): unstretched intervals, and the stretched delta sums of the runs split into their low
+// 16 bits and the rest (at most 1,056 runs of under 2^37 each: both halves stay below 2^32,
+// so 32-bit shared atomics suffice)
 struct WarpAcc {
-    unsigned long long s[kLevels];  // stretched delta sums per rung
-    uint32_t n[kLevels];            // unstretched intervals per rung
+    uint32_t n[kLevels];
+    uint32_t slo[kLevels];
+    uint32_t shi[kLevels];
 };
 struct LadderShared {
     uint64_t bar[LW][2];
@@ -123,9 +129,11 @@ __global__ void __launch_bounds__(LW * 32) replay_ladder_kernel(const LadderPara
             h1 = st.hist[32 + lane];
         }
         for (int k = lane; k < kLevels; k += 32) {
-            wa.s[k] = 0;
             wa.n[k] = 0;
+            wa.slo[k] = 0;
+            wa.shi[k] = 0;
         }
+        unsigned long long tot_n = 0, tot_s = 0;   // rung `lane`
         {
             const uint32_t b0 = stage_base(seq & 1);
             core::sts32(core::swz_elem(b0, lane - 64), h0);
@@ -220,7 +228,8 @@ __global__ void __launch_bounds__(LW * 32) replay_ladder_kernel(const LadderPara
                             const int nxt = step(cur, (HF >> k) & 1u, (UPm >> k) & 1u, km1);
                             if (nxt != cur) {
                                 atomicAdd(&wa.n[cur], run_n);
-                                atomicAdd(&wa.s[cur], run_s);
+                                atomicAdd(&wa.slo[cur], (uint32_t)run_s & 0xffffu);
+                                atomicAdd(&wa.shi[cur], (uint32_t)(run_s >> 16));
                                 run_n = 0;
                                 run_s = 0;
                                 cur = nxt;
@@ -231,7 +240,10 @@ __global__ void __launch_bounds__(LW * 32) replay_ladder_kernel(const LadderPara
                     }
                 }
                 if (run_n) atomicAdd(&wa.n[cur], run_n);
-                if (run_s) atomicAdd(&wa.s[cur], run_s);
+                if (run_s) {
+                    atomicAdd(&wa.slo[cur], (uint32_t)run_s & 0xffffu);
+                    atomicAdd(&wa.shi[cur], (uint32_t)(run_s >> 16));
+                }
 
                 // ---- change log: slots from a warp scan of the rows' counts
                 uint32_t incl = nch;
@@ -265,6 +277,16 @@ __global__ void __launch_bounds__(LW * 32) replay_ladder_kernel(const LadderPara
                 so.flags = (H >> (pl + 1)) | ((uint64_t)FL << (63 - pl));
                 core::read_hist(base, 32 * lane + pl, so.hist);
             }
+            // this sub-block's rung totals into lane k's 64-bit totals
+            __syncwarp();
+            if (lane < M.K) {
+                tot_n += wa.n[lane];
+                tot_s += (unsigned long long)wa.slo[lane] + ((unsigned long long)wa.shi[lane] << 16);
+                wa.n[lane] = 0;
+                wa.slo[lane] = 0;
+                wa.shi[lane] = 0;
+            }
+            __syncwarp();
             level = exit_level;
             const uint32_t f30 = __shfl_sync(FULL, FL, 30), f31 = __shfl_sync(FULL, FL, 31);
             tailH = (uint64_t)f30 | ((uint64_t)f31 << 32);
@@ -276,7 +298,7 @@ __global__ void __launch_bounds__(LW * 32) replay_ladder_kernel(const LadderPara
         // ---- totals: lane k sums rung k, FP64 reduction in a fixed order
         double t_k = 0.0, e_k = 0.0;
         if (lane < M.K) {
-            t_k = M.dt * (double)wa.n[lane] + M.ak[lane] * (double)wa.s[lane];
+            t_k = M.dt * (double)tot_n + M.ak[lane] * (double)tot_s;
             e_k = M.pw[lane] * t_k;
         }
 #pragma unroll

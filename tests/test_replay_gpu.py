@@ -433,6 +433,32 @@ def test_static_kernel_ladders(mg, ladder):
         h.close()
 
 
+def test_static_kernel_long_traces_in_many_parts(mg):
+    """A few long traces (1.5M and 0.9M intervals and a short one): the static kernel splits
+    each long trace into tens of CTAs whose per-rung totals meet in the trace's accumulators;
+    the last part to arrive charges the rungs.  Pins at the bottom, middle and top rung in
+    jump mode (the bound pins join the static kernel), against the oracle, twice in a row (the
+    accumulators start from zero every call)."""
+    model = tracegen.default_model()
+    K = len(model["f_ghz"])
+    ts = tracegen.make_traces(np.array([1_500_001, 900_000, 4_097], dtype=np.uint64), seed=29, mean_phase=40.0)
+    base = tracegen.default_policy()
+    pols = [dict(base, pin_level=k) for k in (1, 9, K)]
+    ref = oracle_pairs(ts, pols, model, log=False)
+    h = mg.Replay(model)
+    try:
+        for rep in range(2):
+            h.kernel_time()
+            out = to_numpy(h.run(to_device(ts), ts.lengths, pols, log_capacity=0))
+            tot, main, runs, kernels = h.kernel_time(detail=True)
+            assert h.status() == 0
+            for p, r in ref.items():
+                assert_pair(out, p, r, cap=0, check_log=False, tag=f"static long, call {rep}")
+            assert runs == 1 and kernels == 1
+    finally:
+        h.close()
+
+
 def test_literal_split_replay_with_state(rp, mg):
     """Ladder mode and an inner pin carry their state across calls (open loop); a closed
     loop can only start from a fresh state (EINVAL otherwise)."""
