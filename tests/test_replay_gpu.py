@@ -433,6 +433,33 @@ def test_static_kernel_ladders(mg, ladder):
         h.close()
 
 
+@pytest.mark.parametrize("seg", [0, 2048])
+def test_controlled_policies_beside_pins(rp, seg):
+    """Controlled jump-mode policies next to pins at the bounds and inside the ladder, on the
+    tile kernel (seg 0) and on the segment kernel (seg 2048: its plan carries the static
+    kernel's items too): the bound pins join the static kernel once an inner pin makes it
+    run; every pair against the oracle, ragged lengths, with logs."""
+    model = tracegen.default_model()
+    K = len(model["f_ghz"])
+    ts = tracegen.make_traces(np.array([0, 5, 2048, 9_001, 70_003], dtype=np.uint64), seed=37, mean_phase=20.0)
+    base = tracegen.default_policy()
+    pols = [base, dict(base, pin_level=1), dict(base, inc_threshold=3.0, dec_threshold=-3.0),
+            dict(base, pin_level=7), dict(base, pin_level=K)]
+    ref = oracle_pairs(ts, pols, model)
+    rp.set_segments(seg)
+    try:
+        rp.kernel_time()
+        out = to_numpy(rp.run(to_device(ts), ts.lengths, pols, log_capacity=300))
+        tot, main, runs, kernels = rp.kernel_time(detail=True)
+    finally:
+        rp.set_segments(-1)
+    assert rp.status() == 0
+    for p, r in ref.items():
+        assert_pair(out, p, r, cap=300, tag=f"pins beside controlled, seg {seg}")
+    # tile kernel + static kernel, or segment kernel + combine + static kernel
+    assert runs == 1 and kernels == (2 if seg == 0 else 3)
+
+
 def test_static_kernel_long_traces_in_many_parts(mg):
     """A few long traces (1.5M and 0.9M intervals and a short one): the static kernel splits
     each long trace into tens of CTAs whose per-rung totals meet in the trace's accumulators;
