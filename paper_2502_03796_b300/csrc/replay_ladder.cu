@@ -217,7 +217,7 @@ __global__ void __launch_bounds__(LW * 32) replay_ladder_kernel(const LadderPara
                 uint32_t thr = sh.thr[cur];
                 uint32_t run_n = 0;
                 unsigned long long run_s = 0;
-                uint32_t nch = 0;
+                uint32_t nch = 0, CH = 0;
 #pragma unroll
                 for (int k = 0; k < 32; k++) {
                     if ((vmask >> k) & 1u) {
@@ -234,6 +234,7 @@ __global__ void __launch_bounds__(LW * 32) replay_ladder_kernel(const LadderPara
                                 run_s = 0;
                                 cur = nxt;
                                 thr = sh.thr[cur];
+                                CH |= 1u << k;
                                 nch++;
                             }
                         }
@@ -256,16 +257,16 @@ __global__ void __launch_bounds__(LW * 32) replay_ladder_kernel(const LadderPara
                     uint64_t off = cnt + incl - nch;
                     uint32_t *log = p.log_entries ? p.log_entries + (uint64_t)pair * p.log_cap : nullptr;
                     int c2 = enter;
-                    for (uint32_t bits = EV; bits; bits &= bits - 1) {
+                    // only the rounds where the rung changed (CH): the other events are
+                    // clamped no-ops
+                    for (uint32_t bits = CH; bits; bits &= bits - 1) {
                         const int q = __ffs(bits) - 1;
                         const int nxt = step(c2, (HF >> q) & 1u, (UPm >> q) & 1u, km1);
-                        if (nxt != c2) {
-                            const uint64_t when = n_seen0 + r0 + (uint64_t)q + 1u;
-                            if (log && off < p.log_cap) log[off] = (uint32_t)(when << 5) | (uint32_t)nxt;
-                            hash += core::mix64((when << 8) | (uint64_t)nxt);
-                            off++;
-                            c2 = nxt;
-                        }
+                        const uint64_t when = n_seen0 + r0 + (uint64_t)q + 1u;
+                        if (log && off < p.log_cap) log[off] = (uint32_t)(when << 5) | (uint32_t)nxt;
+                        hash += core::mix64((when << 8) | (uint64_t)nxt);
+                        off++;
+                        c2 = nxt;
                     }
                 }
                 cnt += __shfl_sync(FULL, incl, 31);
