@@ -645,6 +645,33 @@ def test_full_size_batched_workload(rp):
         assert_pair(out, p, r, cap=cap)
 
 
+def test_full_size_static_workload(rp):
+    """4,096 traces x 100,000 intervals pinned at each of the 17 rungs, the call
+    `bench.py --workload static` times (one static-kernel launch, every trace in parts):
+    the pairs of four traces against the oracle; for every trace, time does not grow with
+    the rung (more capacity stretches no more intervals: the same deltas, higher thresholds)
+    and energy / time is the rung's power, P(f) = 15 W + 10 W (f / 2.4 GHz)^2."""
+    model = tracegen.default_model()
+    K = len(model["f_ghz"])
+    ts = tracegen.batched()
+    pols = [dict(tracegen.default_policy(), pin_level=k) for k in range(1, K + 1)]
+    rp.kernel_time()
+    out = to_numpy(rp.run(to_device(ts), ts.lengths, pols, log_capacity=0))
+    tot, main, runs, kernels = rp.kernel_time(detail=True)
+    assert rp.status() == 0
+    assert runs == 1 and kernels == 1
+    pairs = [t * K + k for t in (0, 1, 2047, 4095) for k in range(K)]
+    for p, r in oracle_pairs(ts, pols, model, pairs=pairs, log=False).items():
+        assert_pair(out, p, r, cap=0, check_log=False, tag="static full size")
+    T = out["time_s"].reshape(ts.n_traces, K)
+    E = out["energy_j"].reshape(ts.n_traces, K)
+    assert np.all(np.diff(T, axis=1) <= 0)
+    assert np.all(T[:, -1] >= 100_000 * model["dt_s"] * (1 - 1e-12))
+    f = np.array(model["f_ghz"])
+    np.testing.assert_allclose(E / T, np.broadcast_to(15.0 + 10.0 * (f / 2.4) ** 2, E.shape), rtol=1e-12)
+    assert not np.any(out["n_changes"]) and not np.any(out["n_hf"]) and not np.any(out["change_hash"])
+
+
 def test_static_baselines_every_rung_every_mode(rp, mg):
     """Static baselines (pin_level 1..K) in all four step modes, ragged lengths, in one call:
     without carried state the pins outside the tile kernel's reach take the static kernel
