@@ -9,7 +9,7 @@
 // predictor).  Only the carried state would need the predictions (its flag history): with
 // io_state these policies take the literal kernel.
 //
-// One CTA per trace charges every rung in one pass.  The stretch thresholds increase with
+// One pass over each trace charges every rung.  The stretch thresholds increase with
 // the rung, so a delta a is stretched exactly at the rungs below r(a) = #{k : thr[k] < a};
 // each delta adds a to a sum and 1 to a count kept per r in shared-memory columns (one per
 // thread, so no two lanes touch one word), and the rung totals are prefix / suffix sums of
