@@ -6,6 +6,10 @@ One step = one replay of the batched workload: 4,096 synthetic traces x 100,000 
 Algorithm 2, the jump-to-bound decision, the energy/EDP charge and the full change log,
 in one persistent launch of the time-parallel kernel.  Inputs are resident in HBM when
 the timed region starts (1.64 GB, larger than the 126 MB L2, so no flush is needed).
+The same line carries the policy sweep (1,024 traces x 200,000 intervals x 256 policies)
+and the uneven-length workload (16,384 traces, 1e3..1e6 intervals, 16 policies) under
+the keys "sweep" and "uneven", each timed on its own with its roofline, one launch per
+trace and the CPU oracle beside it.
 
 With torchrun (N > 1) every rank replays its own 4,096 traces (weak scaling, no data-path
 collective; a barrier and a max-reduction of the elapsed time only).
@@ -329,39 +333,106 @@ def time_steps(fn, steps: int, warmup: int, stream, after_warmup=None) -> float:
     return e0.elapsed_time(e1) / steps
 
 
+def sm_count(dev) -> int:
+    """Streaming multiprocessors of the device (cudaDevAttrMultiProcessorCount)."""
+    import torch
+    return int(torch.cuda.get_device_properties(dev).multi_processor_count)
+
+
+def alu_peak_lane_ops(sms: int, sm_mhz: float) -> float:
+    """Integer-ALU pipe peak: per SM 4 partitions x 16 lanes per cycle, at the sampled clock."""
+    return sms * 4 * 16 * sm_mhz * 1e6
+
+
+def oracle_rate(ts, pols, model, target_s: float = 6.0):
+    """The CPU oracle (all host cores, OpenMP over pairs) on a bounded prefix of the traces,
+    sized from a one-trace probe to about target_s of wall time.  Returns (pair-samples/s,
+    threads, sample description)."""
+    import oracle
+    t0 = time.perf_counter()
+    oracle.replay_batch(ts.data, ts.offsets[:1], ts.lengths[:1], pols, model)
+    per = max(time.perf_counter() - t0, 1e-6) / max(float(ts.lengths[0]), 1.0)
+    k, tot = 0, 0.0
+    while k < ts.n_traces and tot * per < target_s:
+        tot += float(ts.lengths[k])
+        k += 1
+    t0 = time.perf_counter()
+    _, used = oracle.replay_batch(ts.data, ts.offsets[:k], ts.lengths[:k], pols, model)
+    dt = time.perf_counter() - t0
+    n = float(ts.lengths[:k].sum()) * len(pols)
+    return n / dt, used, f"first {k} of {ts.n_traces} traces x {len(pols)} policies ({dt:.1f} s wall)"
+
+
+def per_trace_launches(rp, d_tr, ts, pols, stream, k: int = 256) -> dict:
+    """The same replay entry point called once per trace (automatic kernel choice) on the
+    first k traces: the one-launch-per-trace form the batched launch is compared with."""
+    import torch
+    k = min(k, ts.n_traces)
+    total_ms, kernels, runs = 0.0, 0, 0
+    rp.kernel_time()
+    for i in range(k):
+        sub_len = ts.lengths[i:i + 1]
+        o = int(ts.offsets[i])
+        sub = d_tr[o:o + int((sub_len[0] + 31) // 32 * 32) + 32]
+        if i == 0:
+            rp.run(sub, sub_len, pols, stream=stream)
+            torch.cuda.synchronize()
+            rp.kernel_time()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        rp.run(sub, sub_len, pols, stream=stream)
+        t1.record(stream)
+        torch.cuda.synchronize()
+        total_ms += t0.elapsed_time(t1)
+    _, _, runs, kernels = rp.kernel_time(detail=True)
+    return dict(value=float(ts.lengths[:k].sum()) * len(pols) / (total_ms * 1e-3), unit="pair-interval samples/s",
+                sample=f"first {k} traces, one call (automatic kernel choice) each", kernels_launched=kernels,
+                ms_per_trace=total_ms / k)
+
+
 def run_other(args, world, rank, local) -> int:
     """Lines for the other replay workloads: policy sweep, uneven lengths, single trace, few
     long traces."""
+    line = measure_workload(args.workload, args, world, rank, local, args.steps, args.warmup,
+                            plain=not args.no_plain, cpu=not args.no_cpu_baseline)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def measure_workload(kind, args, world, rank, local, steps, warmup, plain=True, cpu=True) -> dict:
+    """One workload's line: the replay timed over `steps` calls after `warmup`, its roofline,
+    and (rank 0) one launch per trace, the plain form and the CPU oracle beside it."""
     import torch
     from paper_2502_03796_b300 import magus
-    import oracle
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
     model = tracegen.default_model()
-    if args.workload == "sweep":
+    if kind == "sweep":
         ts = tracegen.sweep(first_id=rank * 1024)
         pols = tracegen.sweep_policies()
         desc = "policy sweep: 1024 traces x 200000 intervals (bursty mean 10 / long mean 500 regimes), 256 policies"
-    elif args.workload in ("ladder", "closed", "closed_ladder"):
+    elif kind in ("ladder", "closed", "closed_ladder"):
         ts = tracegen.batched(n_traces=args.traces, seed=rank, first_id=rank * args.traces)
-        mode = {"ladder": 1, "closed": 2, "closed_ladder": 3}[args.workload]
+        mode = {"ladder": 1, "closed": 2, "closed_ladder": 3}[kind]
         pols = [dict(tracegen.default_policy(), step_mode=mode)]
         kern = "ladder kernel" if mode == 1 else ("literal kernel" if args.closed.startswith("-1") else
                                                   "segmented closed-loop kernels")
         what = {1: "one rung per decision", 2: "closed loop", 3: "closed loop, one rung per decision"}[mode]
         desc = (f"batched replay, {what} ({kern}): "
                 f"{args.traces} traces x 100000 intervals (phase mean 40), 1 policy")
-    elif args.workload == "static":
+    elif kind == "static":
         ts = tracegen.batched(n_traces=args.traces, seed=rank, first_id=rank * args.traces)
         K = len(model["f_ghz"])
         pols = [dict(tracegen.default_policy(), pin_level=k) for k in range(1, K + 1)]
         desc = (f"static baselines at every rung ({K} pinned policies, one pass of the static kernel): "
                 f"{args.traces} traces x 100000 intervals (phase mean 40)")
-    elif args.workload == "long":
+    elif kind == "long":
         ts = tracegen.batched(n_traces=16, n=4_000_000, seed=rank, first_id=rank * 16)
         pols = [tracegen.default_policy()]
         desc = "few long traces: 16 traces x 4000000 intervals (phase mean 40), 1 policy"
-    elif args.workload == "uneven":
+    elif kind == "uneven":
         nt = 16384 if args.traces == N_TRACES else args.traces
         ts = tracegen.uneven(n_traces=nt, seed=rank)
         pols = tracegen.sweep_policies()[:16]
@@ -381,22 +452,25 @@ def run_other(args, world, rank, local) -> int:
     rp.set_segments(args.segments)
     if args.closed:
         rp.set_closed(*[int(x) for x in args.closed.split(",")])
-    if args.workload in ("sweep", "uneven") and not args.tile and args.segments < 0:
+    if kind in ("sweep", "uneven") and not args.tile and args.segments < 0:
         tuned, tms = rp.autotune(d_tr, ts.lengths, pols, stream=stream)
     clocks = ClockSampler(local)
+    barrier(world)
     clocks.start()
     # the kernel events restart after the warm-up: they cover the timed steps only
-    ms = time_steps(lambda: rp.run(d_tr, ts.lengths, pols, stream=stream, out=outs), args.steps, args.warmup, stream,
+    ms = time_steps(lambda: rp.run(d_tr, ts.lengths, pols, stream=stream, out=outs), steps, warmup, stream,
                     after_warmup=rp.kernel_time)
     clk = clocks.stop()
+    barrier(world)
+    ms = max_over_ranks(world, ms, dev)
     k_ms, k_main, k_n, k_kernels = rp.kernel_time(detail=True)
     pair_steps = ts.n_samples * len(pols)
     value = pair_steps * world / (ms * 1e-3)
     alg_bytes = 4 * ts.n_samples + 48 * n_pairs
     k_avg = k_ms / max(k_n, 1)
     peaks = measured_peaks()
-    line = dict(metric=METRIC, value=value, unit="pair-interval samples/s", n_gpus=world, steps=args.steps,
-                warmup=args.warmup, ms_per_step=ms, higher_is_better=True, scaling="weak", vs_baseline=None,
+    line = dict(metric=METRIC, value=value, unit="pair-interval samples/s", n_gpus=world, steps=steps,
+                warmup=warmup, ms_per_step=ms, higher_is_better=True, scaling="weak", vs_baseline=None,
                 dtype="u32/f64", data="synthetic",
                 config=dict(workload=desc, traces=ts.n_traces, samples=ts.n_samples, policies=len(pols),
                             tile=list(tuned) if tuned else None, outputs="energy, EDP, time, counts, hash (no entries)"),
@@ -405,20 +479,20 @@ def run_other(args, world, rank, local) -> int:
                               traffic=None, kernel_ms=k_avg, main_kernel_ms=k_main / max(k_n, 1),
                               alg_bytes_per_launch=alg_bytes),
                 gpu_launches=k_kernels, clocks=clk)
-    if args.workload in ("closed", "closed_ladder"):
+    if kind in ("closed", "closed_ladder"):
         segs, second, final, logged = rp.closed_stats()
         line["config"]["closed_replay"] = dict(segments=segs, second_replays=second, final_pass_replays=final,
                                                log_pass_replays=logged)
     # many policies per byte read: the integer ALU pipe bounds these launches; report that
     # roofline (ncu lane-operations per (interval, policy), committed with the source hash,
-    # against 148 SMs x 64 integer lanes per cycle at the sampled SM clock)
+    # against the device's SMs x 64 integer lanes per cycle at the sampled SM clock)
     # (the closed loop: one thread per segment replays its rounds in order, integer ALU work;
     # its record holds for the benchmark's 4,096 traces, whose automatic segments fix the
     # share of burn-in rounds)
-    if args.workload in ("closed", "closed_ladder"):
-        key = "replay_closed_batched" if args.workload == "closed" else "replay_closed_ladder_batched"
+    if kind in ("closed", "closed_ladder"):
+        key = "replay_closed_batched" if kind == "closed" else "replay_closed_ladder_batched"
         rec = ncu_record(key) if ts.n_traces == N_TRACES else None
-    elif args.workload == "static":
+    elif kind == "static":
         # one pass over the traces: the HBM roofline stands; the record gives the DRAM bytes
         # of one launch on the benchmark's 4,096 traces
         rec = ncu_record("replay_static_batched") if ts.n_traces == N_TRACES else None
@@ -427,63 +501,43 @@ def run_other(args, world, rank, local) -> int:
             line["roofline"]["kernel"] = "replay_static_kernel"
         rec = None
     else:
-        rec = ncu_record(f"replay_tp_{args.workload}")
+        rec = ncu_record(f"replay_tp_{kind}")
+    sms = sm_count(dev)
+    line["config"]["sms"] = sms
     if rec and rec.get("alu_lane_ops_per_pair_interval") and clk.get("sm_mhz"):
         alu_ach = rec["alu_lane_ops_per_pair_interval"] * pair_steps / (k_avg * 1e-3)
-        alu_peak = 148 * 4 * 16 * clk["sm_mhz"] * 1e6
+        alu_peak = alu_peak_lane_ops(sms, clk["sm_mhz"])
         hbm = dict(line["roofline"])
         line["roofline"] = dict(bound="alu", achieved=alu_ach, peak=alu_peak, unit="lane-ops/s",
                                 frac=alu_ach / alu_peak, ops_per_pair_interval=rec["alu_lane_ops_per_pair_interval"],
-                                peak_source="derived: 148 SMs x 64 integer lanes per cycle x sampled SM clock",
+                                peak_source=f"derived: {sms} SMs (device query) x 64 integer lanes per cycle x "
+                                            "sampled SM clock",
                                 traffic=None, kernel_ms=k_avg, hbm=hbm)
-    if args.no_plain:
-        if rank == 0:
-            print(json.dumps(line), flush=True)
-        rp.close()
-        return 0
-    # one launch per trace (time-parallel kernel) on a sample of traces
-    k = min(256, ts.n_traces)
-    per_ms = 0.0
-    for i in range(k):
-        sub_len = ts.lengths[i:i + 1]
-        o = int(ts.offsets[i])
-        sub = d_tr[o:o + int((sub_len[0] + 31) // 32 * 32) + 32]
-        if i == 0:
-            rp.run(sub, sub_len, pols, stream=stream)
-        t0 = torch.cuda.Event(enable_timing=True); t1 = torch.cuda.Event(enable_timing=True)
-        t0.record(stream)
-        rp.run(sub, sub_len, pols, stream=stream)
-        t1.record(stream)
+    if plain and rank == 0:
+        line["one_launch_per_trace"] = per_trace_launches(rp, d_tr, ts, pols, stream)
+        # plain form (one launch per trace, literal FP64) on a small sample
+        if kind == "long":
+            kp, p_len = 1, np.array([200_000], dtype=np.uint64)     # a prefix of the first trace
+        else:
+            kp = 4 if kind != "single" else 1
+            p_len = ts.lengths[:kp]
+        sub = d_tr[:int(ts.offsets[kp - 1]) + int((ts.lengths[kp - 1] + 31) // 32 * 32)] if kp > 1 else d_tr
+        rp.plain(sub, p_len, pols, stream=stream)
         torch.cuda.synchronize()
-        per_ms += t0.elapsed_time(t1)
-    line["one_launch_per_trace"] = dict(value=float(ts.lengths[:k].sum()) * len(pols) / (per_ms * 1e-3),
-                                        unit="pair-interval samples/s", sample=f"first {k} traces, one launch each")
-    # plain form (one launch per trace, literal FP64) on a small sample
-    if args.workload == "long":
-        kp, p_len = 1, np.array([200_000], dtype=np.uint64)     # a prefix of the first trace
-    else:
-        kp = 4 if args.workload != "single" else 1
-        p_len = ts.lengths[:kp]
-    sub = d_tr[:int(ts.offsets[kp - 1]) + int((ts.lengths[kp - 1] + 31) // 32 * 32)] if kp > 1 else d_tr
-    rp.plain(sub, p_len, pols, stream=stream)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    rp.plain(sub, p_len, pols, stream=stream)
-    torch.cuda.synchronize()
-    line["plain_launch"] = dict(value=float(p_len.sum()) * len(pols) / (time.perf_counter() - t0),
-                                unit="pair-interval samples/s",
-                                sample=f"first {kp} traces" if args.workload != "long" else "first 200000 intervals of trace 0")
-    if rank == 0:
-        # CPU oracle on a bounded sample
-        kc = min(ts.n_traces, 8 if args.workload != "single" else 1)
         t0 = time.perf_counter()
-        _, used = oracle.replay_batch(ts.data, ts.offsets[:kc], ts.lengths[:kc], pols, model)
-        dt = time.perf_counter() - t0
-        line["cpu_baseline"] = dict(value=float(ts.lengths[:kc].sum()) * len(pols) / dt, unit="pair-interval samples/s",
-                                    cores=used, kind="oracle", sample=f"first {kc} traces x {len(pols)} policies")
-        print(json.dumps(line), flush=True)
+        rp.plain(sub, p_len, pols, stream=stream)
+        torch.cuda.synchronize()
+        line["plain_launch"] = dict(value=float(p_len.sum()) * len(pols) / (time.perf_counter() - t0),
+                                    unit="pair-interval samples/s",
+                                    sample=f"first {kp} traces" if kind != "long" else "first 200000 intervals of trace 0")
+    if cpu and rank == 0:
+        rate, used, sample = oracle_rate(ts, pols, model)
+        line["cpu_baseline"] = dict(value=rate, unit="pair-interval samples/s", cores=used, kind="oracle",
+                                    sample=sample)
     rp.close()
-    return 0
+    del d_tr
+    torch.cuda.empty_cache()
+    return line
 
 
 def main() -> int:
@@ -503,6 +557,9 @@ def main() -> int:
     ap.add_argument("--traces", type=int, default=N_TRACES, help="traces per GPU (profiling runs use fewer)")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-savings", action="store_true")
+    ap.add_argument("--no-sweep", action="store_true", help="leave the policy-sweep workload out of the default line")
+    ap.add_argument("--no-uneven", action="store_true", help="leave the uneven-length workload out of the default line")
+    ap.add_argument("--mw-steps", type=int, default=10, help="timed steps of the sweep / uneven workloads")
     ap.add_argument("--workload", default="batched",
                     choices=["batched", "sweep", "uneven", "single", "long", "ladder", "closed", "closed_ladder",
                              "static"],
@@ -580,12 +637,14 @@ def main() -> int:
     # (ncu, committed with the kernel-source hash) against 148 SMs x 4 partitions x 16 lanes
     # x the SM clock sampled during the timed region
     rec = ncu_record("replay_tp_batched") if not seg_path else None
+    sms = sm_count(dev)
     if rec and rec.get("alu_lane_ops_per_interval") and clk.get("sm_mhz"):
         alu_ach = rec["alu_lane_ops_per_interval"] * samples_per_step / (k_main_ms / max(k_n, 1) * 1e-3)
-        alu_peak = 148 * 4 * 16 * clk["sm_mhz"] * 1e6
+        alu_peak = alu_peak_lane_ops(sms, clk["sm_mhz"])
         roofline["alu"] = dict(achieved=alu_ach, peak=alu_peak, unit="lane-ops/s", frac=alu_ach / alu_peak,
                                ops_per_interval=rec["alu_lane_ops_per_interval"],
-                               peak_source="derived: 148 SMs x 64 integer lanes per cycle x sampled SM clock")
+                               peak_source=f"derived: {sms} SMs (device query) x 64 integer lanes per cycle x "
+                                           "sampled SM clock")
 
     line = dict(metric=METRIC, value=value, unit="samples/s", n_gpus=world, steps=args.steps,
                 warmup=args.warmup, ms_per_step=ms / args.steps, higher_is_better=True, scaling="weak",
@@ -611,6 +670,11 @@ def main() -> int:
         plain_rate = sub.n_samples / pdt
         line["plain_launch"] = dict(value=plain_rate, unit="samples/s", sample=f"{k} traces, {k} launches",
                                     speedup=value / world / plain_rate)
+        # the same entry point called once per trace (the time-parallel kernels, chosen
+        # automatically per call) on the first 256 traces
+        olt = per_trace_launches(rp, d_tr, ts, [policy], stream)
+        olt["speedup"] = value / world / olt["value"]
+        line["one_launch_per_trace"] = olt
 
     if rank == 0 and not args.no_e2e:
         # end to end through the public API with host buffers: pinned host traces in,
@@ -622,8 +686,10 @@ def main() -> int:
                 for k in ("energy_j", "edp_js", "time_s")}
         for k in ("n_changes", "change_hash", "n_hf"):
             hout[k] = torch.zeros(n_pairs, dtype=torch.int64).pin_memory().numpy().view(np.uint64)
+        # the full change log comes back too: the same work as the device-timed replay
+        hout["log"] = torch.zeros(n_pairs * LOG_CAP, dtype=torch.int32).pin_memory().numpy().view(np.uint32)
         rp.run_host(host_tr, ts.lengths, [policy], out=hout)
-        ksteps = max(1, min(args.steps, 5))
+        ksteps = max(10, min(args.steps, 20))
         t0 = time.perf_counter()
         for _ in range(ksteps):
             rp.run_host(host_tr, ts.lengths, [policy], out=hout)
@@ -640,9 +706,10 @@ def main() -> int:
         del dst
         h2d_gbs = ts.data.nbytes * ksteps / edt / 1e9
         line["e2e"] = dict(value=samples_per_step * ksteps / edt, unit="samples/s",
-                           h2d_bytes_per_step=int(ts.data.nbytes), d2h_bytes_per_step=48 * n_pairs,
-                           steps=ksteps, api="magus_replay_run_host",
+                           h2d_bytes_per_step=int(ts.data.nbytes), d2h_bytes_per_step=48 * n_pairs + 4 * LOG_CAP * n_pairs,
+                           steps=ksteps, api="magus_replay_run_host", log="full change log copied back",
                            h2d_gbs=h2d_gbs, link_gbs=link_gbs, link_frac=h2d_gbs / link_gbs)
+        del hout
         rp.kernel_time()
 
     if rank == 0 and not args.no_savings:
@@ -655,9 +722,24 @@ def main() -> int:
         rate, used, sample = cpu_oracle_sample(ts, policy, model)
         line["cpu_baseline"] = dict(value=rate, unit="samples/s", cores=used, kind="oracle", sample=sample)
 
+    rp.close()
+    del d_tr, outs
+    torch.cuda.empty_cache()
+    # the many-policy workloads (policy sweep, uneven lengths) at full size: each with its own
+    # timing, roofline, one launch per trace and CPU oracle
+    for kind, skip in (("sweep", args.no_sweep), ("uneven", args.no_uneven)):
+        if skip:
+            continue
+        sub = argparse.Namespace(**vars(args))
+        sub.traces = N_TRACES
+        w = measure_workload(kind, sub, world, rank, local, args.mw_steps, 3, plain=not args.no_plain,
+                             cpu=not args.no_cpu_baseline)
+        line[kind] = {k: w[k] for k in ("metric", "value", "unit", "steps", "warmup", "ms_per_step", "config",
+                                        "roofline", "gpu_launches", "clocks", "one_launch_per_trace",
+                                        "plain_launch", "cpu_baseline") if k in w}
+
     if rank == 0:
         print(json.dumps(line), flush=True)
-    rp.close()
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()

@@ -212,6 +212,17 @@ int magus_replay_set_tile(magus_replay_t *h, int32_t time_groups, int32_t policy
  * otherwise. */
 int magus_replay_set_segments(magus_replay_t *h, int32_t seg_rounds);
 
+/* Failure detection (bounded device-side waits).  Every wait of the tile kernel for a trace
+ * chunk's copy, and for a ring stage to be released, gives up after chunk_wait_ns
+ * nanoseconds (0, the default, restores 2 s): the kernel then records MAGUS_ETIMEDOUT,
+ * stops issuing copies, lets the copies already in flight land (that last wait always keeps
+ * the 2 s limit) and returns; magus_replay_status reports the timeout and clears it, and the
+ * handle stays usable.  The outputs of a call that timed out are unspecified.  A short limit
+ * detects a stalled copy engine sooner; a limit below the copy latency (about a
+ * microsecond) makes the waits run out on purpose, which is how the timeout path is tested.
+ * EINVAL for a NULL handle. */
+int magus_replay_set_wait(magus_replay_t *h, uint64_t chunk_wait_ns);
+
 /* Closed loop (step_mode 2 or 3, pin_level 0): replayed time-parallel.  Every
  * (trace, policy, segment of seg_rounds rounds) is replayed on its own from a guessed state
  * burn_rounds earlier; a segment whose guess did not reach the state its predecessor ended
@@ -255,16 +266,21 @@ int magus_replay_close(magus_replay_t *h);
  * counter, status word) lives in a fixed file-scope device array of
  * MAGUS_STATIC_SCRATCH_BYTES that every GPU loading the library holds until the process
  * exits.  It calls no cudaMalloc / cudaFree.
- *   - Arguments and outputs as magus_replay_run (traces, outputs, log, io_state: device).
+ *   - Arguments and outputs as magus_replay_run (traces, outputs, log, io_state: device),
+ *     but only for the policies the time-parallel tile kernel replays: step_mode 0 (open
+ *     loop, jump to a bound) with pin_level 0, 1 or n_levels.  Any other step_mode or pin
+ *     is refused with EINVAL (magus_replay_run takes them).
  *   - Workloads whose plan does not fit the scratch (about 100 B per policy, 16 B per
  *     trace and 8 B per trace for every block of up to 8 policy groups) are rejected with
  *     EINVAL and a message.
  *   - The first call on a device looks up the array's device address (set-up, once per
  *     device); make that first call before any stream capture on that device.
- *   - Every call shares the one array: the call uploads the plan on `stream`, zeroes the
- *     work counter and status word, runs the kernel and waits for `stream` before
- *     returning, so sequential calls are safe, but calls that overlap on the GPU (other
- *     threads or streams at the same time) race on the scratch and give wrong results.
+ *   - The call is synchronous: it uploads the plan on `stream` from pageable host memory,
+ *     zeroes the work counter and status word, runs the kernel, waits for `stream` and
+ *     reads the status word back before returning.
+ *   - Every call shares the one array, so sequential calls are safe, but calls that overlap
+ *     on the GPU (other threads or streams at the same time) race on the scratch and give
+ *     wrong results.
  *   - Returns device-side input errors (EINVAL for a carried level that is neither 0 nor
  *     K-1) directly. */
 int magus_replay_run_static(const magus_model_t *model, const uint32_t *traces, const uint64_t *lengths,
@@ -364,10 +380,12 @@ int magus_serve_export(magus_serve_t *s, magus_state_t *out_states);
  * call starts (host busy-wait), stream stream_id[i], size[i] deltas read from
  * payload + payload_off[i] (host); then drain and poll every request.  out_latency_s (host,
  * n_req, optional) receives each latency, -1 for requests refused by admission control;
- * out_wall_s the time from the first arrival to the end of the drain. */
+ * out_wall_s the time from the first arrival to the end of the drain; out_results (host,
+ * n_req, optional) each request's full result as magus_serve_poll returns it (all zero
+ * with latency_s = -1 for a refused request). */
 int magus_serve_load(magus_serve_t *s, const double *arrival_s, const uint32_t *stream_id,
                      const uint32_t *size, const uint32_t *payload, const uint64_t *payload_off,
-                     int64_t n_req, double *out_latency_s, double *out_wall_s);
+                     int64_t n_req, double *out_latency_s, double *out_wall_s, magus_result_t *out_results);
 
 int magus_serve_close(magus_serve_t *s);
 

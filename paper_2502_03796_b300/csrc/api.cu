@@ -369,6 +369,12 @@ int magus_replay_set_segments(magus_replay_t *h, int32_t seg_rounds) {
     return MAGUS_OK;
 }
 
+int magus_replay_set_wait(magus_replay_t *h, uint64_t chunk_wait_ns) {
+    if (!h) { set_error("NULL handle"); return MAGUS_EINVAL; }
+    h->chunk_wait_ns = chunk_wait_ns;
+    return MAGUS_OK;
+}
+
 int magus_replay_set_closed(magus_replay_t *h, int32_t seg_rounds, int32_t burn_rounds) {
     if (!h) { set_error("NULL handle"); return MAGUS_EINVAL; }
     if (seg_rounds < -1 || (seg_rounds > 0 && (seg_rounds % 64 != 0 || seg_rounds > (1 << 24)))) {

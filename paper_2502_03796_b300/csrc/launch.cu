@@ -364,6 +364,7 @@ int launch_plan(magus_replay *h, const Plan &pl, const uint32_t *traces, const O
     p.change_hash = o.change_hash;
     p.n_hf = o.n_hf;
     p.state = o.state;
+    p.chunk_wait_ns = h->chunk_wait_ns;
     int smem = 0;
     const int per_sm = tp_max_ctas_per_sm(pl.tg, pl.cw, pl.gp, &smem);
     if (per_sm <= 0) {
@@ -377,14 +378,16 @@ int launch_plan(magus_replay *h, const Plan &pl, const uint32_t *traces, const O
         CK(cudaEventCreate(&e1), "cudaEventCreate");
         CK(cudaEventRecord(e0, stream), "cudaEventRecord");
     }
-    CUtensorMap tmap;
+    CUtensorMap tmap, tmap_tail;
     memset(&tmap, 0, sizeof(tmap));
+    memset(&tmap_tail, 0, sizeof(tmap_tail));
     if (n_items) {
         uint64_t total_elems = 0;
         for (size_t i = 0; i < pl.lengths.size(); i++)
             total_elems += (pl.lengths[i] + kTraceAlign - 1) / kTraceAlign * kTraceAlign;
         std::string err;
         rc = make_trace_tmap(traces, total_elems, tp_box_rows(pl.tg), &tmap, &err);
+        if (!rc) rc = make_trace_tmap(traces, total_elems, kTailRows, &tmap_tail, &err);
         if (rc) { set_error(err); return rc; }
     }
     const bool has_lit = !pl.lit.empty() && !pl.lengths.empty();
@@ -403,7 +406,7 @@ int launch_plan(magus_replay *h, const Plan &pl, const uint32_t *traces, const O
         };
         CK(cudaEventRecord(h->k_ev[slot_k].a, stream), "cudaEventRecord");
         if (n_items) {
-            CK(launch_replay_tp(pl.tg, pl.cw, pl.gp, p, tmap, grid, stream), "replay kernel launch");
+            CK(launch_replay_tp(pl.tg, pl.cw, pl.gp, p, tmap, tmap_tail, grid, stream), "replay kernel launch");
             if ((rc = mark())) return rc;
         }
         if (has_lad) {

@@ -83,6 +83,9 @@ struct TpParams {
     uint64_t log_cap;
     uint64_t *n_changes, *change_hash, *n_hf;
     magus_state_t *state;
+    // limit of each per-chunk copy wait in ns (0: the default 2 s); the wait for the copies
+    // still in flight when a CTA stops always keeps the default
+    uint64_t chunk_wait_ns;
 };
 
 // Traces are read through a 2-D TMA tensor map over the packed buffer viewed as
@@ -94,8 +97,11 @@ int tp_box_rows(int time_groups);
 // Tile: time_groups warps split a chunk in time for each of policy_slots policy groups of
 // up to group_size members (time_groups * policy_slots = 8; group_size 1 or 4).
 bool tp_tile_supported(int time_groups, int policy_slots, int group_size);
+// tmap: boxes of tp_box_rows(time_groups) rows; tmap_tail: boxes of kTailRows rows, for the
+// last, partial chunk of each trace (the copy stops within kTailRows - 1 rows of its end).
+constexpr int kTailRows = 8;
 cudaError_t launch_replay_tp(int time_groups, int policy_slots, int group_size, const TpParams &p,
-                             const CUtensorMap &tmap, int grid, cudaStream_t stream);
+                             const CUtensorMap &tmap, const CUtensorMap &tmap_tail, int grid, cudaStream_t stream);
 int tp_max_ctas_per_sm(int time_groups, int policy_slots, int group_size, int *smem_bytes);
 
 // ---- segment-parallel replay (replay_seg.cu)

@@ -63,6 +63,13 @@ extern "C" int magus_replay_run_static(const magus_model_t *model, const uint32_
         if (configs[c].pin_level != 0 && configs[c].pin_level != 1 && configs[c].pin_level != model->n_levels)
             return fail("pin_level must be 0, 1 or n_levels", MAGUS_EINVAL);
     }
+    // every trace needs at least 24 bytes of plan (offset, length, one work item): refuse a
+    // trace count the scratch cannot hold before laying out the plan
+    if ((size_t)n_traces * (2 * sizeof(uint64_t) + sizeof(WorkItem)) > kStaticScratchBytes)
+        return fail("workload needs more than " + std::to_string(kStaticScratchBytes) +
+                        " bytes of planning scratch; the static scratch holds " + std::to_string(kStaticScratchBytes) +
+                        " (use magus_replay_run)",
+                    MAGUS_EINVAL);
     for (int i = 0; i < n_traces; i++) {
         if (lengths[i] >= (1ull << 40)) return fail("trace length too large", MAGUS_EINVAL);
         if (log && log->entries && lengths[i] >= (1ull << 27) - 1)
@@ -85,8 +92,9 @@ extern "C" int magus_replay_run_static(const magus_model_t *model, const uint32_
     const size_t off_grp = off_pol + align_up(pols.size() * sizeof(DevPolicy), 256);
     const size_t off_items = off_grp + align_up(groups.size() * sizeof(PolicyGroup), 256);
     const size_t off_off = off_items + align_up(std::max<size_t>(n_items, 1) * sizeof(WorkItem), 256);
-    const size_t off_len = off_off + align_up(std::max<int>(n_traces, 1) * 8, 256);
-    const size_t total = off_len + align_up(std::max<int>(n_traces, 1) * 8, 256);
+    const size_t per_trace = align_up((size_t)std::max(n_traces, 1) * sizeof(uint64_t), 256);
+    const size_t off_len = off_off + per_trace;
+    const size_t total = off_len + per_trace;
     if (total > kStaticScratchBytes)
         return fail("workload needs " + std::to_string(total) + " bytes of planning scratch; the static scratch holds " +
                         std::to_string(kStaticScratchBytes) + " (use magus_replay_run)",
@@ -165,10 +173,11 @@ extern "C" int magus_replay_run_static(const magus_model_t *model, const uint32_
         e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (e != cudaSuccess || per_sm <= 0) return fail("device query failed", MAGUS_ECUDA);
         const int grid = (int)std::max<size_t>(1, std::min<size_t>(n_items, (size_t)sms * per_sm));
-        CUtensorMap tmap;
+        CUtensorMap tmap, tmap_tail;
         rc = make_trace_tmap(traces, o, tp_box_rows(tg), &tmap, &err);
+        if (!rc) rc = make_trace_tmap(traces, o, kTailRows, &tmap_tail, &err);
         if (rc) return fail(err, rc);
-        e = launch_replay_tp(tg, cw, gp, p, tmap, grid, s);
+        e = launch_replay_tp(tg, cw, gp, p, tmap, tmap_tail, grid, s);
         if (e != cudaSuccess) return fail(std::string("replay kernel launch: ") + cudaGetErrorString(e), MAGUS_ECUDA);
     }
     // synchronous: the scratch is reused by the next call, and device-side input errors

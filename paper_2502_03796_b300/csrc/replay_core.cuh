@@ -349,6 +349,47 @@ __device__ __forceinline__ void emit_changes(uint32_t CHG, uint32_t Lv, uint64_t
     }
 }
 
+// Change-log staging (one warp, one pair).  A staged entry keeps the pair's log slot and
+// (interval index << 1 | at the top).  Entries wait in the warp's table until 32 are
+// pending; then lane i takes entry i, so the log stores and the hash run on full warps and
+// the stores leave as whole lines, where emitting each sub-block's few changes at once keeps
+// most lanes idle.  Usable while interval indices stay below 2^31.
+struct Staged {
+    uint32_t slot;   // index in the pair's log
+    uint32_t tw;     // (t + 1) << 1 | level is the top
+};
+constexpr int kStageCap = 64;   // up to 31 waiting + up to 32 of one sub-block
+
+// Append the changes of a warp's 32 rows (CHG / Lv as in emit_changes; `excl`: this lane's
+// changes before it, in the warp's order) behind the `pending` entries already waiting.
+__device__ __forceinline__ void stage_changes(uint32_t CHG, uint32_t Lv, uint32_t row0, uint32_t slot0,
+                                              Staged *tab, uint32_t pending, uint32_t excl, int lane) {
+    uint32_t bits = CHG;
+    uint32_t k = excl;
+    while (bits) {
+        const int q = __ffs(bits) - 1;
+        bits &= bits - 1;
+        const uint32_t when = row0 + 32u * (uint32_t)lane + (uint32_t)q + 1u;
+        Staged e;
+        e.slot = slot0 + k;
+        e.tw = (when << 1) | ((Lv >> q) & 1u);
+        tab[pending + k] = e;
+        k++;
+    }
+}
+
+// Store and hash the first `count` (<= 32) staged entries: lane i takes entry i.
+__device__ __forceinline__ void flush_staged(const Staged *tab, uint32_t count, uint32_t topK, uint32_t *log,
+                                             uint64_t log_cap, unsigned long long &hash, int lane) {
+    if ((uint32_t)lane < count) {
+        const Staged e = tab[lane];
+        const uint32_t when = e.tw >> 1;
+        const uint32_t lv = (e.tw & 1u) ? topK : 0u;
+        if (log && e.slot < log_cap) log[e.slot] = (when << 5) | lv;
+        hash += mix64(((uint64_t)when << 8) | lv);
+    }
+}
+
 // Sum of the row's deltas at the rounds selected by mask Msel (bit p = round p).
 __device__ __forceinline__ unsigned long long row_masked_sum(uint32_t base, int lane, uint32_t Msel, bool fast) {
     uint32_t v[32];
@@ -389,8 +430,18 @@ __device__ __forceinline__ void row_energy(uint32_t base, int lane, uint32_t Fle
     const bool fast = __all_sync(FULL, r.fast);
     const uint32_t M0 = ~Flev & r.S0 & vmask;
     if (__any_sync(FULL, M0 != 0)) acc.s0 += row_masked_sum(base, lane, M0, fast);
-    const uint32_t MM = Flev & r.SM & vmask;
-    if (__any_sync(FULL, MM != 0)) acc.sm += row_masked_sum(base, lane, MM, fast);
+    // stretched rounds at the top are rare (throughput above the top capacity): add them
+    // one by one instead of a pass over the whole row
+    uint32_t MM = Flev & r.SM & vmask;
+    if (__any_sync(FULL, MM != 0)) {
+        unsigned long long sm = 0;
+        while (MM) {
+            const int q = __ffs(MM) - 1;
+            MM &= MM - 1;
+            sm += lds32(swz_elem(base, 32 * lane + q));
+        }
+        acc.sm += sm;
+    }
 }
 
 // Rounds of a row whose level is not known yet (before the first event of a time segment):

@@ -53,6 +53,7 @@ struct magus_replay {
     size_t k_used = 0;
     int tile_tg = 0, tile_cw = 0;     // 0: automatic
     int seg_rounds = -1;              // -1: automatic; 0: tile kernel; > 0: segment kernel
+    uint64_t chunk_wait_ns = 0;       // tile kernel's per-chunk wait limit (0: default 2 s)
     void *segbuf = nullptr;           // segment summaries, tails, log scratch
     size_t seg_size = 0;
     void *stbuf = nullptr;            // static kernel: per-trace accumulators of split traces

@@ -68,6 +68,8 @@ struct Shared {
     MemberCarry carry[CW][GP][2];     // per member, double-buffered by chunk parity
     unsigned long long red_s0[TG * CW][GP], red_sm[TG * CW][GP], red_hash[TG * CW][GP];
     uint32_t red_n0[TG * CW][GP], red_nm[TG * CW][GP], red_hf[TG * CW][GP];
+    // per warp, one-member groups only: change-log entries waiting for a full warp's worth
+    core::Staged stage[GP == 1 ? TG * CW : 1][GP == 1 ? core::kStageCap : 1];
     int item;
     int abort;
 };
@@ -89,7 +91,8 @@ __host__ __device__ constexpr size_t smem_bytes() {
 
 template <int TG, int CW, int GP>
 __global__ void __launch_bounds__(TG * CW * 32) replay_tp_kernel(const TpParams p,
-                                                                   const __grid_constant__ CUtensorMap tmap) {
+                                                                   const __grid_constant__ CUtensorMap tmap,
+                                                                   const __grid_constant__ CUtensorMap tmap_tail) {
     constexpr int CH = TG * SB;              // rounds per chunk
     constexpr int CH_ROWS = TG * 32;         // 32-delta rows per chunk
     extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -115,6 +118,7 @@ __global__ void __launch_bounds__(TG * CW * 32) replay_tp_kernel(const TpParams 
     }
     __syncthreads();
 
+    const unsigned long long wlim = p.chunk_wait_ns ? p.chunk_wait_ns : tma::kWaitNs;   // per-chunk waits
     uint32_t seq = 0;         // chunks loaded by this CTA so far (selects stage and parity)
     int pend[2] = {-1, -1};   // thread 0: parity of an outstanding bulk copy per stage
 
@@ -177,9 +181,22 @@ __global__ void __launch_bounds__(TG * CW * 32) replay_tp_kernel(const TpParams 
 
         const uint32_t nchunks = (uint32_t)((n + CH - 1) / CH);
         const int row0 = (int)(p.offsets[wi.trace] / 32);   // first tensor row of the trace
+        const uint32_t rows = (uint32_t)((n + 31) / 32);    // rows holding the trace
         auto issue = [&](uint32_t c, uint32_t sq) {
-            mbar_expect_tx(&sh.bar[sq & 1], (uint32_t)CH_ROWS * 128u);
-            tma_rows(stage_base(sq & 1), &tmap, row0 + (int)c * CH_ROWS, &sh.bar[sq & 1]);
+            const uint32_t left_rows = rows - c * (uint32_t)CH_ROWS;
+            if (left_rows >= (uint32_t)CH_ROWS) {
+                mbar_expect_tx(&sh.bar[sq & 1], (uint32_t)CH_ROWS * 128u);
+                tma_rows(stage_base(sq & 1), &tmap, row0 + (int)c * CH_ROWS, &sh.bar[sq & 1]);
+            } else {
+                // the trace's last, partial chunk: boxes of kTailRows rows up to its end only
+                // (rows past it in the stage keep stale deltas; they lie past the trace's
+                // end, where every mask is zero)
+                const uint32_t nb = (left_rows + kTailRows - 1) / kTailRows;
+                mbar_expect_tx(&sh.bar[sq & 1], nb * (uint32_t)kTailRows * 128u);
+                for (uint32_t b = 0; b < nb; b++)
+                    tma_rows(stage_base(sq & 1) + b * (uint32_t)kTailRows * 128u, &tmap_tail,
+                             row0 + (int)c * CH_ROWS + (int)(b * kTailRows), &sh.bar[sq & 1]);
+            }
             pend[sq & 1] = (int)((sq >> 1) & 1);
         };
         if (tid == 0 && nchunks > 0) issue(0, seq);
@@ -187,6 +204,11 @@ __global__ void __launch_bounds__(TG * CW * 32) replay_tp_kernel(const TpParams 
         core::Acc acc[GP];
 #pragma unroll
         for (int m = 0; m < GP; m++) core::acc_zero(acc[m]);
+        // one-member groups stage their change-log entries while interval indices fit 31 bits
+        const bool can_stage = GP == 1 && n_seen0 + n < (1ull << 31);
+        core::Staged *tabw = sh.stage[GP == 1 ? warp : 0];
+        uint32_t pending = 0;
+        uint32_t *const log_pair = p.log_entries ? p.log_entries + (uint64_t)(pbase + G.member[0]) * p.log_cap : nullptr;
 
         for (uint32_t c = 0; c < nchunks; c++) {
             const uint32_t sq = seq + c;
@@ -199,7 +221,7 @@ __global__ void __launch_bounds__(TG * CW * 32) replay_tp_kernel(const TpParams 
                 // bounded wait that gives up marks the CTA aborted; later waits are skipped
                 // and the chunk loop runs to the end of the item, where the CTA stops.
                 if (!*(volatile int *)&sh.abort) {
-                    if (mbar_wait_bounded(&sh.bar[s], (sq >> 1) & 1)) {
+                    if (mbar_wait_bounded(&sh.bar[s], (sq >> 1) & 1, wlim)) {
                         if (tid == 0) pend[s] = -1;
                     } else {
                         atomicCAS(p.status, 0, MAGUS_ETIMEDOUT);
@@ -218,7 +240,7 @@ __global__ void __launch_bounds__(TG * CW * 32) replay_tp_kernel(const TpParams 
                     if (lane == 0 && c + 1 < nchunks && !*(volatile int *)&sh.abort) {
                         // stage s ^ 1 last held chunk sq - 1: wait until every warp released it
                         bool free = true;
-                        if (sq >= 1) free = mbar_wait_bounded(&sh.empty[s ^ 1], ((sq - 1) >> 1) & 1);
+                        if (sq >= 1) free = mbar_wait_bounded(&sh.empty[s ^ 1], ((sq - 1) >> 1) & 1, wlim);
                         if (free) {
                             issue(c + 1, sq + 1);
                         } else {
@@ -229,7 +251,7 @@ __global__ void __launch_bounds__(TG * CW * 32) replay_tp_kernel(const TpParams 
                 }
             } else {
                 if (tid == 0) {
-                    if (!mbar_wait_bounded(&sh.bar[s], (sq >> 1) & 1)) {
+                    if (!mbar_wait_bounded(&sh.bar[s], (sq >> 1) & 1, wlim)) {
                         atomicCAS(p.status, 0, MAGUS_ETIMEDOUT);
                         sh.abort = 1;
                     } else {
@@ -239,7 +261,7 @@ __global__ void __launch_bounds__(TG * CW * 32) replay_tp_kernel(const TpParams 
                 __syncthreads();
                 if (sh.abort) break;
                 // every thread observes the completed phase (acquire of the bulk-copy data)
-                if (tid != 0) (void)mbar_wait_bounded(&sh.bar[s], (sq >> 1) & 1);
+                if (tid != 0) (void)mbar_wait_bounded(&sh.bar[s], (sq >> 1) & 1, wlim);
                 if (c > 0 && warp == 0) {
                     // the previous chunk's last two rows become rows -2, -1 (same swizzle
                     // phase: CH_ROWS is a multiple of 8)
@@ -355,10 +377,39 @@ __global__ void __launch_bounds__(TG * CW * 32) replay_tp_kernel(const TpParams 
                 acc[m].hf += __popc(HF);
                 const int64_t pair = pbase + G.member[m];
                 // frequency-change log
-                if (__any_sync(FULL, CHG != 0))
-                    core::emit_changes(CHG, Lv, n_seen0 + (uint64_t)c * CH + (uint64_t)g * SB, topK,
-                                       p.log_entries ? p.log_entries + (uint64_t)pair * p.log_cap : nullptr,
-                                       p.log_cap, cr.count + before, acc[m].hash, lane);
+                if (__any_sync(FULL, CHG != 0)) {
+                    const uint64_t row0 = n_seen0 + (uint64_t)c * CH + (uint64_t)g * SB;
+                    bool staged = false;
+                    if (can_stage) {
+                        const uint32_t nch = __popc(CHG);
+                        uint32_t incl = nch;
+#pragma unroll
+                        for (int d = 1; d < 32; d <<= 1) {
+                            const uint32_t t = __shfl_up_sync(FULL, incl, d);
+                            if (lane >= d) incl += t;
+                        }
+                        const uint32_t total = __shfl_sync(FULL, incl, 31);
+                        if (total <= 32) {
+                            core::stage_changes(CHG, Lv, (uint32_t)row0, (uint32_t)(cr.count + before), tabw, pending,
+                                                incl - nch, lane);
+                            pending += total;
+                            if (pending >= 32) {
+                                __syncwarp();
+                                core::flush_staged(tabw, 32, topK, log_pair, p.log_cap, acc[m].hash, lane);
+                                __syncwarp();
+                                const uint32_t rem = pending - 32;
+                                if ((uint32_t)lane < rem) tabw[lane] = tabw[32 + lane];
+                                __syncwarp();
+                                pending = rem;
+                            }
+                            staged = true;
+                        }
+                    }
+                    if (!staged)
+                        core::emit_changes(CHG, Lv, row0, topK,
+                                           p.log_entries ? p.log_entries + (uint64_t)pair * p.log_cap : nullptr,
+                                           p.log_cap, cr.count + before, acc[m].hash, lane);
+                }
                 // carry into the next chunk
                 if (g == TG - 1 && lane == 0) {
                     uint32_t lv = wcin;
@@ -390,6 +441,12 @@ __global__ void __launch_bounds__(TG * CW * 32) replay_tp_kernel(const TpParams 
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&sh.empty[s]);
             }
+        }
+        // the change-log entries still waiting
+        if (pending) {
+            __syncwarp();
+            core::flush_staged(tabw, pending, topK, log_pair, p.log_cap, acc[0].hash, lane);
+            pending = 0;
         }
         if constexpr (CW == 1) __syncthreads();   // every warp sees the same abort flag
         if (sh.abort) break;
@@ -438,7 +495,8 @@ __global__ void __launch_bounds__(TG * CW * 32) replay_tp_kernel(const TpParams 
         }
         __syncthreads();
     }
-    // On abort, let outstanding bulk copies land before the CTA's shared memory goes away.
+    // On abort, let outstanding bulk copies land before the CTA's shared memory goes away
+    // (with the full default limit, whatever the per-chunk limit).
     if (tid == 0) {
         for (int s = 0; s < 2; s++)
             if (pend[s] >= 0) (void)mbar_wait_bounded(&sh.bar[s], (uint32_t)pend[s]);
@@ -446,12 +504,13 @@ __global__ void __launch_bounds__(TG * CW * 32) replay_tp_kernel(const TpParams 
 }
 
 template <int TG, int CW, int GP>
-cudaError_t launch_t(const TpParams &p, const CUtensorMap &tmap, int grid, cudaStream_t stream) {
+cudaError_t launch_t(const TpParams &p, const CUtensorMap &tmap, const CUtensorMap &tmap_tail, int grid,
+                     cudaStream_t stream) {
     const size_t smem = smem_bytes<TG, CW, GP>();
     cudaError_t e = cudaFuncSetAttribute(replay_tp_kernel<TG, CW, GP>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    replay_tp_kernel<TG, CW, GP><<<grid, TG * CW * 32, smem, stream>>>(p, tmap);
+    replay_tp_kernel<TG, CW, GP><<<grid, TG * CW * 32, smem, stream>>>(p, tmap, tmap_tail);
     return cudaGetLastError();
 }
 
@@ -482,9 +541,10 @@ bool tp_tile_supported(int tg, int cw, int gp) {
     return false;
 }
 
-cudaError_t launch_replay_tp(int tg, int cw, int gp, const TpParams &p, const CUtensorMap &tmap, int grid,
-                             cudaStream_t stream) {
-#define MAGUS_LAUNCH(a, b, c) if (tg == a && cw == b && gp == c) return launch_t<a, b, c>(p, tmap, grid, stream);
+cudaError_t launch_replay_tp(int tg, int cw, int gp, const TpParams &p, const CUtensorMap &tmap,
+                             const CUtensorMap &tmap_tail, int grid, cudaStream_t stream) {
+#define MAGUS_LAUNCH(a, b, c) \
+    if (tg == a && cw == b && gp == c) return launch_t<a, b, c>(p, tmap, tmap_tail, grid, stream);
     MAGUS_TILES(MAGUS_LAUNCH)
 #undef MAGUS_LAUNCH
     return cudaErrorInvalidValue;

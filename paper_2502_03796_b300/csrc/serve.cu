@@ -528,7 +528,7 @@ int magus_serve_export(magus_serve_t *s, magus_state_t *out_states) {
 
 int magus_serve_load(magus_serve_t *s, const double *arrival_s, const uint32_t *stream_id,
                      const uint32_t *size, const uint32_t *payload, const uint64_t *payload_off, int64_t n_req,
-                     double *out_latency_s, double *out_wall_s) {
+                     double *out_latency_s, double *out_wall_s, magus_result_t *out_results) {
     if (!s || !arrival_s || !stream_id || !size || !payload || !payload_off || n_req < 0)
         return serve_fail(nullptr, "NULL argument", MAGUS_EINVAL);
     std::vector<uint64_t> ids((size_t)n_req, 0);
@@ -550,9 +550,12 @@ int magus_serve_load(magus_serve_t *s, const double *arrival_s, const uint32_t *
     if (!rc) rc = d;
     for (int64_t i = 0; i < n_req; i++) {
         magus_result_t res;
+        memset(&res, 0, sizeof(res));
         double lat = -1.0;
         if (ids[i] && magus_serve_poll(s, ids[i], &res) == MAGUS_OK) lat = res.latency_s;
+        else res.latency_s = -1.0;
         if (out_latency_s) out_latency_s[i] = lat;
+        if (out_results) out_results[i] = res;
     }
     return rc;
 }

@@ -79,6 +79,7 @@ SIGNATURES = {
     "magus_replay_status": ([P, P], ctypes.c_int),
     "magus_replay_set_tile": ([P, _I32, _I32], ctypes.c_int),
     "magus_replay_set_segments": ([P, _I32], ctypes.c_int),
+    "magus_replay_set_wait": ([P, _U64], ctypes.c_int),
     "magus_replay_set_closed": ([P, _I32, _I32], ctypes.c_int),
     "magus_replay_closed_stats": ([P, P], ctypes.c_int),
     "magus_replay_kernel_time": ([P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
@@ -99,7 +100,7 @@ SIGNATURES = {
     "magus_serve_drain": ([P], ctypes.c_int),
     "magus_serve_stats": ([P, ctypes.POINTER(ServeStats)], ctypes.c_int),
     "magus_serve_export": ([P, P], ctypes.c_int),
-    "magus_serve_load": ([P, P, P, P, P, P, _I64, P, P], ctypes.c_int),
+    "magus_serve_load": ([P, P, P, P, P, P, _I64, P, P, P], ctypes.c_int),
     "magus_serve_close": ([P], ctypes.c_int),
 }
 
@@ -339,6 +340,10 @@ class Replay:
         """-1 automatic, 0 tile kernel, > 0 segment kernel with that many rounds per segment."""
         check(lib().magus_replay_set_segments(self.h, seg_rounds))
 
+    def set_wait(self, chunk_wait_ns: int = 0):
+        """Limit of the tile kernel's per-chunk copy waits in ns (0: the default 2 s)."""
+        check(lib().magus_replay_set_wait(self.h, chunk_wait_ns))
+
     def set_closed(self, seg_rounds: int = 0, burn_rounds: int = -1):
         """Closed loop in jump mode: 0 automatic segments, > 0 rounds per segment (multiple
         of 64), -1 the literal kernel; burn_rounds -1 automatic."""
@@ -418,7 +423,8 @@ class Serve:
         check(lib().magus_serve_export(self.h, out.ctypes.data))
         return out
 
-    def load(self, arrival_s, stream_id, size, payload, payload_off):
+    def load(self, arrival_s, stream_id, size, payload, payload_off, results: bool = False):
+        """magus_serve_load: (latencies, wall seconds[, per-request result dicts as arrays])."""
         a = np.ascontiguousarray(arrival_s, dtype=np.float64)
         sid = np.ascontiguousarray(stream_id, dtype=np.uint32)
         sz = np.ascontiguousarray(size, dtype=np.uint32)
@@ -426,9 +432,14 @@ class Serve:
         off = np.ascontiguousarray(payload_off, dtype=np.uint64)
         lat = np.zeros(len(a))
         wall = ctypes.c_double()
+        res = (Result * max(len(a), 1))() if results else None
         check(lib().magus_serve_load(self.h, a.ctypes.data, sid.ctypes.data, sz.ctypes.data, pay.ctypes.data,
-                                     off.ctypes.data, len(a), lat.ctypes.data, ctypes.byref(wall)))
-        return lat, wall.value
+                                     off.ctypes.data, len(a), lat.ctypes.data, ctypes.byref(wall),
+                                     ctypes.cast(res, P) if results else None))
+        if not results:
+            return lat, wall.value
+        arr = np.ctypeslib.as_array(res)[:len(a)]
+        return lat, wall.value, {k: np.array(arr[k]) for k, _ in Result._fields_ if k != "reserved"}
 
     def close(self):
         if getattr(self, "h", None):

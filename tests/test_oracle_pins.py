@@ -206,7 +206,7 @@ def test_ladder_step_mode(model):
 
 
 # ----------------------------------------------------------------------------- brute force
-def naive_exact(deltas, W, L, inc, dec, th, model, pin=0, closed=False, ladder=False):
+def naive_exact(deltas, W, L, inc, dec, th, model, pin=0, closed=False, ladder=False, top=None):
     """Second, naive restatement in exact rationals: the window is rebuilt from the raw
     trace every round, the comparisons are exact.  pin > 0: a static baseline that holds
     ladder index pin - 1 and runs no control (Sec. 5.3, Sec. 6.3).  closed: the monitor
@@ -219,6 +219,7 @@ def naive_exact(deltas, W, L, inc, dec, th, model, pin=0, closed=False, ladder=F
     inc, dec, th = Fraction(inc), Fraction(dec), Fraction(th)
     level, preds, levels, log = (pin - 1 if pin else 0), [], [], []
     n_hf = 0
+    top = len(model["f_ghz"]) - 1 if top is None else top
     for t in range(len(deltas)):
         levels.append(level)
         obs.append(min(xs[t], cap[level]) if closed else xs[t])
@@ -231,8 +232,8 @@ def naive_exact(deltas, W, L, inc, dec, th, model, pin=0, closed=False, ladder=F
         window = [1 if p != 0 else 0 for p in preds[max(0, t - L + 1):t + 1]]
         hf = Fraction(sum(window), L) >= th and not pin
         n_hf += hf
-        up, dn = (min(level + 1, TOP), max(level - 1, 0)) if ladder else (TOP, 0)
-        nxt = level if pin else (TOP if hf else (up if pred == 1 else (dn if pred == -1 else level)))
+        up, dn = (min(level + 1, top), max(level - 1, 0)) if ladder else (top, 0)
+        nxt = level if pin else (top if hf else (up if pred == 1 else (dn if pred == -1 else level)))
         if nxt != level:
             log.append((t + 1, nxt))
         level = nxt
@@ -260,6 +261,40 @@ def test_brute_force_tiny_traces(model):
                     assert close(r["energy_j"], E) and close(r["time_s"], T)
                 cases += 1
     assert cases > 20000
+
+
+def test_brute_force_ladder_open_loop(model):
+    """One rung per decision in the open loop (step_mode 1) on every short trace, on the
+    default 17-rung ladder and on a 3-rung ladder where runs of +1 / -1 reach both ends (the
+    clamp at the top and at the bottom), against the exact-rational restatement."""
+    alphabet = [0, 10_000_000, 30_000_000, 100_000_000]
+    small = dict(model, f_ghz=[0.8, 1.6, 2.4], f_ref_ghz=2.4)
+    cases = 0
+    for mdl, max_n in ((model, 5), (small, 6)):
+        for n in range(1, max_n + 1):
+            for tr in itertools.product(alphabet, repeat=n):
+                d = np.array(tr, dtype=np.uint32)
+                for W, L, th in [(1, 2, 0.5), (2, 3, 0.6), (1, 4, 1.0), (3, 4, 0.75)]:
+                    pol = dict(inc_threshold=5.0, dec_threshold=-3.3, direv_length=W, tune_window=L,
+                               high_freq_threshold=th, step_mode=1)
+                    r = oracle.replay(d, pol, mdl, detail=True)
+                    levels, log, n_hf = naive_exact(tr, W, L, 5.0, -3.3, th, mdl, ladder=True)
+                    assert r["level_log"].tolist() == levels
+                    assert list(zip(r["log_t"].tolist(), r["log_level"].tolist())) == log
+                    assert r["n_hf"] == n_hf
+                    if n <= 3:
+                        E, T = exact_energy(tr, levels, mdl)
+                        assert close(r["energy_j"], E) and close(r["time_s"], T)
+                    cases += 1
+    assert cases > 20000
+    # a rising ramp climbs one rung per round and stays at the top of the small ladder (a +1
+    # there changes nothing); the oracle agrees with the hand-derived sequence
+    ramp = [0, 100_000_000, 200_000_000, 300_000_000, 400_000_000]
+    lv, lg, _ = naive_exact(ramp, 1, 2, 5.0, -3.3, 2.0, small, ladder=True)
+    assert lv == [0, 0, 1, 2, 2] and lg == [(2, 1), (3, 2)]
+    r = oracle.replay(np.array(ramp, dtype=np.uint32), dict(inc_threshold=5.0, dec_threshold=-3.3, direv_length=1,
+                      tune_window=2, high_freq_threshold=2.0, step_mode=1), small, detail=True)
+    assert r["level_log"].tolist() == lv and r["log_t"].tolist() == [2, 3] and r["log_level"].tolist() == [1, 2]
 
 
 def test_brute_force_inverted_thresholds(model):

@@ -715,3 +715,37 @@ def test_static_baselines_every_rung_every_mode(rp, mg):
         for p, r in ref.items():
             assert_pair(out, p, r, cap=50, tag=f"mix of {len(mix)}")
         assert runs == 1 and kernels == n_k
+
+
+def test_chunk_wait_timeout_reports_etimedout(mg):
+    """Failure detection without a fault: a per-chunk wait limit below the copy latency
+    makes the tile kernel's bounded waits run out.  The kernel records MAGUS_ETIMEDOUT, lets
+    the copies in flight land and returns; the status is reported once, and the next call
+    on the same handle with the default limit is exact against the oracle."""
+    model = tracegen.default_model()
+    ts = tracegen.batched(64, 40_000, seed=9)
+    d = to_device(ts)
+    pols = [tracegen.default_policy()]
+    h = mg.Replay(model)
+    try:
+        h.set_segments(0)
+        h.set_tile(8, 1)
+        h.set_wait(1)
+        seen = False
+        for _ in range(3):
+            h.run(d, ts.lengths, pols, log_capacity=64)
+            st = h.status()
+            assert st in (0, mg.ETIMEDOUT), st
+            if st == mg.ETIMEDOUT:
+                seen = True
+                break
+        assert seen, "a 1 ns chunk-wait limit never ran out"
+        assert h.status() == 0
+        h.set_wait(0)
+        cap = 4000
+        out = to_numpy(h.run(d, ts.lengths, pols, log_capacity=cap))
+        assert h.status() == 0
+        for p, ref in oracle_pairs(ts, pols, model, pairs=range(0, 64, 7)).items():
+            assert_pair(out, p, ref, cap=cap, tag="after a timed-out call")
+    finally:
+        h.close()

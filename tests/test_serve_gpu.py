@@ -73,7 +73,7 @@ def test_requests_match_oracle_and_mix(mg):
     assert st["completed"] == len(order) and st["launches"] > 1
     states = sv.export().view(np.uint64)
     sv.close()
-    for s in (0, 1, 17, 299):
+    for s in range(n_streams):
         refs = oracle_split(ts.trace(s), plans[s], pol, model)
         for k, ref in enumerate(refs):
             r = mix[(s, k)]
@@ -147,3 +147,39 @@ def test_load_driver_smoke(mg):
     sv.close()
     assert st["completed"] == 2000 and np.all(lat > 0)
     assert wall >= rq.arrival_s[-1]
+
+
+def test_load_20k_streams_sampled_against_oracle(mg):
+    """The serving load driver over 20,000 streams: Poisson arrivals at 200k requests/s,
+    request sizes log-uniform in 1..4096, continuous batching.  For a sample of 300 streams,
+    every request's result (counts, hash, high-frequency rounds, energy, time, intervals
+    seen, level) equals the oracle replaying that stream's requests in submission order with
+    carried state."""
+    model, pol = tracegen.default_model(), tracegen.default_policy()
+    n_streams = 20_000
+    rq = tracegen.requests(60_000, rate_per_s=200_000.0, n_streams=n_streams, seed=5)
+    pool = tracegen.batched(16, 100_000, seed=2).data
+    rng = np.random.default_rng(1)
+    off = rng.integers(0, len(pool) - 4096, size=len(rq.size)).astype(np.uint64)
+    sv = mg.Serve(model, pol, n_streams, mem_budget=8 << 30)
+    lat, wall, res = sv.load(rq.arrival_s, rq.stream_id, rq.size, pool, off, results=True)
+    st = sv.stats()
+    sv.close()
+    assert st["rejected"] == 0 and st["completed"] == len(rq.size) and st["launches"] > 1
+    assert np.all(lat > 0)
+    active = np.unique(rq.stream_id)
+    sample = rng.choice(active, size=300, replace=False)
+    for s in sample:
+        idx = np.nonzero(rq.stream_id == s)[0]
+        ost = oracle.new_state()
+        seen = 0
+        for i in idx:
+            a, n = int(off[i]), int(rq.size[i])
+            ref = oracle.replay(pool[a:a + n], pol, model, state=ost)
+            seen += n
+            r = {k: res[k][i] for k in ("n_changes", "change_hash", "n_hf", "energy_j", "time_s")}
+            r = dict(n_changes=int(r["n_changes"]), change_hash=int(r["change_hash"]), n_hf=int(r["n_hf"]),
+                     energy_j=float(r["energy_j"]), time_s=float(r["time_s"]))
+            same(r, ref)
+            assert int(res["n_seen"][i]) == seen
+            assert int(res["level"][i]) == ost.level
