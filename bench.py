@@ -630,7 +630,8 @@ def main() -> int:
                     frac=achieved / peaks["hbm_gbs"], traffic=traffic,
                     peak_source=f"{peaks['source']} (MEASURED_PEAKS.json hbm_gbs)" if peaks["source"] == "measured"
                     else "fallback 6.4 TB/s",
-                    kernel=("replay_seg_kernel<1> + combine_kernel" if seg_path else "replay_tp_kernel<8,1>"),
+                    kernel=("replay_seg_kernel<1> + combine_kernel" if seg_path else
+                            "replay_tp_kernel<4,1,1> (the automatic tile for one policy group)"),
                     kernel_ms=k_avg_ms, main_kernel_ms=k_main_ms / max(k_n, 1),
                     alg_bytes_per_launch=alg_bytes, frac_of_nominal_8tbs=achieved / 8000.0)
     # the pipe that actually bounds the kernel: integer ALU lane-operations per interval

@@ -350,8 +350,9 @@ int magus_replay_set_tile(magus_replay_t *h, int32_t tg, int32_t cw) {
         h->tile_tg = h->tile_cw = 0;
         return MAGUS_OK;
     }
-    if (!((tg == 8 && cw == 1) || (tg == 4 && cw == 2) || (tg == 2 && cw == 4) || (tg == 1 && cw == 8))) {
-        set_error("supported tiles: (8,1) (4,2) (2,4) (1,8)");
+    if (!((tg == 8 && cw == 1) || (tg == 4 && cw == 2) || (tg == 2 && cw == 4) || (tg == 1 && cw == 8) ||
+          (tg == 4 && cw == 1))) {
+        set_error("supported tiles: (8,1) (4,2) (2,4) (1,8) (4,1)");
         return MAGUS_EINVAL;
     }
     h->tile_tg = tg;
@@ -483,7 +484,7 @@ int magus_replay_autotune(magus_replay_t *h, const uint32_t *traces, const uint6
         memset(&o, 0, sizeof(o));
         o.energy = (double *)h->scratch;
         o.edp = o.energy + pairs;
-        static const int shapes[14][4] = {{8, 1, 1, 0}, {4, 2, 1, 0}, {2, 4, 1, 0}, {1, 8, 1, 0},
+        static const int shapes[15][4] = {{8, 1, 1, 0}, {4, 1, 1, 0}, {4, 2, 1, 0}, {2, 4, 1, 0}, {1, 8, 1, 0},
                                           {8, 1, 4, 0}, {4, 2, 4, 0}, {2, 4, 4, 0}, {1, 8, 4, 0},
                                           {8, 1, 1, 8192}, {8, 1, 1, 16384}, {8, 1, 1, 32768},
                                           {8, 1, 4, 8192}, {8, 1, 4, 16384}, {8, 1, 4, 32768}};

@@ -84,7 +84,7 @@ extern "C" int magus_replay_run_static(const magus_model_t *model, const uint32_
     const int n_groups = (int)groups.size();
     int cw = 1;
     while (cw * 2 <= std::min(8, n_groups)) cw *= 2;
-    const int tg = 8 / cw;
+    const int tg = (cw == 1 && gp == 1) ? 4 : 8 / cw;   // the tile magus_replay_run picks
     const size_t blocks = (size_t)(n_groups + cw - 1) / cw;
     const size_t n_items = (size_t)n_traces * blocks;
     // scratch layout: [status, counter | policies | groups | items | offsets | lengths]

@@ -390,20 +390,43 @@ __device__ __forceinline__ void flush_staged(const Staged *tab, uint32_t count, 
     }
 }
 
+// part + v if bit K of M is set: the bit test sets a predicate and the add is predicated
+// (two instructions; the select form costs more).
+template <int K>
+__device__ __forceinline__ uint32_t add_if_bit(uint32_t part, uint32_t M, uint32_t v) {
+    asm("{\n\t.reg .pred p;\n\t.reg .b32 t;\n\t"
+        "and.b32 t, %1, %3;\n\t"
+        "setp.ne.b32 p, t, 0;\n\t"
+        "@p add.u32 %0, %0, %2;\n\t}"
+        : "+r"(part)
+        : "r"(M), "r"(v), "n"(1u << K));
+    return part;
+}
+template <int C>
+__device__ __forceinline__ unsigned long long add_masked4(unsigned long long s, uint32_t M, const uint32_t (&v)[32]) {
+    uint32_t part = 0;   // four deltas below 2^30 fit 32 bits
+    part = add_if_bit<4 * C + 0>(part, M, v[4 * C + 0]);
+    part = add_if_bit<4 * C + 1>(part, M, v[4 * C + 1]);
+    part = add_if_bit<4 * C + 2>(part, M, v[4 * C + 2]);
+    part = add_if_bit<4 * C + 3>(part, M, v[4 * C + 3]);
+    return s + part;
+}
+
 // Sum of the row's deltas at the rounds selected by mask Msel (bit p = round p).
 __device__ __forceinline__ unsigned long long row_masked_sum(uint32_t base, int lane, uint32_t Msel, bool fast) {
     uint32_t v[32];
     load_row(base, lane, v);
     unsigned long long s = 0;
     if (fast) {
-        // every delta < 2^30: four of them fit a 32-bit partial sum
-#pragma unroll
-        for (int c = 0; c < 8; c++) {
-            uint32_t part = 0;
-#pragma unroll
-            for (int e = 0; e < 4; e++) part += ((Msel >> (4 * c + e)) & 1u) ? v[4 * c + e] : 0u;
-            s += part;
-        }
+        // every delta < 2^30
+        s = add_masked4<0>(s, Msel, v);
+        s = add_masked4<1>(s, Msel, v);
+        s = add_masked4<2>(s, Msel, v);
+        s = add_masked4<3>(s, Msel, v);
+        s = add_masked4<4>(s, Msel, v);
+        s = add_masked4<5>(s, Msel, v);
+        s = add_masked4<6>(s, Msel, v);
+        s = add_masked4<7>(s, Msel, v);
     } else {
 #pragma unroll
         for (int k = 0; k < 32; k++) s += ((Msel >> k) & 1u) ? v[k] : 0u;
@@ -423,6 +446,10 @@ __device__ __forceinline__ void acc_zero(Acc &a) {
 }
 
 // Energy bookkeeping of a row once its levels Flev (bit p = level during round p) are known.
+// kSparseTop: stretched rounds at the top (throughput above the top capacity, rare) are
+// added one by one instead of a pass over the whole row; kernels that replay several group
+// members per row keep the straight-line pass (the loop raises their register demand).
+template <bool kSparseTop = true>
 __device__ __forceinline__ void row_energy(uint32_t base, int lane, uint32_t Flev, const RowPred &r,
                                            uint32_t vmask, Acc &acc) {
     acc.n0 += __popc(~Flev & ~r.S0 & vmask);
@@ -430,10 +457,10 @@ __device__ __forceinline__ void row_energy(uint32_t base, int lane, uint32_t Fle
     const bool fast = __all_sync(FULL, r.fast);
     const uint32_t M0 = ~Flev & r.S0 & vmask;
     if (__any_sync(FULL, M0 != 0)) acc.s0 += row_masked_sum(base, lane, M0, fast);
-    // stretched rounds at the top are rare (throughput above the top capacity): add them
-    // one by one instead of a pass over the whole row
     uint32_t MM = Flev & r.SM & vmask;
-    if (__any_sync(FULL, MM != 0)) {
+    if (!kSparseTop) {
+        if (__any_sync(FULL, MM != 0)) acc.sm += row_masked_sum(base, lane, MM, fast);
+    } else if (__any_sync(FULL, MM != 0)) {
         unsigned long long sm = 0;
         while (MM) {
             const int q = __ffs(MM) - 1;

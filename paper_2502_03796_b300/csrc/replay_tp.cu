@@ -37,7 +37,6 @@ namespace magus {
 namespace {
 
 using tma::mbar_init;
-using tma::mbar_arrive;
 using tma::fence_mbar_init;
 using tma::mbar_expect_tx;
 using tma::mbar_wait_bounded;
@@ -61,7 +60,8 @@ struct MemberCarry {
 template <int TG, int CW, int GP>
 struct Shared {
     uint64_t bar[2];                  // stage s holds its chunk (copy complete)
-    uint64_t empty[2];                // stage s is free again (every warp done with it; one slot)
+    uint32_t rel[2];                  // one slot: warps done with stage s's chunk
+    int issued[2];                    // one slot: sequence number of the last copy into stage s, -1 none
     uint64_t xf[CW][TG];              // flags of the last 64 rounds of each sub-block
     uint64_t hist[CW][2];             // flags of the 64 rounds before the chunk (by parity)
     uint32_t xs[CW][GP][TG];          // sub-block summary: has | exit<<1 | first<<2 | nch<<3
@@ -89,8 +89,14 @@ __host__ __device__ constexpr size_t smem_bytes() {
     return 1024 /* alignment slack */ + stage_offset<TG, CW, GP>() + 2 * stage_bytes<TG>();
 }
 
+// Register budgets per tile: 80 for the 8-warp one-slot tile of one-member groups (three
+// CTAs of 256 threads per SM), 88 for the 4-warp one (five CTAs of 128 threads), 96 for the
+// other one-member tiles and 128 for grouped tiles (two CTAs per SM).  The kernel's
+// allocation is sensitive: left alone the compiler has taken from 74 to 224 registers for
+// these shapes as the source changed.
 template <int TG, int CW, int GP>
-__global__ void __launch_bounds__(TG * CW * 32) replay_tp_kernel(const TpParams p,
+__global__ void __launch_bounds__(TG * CW * 32)
+    __maxnreg__(GP == 1 ? (CW == 1 ? (TG == 8 ? 80 : 88) : 96) : 128) replay_tp_kernel(const TpParams p,
                                                                    const __grid_constant__ CUtensorMap tmap,
                                                                    const __grid_constant__ CUtensorMap tmap_tail) {
     constexpr int CH = TG * SB;              // rounds per chunk
@@ -111,14 +117,16 @@ __global__ void __launch_bounds__(TG * CW * 32) replay_tp_kernel(const TpParams 
     if (tid == 0) {
         mbar_init(&sh.bar[0], 1);
         mbar_init(&sh.bar[1], 1);
-        mbar_init(&sh.empty[0], TG);
-        mbar_init(&sh.empty[1], TG);
         fence_mbar_init();
         sh.abort = 0;
+        sh.rel[0] = sh.rel[1] = 0;
+        sh.issued[0] = sh.issued[1] = -1;
     }
     __syncthreads();
 
-    const unsigned long long wlim = p.chunk_wait_ns ? p.chunk_wait_ns : tma::kWaitNs;   // per-chunk waits
+    // per-chunk wait limit (one-slot tiles; the others keep the default, which also keeps
+    // their register allocation where it was measured)
+    const unsigned long long wlim = (CW == 1 && p.chunk_wait_ns) ? p.chunk_wait_ns : tma::kWaitNs;
     uint32_t seq = 0;         // chunks loaded by this CTA so far (selects stage and parity)
     int pend[2] = {-1, -1};   // thread 0: parity of an outstanding bulk copy per stage
 
@@ -184,31 +192,42 @@ __global__ void __launch_bounds__(TG * CW * 32) replay_tp_kernel(const TpParams 
         const uint32_t rows = (uint32_t)((n + 31) / 32);    // rows holding the trace
         auto issue = [&](uint32_t c, uint32_t sq) {
             const uint32_t left_rows = rows - c * (uint32_t)CH_ROWS;
-            if (left_rows >= (uint32_t)CH_ROWS) {
-                mbar_expect_tx(&sh.bar[sq & 1], (uint32_t)CH_ROWS * 128u);
+            // one slot: the 8 rows before a later chunk (its 64-delta halo in rows -2, -1)
+            // come with the copy, so a stage can be refilled before the chunk ahead of it
+            // has been read (same swizzle phase: CH_ROWS is a multiple of 8)
+            const uint32_t halo = (CW == 1 && c > 0) ? (uint32_t)kTailRows * 128u : 0u;
+            if (GP > 1 || left_rows >= (uint32_t)CH_ROWS) {
+                mbar_expect_tx(&sh.bar[sq & 1], (uint32_t)CH_ROWS * 128u + halo);
                 tma_rows(stage_base(sq & 1), &tmap, row0 + (int)c * CH_ROWS, &sh.bar[sq & 1]);
             } else {
                 // the trace's last, partial chunk: boxes of kTailRows rows up to its end only
                 // (rows past it in the stage keep stale deltas; they lie past the trace's
-                // end, where every mask is zero)
+                // end, where every mask is zero).  One-member tiles only: the grouped tiles
+                // are bound by arithmetic, not by the bytes they read, and the extra branch
+                // doubles their register demand.
                 const uint32_t nb = (left_rows + kTailRows - 1) / kTailRows;
-                mbar_expect_tx(&sh.bar[sq & 1], nb * (uint32_t)kTailRows * 128u);
+                mbar_expect_tx(&sh.bar[sq & 1], nb * (uint32_t)kTailRows * 128u + halo);
                 for (uint32_t b = 0; b < nb; b++)
                     tma_rows(stage_base(sq & 1) + b * (uint32_t)kTailRows * 128u, &tmap_tail,
                              row0 + (int)c * CH_ROWS + (int)(b * kTailRows), &sh.bar[sq & 1]);
             }
-            pend[sq & 1] = (int)((sq >> 1) & 1);
+            if (halo)   // after the expect-tx above, which counts its bytes
+                tma_rows(stage_base(sq & 1) - halo, &tmap_tail, row0 + (int)c * CH_ROWS - kTailRows, &sh.bar[sq & 1]);
+            if (CW == 1) sh.issued[sq & 1] = (int)sq;
+            else pend[sq & 1] = (int)((sq >> 1) & 1);
         };
         if (tid == 0 && nchunks > 0) issue(0, seq);
+        // one slot: the second stage is free as well (every warp finished the last item)
+        if (CW == 1 && tid == 0 && nchunks > 1) issue(1, seq + 1);
 
         core::Acc acc[GP];
 #pragma unroll
         for (int m = 0; m < GP; m++) core::acc_zero(acc[m]);
-        // one-member groups stage their change-log entries while interval indices fit 31 bits
+        // one-member groups stage their change-log entries while interval indices fit 31
+        // bits (grouped tiles write them directly: staging per member raised their register
+        // demand past two CTAs per SM, which cost more than it saved)
         const bool can_stage = GP == 1 && n_seen0 + n < (1ull << 31);
-        core::Staged *tabw = sh.stage[GP == 1 ? warp : 0];
-        uint32_t pending = 0;
-        uint32_t *const log_pair = p.log_entries ? p.log_entries + (uint64_t)(pbase + G.member[0]) * p.log_cap : nullptr;
+        uint32_t pending = 0;   // entries waiting in this warp's table
 
         for (uint32_t c = 0; c < nchunks; c++) {
             const uint32_t sq = seq + c;
@@ -216,37 +235,15 @@ __global__ void __launch_bounds__(TG * CW * 32) replay_tp_kernel(const TpParams 
             const uint32_t sbase = stage_base(s);
             if constexpr (CW == 1) {
                 // One policy slot: no CTA barrier per chunk.  Every warp waits for its stage
-                // itself; a stage is refilled once all TG warps have released it (empty
-                // barrier), so a warp that finishes a chunk early starts the next one.  A
-                // bounded wait that gives up marks the CTA aborted; later waits are skipped
-                // and the chunk loop runs to the end of the item, where the CTA stops.
+                // itself; the last warp to finish a chunk refills its stage with the chunk
+                // two ahead (see the end of the loop), so copies run up to two chunks ahead
+                // and a warp that finishes a chunk early starts the next one.  A bounded wait
+                // that gives up marks the CTA aborted; later waits are skipped and the chunk
+                // loop runs to the end of the item, where the CTA stops.
                 if (!*(volatile int *)&sh.abort) {
-                    if (mbar_wait_bounded(&sh.bar[s], (sq >> 1) & 1, wlim)) {
-                        if (tid == 0) pend[s] = -1;
-                    } else {
+                    if (!mbar_wait_bounded(&sh.bar[s], (sq >> 1) & 1, wlim)) {
                         atomicCAS(p.status, 0, MAGUS_ETIMEDOUT);
                         sh.abort = 1;
-                    }
-                }
-                if (warp == 0) {
-                    if (c > 0) {
-                        // the previous chunk's last two rows become rows -2, -1 (same swizzle
-                        // phase: CH_ROWS is a multiple of 8); only warp 0 reads them
-                        const uint32_t prev = stage_base(s ^ 1) + (uint32_t)(CH_ROWS - 2) * 128u;
-                        for (int k = lane; k < HALO; k += 32)
-                            core::sts32(sbase - 256u + 4u * k, core::lds32(prev + 4u * k));
-                    }
-                    __syncwarp();
-                    if (lane == 0 && c + 1 < nchunks && !*(volatile int *)&sh.abort) {
-                        // stage s ^ 1 last held chunk sq - 1: wait until every warp released it
-                        bool free = true;
-                        if (sq >= 1) free = mbar_wait_bounded(&sh.empty[s ^ 1], ((sq - 1) >> 1) & 1, wlim);
-                        if (free) {
-                            issue(c + 1, sq + 1);
-                        } else {
-                            atomicCAS(p.status, 0, MAGUS_ETIMEDOUT);
-                            sh.abort = 1;
-                        }
                     }
                 }
             } else {
@@ -373,10 +370,11 @@ __global__ void __launch_bounds__(TG * CW * 32) replay_tp_kernel(const TpParams 
                 const uint32_t Flev = (Lv << 1) | cin;            // level during each round
                 const uint32_t CHG = (Lv ^ Flev) & vmask;
 
-                core::row_energy(sub, lane, Flev, rp, vmask, acc[m]);
+                core::row_energy<GP == 1>(sub, lane, Flev, rp, vmask, acc[m]);
                 acc[m].hf += __popc(HF);
                 const int64_t pair = pbase + G.member[m];
                 // frequency-change log
+                uint32_t *const log_pair = p.log_entries ? p.log_entries + (uint64_t)pair * p.log_cap : nullptr;
                 if (__any_sync(FULL, CHG != 0)) {
                     const uint64_t row0 = n_seen0 + (uint64_t)c * CH + (uint64_t)g * SB;
                     bool staged = false;
@@ -390,25 +388,24 @@ __global__ void __launch_bounds__(TG * CW * 32) replay_tp_kernel(const TpParams 
                         }
                         const uint32_t total = __shfl_sync(FULL, incl, 31);
                         if (total <= 32) {
-                            core::stage_changes(CHG, Lv, (uint32_t)row0, (uint32_t)(cr.count + before), tabw, pending,
+                            core::Staged *tab = sh.stage[GP == 1 ? warp : 0];
+                            core::stage_changes(CHG, Lv, (uint32_t)row0, (uint32_t)(cr.count + before), tab, pending,
                                                 incl - nch, lane);
                             pending += total;
                             if (pending >= 32) {
                                 __syncwarp();
-                                core::flush_staged(tabw, 32, topK, log_pair, p.log_cap, acc[m].hash, lane);
+                                core::flush_staged(tab, 32, topK, log_pair, p.log_cap, acc[m].hash, lane);
                                 __syncwarp();
-                                const uint32_t rem = pending - 32;
-                                if ((uint32_t)lane < rem) tabw[lane] = tabw[32 + lane];
+                                pending -= 32;
+                                if ((uint32_t)lane < pending) tab[lane] = tab[32 + lane];
                                 __syncwarp();
-                                pending = rem;
                             }
                             staged = true;
                         }
                     }
                     if (!staged)
-                        core::emit_changes(CHG, Lv, row0, topK,
-                                           p.log_entries ? p.log_entries + (uint64_t)pair * p.log_cap : nullptr,
-                                           p.log_cap, cr.count + before, acc[m].hash, lane);
+                        core::emit_changes(CHG, Lv, row0, topK, log_pair, p.log_cap, cr.count + before, acc[m].hash,
+                                           lane);
                 }
                 // carry into the next chunk
                 if (g == TG - 1 && lane == 0) {
@@ -437,15 +434,25 @@ __global__ void __launch_bounds__(TG * CW * 32) replay_tp_kernel(const TpParams 
                 }
             }
             if constexpr (CW == 1) {
-                // this warp is done with the chunk's stage
+                // this warp is done with the chunk's stage; the last of the TG warps refills
+                // it with chunk c + 2 (ordering the warps' generic-proxy reads before the
+                // copy's async-proxy writes)
                 __syncwarp();
-                if (lane == 0) mbar_arrive(&sh.empty[s]);
+                if (lane == 0 && atomicAdd(&sh.rel[s], 1u) == (uint32_t)(TG - 1)) {
+                    sh.rel[s] = 0;
+                    if (c + 2 < nchunks && !*(volatile int *)&sh.abort) {
+                        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                        issue(c + 2, sq + 2);
+                    }
+                }
             }
         }
-        // the change-log entries still waiting
+        // the change-log entries still waiting (one-member groups)
         if (pending) {
             __syncwarp();
-            core::flush_staged(tabw, pending, topK, log_pair, p.log_cap, acc[0].hash, lane);
+            uint32_t *const log_pair =
+                p.log_entries ? p.log_entries + (uint64_t)(pbase + G.member[0]) * p.log_cap : nullptr;
+            core::flush_staged(sh.stage[GP == 1 ? warp : 0], pending, topK, log_pair, p.log_cap, acc[0].hash, lane);
             pending = 0;
         }
         if constexpr (CW == 1) __syncthreads();   // every warp sees the same abort flag
@@ -496,10 +503,17 @@ __global__ void __launch_bounds__(TG * CW * 32) replay_tp_kernel(const TpParams 
         __syncthreads();
     }
     // On abort, let outstanding bulk copies land before the CTA's shared memory goes away
-    // (with the full default limit, whatever the per-chunk limit).
+    // (with the full default limit, whatever the per-chunk limit).  One slot: the last copy
+    // into each stage (a completed phase passes at once); else the copies thread 0 has not
+    // seen complete.
     if (tid == 0) {
-        for (int s = 0; s < 2; s++)
-            if (pend[s] >= 0) (void)mbar_wait_bounded(&sh.bar[s], (uint32_t)pend[s]);
+        for (int s = 0; s < 2; s++) {
+            if (CW == 1) {
+                if (sh.issued[s] >= 0) (void)mbar_wait_bounded(&sh.bar[s], ((uint32_t)sh.issued[s] >> 1) & 1);
+            } else if (pend[s] >= 0) {
+                (void)mbar_wait_bounded(&sh.bar[s], (uint32_t)pend[s]);
+            }
+        }
     }
 }
 
@@ -528,7 +542,7 @@ int occ_t(int *smem_out) {
     return blocks;
 }
 
-#define MAGUS_TILES(X) X(8, 1, 1) X(4, 2, 1) X(2, 4, 1) X(1, 8, 1) X(8, 1, 4) X(4, 2, 4) X(2, 4, 4) X(1, 8, 4)
+#define MAGUS_TILES(X) X(8, 1, 1) X(4, 2, 1) X(2, 4, 1) X(1, 8, 1) X(8, 1, 4) X(4, 2, 4) X(2, 4, 4) X(1, 8, 4) X(4, 1, 1)
 
 }  // namespace
 

@@ -13,7 +13,7 @@ from gpu_util import REL_TOL, assert_pair, oracle_pairs, to_device, to_numpy
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-TILES = [(8, 1), (4, 2), (2, 4), (1, 8)]
+TILES = [(8, 1), (4, 1), (4, 2), (2, 4), (1, 8)]
 
 
 @pytest.fixture(scope="module")
