@@ -136,26 +136,41 @@ static __device__ __noinline__ void row_predict_general(uint32_t base, int lane,
 // with a run-time multiplier of -1 so that it issues on the FMA pipe: the kernel is bound by
 // the half-rate integer ALU pipe (measured: this form is the fastest of the all-ALU,
 // all-IMAD and mixed forms).
-template <int S>
+// WC > 0: W = WC is known at compile time (WC <= 28, so W + S <= 32): the deltas W rounds
+// earlier are the row's own deltas shifted by W, except the first W, which are the last
+// W + S of the row before (its last (W + S) / 4 chunks) -- 8 + (W + S) / 4 loads instead of
+// 17.  WC = 0: W at run time, the 36-delta window loaded separately.
+template <int S, int WC = 0>
 __device__ __forceinline__ void row_predict_fast(uint32_t base, int lane, int W, uint32_t one, int32_t upc,
                                                  int32_t dnc, int32_t thr0c, uint32_t &UPr, uint32_t &DNr,
                                                  uint32_t &S0r, uint32_t &band, uint32_t &amax,
                                                  uint32_t (&v)[32]) {
     load_row(base, lane, v);
     // window of the deltas W rounds earlier: 36 deltas from the 4-aligned element E0
-    uint32_t u[36];
-    const int E0 = 32 * lane - (W + S);
+    constexpr int NP = WC > 0 ? (WC + S) / 4 : 9;
+    uint32_t u[4 * NP];
+    if constexpr (WC > 0) {
+        static_assert(((WC + S) & 3) == 0 && WC + S <= 32, "window of the row before");
 #pragma unroll
-    for (int c = 0; c < 9; c++) {
-        const int E = E0 + 4 * c;
-        lds128(swz_chunk(base, E >> 5, (E >> 2) & 7), u[4 * c], u[4 * c + 1], u[4 * c + 2], u[4 * c + 3]);
+        for (int c = 0; c < NP; c++)
+            lds128(swz_chunk(base, lane - 1, 8 - NP + c), u[4 * c], u[4 * c + 1], u[4 * c + 2], u[4 * c + 3]);
+    } else {
+        const int E0 = 32 * lane - (W + S);
+#pragma unroll
+        for (int c = 0; c < 9; c++) {
+            const int E = E0 + 4 * c;
+            lds128(swz_chunk(base, E >> 5, (E >> 2) & 7), u[4 * c], u[4 * c + 1], u[4 * c + 2], u[4 * c + 3]);
+        }
     }
     const uint32_t neg1 = 0u - one;
     const uint32_t up3 = (uint32_t)upc + 3u, dn2 = (uint32_t)dnc - 2u;
     uint32_t bd = 0xffffffffu, mx = 0;
 #pragma unroll
     for (int k = 0; k < 32; k++) {
-        const uint32_t a = v[k], b = u[k + S];
+        const uint32_t a = v[k];
+        uint32_t b;
+        if constexpr (WC > 0) b = k < WC ? u[k + S] : v[k - WC];
+        else b = u[k + S];
         const uint32_t tu = up3 - a + b;                  // < 0: +1;  in [0, 5]: up band
         const uint32_t td = a - b - dn2;                  // < 0: -1;  in [0, 5]: dn band
         const uint32_t ts = a * neg1 + (uint32_t)thr0c;   // < 0  <=>  a > thr0 (an IMAD)
@@ -169,12 +184,12 @@ __device__ __forceinline__ void row_predict_fast(uint32_t base, int lane, int W,
     amax = mx;
 }
 
-template <int S>
+template <int S, int WC = 0>
 __device__ __forceinline__ bool row_predict_fast_dispatch(uint32_t base, int lane, const DevPolicy &P,
                                                           const DevModel &M, RowPred &r, uint32_t (&v)[32]) {
     uint32_t UPr = 0, DNr = 0, S0r = 0, band, amax;
-    row_predict_fast<S>(base, lane, P.W, (uint32_t)M.one, clamp_mid(P.up_mid), clamp_mid(P.dn_mid),
-                        clamp_thr(M.thr0), UPr, DNr, S0r, band, amax, v);
+    row_predict_fast<S, WC>(base, lane, P.W, (uint32_t)M.one, clamp_mid(P.up_mid), clamp_mid(P.dn_mid),
+                            clamp_thr(M.thr0), UPr, DNr, S0r, band, amax, v);
     // every delta of the sub-block is some lane's row element; the 64 before it (rows -1, -2)
     // are checked here: the fast path needs all of them below 2^30
     const uint32_t h0 = lds32(swz_elem(base, lane - 64)), h1 = lds32(swz_elem(base, lane - 32));
@@ -196,16 +211,27 @@ __device__ __forceinline__ bool row_predict_fast_dispatch(uint32_t base, int lan
 }
 
 // Alg. 1 predictions and stretch bits of this lane's row (rows of the sub-block at `base`).
+// kSpecW: the common window lengths take the compile-time-W path (more code per kernel, so
+// only kernels with one policy per slot use it; grouped tiles keep the run-time path).
+template <bool kSpecW = false>
 __device__ __forceinline__ RowPred row_predict(uint32_t base, int lane, const DevPolicy &P, const DevModel &M,
                                                uint32_t vmask, uint32_t pmask) {
     RowPred r;
     uint32_t v[32];
     bool ok;
-    switch ((-P.W) & 3) {
-        case 0: ok = row_predict_fast_dispatch<0>(base, lane, P, M, r, v); break;
-        case 1: ok = row_predict_fast_dispatch<1>(base, lane, P, M, r, v); break;
-        case 2: ok = row_predict_fast_dispatch<2>(base, lane, P, M, r, v); break;
-        default: ok = row_predict_fast_dispatch<3>(base, lane, P, M, r, v); break;
+    switch (kSpecW ? P.W : 0) {
+#define MAGUS_PRED_W(w) \
+        case w: ok = row_predict_fast_dispatch<(-(w)) & 3, w>(base, lane, P, M, r, v); break;
+        MAGUS_PRED_W(1) MAGUS_PRED_W(2) MAGUS_PRED_W(3) MAGUS_PRED_W(4) MAGUS_PRED_W(5) MAGUS_PRED_W(6)
+        MAGUS_PRED_W(7) MAGUS_PRED_W(8) MAGUS_PRED_W(10) MAGUS_PRED_W(12) MAGUS_PRED_W(16)
+#undef MAGUS_PRED_W
+        default:
+            switch ((-P.W) & 3) {
+                case 0: ok = row_predict_fast_dispatch<0>(base, lane, P, M, r, v); break;
+                case 1: ok = row_predict_fast_dispatch<1>(base, lane, P, M, r, v); break;
+                case 2: ok = row_predict_fast_dispatch<2>(base, lane, P, M, r, v); break;
+                default: ok = row_predict_fast_dispatch<3>(base, lane, P, M, r, v); break;
+            }
     }
     r.fast = ok;
     if (!ok) row_predict_general(base, lane, P, M, r.UP, r.DN, r.S0, r.SM);
@@ -300,6 +326,20 @@ __device__ __forceinline__ uint32_t latch_row(uint32_t SETM, uint32_t SET0, uint
 __device__ __forceinline__ void emit_changes(uint32_t CHG, uint32_t Lv, uint64_t row0, uint32_t topK,
                                              uint32_t *log, uint64_t log_cap, uint64_t first,
                                              unsigned long long &hash, int lane) {
+    if (!log) {
+        // hash only: the sum is order-free and no slot is needed, so every lane hashes its
+        // own row's changes (no scan, no search; measured 5-6 % faster on the many-policy
+        // workloads, which write no entries)
+        uint32_t bits = CHG;
+        while (bits) {
+            const int q = __ffs(bits) - 1;
+            bits &= bits - 1;
+            const uint64_t when = row0 + 32u * (uint32_t)lane + (uint32_t)q + 1u;
+            const uint32_t lv = ((Lv >> q) & 1u) ? topK : 0u;
+            hash += mix64((when << 8) | lv);
+        }
+        return;
+    }
     const uint32_t nch = __popc(CHG);
     uint32_t incl = nch;
 #pragma unroll
