@@ -17,7 +17,10 @@
 // 32 deltas, 128-byte swizzled so that every lane reads its own row with conflict-free
 // 128-bit loads; each stage keeps the 2 rows (64 deltas) that precede it so the window
 // W <= 64 never reaches outside shared memory.  One staged chunk feeds every policy the
-// CTA holds (policy_slots groups of time_groups warps).
+// CTA holds (policy_slots groups of time_groups warps).  With one policy slot the 8 rows
+// before a chunk arrive with its copy and the last warp done with a stage refills it with
+// the chunk two ahead; a trace's last chunk is copied only up to the trace's end.  One-member
+// groups stage their change-log entries per warp and write them 32 at a time.
 //
 // Policies that share Alg. 1's parameters (W, inc, dec) make identical predictions and
 // flags; they differ only in Alg. 2 (L, threshold).  A slot therefore holds a policy group
@@ -74,8 +77,9 @@ struct Shared {
     int abort;
 };
 
-// Stage: a 1024-byte block whose last two rows hold the preceding 64 deltas, then the
-// chunk's TG * 32 rows; both 1024-byte aligned (the 128-byte swizzle repeats every 8 rows).
+// Stage: a 1024-byte block whose last two rows hold the preceding 64 deltas (one slot: the
+// block holds the 8 rows before the chunk, copied with it), then the chunk's TG * 32 rows;
+// both 1024-byte aligned (the 128-byte swizzle repeats every 8 rows).
 template <int TG>
 __host__ __device__ constexpr size_t stage_bytes() {
     return 1024 + (size_t)TG * SB * sizeof(uint32_t);
