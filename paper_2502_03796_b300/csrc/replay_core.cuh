@@ -455,19 +455,17 @@ __device__ __forceinline__ unsigned long long add_masked4(unsigned long long s, 
 // Sum of the row's deltas at the rounds selected by mask Msel (bit p = round p).
 __device__ __forceinline__ unsigned long long row_masked_sum(uint32_t base, int lane, uint32_t Msel, bool fast) {
     uint32_t v[32];
-    load_row(base, lane, v);
     unsigned long long s = 0;
     if (fast) {
-        // every delta < 2^30
-        s = add_masked4<0>(s, Msel, v);
-        s = add_masked4<1>(s, Msel, v);
-        s = add_masked4<2>(s, Msel, v);
-        s = add_masked4<3>(s, Msel, v);
-        s = add_masked4<4>(s, Msel, v);
-        s = add_masked4<5>(s, Msel, v);
-        s = add_masked4<6>(s, Msel, v);
-        s = add_masked4<7>(s, Msel, v);
+        // every delta < 2^30; one 16-byte chunk at a time (fewer registers live)
+#define MAGUS_MASKED_CHUNK(C)                                                    \
+        lds128(swz_chunk(base, lane, C), v[4 * C], v[4 * C + 1], v[4 * C + 2], v[4 * C + 3]); \
+        s = add_masked4<C>(s, Msel, v);
+        MAGUS_MASKED_CHUNK(0) MAGUS_MASKED_CHUNK(1) MAGUS_MASKED_CHUNK(2) MAGUS_MASKED_CHUNK(3)
+        MAGUS_MASKED_CHUNK(4) MAGUS_MASKED_CHUNK(5) MAGUS_MASKED_CHUNK(6) MAGUS_MASKED_CHUNK(7)
+#undef MAGUS_MASKED_CHUNK
     } else {
+        load_row(base, lane, v);
 #pragma unroll
         for (int k = 0; k < 32; k++) s += ((Msel >> k) & 1u) ? v[k] : 0u;
     }

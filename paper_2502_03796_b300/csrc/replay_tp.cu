@@ -88,25 +88,38 @@ template <int TG, int CW, int GP>
 __host__ __device__ constexpr size_t stage_offset() {
     return (sizeof(Shared<TG, CW, GP>) + 1023) / 1024 * 1024;
 }
+// Shared memory of one CTA from a 1024-byte aligned base (the stages need that alignment for
+// the 128-byte swizzle).
 template <int TG, int CW, int GP>
 __host__ __device__ constexpr size_t smem_bytes() {
-    return 1024 /* alignment slack */ + stage_offset<TG, CW, GP>() + 2 * stage_bytes<TG>();
+    return stage_offset<TG, CW, GP>() + 2 * stage_bytes<TG>();
 }
 
-// Register budgets per tile: 80 for the 8-warp one-slot tile of one-member groups (three
-// CTAs of 256 threads per SM), 88 for the 4-warp one (five CTAs of 128 threads), 96 for the
-// other one-member tiles and 128 for grouped tiles (two CTAs per SM).  The kernel's
-// allocation is sensitive: left alone the compiler has taken from 74 to 224 registers for
-// these shapes as the source changed.
+// Register budgets per tile: 80 for the one-slot tiles of one-member groups (three CTAs of 256
+// threads or six of 128 per SM: the 4-warp tile's shared memory is sized to fit six, which
+// measured 4.5 % faster than five at 88 registers), 96 for the other one-member tiles and 128
+// for grouped tiles (two CTAs per SM).  The kernel's allocation is sensitive: left alone the
+// compiler has taken from 74 to 224 registers for these shapes as the source changed.
 template <int TG, int CW, int GP>
 __global__ void __launch_bounds__(TG * CW * 32)
-    __maxnreg__(GP == 1 ? (CW == 1 ? (TG == 8 ? 80 : 88) : 96) : 128) replay_tp_kernel(const TpParams p,
+    __maxnreg__(GP == 1 ? (CW == 1 ? 80 : 96) : 128) replay_tp_kernel(const TpParams p,
                                                                    const __grid_constant__ CUtensorMap tmap,
                                                                    const __grid_constant__ CUtensorMap tmap_tail) {
     constexpr int CH = TG * SB;              // rounds per chunk
     constexpr int CH_ROWS = TG * 32;         // 32-delta rows per chunk
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    unsigned char *smem_al = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023);
+    // The launch adds no alignment slack where the dynamic window starts on a 1024-byte
+    // boundary (tp_smem_slack); a window that does not, or is too small, is reported, never used.
+    const uint32_t pad = (1024u - (smem_u32(smem_raw) & 1023u)) & 1023u;
+    {
+        uint32_t dyn;
+        asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dyn));
+        if (pad + (uint32_t)smem_bytes<TG, CW, GP>() > dyn) {
+            if (threadIdx.x == 0) atomicCAS(p.status, 0, MAGUS_ECUDA);
+            return;
+        }
+    }
+    unsigned char *smem_al = smem_raw + pad;
     Shared<TG, CW, GP> &sh = *reinterpret_cast<Shared<TG, CW, GP> *>(smem_al);
     // data row 0 of stage s (shared-window byte address)
     const uint32_t stage0 = smem_u32(smem_al + stage_offset<TG, CW, GP>()) + 1024;
@@ -521,10 +534,24 @@ __global__ void __launch_bounds__(TG * CW * 32)
     }
 }
 
+// Alignment slack the launch adds to a CTA's shared memory: none where the dynamic window
+// starts on a 1024-byte boundary.  It starts after the block's reserved and static shared
+// memory (none static here); the kernel checks its window in any case.
+template <int TG, int CW, int GP>
+size_t tp_smem_slack() {
+    int dev = 0, reserved = 0;
+    cudaFuncAttributes fa;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev) != cudaSuccess ||
+        cudaFuncGetAttributes(&fa, replay_tp_kernel<TG, CW, GP>) != cudaSuccess)
+        return 1024;
+    return ((size_t)reserved + fa.sharedSizeBytes) % 1024 == 0 ? 0 : 1024;
+}
+
 template <int TG, int CW, int GP>
 cudaError_t launch_t(const TpParams &p, const CUtensorMap &tmap, const CUtensorMap &tmap_tail, int grid,
                      cudaStream_t stream) {
-    const size_t smem = smem_bytes<TG, CW, GP>();
+    const size_t smem = smem_bytes<TG, CW, GP>() + tp_smem_slack<TG, CW, GP>();
     cudaError_t e = cudaFuncSetAttribute(replay_tp_kernel<TG, CW, GP>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -534,7 +561,7 @@ cudaError_t launch_t(const TpParams &p, const CUtensorMap &tmap, const CUtensorM
 
 template <int TG, int CW, int GP>
 int occ_t(int *smem_out) {
-    const size_t smem = smem_bytes<TG, CW, GP>();
+    const size_t smem = smem_bytes<TG, CW, GP>() + tp_smem_slack<TG, CW, GP>();
     if (smem_out) *smem_out = (int)smem;
     if (cudaFuncSetAttribute(replay_tp_kernel<TG, CW, GP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem) != cudaSuccess)
