@@ -300,6 +300,51 @@ __device__ __forceinline__ uint32_t hf_from_counts(const uint32_t (&w)[8], int k
     return HF;
 }
 
+// Algorithm 2 for a 10-round tune window, bit-sliced.  S_i (bit p = flag of round p - i,
+// i = 0..9) are summed position by position by a carry-save adder tree (full adders: sum =
+// three-input xor, carry = majority) into the 4-bit count c3 c2 c1 c0 of every round's
+// window; the comparison with kmin is then a fixed boolean form of those four words.
+struct Count4 {
+    uint32_t c0, c1, c2, c3;
+};
+__device__ __forceinline__ uint32_t maj3(uint32_t a, uint32_t b, uint32_t c) { return (a & b) | (a & c) | (b & c); }
+__device__ __forceinline__ Count4 window10_counts(uint64_t H, uint32_t FL) {
+    const uint32_t Hh = (uint32_t)(H >> 32);   // flags of rounds -32 .. -1
+    uint32_t S[10];
+    S[0] = FL;
+#pragma unroll
+    for (int i = 1; i < 10; i++) S[i] = __funnelshift_l(Hh, FL, i);
+    const uint32_t s1 = S[0] ^ S[1] ^ S[2], k1 = maj3(S[0], S[1], S[2]);
+    const uint32_t s2 = S[3] ^ S[4] ^ S[5], k2 = maj3(S[3], S[4], S[5]);
+    const uint32_t s3 = S[6] ^ S[7] ^ S[8], k3 = maj3(S[6], S[7], S[8]);
+    const uint32_t s4 = s1 ^ s2 ^ s3, k4 = maj3(s1, s2, s3);
+    Count4 r;
+    r.c0 = s4 ^ S[9];
+    const uint32_t k5 = s4 & S[9];
+    const uint32_t s6 = k1 ^ k2 ^ k3, k6 = maj3(k1, k2, k3);
+    r.c1 = k4 ^ k5 ^ s6;
+    const uint32_t k7 = maj3(k4, k5, s6);
+    r.c2 = k6 ^ k7;
+    r.c3 = k6 & k7;
+    return r;
+}
+// bit p: count of round p's window >= kmin (counts are at most 10)
+__device__ __forceinline__ uint32_t count4_ge(const Count4 &c, int kmin) {
+    switch (kmin) {
+        case 1: return c.c0 | c.c1 | c.c2 | c.c3;
+        case 2: return c.c1 | c.c2 | c.c3;
+        case 3: return c.c2 | c.c3 | (c.c1 & c.c0);
+        case 4: return c.c2 | c.c3;
+        case 5: return c.c3 | (c.c2 & (c.c1 | c.c0));
+        case 6: return c.c3 | (c.c2 & c.c1);
+        case 7: return c.c3 | (c.c2 & c.c1 & c.c0);
+        case 8: return c.c3;
+        case 9: return c.c3 & (c.c1 | c.c0);
+        case 10: return c.c3 & c.c1;
+        default: return kmin <= 0 ? 0xffffffffu : 0u;
+    }
+}
+
 // Flag history before each lane's row: lanes 0 and 1 take the 64 flags before the first
 // row (tailH), the others their two predecessor rows.
 __device__ __forceinline__ uint64_t row_history(uint32_t FL, uint64_t tailH, int lane) {

@@ -119,6 +119,30 @@ def test_grouped_policies_all_tiles(rp, tile):
         assert_pair(out, p, r, cap=cap, tag=f"grouped tile{tile}")
 
 
+@pytest.mark.parametrize("tile", [(4, 1), (8, 1)])
+def test_window10_every_kmin(rp, tile):
+    """A 10-round tune window with every flag-count threshold 0..11 (the bit-sliced Alg. 2
+    path of one-member groups), on two predictor settings."""
+    ts = ragged_set(seed=21)
+    model = tracegen.default_model()
+    pols = []
+    for W, inc, dec in [(5, 5.0, -5.0), (2, 1.0, -1.0)]:
+        for th in (0.0, 0.1, 0.15, 0.3, 0.4, 0.45, 0.6, 0.7, 0.8, 0.9, 1.0, 1.05):
+            pols.append(dict(inc_threshold=inc, dec_threshold=dec, direv_length=W, tune_window=10,
+                             high_freq_threshold=th, step_mode=0))
+    cap = 40_000
+    rp.set_tile(*tile)
+    try:
+        out = to_numpy(rp.run(to_device(ts), ts.lengths, pols, log_capacity=cap))
+    finally:
+        rp.set_tile(0, 0)
+    assert rp.status() == 0
+    ref = oracle_pairs(ts, pols, model)
+    assert len({r["n_hf"] for r in ref.values()}) > 12   # the thresholds make different detectors
+    for p, r in ref.items():
+        assert_pair(out, p, r, cap=cap, tag=f"window10 tile{tile}")
+
+
 def test_autotune_picks_a_tile(rp):
     ts = tracegen.sweep(n_traces=8, n=30_000, seed=2)
     pols = tracegen.sweep_policies()[:32]
