@@ -291,10 +291,12 @@ __global__ void __launch_bounds__(TG * CW * 32)
             // ---------------------------------------------------------------- phase A
             // Alg. 1 predictions and stretch bits of this lane's row (shared by the group)
             const uint32_t sub = sbase + (uint32_t)g * (SB * 4u);   // data row 0 of the sub-block
+            // a chunk between the first and the last: every row full and past the first W rounds
+            const bool interior = c > 0 && c + 1 < nchunks;
             const int64_t r0 = (int64_t)c * CH + g * SB + 32 * lane;  // row start (local)
-            const int64_t left = (int64_t)n - r0;
-            const uint32_t vmask = core::valid_mask(left);
-            const uint32_t pmask = core::predict_mask(vmask, n_seen0 + (uint64_t)r0, P.W);
+            const int64_t left = interior ? (int64_t)CH : (int64_t)n - r0;
+            const uint32_t vmask = interior ? FULL : core::valid_mask(left);
+            const uint32_t pmask = interior ? FULL : core::predict_mask(vmask, n_seen0 + (uint64_t)r0, P.W);
             const core::RowPred rp = core::row_predict<GP == 1>(sub, lane, P, M, vmask, pmask);
             const uint32_t UP = rp.UP, DN = rp.DN;
             const uint32_t FL = UP | DN;   // uncore_tune_ls entries of the row
