@@ -368,8 +368,12 @@ int launch_plan(magus_replay *h, const Plan &pl, const uint32_t *traces, const O
     p.n_hf = o.n_hf;
     p.state = o.state;
     p.chunk_wait_ns = h->chunk_wait_ns;
+    // the window length every policy group shares, if any (selects a W-specific instance)
+    int window = pl.groups.empty() ? 0 : pl.pols[pl.groups[0].member[0]].W;
+    for (const PolicyGroup &g : pl.groups)
+        if (pl.pols[g.member[0]].W != window) window = 0;
     int smem = 0;
-    const int per_sm = tp_max_ctas_per_sm(pl.tg, pl.cw, pl.gp, &smem);
+    const int per_sm = tp_max_ctas_per_sm(pl.tg, pl.cw, pl.gp, &smem, window);
     if (per_sm <= 0) {
         set_error("tile shape does not fit on this device");
         return MAGUS_ECUDA;
@@ -409,7 +413,7 @@ int launch_plan(magus_replay *h, const Plan &pl, const uint32_t *traces, const O
         };
         CK(cudaEventRecord(h->k_ev[slot_k].a, stream), "cudaEventRecord");
         if (n_items) {
-            CK(launch_replay_tp(pl.tg, pl.cw, pl.gp, p, tmap, tmap_tail, grid, stream), "replay kernel launch");
+            CK(launch_replay_tp(pl.tg, pl.cw, pl.gp, p, tmap, tmap_tail, grid, stream, window), "replay kernel launch");
             if ((rc = mark())) return rc;
         }
         if (has_lad) {

@@ -101,9 +101,13 @@ bool tp_tile_supported(int time_groups, int policy_slots, int group_size);
 // tmap: boxes of tp_box_rows(time_groups) rows; tmap_tail: boxes of kTailRows rows, for the
 // last, partial chunk of each trace (the copy stops within kTailRows - 1 rows of its end).
 constexpr int kTailRows = 8;
+// window: the window length W shared by every policy group of the launch, or 0; where the
+// tile has an instance for that W it runs that instance (tp_kernel_window names it, 0: none).
+int tp_kernel_window(int time_groups, int policy_slots, int group_size, int window);
 cudaError_t launch_replay_tp(int time_groups, int policy_slots, int group_size, const TpParams &p,
-                             const CUtensorMap &tmap, const CUtensorMap &tmap_tail, int grid, cudaStream_t stream);
-int tp_max_ctas_per_sm(int time_groups, int policy_slots, int group_size, int *smem_bytes);
+                             const CUtensorMap &tmap, const CUtensorMap &tmap_tail, int grid, cudaStream_t stream,
+                             int window = 0);
+int tp_max_ctas_per_sm(int time_groups, int policy_slots, int group_size, int *smem_bytes, int window = 0);
 
 // ---- segment-parallel replay (replay_seg.cu)
 struct SegItem {

@@ -167,8 +167,12 @@ extern "C" int magus_replay_run_static(const magus_model_t *model, const uint32_
             p.n_hf = log->n_hf;
         }
         p.state = io_state;
+        // the window length every policy group shares, if any (selects a W-specific instance)
+        int window = groups.empty() ? 0 : pols[groups[0].member[0]].W;
+        for (const PolicyGroup &g : groups)
+            if (pols[g.member[0]].W != window) window = 0;
         int smem = 0;
-        const int per_sm = tp_max_ctas_per_sm(tg, cw, gp, &smem);
+        const int per_sm = tp_max_ctas_per_sm(tg, cw, gp, &smem, window);
         int sms = 0;
         e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (e != cudaSuccess || per_sm <= 0) return fail("device query failed", MAGUS_ECUDA);
@@ -177,7 +181,7 @@ extern "C" int magus_replay_run_static(const magus_model_t *model, const uint32_
         rc = make_trace_tmap(traces, o, tp_box_rows(tg), &tmap, &err);
         if (!rc) rc = make_trace_tmap(traces, o, kTailRows, &tmap_tail, &err);
         if (rc) return fail(err, rc);
-        e = launch_replay_tp(tg, cw, gp, p, tmap, tmap_tail, grid, s);
+        e = launch_replay_tp(tg, cw, gp, p, tmap, tmap_tail, grid, s, window);
         if (e != cudaSuccess) return fail(std::string("replay kernel launch: ") + cudaGetErrorString(e), MAGUS_ECUDA);
     }
     // synchronous: the scratch is reused by the next call, and device-side input errors

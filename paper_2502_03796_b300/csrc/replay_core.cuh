@@ -214,15 +214,18 @@ __device__ __forceinline__ bool row_predict_fast_dispatch(uint32_t base, int lan
 }
 
 // Alg. 1 predictions and stretch bits of this lane's row (rows of the sub-block at `base`).
-// kSpecW: the common window lengths take the compile-time-W path (more code per kernel, so
-// only kernels with one policy per slot use it; grouped tiles keep the run-time path).
-template <bool kSpecW = false>
+// WC > 0: W = WC, known at compile time.  Otherwise kSpecW: the common window lengths take
+// the compile-time-W path through a switch per row (more code per kernel, so only kernels
+// with one policy per slot use it; grouped tiles keep the run-time path).
+template <int WC = -1, bool kSpecW = false>
 __device__ __forceinline__ RowPred row_predict(uint32_t base, int lane, const DevPolicy &P, const DevModel &M,
                                                uint32_t vmask, uint32_t pmask) {
     RowPred r;
     uint32_t v[32];
-    bool ok;
-    switch (kSpecW ? P.W : 0) {
+    bool ok = false;
+    if constexpr (WC > 0) {
+        ok = row_predict_fast_dispatch<(-WC) & 3, WC>(base, lane, P, M, r, v);
+    } else switch (kSpecW ? P.W : 0) {
 #define MAGUS_PRED_W(w) \
         case w: ok = row_predict_fast_dispatch<(-(w)) & 3, w>(base, lane, P, M, r, v); break;
         MAGUS_PRED_W(1) MAGUS_PRED_W(2) MAGUS_PRED_W(3) MAGUS_PRED_W(4) MAGUS_PRED_W(5) MAGUS_PRED_W(6)

@@ -100,7 +100,10 @@ __host__ __device__ constexpr size_t smem_bytes() {
 // measured 4.5 % faster than five at 88 registers), 96 for the other one-member tiles and 128
 // for grouped tiles (two CTAs per SM).  The kernel's allocation is sensitive: left alone the
 // compiler has taken from 74 to 224 registers for these shapes as the source changed.
-template <int TG, int CW, int GP>
+// WK > 0: an instance for policy groups whose window length W is WK (the predictor inline for
+// that W alone: with all the common W behind a switch per row, instruction fetch cost the
+// batched replay 2.4 %); WK = 0: any W.
+template <int TG, int CW, int GP, int WK = 0>
 __global__ void __launch_bounds__(TG * CW * 32)
     __maxnreg__(GP == 1 ? (CW == 1 ? 80 : 96) : 128) replay_tp_kernel(const TpParams p,
                                                                    const __grid_constant__ CUtensorMap tmap,
@@ -297,7 +300,7 @@ __global__ void __launch_bounds__(TG * CW * 32)
             const int64_t left = interior ? (int64_t)CH : (int64_t)n - r0;
             const uint32_t vmask = interior ? FULL : core::valid_mask(left);
             const uint32_t pmask = interior ? FULL : core::predict_mask(vmask, n_seen0 + (uint64_t)r0, P.W);
-            const core::RowPred rp = core::row_predict<GP == 1>(sub, lane, P, M, vmask, pmask);
+            const core::RowPred rp = core::row_predict<(WK > 0 ? WK : -1), GP == 1>(sub, lane, P, M, vmask, pmask);
             const uint32_t UP = rp.UP, DN = rp.DN;
             const uint32_t FL = UP | DN;   // uncore_tune_ls entries of the row
             {
@@ -542,43 +545,45 @@ __global__ void __launch_bounds__(TG * CW * 32)
 // Alignment slack the launch adds to a CTA's shared memory: none where the dynamic window
 // starts on a 1024-byte boundary.  It starts after the block's reserved and static shared
 // memory (none static here); the kernel checks its window in any case.
-template <int TG, int CW, int GP>
+template <int TG, int CW, int GP, int WK>
 size_t tp_smem_slack() {
     int dev = 0, reserved = 0;
     cudaFuncAttributes fa;
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev) != cudaSuccess ||
-        cudaFuncGetAttributes(&fa, replay_tp_kernel<TG, CW, GP>) != cudaSuccess)
+        cudaFuncGetAttributes(&fa, replay_tp_kernel<TG, CW, GP, WK>) != cudaSuccess)
         return 1024;
     return ((size_t)reserved + fa.sharedSizeBytes) % 1024 == 0 ? 0 : 1024;
 }
 
-template <int TG, int CW, int GP>
+template <int TG, int CW, int GP, int WK = 0>
 cudaError_t launch_t(const TpParams &p, const CUtensorMap &tmap, const CUtensorMap &tmap_tail, int grid,
                      cudaStream_t stream) {
-    const size_t smem = smem_bytes<TG, CW, GP>() + tp_smem_slack<TG, CW, GP>();
-    cudaError_t e = cudaFuncSetAttribute(replay_tp_kernel<TG, CW, GP>,
+    const size_t smem = smem_bytes<TG, CW, GP>() + tp_smem_slack<TG, CW, GP, WK>();
+    cudaError_t e = cudaFuncSetAttribute(replay_tp_kernel<TG, CW, GP, WK>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    replay_tp_kernel<TG, CW, GP><<<grid, TG * CW * 32, smem, stream>>>(p, tmap, tmap_tail);
+    replay_tp_kernel<TG, CW, GP, WK><<<grid, TG * CW * 32, smem, stream>>>(p, tmap, tmap_tail);
     return cudaGetLastError();
 }
 
-template <int TG, int CW, int GP>
+template <int TG, int CW, int GP, int WK = 0>
 int occ_t(int *smem_out) {
-    const size_t smem = smem_bytes<TG, CW, GP>() + tp_smem_slack<TG, CW, GP>();
+    const size_t smem = smem_bytes<TG, CW, GP>() + tp_smem_slack<TG, CW, GP, WK>();
     if (smem_out) *smem_out = (int)smem;
-    if (cudaFuncSetAttribute(replay_tp_kernel<TG, CW, GP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if (cudaFuncSetAttribute(replay_tp_kernel<TG, CW, GP, WK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem) != cudaSuccess)
         return 0;
     int blocks = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, replay_tp_kernel<TG, CW, GP>, TG * CW * 32,
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, replay_tp_kernel<TG, CW, GP, WK>, TG * CW * 32,
                                                       smem) != cudaSuccess)
         return 0;
     return blocks;
 }
 
 #define MAGUS_TILES(X) X(8, 1, 1) X(4, 2, 1) X(2, 4, 1) X(1, 8, 1) X(8, 1, 4) X(4, 2, 4) X(2, 4, 4) X(1, 8, 4) X(4, 1, 1)
+// window lengths with their own instance of the 4-warp one-slot tile
+#define MAGUS_TP_WINDOWS(X) X(1) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(10) X(12) X(16)
 
 }  // namespace
 
@@ -591,8 +596,23 @@ bool tp_tile_supported(int tg, int cw, int gp) {
     return false;
 }
 
+int tp_kernel_window(int tg, int cw, int gp, int window) {
+    if (tg != 4 || cw != 1 || gp != 1) return 0;
+#define MAGUS_HAS_W(w) if (window == w) return w;
+    MAGUS_TP_WINDOWS(MAGUS_HAS_W)
+#undef MAGUS_HAS_W
+    return 0;
+}
+
 cudaError_t launch_replay_tp(int tg, int cw, int gp, const TpParams &p, const CUtensorMap &tmap,
-                             const CUtensorMap &tmap_tail, int grid, cudaStream_t stream) {
+                             const CUtensorMap &tmap_tail, int grid, cudaStream_t stream, int window) {
+    switch (tp_kernel_window(tg, cw, gp, window)) {
+#define MAGUS_LAUNCH_W(w) \
+        case w: return launch_t<4, 1, 1, w>(p, tmap, tmap_tail, grid, stream);
+        MAGUS_TP_WINDOWS(MAGUS_LAUNCH_W)
+#undef MAGUS_LAUNCH_W
+        default: break;
+    }
 #define MAGUS_LAUNCH(a, b, c) \
     if (tg == a && cw == b && gp == c) return launch_t<a, b, c>(p, tmap, tmap_tail, grid, stream);
     MAGUS_TILES(MAGUS_LAUNCH)
@@ -600,7 +620,14 @@ cudaError_t launch_replay_tp(int tg, int cw, int gp, const TpParams &p, const CU
     return cudaErrorInvalidValue;
 }
 
-int tp_max_ctas_per_sm(int tg, int cw, int gp, int *smem) {
+int tp_max_ctas_per_sm(int tg, int cw, int gp, int *smem, int window) {
+    switch (tp_kernel_window(tg, cw, gp, window)) {
+#define MAGUS_OCC_W(w) \
+        case w: return occ_t<4, 1, 1, w>(smem);
+        MAGUS_TP_WINDOWS(MAGUS_OCC_W)
+#undef MAGUS_OCC_W
+        default: break;
+    }
 #define MAGUS_OCC(a, b, c) if (tg == a && cw == b && gp == c) return occ_t<a, b, c>(smem);
     MAGUS_TILES(MAGUS_OCC)
 #undef MAGUS_OCC
