@@ -141,12 +141,16 @@ static __device__ __noinline__ void row_predict_general(uint32_t base, int lane,
 // earlier are the row's own deltas shifted by W, except the first W, which are the last
 // W + S of the row before (its last (W + S) / 4 chunks) -- 8 + (W + S) / 4 loads instead of
 // 17.  WC = 0: W at run time, the 36-delta window loaded separately.
-template <int S, int WC = 0>
+template <int S, int WC = 0, bool kChunked = false>
 __device__ __forceinline__ void row_predict_fast(uint32_t base, int lane, int W, uint32_t one, int32_t upc,
                                                  int32_t dnc, int32_t thr0c, uint32_t &UPr, uint32_t &DNr,
                                                  uint32_t &S0r, uint32_t &band, uint32_t &amax,
                                                  uint32_t (&v)[32]) {
-    load_row(base, lane, v);
+    // kChunked: the row's deltas are loaded one 16-byte chunk at a time as the loop reaches
+    // them, so a delta need not stay in a register for longer than W rounds (2.7 % faster on
+    // the batched replay in the tile instances for one W; kernels that inline several
+    // predictors load the row first, which keeps their register demand where it was)
+    if constexpr (!kChunked) load_row(base, lane, v);
     // window of the deltas W rounds earlier: 36 deltas from the 4-aligned element E0
     constexpr int NP = WC > 0 ? (WC + S) / 4 : 9;
     uint32_t u[4 * NP];
@@ -169,6 +173,7 @@ __device__ __forceinline__ void row_predict_fast(uint32_t base, int lane, int W,
     uint32_t bd = 0xffffffffu, mx = 0;
 #pragma unroll
     for (int k = 0; k < 32; k++) {
+        if (kChunked && (k & 3) == 0) lds128(swz_chunk(base, lane, k >> 2), v[k], v[k + 1], v[k + 2], v[k + 3]);
         const uint32_t a = v[k];
         uint32_t b;
         if constexpr (WC > 0) b = k < WC ? u[k + S] : v[k - WC];
@@ -186,11 +191,11 @@ __device__ __forceinline__ void row_predict_fast(uint32_t base, int lane, int W,
     amax = mx;
 }
 
-template <int S, int WC = 0>
+template <int S, int WC = 0, bool kChunked = false>
 __device__ __forceinline__ bool row_predict_fast_dispatch(uint32_t base, int lane, const DevPolicy &P,
                                                           const DevModel &M, RowPred &r, uint32_t (&v)[32]) {
     uint32_t UPr = 0, DNr = 0, S0r = 0, band, amax;
-    row_predict_fast<S, WC>(base, lane, P.W, (uint32_t)M.one, clamp_mid(P.up_mid), clamp_mid(P.dn_mid),
+    row_predict_fast<S, WC, kChunked>(base, lane, P.W, (uint32_t)M.one, clamp_mid(P.up_mid), clamp_mid(P.dn_mid),
                             clamp_thr(M.thr0), UPr, DNr, S0r, band, amax, v);
     // every delta of the sub-block is some lane's row element; the 64 before it (rows -1, -2)
     // are checked here: the fast path needs all of them below 2^30
@@ -203,6 +208,7 @@ __device__ __forceinline__ bool row_predict_fast_dispatch(uint32_t base, int lan
     r.S0 = __brev(S0r);
     r.SM = 0;
     if (__any_sync(FULL, amax > M.thrM)) {
+        if constexpr (kChunked) load_row(base, lane, v);
         uint32_t SMr = 0;
         const int32_t tm = clamp_thr(M.thrM);
         const uint32_t neg1 = 0u - (uint32_t)M.one;
@@ -224,7 +230,7 @@ __device__ __forceinline__ RowPred row_predict(uint32_t base, int lane, const De
     uint32_t v[32];
     bool ok = false;
     if constexpr (WC > 0) {
-        ok = row_predict_fast_dispatch<(-WC) & 3, WC>(base, lane, P, M, r, v);
+        ok = row_predict_fast_dispatch<(-WC) & 3, WC, true>(base, lane, P, M, r, v);
     } else switch (kSpecW ? P.W : 0) {
 #define MAGUS_PRED_W(w) \
         case w: ok = row_predict_fast_dispatch<(-(w)) & 3, w>(base, lane, P, M, r, v); break;
