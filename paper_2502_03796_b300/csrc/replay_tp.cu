@@ -428,9 +428,14 @@ __global__ void __launch_bounds__(TG * CW * 32)
                             staged = true;
                         }
                     }
-                    if (!staged)
-                        core::emit_changes(CHG, Lv, row0, topK, log_pair, p.log_cap, cr.count + before, acc[m].hash,
-                                           lane);
+                    if (!staged) {
+                        if constexpr (GP == 1)
+                            acc[m].hash += core::emit_changes_cold(CHG, Lv, row0, topK, log_pair, p.log_cap,
+                                                                   cr.count + before, lane);
+                        else
+                            core::emit_changes(CHG, Lv, row0, topK, log_pair, p.log_cap, cr.count + before,
+                                               acc[m].hash, lane);
+                    }
                 }
                 // carry into the next chunk
                 if (g == TG - 1 && lane == 0) {
