@@ -631,7 +631,8 @@ def main() -> int:
                     peak_source=f"{peaks['source']} (MEASURED_PEAKS.json hbm_gbs)" if peaks["source"] == "measured"
                     else "fallback 6.4 TB/s",
                     kernel=("replay_seg_kernel<1> + combine_kernel" if seg_path else
-                            "replay_tp_kernel<4,1,1> (the automatic tile for one policy group)"),
+                            f"replay_tp_kernel<4,1,1,{policy['direv_length']}> (the automatic tile for one "
+                            f"policy group, its instance for W = {policy['direv_length']})"),
                     kernel_ms=k_avg_ms, main_kernel_ms=k_main_ms / max(k_n, 1),
                     alg_bytes_per_launch=alg_bytes, frac_of_nominal_8tbs=achieved / 8000.0)
     # the pipe that actually bounds the kernel: integer ALU lane-operations per interval
