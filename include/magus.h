@@ -197,8 +197,9 @@ int magus_replay_kernel_time(magus_replay_t *h, double *total_ms, double *main_m
                              int32_t *kernels);
 
 /* Tile shape of the batched kernel: warps that split a trace chunk in time (time_groups) x
- * policy groups per CTA (policy_slots); time_groups * policy_slots = 8, or the 4-warp tile
- * (4, 1) (one policy group, five CTAs per SM instead of three).  Policies sharing
+ * policy groups per CTA (policy_slots); time_groups * policy_slots = 8, or a 4-warp tile:
+ * (4, 1) for one-member groups (six CTAs per SM instead of three), (1, 4) and (2, 2) for
+ * groups of up to 4 (five and four CTAs per SM instead of two).  Policies sharing
  * Algorithm 1's parameters (W, inc, dec) are grouped (up to 4 per group, predictions made
  * once per group) whenever that at least halves the group count.  (0, 0) restores the
  * automatic choice.  EINVAL for unsupported shapes. */

@@ -351,8 +351,8 @@ int magus_replay_set_tile(magus_replay_t *h, int32_t tg, int32_t cw) {
         return MAGUS_OK;
     }
     if (!((tg == 8 && cw == 1) || (tg == 4 && cw == 2) || (tg == 2 && cw == 4) || (tg == 1 && cw == 8) ||
-          (tg == 4 && cw == 1))) {
-        set_error("supported tiles: (8,1) (4,2) (2,4) (1,8) (4,1)");
+          (tg == 4 && cw == 1) || (tg == 1 && cw == 4) || (tg == 2 && cw == 2))) {
+        set_error("supported tiles: (8,1) (4,2) (2,4) (1,8) (4,1) (1,4) (2,2)");
         return MAGUS_EINVAL;
     }
     h->tile_tg = tg;
@@ -484,8 +484,9 @@ int magus_replay_autotune(magus_replay_t *h, const uint32_t *traces, const uint6
         memset(&o, 0, sizeof(o));
         o.energy = (double *)h->scratch;
         o.edp = o.energy + pairs;
-        static const int shapes[15][4] = {{8, 1, 1, 0}, {4, 1, 1, 0}, {4, 2, 1, 0}, {2, 4, 1, 0}, {1, 8, 1, 0},
-                                          {8, 1, 4, 0}, {4, 2, 4, 0}, {2, 4, 4, 0}, {1, 8, 4, 0},
+        static const int shapes[17][4] = {{8, 1, 1, 0}, {4, 1, 1, 0}, {4, 2, 1, 0}, {2, 4, 1, 0}, {1, 8, 1, 0},
+                                          {8, 1, 4, 0}, {4, 2, 4, 0}, {2, 4, 4, 0}, {1, 8, 4, 0}, {1, 4, 4, 0},
+                                          {2, 2, 4, 0},
                                           {8, 1, 1, 8192}, {8, 1, 1, 16384}, {8, 1, 1, 32768},
                                           {8, 1, 4, 8192}, {8, 1, 4, 16384}, {8, 1, 4, 32768}};
         float best = 1e30f;

@@ -38,13 +38,21 @@ void choose_tile(magus_replay *h, const std::vector<DevPolicy> &pols, const uint
     if (h->tile_tg) {
         *tg = h->tile_tg;
         *cw = h->tile_cw;
-        if (!tp_tile_supported(*tg, *cw, *gp)) *gp = 1;   // the 4-warp tile takes one-member groups
+        // (4, 1) takes one-member groups only, (1, 4) and (2, 2) groups of up to four (of one
+        // member each, where no policies share Algorithm 1)
+        if (!tp_tile_supported(*tg, *cw, *gp)) *gp = (*gp == 1) ? kMaxGroup : 1;
+    } else if (*gp > 1 && n_groups >= 2) {
+        // grouped policies: a 4-warp tile, four slots from eight groups on (policy sweep,
+        // 64 groups: 39.9 ms against 44.0 for 1 x 8), else two slots of two warps (uneven
+        // lengths, 4 groups: 35.3 ms against 38.9 for 2 x 4)
+        *cw = n_groups >= 8 ? 4 : 2;
+        *tg = n_groups >= 8 ? 1 : 2;
     } else {
         int c = 1;
         while (c * 2 <= std::min(8, n_groups)) c *= 2;
         *cw = c;
-        // one policy group: the 4-warp tile (five CTAs per SM, barriers among 4 warps; 3.6 %
-        // faster than 8 warps on 4,096 x 100,000)
+        // one policy group: the 4-warp tile (six CTAs per SM, barriers among 4 warps; 3.6 %
+        // faster than 8 warps on 4,096 x 100,000 at equal residency)
         *tg = (c == 1 && *gp == 1) ? 4 : 8 / c;
     }
     // an explicit tile shape selects the tile kernel unless segments were asked for as well

@@ -96,7 +96,7 @@ int make_trace_tmap(const uint32_t *traces, uint64_t total_elems, int box_rows, 
 int tp_box_rows(int time_groups);
 // Tile: time_groups warps split a chunk in time for each of policy_slots policy groups of
 // up to group_size members (time_groups * policy_slots = 8, group_size 1 or 4; or the
-// 4-warp tile 4 x 1 x 1).
+// 4-warp tiles 4 x 1 x 1, 1 x 4 x 4 and 2 x 2 x 4).
 bool tp_tile_supported(int time_groups, int policy_slots, int group_size);
 // tmap: boxes of tp_box_rows(time_groups) rows; tmap_tail: boxes of kTailRows rows, for the
 // last, partial chunk of each trace (the copy stops within kTailRows - 1 rows of its end).

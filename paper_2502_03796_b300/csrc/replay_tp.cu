@@ -97,15 +97,17 @@ __host__ __device__ constexpr size_t smem_bytes() {
 
 // Register budgets per tile: 80 for the one-slot tiles of one-member groups (three CTAs of 256
 // threads or six of 128 per SM: the 4-warp tile's shared memory is sized to fit six, which
-// measured 4.5 % faster than five at 88 registers), 96 for the other one-member tiles and 128
-// for grouped tiles (two CTAs per SM).  The kernel's allocation is sensitive: left alone the
-// compiler has taken from 74 to 224 registers for these shapes as the source changed.
+// measured 4.5 % faster than five at 88 registers), 96 for the other one-member tiles and for
+// the 4-slot grouped tile of 4 warps (five CTAs of 128 threads: 3 % faster on the policy sweep
+// than four at 128, despite 20 bytes of spill), 128 for the other grouped tiles.  The kernel's
+// allocation is sensitive: left alone the compiler has taken from 74 to 224 registers for
+// these shapes as the source changed.
 // WK > 0: an instance for policy groups whose window length W is WK (the predictor inline for
 // that W alone: with all the common W behind a switch per row, instruction fetch cost the
 // batched replay 2.4 %); WK = 0: any W.
 template <int TG, int CW, int GP, int WK = 0>
 __global__ void __launch_bounds__(TG * CW * 32)
-    __maxnreg__(GP == 1 ? (CW == 1 ? 80 : 96) : 128) replay_tp_kernel(const TpParams p,
+    __maxnreg__(GP == 1 ? (CW == 1 ? 80 : 96) : (TG == 1 && CW == 4 ? 96 : 128)) replay_tp_kernel(const TpParams p,
                                                                    const __grid_constant__ CUtensorMap tmap,
                                                                    const __grid_constant__ CUtensorMap tmap_tail) {
     constexpr int CH = TG * SB;              // rounds per chunk
@@ -314,8 +316,18 @@ __global__ void __launch_bounds__(TG * CW * 32)
             // Algorithm 2's sliding counts once for a group whose members share L
             uint32_t hw[GP > 1 ? 8 : 1];
             const bool shared_counts = GP > 1 && cnt > 1 && G.same_L;
+            // a shared 10-round window: the bit-sliced counts (four words) take hw[0..3]
+            const bool sliced10 = shared_counts && (Lm[0] & 0xff) == 10;
             if constexpr (GP > 1) {
-                if (shared_counts) core::hf_counts(H, FL, Lm[0] & 0xff, hw);
+                if (sliced10) {
+                    const core::Count4 c10 = core::window10_counts(H, FL);
+                    hw[0] = c10.c0;
+                    hw[1] = c10.c1;
+                    hw[2] = c10.c2;
+                    hw[3] = c10.c3;
+                } else if (shared_counts) {
+                    core::hf_counts(H, FL, Lm[0] & 0xff, hw);
+                }
             }
             // members one after another (not unrolled: unrolling four members doubles the
             // registers and halves the resident CTAs, measured slower)
@@ -325,7 +337,8 @@ __global__ void __launch_bounds__(TG * CW * 32)
                 const uint32_t act = (Lm[m] & 0x100) ? 0u : FULL;
                 uint32_t HFr;
                 if constexpr (GP > 1) {
-                    HFr = shared_counts ? core::hf_from_counts(hw, Km[m]) : core::hf_row(H, FL, Lm[m] & 0xff, Km[m]);
+                    HFr = sliced10 ? core::count4_ge(core::Count4{hw[0], hw[1], hw[2], hw[3]}, Km[m])
+                        : shared_counts ? core::hf_from_counts(hw, Km[m]) : core::hf_row(H, FL, Lm[m] & 0xff, Km[m]);
                 } else {
                     // the 10-round tune window bit-sliced (measured 1.5 % faster on the batched
                     // replay than the byte-parallel counts, which serve every other length)
@@ -586,7 +599,8 @@ int occ_t(int *smem_out) {
     return blocks;
 }
 
-#define MAGUS_TILES(X) X(8, 1, 1) X(4, 2, 1) X(2, 4, 1) X(1, 8, 1) X(8, 1, 4) X(4, 2, 4) X(2, 4, 4) X(1, 8, 4) X(4, 1, 1)
+#define MAGUS_TILES(X) \
+    X(8, 1, 1) X(4, 2, 1) X(2, 4, 1) X(1, 8, 1) X(8, 1, 4) X(4, 2, 4) X(2, 4, 4) X(1, 8, 4) X(4, 1, 1) X(1, 4, 4) X(2, 2, 4)
 // window lengths with their own instance of the 4-warp one-slot tile
 #define MAGUS_TP_WINDOWS(X) X(1) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(10) X(12) X(16)
 
