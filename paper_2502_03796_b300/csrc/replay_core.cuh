@@ -550,8 +550,9 @@ __device__ __forceinline__ void acc_zero(Acc &a) {
 
 // Energy bookkeeping of a row once its levels Flev (bit p = level during round p) are known.
 // kSparseTop: stretched rounds at the top (throughput above the top capacity, rare) are
-// added one by one instead of a pass over the whole row; kernels that replay several group
-// members per row keep the straight-line pass (the loop raises their register demand).
+// added one by one instead of a pass over the whole row (every caller now: with four warps
+// the grouped tiles run the policy sweep 1.2 % faster this way; with eight, the loop had
+// raised their register demand).
 template <bool kSparseTop = true>
 __device__ __forceinline__ void row_energy(uint32_t base, int lane, uint32_t Flev, const RowPred &r,
                                            uint32_t vmask, Acc &acc) {

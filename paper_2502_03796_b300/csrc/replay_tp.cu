@@ -408,7 +408,7 @@ __global__ void __launch_bounds__(TG * CW * 32)
                 const uint32_t Flev = (Lv << 1) | cin;            // level during each round
                 const uint32_t CHG = (Lv ^ Flev) & vmask;
 
-                core::row_energy<GP == 1>(sub, lane, Flev, rp, vmask, acc[m]);
+                core::row_energy<true>(sub, lane, Flev, rp, vmask, acc[m]);
                 acc[m].hf += __popc(HF);
                 const int64_t pair = pbase + G.member[m];
                 // frequency-change log
