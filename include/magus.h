@@ -215,8 +215,10 @@ int magus_replay_set_tile(magus_replay_t *h, int32_t time_groups, int32_t policy
 int magus_replay_set_segments(magus_replay_t *h, int32_t seg_rounds);
 
 /* Failure detection (bounded device-side waits).  Every wait of the tile kernel for a trace
- * chunk's copy, and for a ring stage to be released, gives up after chunk_wait_ns
- * nanoseconds (0, the default, restores 2 s): the kernel then records MAGUS_ETIMEDOUT,
+ * chunk's copy gives up after a limit: chunk_wait_ns nanoseconds in the tiles whose warps
+ * wait for their stages themselves (the one-slot tiles (8, 1) and (4, 1), and (1, 4) with
+ * groups), 2 s in the others and whenever chunk_wait_ns is 0 (the default).  The kernel then
+ * records MAGUS_ETIMEDOUT,
  * stops issuing copies, lets the copies already in flight land (that last wait always keeps
  * the 2 s limit) and returns; magus_replay_status reports the timeout and clears it, and the
  * handle stays usable.  The outputs of a call that timed out are unspecified.  A short limit

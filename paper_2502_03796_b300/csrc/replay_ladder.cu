@@ -183,7 +183,7 @@ __global__ void __launch_bounds__(LW * 32) replay_ladder_kernel(const LadderPara
             const core::RowPred rp = core::row_predict(base, lane, P, M, vmask, pmask);
             const uint32_t FL = rp.UP | rp.DN;
             const uint64_t H = core::row_history(FL, tailH, lane);
-            const uint32_t HF = core::hf_row(H, FL, P.L, P.kmin) & vmask;
+            const uint32_t HF = core::hf_row_any(H, FL, P.L, P.kmin) & vmask;
             // Decisions that can move the rung: +1 / -1 outside the high-frequency state, and
             // the first round of every high-frequency run (it sets the top; the rest of the
             // run keeps it there, so they are no-ops and are left out)

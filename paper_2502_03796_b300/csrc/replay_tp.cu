@@ -151,9 +151,10 @@ __global__ void __launch_bounds__(TG * CW * 32)
     }
     __syncthreads();
 
-    // per-chunk wait limit (one-slot tiles; the others keep the default, which also keeps
-    // their register allocation where it was measured)
-    const unsigned long long wlim = (CW == 1 && p.chunk_wait_ns) ? p.chunk_wait_ns : tma::kWaitNs;
+    // per-chunk wait limit (the tiles whose warps wait for their stages themselves; the
+    // others keep the default, which also keeps their register allocation where it was
+    // measured)
+    const unsigned long long wlim = (kPipe && p.chunk_wait_ns) ? p.chunk_wait_ns : tma::kWaitNs;
     uint32_t seq = 0;         // chunks loaded by this CTA so far (selects stage and parity)
     int pend[2] = {-1, -1};   // thread 0: parity of an outstanding bulk copy per stage
 

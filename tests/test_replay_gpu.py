@@ -763,19 +763,21 @@ def test_static_baselines_every_rung_every_mode(rp, mg):
         assert runs == 1 and kernels == n_k
 
 
-def test_chunk_wait_timeout_reports_etimedout(mg):
+@pytest.mark.parametrize("tile", [(8, 1), (1, 4)])
+def test_chunk_wait_timeout_reports_etimedout(mg, tile):
     """Failure detection without a fault: a per-chunk wait limit below the copy latency
-    makes the tile kernel's bounded waits run out.  The kernel records MAGUS_ETIMEDOUT, lets
-    the copies in flight land and returns; the status is reported once, and the next call
-    on the same handle with the default limit is exact against the oracle."""
+    makes the tile kernel's bounded waits run out (a one-slot tile, and the grouped tile
+    with four single-warp slots, three of them used).  The kernel records MAGUS_ETIMEDOUT,
+    lets the copies in flight land and returns; the status is reported once, and the next
+    call on the same handle with the default limit is exact against the oracle."""
     model = tracegen.default_model()
     ts = tracegen.batched(64, 40_000, seed=9)
     d = to_device(ts)
-    pols = [tracegen.default_policy()]
+    pols = [tracegen.default_policy()] if tile == (8, 1) else grouped_policies()
     h = mg.Replay(model)
     try:
         h.set_segments(0)
-        h.set_tile(8, 1)
+        h.set_tile(*tile)
         h.set_wait(1)
         seen = False
         for _ in range(3):
@@ -791,7 +793,7 @@ def test_chunk_wait_timeout_reports_etimedout(mg):
         cap = 4000
         out = to_numpy(h.run(d, ts.lengths, pols, log_capacity=cap))
         assert h.status() == 0
-        for p, ref in oracle_pairs(ts, pols, model, pairs=range(0, 64, 7)).items():
+        for p, ref in oracle_pairs(ts, pols, model, pairs=range(0, 64 * len(pols), 7)).items():
             assert_pair(out, p, ref, cap=cap, tag="after a timed-out call")
     finally:
         h.close()
