@@ -585,7 +585,11 @@ int launch_seg_plan(magus_replay *h, const Plan &pl, const uint32_t *traces, con
         rc = make_trace_tmap(traces, total_elems, 32, &tmap, &err);
         if (rc) { set_error(err); return rc; }
     }
-    const int per_sm = seg_max_ctas_per_sm(pl.gp);
+    // the window length every policy group shares, if any (selects a W-specific instance)
+    int window = pl.groups.empty() ? 0 : pl.pols[pl.groups[0].member[0]].W;
+    for (const PolicyGroup &g : pl.groups)
+        if (pl.pols[g.member[0]].W != window) window = 0;
+    const int per_sm = seg_max_ctas_per_sm(pl.gp, window);
     if (per_sm <= 0) {
         set_error("segment kernel does not fit on this device");
         return MAGUS_ECUDA;
@@ -611,7 +615,7 @@ int launch_seg_plan(magus_replay *h, const Plan &pl, const uint32_t *traces, con
     };
     CK(cudaEventRecord(h->k_ev[slot_k].a, stream), "cudaEventRecord");
     if (n_items) {
-        CK(launch_replay_seg(pl.gp, p, tmap, grid, stream), "segment kernel launch");
+        CK(launch_replay_seg(pl.gp, p, tmap, grid, stream, window), "segment kernel launch");
         if ((rc = mark())) return rc;
     }
     const bool any_tp = std::count(pl.tp.begin(), pl.tp.end(), (char)1) > 0;

@@ -169,9 +169,10 @@ struct SegParams {
 constexpr uint64_t kInPlace = ~0ull;
 
 int seg_warps_per_cta();
-int seg_max_ctas_per_sm(int group_size);
+// window: as for the tile kernel (the W every policy group shares, or 0)
+int seg_max_ctas_per_sm(int group_size, int window = 0);
 cudaError_t launch_replay_seg(int group_size, const SegParams &p, const CUtensorMap &tmap, int grid,
-                              cudaStream_t stream);
+                              cudaStream_t stream, int window = 0);
 cudaError_t launch_combine(const SegParams &p, int64_t n_pairs, double *energy, double *edp, double *time,
                            uint64_t *n_changes, uint64_t *change_hash, uint64_t *n_hf, cudaStream_t stream);
 
