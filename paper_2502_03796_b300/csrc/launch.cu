@@ -291,7 +291,11 @@ int launch_ladder_part(magus_replay *h, const Plan &pl, const uint32_t *traces, 
     lp.change_hash = o.change_hash;
     lp.n_hf = o.n_hf;
     lp.state = o.state;
-    const int per_sm = ladder_max_ctas_per_sm();
+    // the window length every one-rung item shares, if any
+    int window = pl.lad.empty() ? 0 : pl.pols[pl.lad[0].pol].W;
+    for (const LadderItem &it : pl.lad)
+        if (pl.pols[it.pol].W != window) window = 0;
+    const int per_sm = ladder_max_ctas_per_sm(window);
     if (per_sm <= 0) {
         set_error("ladder kernel does not fit on this device");
         return MAGUS_ECUDA;
@@ -299,7 +303,7 @@ int launch_ladder_part(magus_replay *h, const Plan &pl, const uint32_t *traces, 
     const size_t ctas = (pl.lad.size() + ladder_warps_per_cta() - 1) / ladder_warps_per_cta();
     const int grid = (int)std::max<size_t>(1, std::min<size_t>(ctas, (size_t)h->sms * per_sm));
     CK(cudaMemsetAsync(h->queue, 0, sizeof(unsigned int), stream), "cudaMemsetAsync");
-    CK(launch_replay_ladder(lp, tmap, grid, stream), "ladder kernel launch");
+    CK(launch_replay_ladder(lp, tmap, grid, stream, window), "ladder kernel launch");
     return MAGUS_OK;
 }
 

@@ -253,8 +253,10 @@ struct LadderParams {
     magus_state_t *state;
 };
 int ladder_warps_per_cta();
-int ladder_max_ctas_per_sm();
-cudaError_t launch_replay_ladder(const LadderParams &p, const CUtensorMap &tmap, int grid, cudaStream_t stream);
+// window: the W every one-rung policy of the call shares, or 0 (selects a W-specific instance)
+int ladder_max_ctas_per_sm(int window = 0);
+cudaError_t launch_replay_ladder(const LadderParams &p, const CUtensorMap &tmap, int grid, cudaStream_t stream,
+                                 int window = 0);
 
 // Host planning (plan.cu).
 // Groups over the policies with include[i] != 0 (all when include is NULL).

@@ -143,21 +143,23 @@ def test_window10_every_kmin(rp, tile):
         assert_pair(out, p, r, cap=cap, tag=f"window10 tile{tile}")
 
 
-@pytest.mark.parametrize("kernel", ["tile", "segments"])
+@pytest.mark.parametrize("kernel", ["tile", "segments", "ladder"])
 @pytest.mark.parametrize("W", [1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 12, 16, 33, 64])
 def test_window_instances(rp, W, kernel):
-    """One policy group per call, so every group shares W: the tile kernel and the segment
-    kernel run their instance for that W where they have one (1-8, 10, 12, 16) and the any-W
+    """One policy group per call, so every group shares W: the tile, segment and one-rung
+    kernels run their instance for that W where they have one (1-8, 10, 12, 16) and the any-W
     instance otherwise; two policies with different W in one call share none."""
     ts = ragged_set(seed=30 + W)
     model = tracegen.default_model()
-    pols = [dict(tracegen.default_policy(), direv_length=W, inc_threshold=0.5 * W, dec_threshold=-0.5 * W)]
+    mode = 1 if kernel == "ladder" else 0
+    pols = [dict(tracegen.default_policy(), direv_length=W, inc_threshold=0.5 * W, dec_threshold=-0.5 * W,
+                 step_mode=mode)]
     if W == 64:
-        pols.append(dict(tracegen.default_policy(), direv_length=5))
+        pols.append(dict(tracegen.default_policy(), direv_length=5, step_mode=mode))
     cap = 40_000
     if kernel == "tile":
         rp.set_tile(4, 1)   # the 4-warp one-slot tile (the automatic one for one policy group)
-    else:
+    elif kernel == "segments":
         rp.set_segments(2048)
     try:
         out = to_numpy(rp.run(to_device(ts), ts.lengths, pols, log_capacity=cap))
