@@ -698,6 +698,50 @@ def test_full_size_batched_workload(rp):
         assert_pair(out, p, r, cap=cap)
 
 
+def _sampled_pairs(n_pairs, k, seed):
+    return sorted(int(x) for x in np.random.default_rng(seed).choice(n_pairs, k, replace=False))
+
+
+def _any_size_properties(out, ts, n_pols, dt):
+    """Bounds that hold for every pair at any size: a round lasts at least dt, changes and
+    high-frequency rounds are at most one per round, energy and EDP are positive."""
+    n = np.repeat(ts.lengths.astype(np.float64), n_pols)
+    assert np.all(out["time_s"] >= n * dt * (1 - 1e-12))
+    assert np.all(out["n_changes"] <= n.astype(np.uint64))
+    assert np.all(out["n_hf"] <= n.astype(np.uint64))
+    assert np.all(out["energy_j"][n > 0] > 0) and np.all(out["edp_js"][n > 0] > 0)
+
+
+def test_full_size_sweep_sampled(rp):
+    """The policy sweep at full size (1,024 traces x 200,000 intervals x 256 policies, the
+    automatic tile, as the benchmark times it): 48 sampled pairs against the oracle, and the
+    any-size bounds on every pair."""
+    ts = tracegen.sweep()
+    pols = tracegen.sweep_policies()
+    model = tracegen.default_model()
+    out = to_numpy(rp.run(to_device(ts), ts.lengths, pols, log_capacity=0))
+    assert rp.status() == 0
+    _any_size_properties(out, ts, len(pols), model["dt_s"])
+    pairs = _sampled_pairs(ts.n_traces * len(pols), 48, seed=5)
+    for p, r in oracle_pairs(ts, pols, model, pairs=pairs, log=False).items():
+        assert_pair(out, p, r, cap=0, tag="full-size sweep")
+
+
+def test_full_size_uneven_sampled(rp):
+    """The uneven-length workload at full size (16,384 traces, 1e3 .. 1e6 intervals, 16
+    policies, 2.35e9 intervals): 32 sampled pairs against the oracle, and the any-size bounds
+    on every pair."""
+    ts = tracegen.uneven(n_traces=16_384, seed=0)
+    pols = tracegen.sweep_policies()[:16]
+    model = tracegen.default_model()
+    out = to_numpy(rp.run(to_device(ts), ts.lengths, pols, log_capacity=0))
+    assert rp.status() == 0
+    _any_size_properties(out, ts, len(pols), model["dt_s"])
+    pairs = _sampled_pairs(ts.n_traces * len(pols), 32, seed=6)
+    for p, r in oracle_pairs(ts, pols, model, pairs=pairs, log=False).items():
+        assert_pair(out, p, r, cap=0, tag="full-size uneven")
+
+
 def test_full_size_static_workload(rp):
     """4,096 traces x 100,000 intervals pinned at each of the 17 rungs, the call
     `bench.py --workload static` times (one static-kernel launch, every trace in parts):
