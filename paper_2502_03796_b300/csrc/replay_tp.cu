@@ -100,7 +100,7 @@ __host__ __device__ constexpr size_t smem_bytes() {
 // threads or six of 128 per SM: the 4-warp tile's shared memory is sized to fit six, which
 // measured 4.5 % faster than five at 88 registers), 96 for the other one-member tiles and for
 // the 4-slot grouped tile of 4 warps (five CTAs of 128 threads: 3 % faster on the policy sweep
-// than four at 128, despite 20 bytes of spill), 128 for the other grouped tiles.  The kernel's
+// than four at 128, despite 8 bytes of spill), 128 for the other grouped tiles.  The kernel's
 // allocation is sensitive: left alone the compiler has taken from 74 to 224 registers for
 // these shapes as the source changed.
 // WK > 0: an instance for policy groups whose window length W is WK (the predictor inline for
