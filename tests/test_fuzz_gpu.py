@@ -132,3 +132,42 @@ def test_random_serving_streams(seed):
                 assert abs(r["energy_j"] - ref["energy_j"]) <= REL_TOL * max(ref["energy_j"], 1e-300)
     finally:
         sv.close()
+
+
+@pytest.mark.parametrize("seed", [21, 22, 23, 24, 25])
+def test_random_grouped_policies(seed):
+    """Random policy groups (members sharing Alg. 1's W, inc, dec; half of them with a
+    10-round tune window, whose counts are bit-sliced and shared) on random lengths, through
+    the automatic tile and each grouped and one-slot tile shape: every pair against the
+    oracle."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2502_03796_b300 import magus
+    rng = np.random.default_rng(seed)
+    model = tracegen.default_model()
+    lengths = rng.integers(0, 30_000, size=7).astype(np.uint64)
+    ts = tracegen.make_traces(lengths, seed=seed, mean_phase=float(rng.uniform(3, 80)))
+    pols = []
+    for _ in range(int(rng.integers(1, 11))):
+        W = int(rng.choice([int(rng.integers(1, 65)), 5, 10]))
+        thr = float(rng.uniform(0.3, 8.0))
+        L = 10 if rng.uniform() < 0.5 else int(rng.integers(1, 65))
+        for _ in range(int(rng.integers(1, 5))):
+            pols.append(dict(inc_threshold=thr, dec_threshold=-thr, direv_length=W, tune_window=L,
+                             high_freq_threshold=float(rng.choice([rng.uniform(0, 1), 0.0, 1.0, 1.2])),
+                             step_mode=0, pin_level=0))
+    order = rng.permutation(len(pols))
+    pols = [pols[i] for i in order]
+    cap = int(rng.choice([0, 40_000]))
+    ref = oracle_pairs(ts, pols, model)
+    rp = magus.Replay(model)
+    try:
+        for tile in ((0, 0), (1, 4), (2, 2), (8, 1), (1, 8), (4, 1)):
+            rp.set_segments(0 if tile != (0, 0) else -1)
+            rp.set_tile(*tile)
+            out = to_numpy(rp.run(to_device(ts), ts.lengths, pols, log_capacity=cap))
+            assert rp.status() == 0
+            for p, r in ref.items():
+                assert_pair(out, p, r, cap=cap, tag=f"seed {seed} tile {tile}")
+    finally:
+        rp.close()
