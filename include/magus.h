@@ -207,8 +207,8 @@ int magus_replay_set_tile(magus_replay_t *h, int32_t time_groups, int32_t policy
 
 /* Kernel choice: seg_rounds > 0 (a multiple of 1024) selects the segment kernel -- every warp
  * replays one (trace, policy group, segment of seg_rounds rounds) on its own, a combine
- * kernel then joins each pair's segments in order; 0 selects the tile kernel (CTAs of 8
- * warps sharing each trace chunk, shaped by magus_replay_set_tile); -1 (the default)
+ * kernel then joins each pair's segments in order; 0 selects the tile kernel (CTAs of 4 or
+ * 8 warps sharing each trace chunk, shaped by magus_replay_set_tile); -1 (the default)
  * restores the automatic choice (the autotuner's pick, else the tile kernel, or the segment
  * kernel with 16,384-round segments when a few long traces would leave SMs idle).  EINVAL
  * otherwise. */
