@@ -191,7 +191,10 @@ __device__ __forceinline__ void row_predict_fast(uint32_t base, int lane, int W,
     amax = mx;
 }
 
-template <int S, int WC = 0, bool kChunked = false>
+// kCoopSM: the top-capacity test by the whole warp, one row at a time, for the rows that need
+// it (the tile kernel's one-member groups and the one-rung kernel: 1.2 % and 3.4 % faster;
+// the segment kernel measured 12 % slower this way and keeps the per-lane pass).
+template <int S, int WC = 0, bool kChunked = false, bool kCoopSM = false>
 __device__ __forceinline__ bool row_predict_fast_dispatch(uint32_t base, int lane, const DevPolicy &P,
                                                           const DevModel &M, RowPred &r, uint32_t (&v)[32]) {
     uint32_t UPr = 0, DNr = 0, S0r = 0, band, amax;
@@ -207,7 +210,17 @@ __device__ __forceinline__ bool row_predict_fast_dispatch(uint32_t base, int lan
     r.DN = __brev(DNr);
     r.S0 = __brev(S0r);
     r.SM = 0;
-    if (__any_sync(FULL, amax > M.thrM)) {
+    if constexpr (kCoopSM) {
+        // rows holding a delta above the top capacity are rare (a lane or two per warp where
+        // any): lane j tests element j of such a row, and the ballot is the row's mask
+        uint32_t need = __ballot_sync(FULL, amax > M.thrM);
+        while (need) {
+            const int L = __ffs(need) - 1;
+            need &= need - 1;
+            const uint32_t bits = __ballot_sync(FULL, lds32(swz_elem(base, 32 * L + lane)) > M.thrM);
+            if (lane == L) r.SM = bits;
+        }
+    } else if (__any_sync(FULL, amax > M.thrM)) {
         if constexpr (kChunked) load_row(base, lane, v);
         uint32_t SMr = 0;
         const int32_t tm = clamp_thr(M.thrM);
@@ -223,26 +236,26 @@ __device__ __forceinline__ bool row_predict_fast_dispatch(uint32_t base, int lan
 // WC > 0: W = WC, known at compile time.  Otherwise kSpecW: the common window lengths take
 // the compile-time-W path through a switch per row (more code per kernel, so only kernels
 // with one policy per slot use it; grouped tiles keep the run-time path).
-template <int WC = -1, bool kSpecW = false>
+template <int WC = -1, bool kSpecW = false, bool kCoopSM = false>
 __device__ __forceinline__ RowPred row_predict(uint32_t base, int lane, const DevPolicy &P, const DevModel &M,
                                                uint32_t vmask, uint32_t pmask) {
     RowPred r;
     uint32_t v[32];
     bool ok = false;
     if constexpr (WC > 0) {
-        ok = row_predict_fast_dispatch<(-WC) & 3, WC, true>(base, lane, P, M, r, v);
+        ok = row_predict_fast_dispatch<(-WC) & 3, WC, true, kCoopSM>(base, lane, P, M, r, v);
     } else switch (kSpecW ? P.W : 0) {
 #define MAGUS_PRED_W(w) \
-        case w: ok = row_predict_fast_dispatch<(-(w)) & 3, w>(base, lane, P, M, r, v); break;
+        case w: ok = row_predict_fast_dispatch<(-(w)) & 3, w, false, kCoopSM>(base, lane, P, M, r, v); break;
         MAGUS_PRED_W(1) MAGUS_PRED_W(2) MAGUS_PRED_W(3) MAGUS_PRED_W(4) MAGUS_PRED_W(5) MAGUS_PRED_W(6)
         MAGUS_PRED_W(7) MAGUS_PRED_W(8) MAGUS_PRED_W(10) MAGUS_PRED_W(12) MAGUS_PRED_W(16)
 #undef MAGUS_PRED_W
         default:
             switch ((-P.W) & 3) {
-                case 0: ok = row_predict_fast_dispatch<0>(base, lane, P, M, r, v); break;
-                case 1: ok = row_predict_fast_dispatch<1>(base, lane, P, M, r, v); break;
-                case 2: ok = row_predict_fast_dispatch<2>(base, lane, P, M, r, v); break;
-                default: ok = row_predict_fast_dispatch<3>(base, lane, P, M, r, v); break;
+                case 0: ok = row_predict_fast_dispatch<0, 0, false, kCoopSM>(base, lane, P, M, r, v); break;
+                case 1: ok = row_predict_fast_dispatch<1, 0, false, kCoopSM>(base, lane, P, M, r, v); break;
+                case 2: ok = row_predict_fast_dispatch<2, 0, false, kCoopSM>(base, lane, P, M, r, v); break;
+                default: ok = row_predict_fast_dispatch<3, 0, false, kCoopSM>(base, lane, P, M, r, v); break;
             }
     }
     r.fast = ok;

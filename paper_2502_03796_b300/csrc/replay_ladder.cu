@@ -183,7 +183,7 @@ __global__ void __launch_bounds__(LW * 32) replay_ladder_kernel(const LadderPara
             const int64_t left = (int64_t)n - (int64_t)r0;
             const uint32_t vmask = core::valid_mask(left);
             const uint32_t pmask = core::predict_mask(vmask, n_seen0 + r0, P.W);
-            const core::RowPred rp = core::row_predict<(WK > 0 ? WK : -1)>(base, lane, P, M, vmask, pmask);
+            const core::RowPred rp = core::row_predict<(WK > 0 ? WK : -1), false, true>(base, lane, P, M, vmask, pmask);
             const uint32_t FL = rp.UP | rp.DN;
             const uint64_t H = core::row_history(FL, tailH, lane);
             const uint32_t HF = core::hf_row_any(H, FL, P.L, P.kmin) & vmask;

@@ -322,7 +322,7 @@ __global__ void __launch_bounds__(TG * CW * 32)
             const int64_t left = interior ? (int64_t)CH : (int64_t)n - r0;
             const uint32_t vmask = interior ? FULL : core::valid_mask(left);
             const uint32_t pmask = interior ? FULL : core::predict_mask(vmask, n_seen0 + (uint64_t)r0, P.W);
-            const core::RowPred rp = core::row_predict<(WK > 0 ? WK : -1), GP == 1>(sub, lane, P, M, vmask, pmask);
+            const core::RowPred rp = core::row_predict<(WK > 0 ? WK : -1), GP == 1, GP == 1>(sub, lane, P, M, vmask, pmask);
             const uint32_t UP = rp.UP, DN = rp.DN;
             const uint32_t FL = UP | DN;   // uncore_tune_ls entries of the row
             {
