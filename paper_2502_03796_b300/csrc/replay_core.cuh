@@ -173,7 +173,11 @@ __device__ __forceinline__ void row_predict_fast(uint32_t base, int lane, int W,
     uint32_t bd = 0xffffffffu, mx = 0;
 #pragma unroll
     for (int k = 0; k < 32; k++) {
-        if (kChunked && (k & 3) == 0) lds128(swz_chunk(base, lane, k >> 2), v[k], v[k + 1], v[k + 2], v[k + 3]);
+        // (each chunk's load one chunk ahead of its use: 0.4 % faster than at its use, and
+        // than two ahead)
+        if (kChunked && k == 0) lds128(swz_chunk(base, lane, 0), v[0], v[1], v[2], v[3]);
+        if (kChunked && (k & 3) == 0 && k + 4 < 32)
+            lds128(swz_chunk(base, lane, (k >> 2) + 1), v[k + 4], v[k + 5], v[k + 6], v[k + 7]);
         const uint32_t a = v[k];
         uint32_t b;
         if constexpr (WC > 0) b = k < WC ? u[k + S] : v[k - WC];
