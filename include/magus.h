@@ -278,10 +278,12 @@ int magus_replay_close(magus_replay_t *h);
  *     trace and 8 B per trace for every block of up to 8 policy groups) are rejected with
  *     EINVAL and a message.
  *   - The first call on a device looks up the array's device address (set-up, once per
- *     device); make that first call before any stream capture on that device.
+ *     device).
  *   - The call is synchronous: it uploads the plan on `stream` from pageable host memory,
  *     zeroes the work counter and status word, runs the kernel, waits for `stream` and
- *     reads the status word back before returning.
+ *     reads the status word back before returning.  None of that may be captured, so no
+ *     call (the first or any later one) may be made while any stream on the device is
+ *     being captured.
  *   - Every call shares the one array, so sequential calls are safe, but calls that overlap
  *     on the GPU (other threads or streams at the same time) race on the scratch and give
  *     wrong results.
