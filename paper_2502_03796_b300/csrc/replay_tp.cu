@@ -437,18 +437,29 @@ __global__ void __launch_bounds__(TG * CW * 32)
                     const uint64_t row0 = n_seen0 + (uint64_t)c * CH + (uint64_t)g * SB;
                     bool staged = false;
                     if (can_stage) {
+                        // this lane's slot among the warp's changes: with at most 3 per
+                        // row (nearly every sub-block) two ballots give it, bit by bit of the
+                        // count (0.4 % faster than the shuffle scan, which takes the rest)
                         const uint32_t nch = __popc(CHG);
-                        uint32_t incl = nch;
+                        uint32_t excl, total;
+                        if (__all_sync(FULL, nch < 4u)) {
+                            const uint32_t b0 = __ballot_sync(FULL, nch & 1u), b1 = __ballot_sync(FULL, nch & 2u);
+                            excl = __popc(b0 & lanemask_lt) + 2u * __popc(b1 & lanemask_lt);
+                            total = __popc(b0) + 2u * __popc(b1);
+                        } else {
+                            uint32_t incl = nch;
 #pragma unroll
-                        for (int d = 1; d < 32; d <<= 1) {
-                            const uint32_t t = __shfl_up_sync(FULL, incl, d);
-                            if (lane >= d) incl += t;
+                            for (int d = 1; d < 32; d <<= 1) {
+                                const uint32_t t = __shfl_up_sync(FULL, incl, d);
+                                if (lane >= d) incl += t;
+                            }
+                            excl = incl - nch;
+                            total = __shfl_sync(FULL, incl, 31);
                         }
-                        const uint32_t total = __shfl_sync(FULL, incl, 31);
                         if (total <= 32) {
                             core::Staged *tab = sh.stage[GP == 1 ? warp : 0];
                             core::stage_changes(CHG, Lv, (uint32_t)row0, (uint32_t)(cr.count + before), tab, pending,
-                                                incl - nch, lane);
+                                                excl, lane);
                             pending += total;
                             if (pending >= 32) {
                                 __syncwarp();
