@@ -326,8 +326,14 @@ __global__ void __launch_bounds__(TG * CW * 32)
             const uint32_t UP = rp.UP, DN = rp.DN;
             const uint32_t FL = UP | DN;   // uncore_tune_ls entries of the row
             {
-                const uint32_t f30 = __shfl_sync(FULL, FL, 30), f31 = __shfl_sync(FULL, FL, 31);
-                if (lane == 0) sh.xf[cw][g] = (uint64_t)f30 | ((uint64_t)f31 << 32);
+                // (one-member tiles: lanes 30 and 31 store their own words, 0.8 % faster on the
+                // batched replay; the grouped tiles measured 0.4 .. 0.8 % slower that way)
+                if constexpr (GP == 1) {
+                    if (lane >= 30) core::sts32(smem_u32(&sh.xf[cw][g]) + 4u * (uint32_t)(lane - 30), FL);
+                } else {
+                    const uint32_t f30 = __shfl_sync(FULL, FL, 30), f31 = __shfl_sync(FULL, FL, 31);
+                    if (lane == 0) sh.xf[cw][g] = (uint64_t)f30 | ((uint64_t)f31 << 32);
+                }
             }
             if (TG > 1) group_sync(1 + cw, TG * 32); else __syncwarp();
             const uint64_t tailH = (g == 0) ? sh.hist[cw][c & 1] : sh.xf[cw][g > 0 ? g - 1 : 0];
@@ -370,27 +376,33 @@ __global__ void __launch_bounds__(TG * CW * 32)
                 const uint32_t SET0 = DN & ~HF & act;
                 const uint32_t EV = SETM | SET0;
                 const bool has = EV != 0;
-                const uint32_t exitv = has ? (SETM >> (31 - __clz(EV))) & 1u : 0u;
-                const uint32_t firstv = has ? (SETM >> (__ffs(EV) - 1)) & 1u : 0u;
+                // SETM and SET0 are disjoint: the row's last event sets the top exactly when
+                // SETM's highest bit lies above SET0's (SETM > SET0), its first event exactly
+                // when SETM holds the lowest bit of EV; the same holds for lane masks
+                const uint32_t exitv = SETM > SET0 ? 1u : 0u;
+                const uint32_t firstv = (SETM & (0u - EV)) != 0u ? 1u : 0u;
                 const uint32_t bev = __ballot_sync(FULL, has), bex = __ballot_sync(FULL, exitv);
                 const uint32_t prior = bev & lanemask_lt;
-                const uint32_t cin_prior = prior ? (bex >> (31 - __clz(prior))) & 1u : 0u;
+                const uint32_t pex = bex & lanemask_lt;   // earlier event rows that exit at the top
+                const uint32_t cin_prior = pex > (prior ^ pex) ? 1u : 0u;
                 {
                     // changes that do not depend on the level entering the sub-block: rows
                     // after the first event row are fixed; the first event row is counted as
                     // if it entered at its own first event's level (no change at that event)
                     uint32_t det = 0;
-                    if (prior || has) {
+                    if (GP == 1 || prior || has) {
+                        // (branch-free in one-member tiles, -0.2 %: a row with no event so far
+                        // latches its entering level, so it counts no change either way)
                         const uint32_t ca = prior ? cin_prior : firstv;
                         const uint32_t lm = core::latch_row(SETM, SET0, ca);
                         det = __popc((lm ^ ((lm << 1) | ca)) & vmask);
                     }
                     const uint32_t wdet = __reduce_add_sync(FULL, det);
-                    const int fl_lane = bev ? __ffs(bev) - 1 : 0;
-                    const uint32_t wfirst = __shfl_sync(FULL, firstv, fl_lane);
+                    const uint32_t bfi = __ballot_sync(FULL, firstv);
                     if (lane == 0) {
                         const uint32_t whas = bev != 0;
-                        const uint32_t wexit = whas ? (bex >> (31 - __clz(bev))) & 1u : 0u;
+                        const uint32_t wfirst = (bfi & (0u - bev)) != 0u ? 1u : 0u;
+                        const uint32_t wexit = bex > (bev ^ bex) ? 1u : 0u;
                         sh.xs[cw][m][g] = whas | (wexit << 1) | (wfirst << 2) | (wdet << 3);
                     }
                 }
@@ -409,11 +421,12 @@ __global__ void __launch_bounds__(TG * CW * 32)
                     const uint32_t sv_i = lane < TG ? sh.xs[cw][m][lane] : 0u;
                     const uint32_t hasb = __ballot_sync(FULL, sv_i & 1u), exb = __ballot_sync(FULL, (sv_i >> 1) & 1u);
                     const uint32_t prior_i = hasb & lanemask_lt;
-                    const uint32_t lin_i = prior_i ? (exb >> (31 - __clz(prior_i))) & 1u : cr.level;
+                    const uint32_t pex_i = exb & lanemask_lt;
+                    const uint32_t lin_i = prior_i ? (pex_i > (prior_i ^ pex_i) ? 1u : 0u) : cr.level;
                     const uint32_t add_i = (sv_i & 1u) ? (sv_i >> 3) + ((((sv_i >> 2) & 1u) != lin_i) ? 1u : 0u) : 0u;
                     before = __reduce_add_sync(FULL, lane < g ? add_i : 0u);
-                    const uint32_t prior_g = hasb & ((1u << g) - 1u);
-                    if (prior_g) wcin = (exb >> (31 - __clz(prior_g))) & 1u;
+                    const uint32_t prior_g = hasb & ((1u << g) - 1u), pex_g = exb & ((1u << g) - 1u);
+                    if (prior_g) wcin = pex_g > (prior_g ^ pex_g) ? 1u : 0u;
                 } else {
                     for (int gg = 0; gg < g; gg++) {
                         const uint32_t sv = sh.xs[cw][m][gg];
