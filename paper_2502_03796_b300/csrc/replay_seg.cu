@@ -206,11 +206,14 @@ __global__ void __launch_bounds__(SEG_WARPS * 32) replay_seg_kernel(const SegPar
                 const uint32_t SET0 = DN & ~HF & act;
                 const uint32_t EV = SETM | SET0;
                 const bool has = EV != 0;
-                const uint32_t exitv = has ? (SETM >> (31 - __clz(EV))) & 1u : 0u;
-                const uint32_t firstv = has ? (SETM >> (__ffs(EV) - 1)) & 1u : 0u;
+                // disjoint masks: the last event sets the top exactly when SETM > SET0, the
+                // first exactly when SETM holds EV's lowest bit (no bit scans)
+                const uint32_t exitv = SETM > SET0 ? 1u : 0u;
+                const uint32_t firstv = (SETM & (0u - EV)) != 0u ? 1u : 0u;
                 const uint32_t bev = __ballot_sync(FULL, has), bex = __ballot_sync(FULL, exitv);
                 const uint32_t prior = bev & lanemask_lt;
-                const uint32_t cin_prior = prior ? (bex >> (31 - __clz(prior))) & 1u : 0u;
+                const uint32_t pex = bex & lanemask_lt;
+                const uint32_t cin_prior = pex > (prior ^ pex) ? 1u : 0u;
                 acc[m].hf += __popc(HF);
                 uint32_t cin, PM = 0;                // PM: rounds at the unknown entering level
                 if (run[m].known) {
@@ -260,7 +263,7 @@ __global__ void __launch_bounds__(SEG_WARPS * 32) replay_seg_kernel(const SegPar
                 }
                 if (bev) {
                     run[m].known = 1u;
-                    run[m].level = (bex >> (31 - __clz(bev))) & 1u;
+                    run[m].level = bex > (bev ^ bex) ? 1u : 0u;
                 }
                 // flags and deltas after the trace's last round (the combine kernel stores
                 // them with the final level)

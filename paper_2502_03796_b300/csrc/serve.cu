@@ -122,10 +122,12 @@ __global__ void __launch_bounds__(SERVE_WARPS * 32) serve_kernel(const ServePara
             const uint32_t SET0 = rp.DN & ~HF & act;
             const uint32_t EV = SETM | SET0;
             const bool has = EV != 0;
-            const uint32_t exitv = has ? (SETM >> (31 - __clz(EV))) & 1u : 0u;
+            // disjoint masks: the last event sets the top exactly when SETM > SET0
+            const uint32_t exitv = SETM > SET0 ? 1u : 0u;
             const uint32_t bev = __ballot_sync(FULL, has), bex = __ballot_sync(FULL, exitv);
             const uint32_t prior = bev & lanemask_lt;
-            const uint32_t cin = prior ? (bex >> (31 - __clz(prior))) & 1u : level;
+            const uint32_t pex = bex & lanemask_lt;
+            const uint32_t cin = prior ? (pex > (prior ^ pex) ? 1u : 0u) : level;
             const uint32_t Lm = latch_row(SETM, SET0, cin);
             const uint32_t Flev = (Lm << 1) | cin;
             const uint32_t CHG = (Lm ^ Flev) & vmask;
@@ -145,7 +147,7 @@ __global__ void __launch_bounds__(SERVE_WARPS * 32) serve_kernel(const ServePara
             // carry into the next sub-block
             const uint32_t fl30 = __shfl_sync(FULL, FL, 30), fl31 = __shfl_sync(FULL, FL, 31);
             tailH = (uint64_t)fl30 | ((uint64_t)fl31 << 32);
-            if (bev) level = (bex >> (31 - __clz(bev))) & 1u;
+            if (bev) level = bex > (bev ^ bex) ? 1u : 0u;
         }
         __syncwarp();
         const uint32_t n0 = __reduce_add_sync(FULL, acc.n0), nm = __reduce_add_sync(FULL, acc.nm);
