@@ -206,7 +206,8 @@ __device__ __forceinline__ bool row_predict_fast_dispatch(uint32_t base, int lan
                             clamp_thr(M.thr0), UPr, DNr, S0r, band, amax, v);
     // every delta of the sub-block is some lane's row element; the 64 before it (rows -1, -2)
     // are checked here: the fast path needs all of them below 2^30
-    const uint32_t h0 = lds32(swz_elem(base, lane - 64)), h1 = lds32(swz_elem(base, lane - 32));
+    // (with W known at compile time only row -1 is read: W + S <= 32)
+    const uint32_t h0 = WC > 0 ? 0u : lds32(swz_elem(base, lane - 64)), h1 = lds32(swz_elem(base, lane - 32));
     const uint32_t hx = max(max(h0, h1), amax);
     // fall back when a delta reaches 2^30 or a round lies in a decision band
     if (__any_sync(FULL, hx >= (uint32_t)kFastLimit || band <= 5u)) return false;

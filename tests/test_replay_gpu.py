@@ -172,6 +172,41 @@ def test_window_instances(rp, W, kernel):
         assert_pair(out, p, r, cap=cap, tag=f"W={W} {kernel}")
 
 
+@pytest.mark.parametrize("kernel", ["tile", "segments", "ladder"])
+@pytest.mark.parametrize("W", [1, 3, 5, 8, 16])
+def test_fast_limit_in_window_before_sub_block(rp, W, kernel):
+    """A delta at or above 2^30 among the W rounds just before a 1,024-round sub-block (the
+    row before it, whose deltas the sub-block's first row reads as the values W rounds
+    earlier) must send that sub-block to the exact path: placed before sub-block and chunk
+    starts, one placement per trace, against the oracle."""
+    n = 12 * 1024 + 77
+    cases = [(k, j, v) for k in (1, 2, 3, 4, 5, 8, 9) for j in sorted({1, (W + 1) // 2, W})
+             for v in (2**30, 2**31 + 7, 2**32 - 5)]
+    ts = tracegen.make_traces(np.full(len(cases), n, dtype=np.uint64), seed=70 + W, mean_phase=20.0)
+    data = np.array(ts.data, copy=True)
+    for i, (k, j, v) in enumerate(cases):
+        data[int(ts.offsets[i]) + 1024 * k - j] = v
+    ts = tracegen.TraceSet(lengths=ts.lengths, offsets=ts.offsets, data=data)
+    model = tracegen.default_model()
+    mode = 1 if kernel == "ladder" else 0
+    pols = [dict(tracegen.default_policy(), direv_length=W, inc_threshold=0.5 * W, dec_threshold=-0.5 * W,
+                 step_mode=mode)]
+    cap = 20_000
+    if kernel == "tile":
+        rp.set_tile(4, 1)
+    elif kernel == "segments":
+        rp.set_segments(2048)
+    try:
+        out = to_numpy(rp.run(to_device(ts), ts.lengths, pols, log_capacity=cap))
+    finally:
+        rp.set_tile(0, 0)
+        rp.set_segments(-1)
+    assert rp.status() == 0
+    ref = oracle_pairs(ts, pols, model)
+    for p, r in ref.items():
+        assert_pair(out, p, r, cap=cap, tag=f"W={W} {kernel} case {cases[p]}")
+
+
 def test_autotune_picks_a_tile(rp):
     ts = tracegen.sweep(n_traces=8, n=30_000, seed=2)
     pols = tracegen.sweep_policies()[:32]
