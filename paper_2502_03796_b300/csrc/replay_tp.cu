@@ -256,6 +256,20 @@ __global__ void __launch_bounds__(TG * CW * 32)
         // demand past two CTAs per SM, which cost more than it saved)
         const bool can_stage = GP == 1 && n_seen0 + n < (1ull << 31);
         uint32_t pending = 0;   // entries waiting in this warp's table
+        // one-member groups: the constants of count4_ge for this item's kmin, formed once
+        uint32_t kA0 = 0, kA1 = 0, kA2 = 0, kA3 = 0, kAll = 0;
+        if (GP == 1) {
+            const int km = Km[0];
+            if (km <= 0) {
+                kAll = FULL;
+            } else if (km <= 10) {
+                const uint32_t a = 16u - (uint32_t)km;
+                kA0 = 0u - (a & 1u);
+                kA1 = 0u - ((a >> 1) & 1u);
+                kA2 = 0u - ((a >> 2) & 1u);
+                kA3 = 0u - ((a >> 3) & 1u);
+            }
+        }
 
         for (uint32_t c = 0; c < nchunks; c++) {
             const uint32_t sq = seq + c;
@@ -368,8 +382,15 @@ __global__ void __launch_bounds__(TG * CW * 32)
                 } else {
                     // the 10-round tune window bit-sliced (measured 1.5 % faster on the batched
                     // replay than the byte-parallel counts, which serve every other length)
-                    HFr = (Lm[m] & 0xff) == 10 ? core::count4_ge(core::window10_counts(H, FL), Km[m])
-                                               : core::hf_row(H, FL, Lm[m] & 0xff, Km[m]);
+                    if ((Lm[m] & 0xff) == 10) {
+                        const core::Count4 c4 = core::window10_counts(H, FL);
+                        uint32_t cy = c4.c0 & kA0;
+                        cy = core::maj3(c4.c1, cy, kA1);
+                        cy = core::maj3(c4.c2, cy, kA2);
+                        HFr = core::maj3(c4.c3, cy, kA3) | kAll;
+                    } else {
+                        HFr = core::hf_row(H, FL, Lm[m] & 0xff, Km[m]);
+                    }
                 }
                 const uint32_t HF = HFr & vmask & act;
                 const uint32_t SETM = (HF | UP) & act;
