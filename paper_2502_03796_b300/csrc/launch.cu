@@ -676,10 +676,15 @@ static int launch_closed_mode(magus_replay *h, const Plan &pl, int mode, const s
     const int n_traces = (int)pl.lengths.size();
     const int n_cls = (int)cls.size();
     const bool ladder = mode == 1;
-    int wmax = 1;
-    for (int32_t c : cls) wmax = std::max(wmax, pl.pols[c].W);
+    int wmax = 1, wmin = 1 << 30;
+    for (int32_t c : cls) {
+        wmax = std::max(wmax, pl.pols[c].W);
+        wmin = std::min(wmin, pl.pols[c].W);
+    }
     uint32_t ring = 1;
     while ((int)ring < wmax) ring <<= 1;
+    // jump mode, every policy with the same W: the first-replay kernel's instance for that W
+    const int window = (!ladder && wmin == wmax) ? closed_window(wmax) : 0;
     // Every thread replays one segment (plus its burn-in) one round after another, so a
     // launch lasts about (waves of threads) x (segment + burn-in rounds).  Automatic choice:
     // for each wave count w, the shortest segment whose items fit w waves of resident
@@ -695,7 +700,8 @@ static int launch_closed_mode(magus_replay *h, const Plan &pl, int mode, const s
     if (h->cls_seg > 0) {
         G = burn_of(S);
     } else {
-        uint64_t key = 1469598103934665603ull ^ ((uint64_t)n_cls << 32) ^ ring ^ ((uint64_t)h->cls_burn << 48);
+        uint64_t key = 1469598103934665603ull ^ ((uint64_t)n_cls << 32) ^ ring ^ ((uint64_t)h->cls_burn << 48) ^
+                       ((uint64_t)window << 24);
         uint64_t longest = 0;
         for (uint64_t n : pl.lengths) {
             key = (key ^ n) * 1099511628211ull;
@@ -705,7 +711,7 @@ static int launch_closed_mode(magus_replay *h, const Plan &pl, int mode, const s
             S = h->cls_auto_seg[mode];
             G = h->cls_auto_burn[mode];
         } else {
-            const int ctas = closed_max_ctas_per_sm(ring, ladder, h->dm.K);
+            const int ctas = closed_max_ctas_per_sm(ring, ladder, h->dm.K, window);
             const uint64_t resident = (uint64_t)h->sms * std::max(ctas, 1) * closed_threads_per_cta();
             auto items_of = [&](uint64_t L) {
                 uint64_t it = 0;
@@ -797,6 +803,7 @@ static int launch_closed_mode(magus_replay *h, const Plan &pl, int mode, const s
     cp.thr = (const ClosedThr *)(buf + sz_cls);
     cp.n_cls = n_cls;
     cp.ring = ring;
+    cp.window = window;
     cp.ibase = (const uint64_t *)(buf + sz_cls + sz_thr);
     cp.n_items = items;
     cp.seg_len = (uint32_t)S;

@@ -36,6 +36,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "replay_closed.h"
 #include "replay_core.cuh"
 
@@ -361,6 +363,52 @@ __device__ __forceinline__ void run_rounds(const uint32_t *tr, uint64_t t0, uint
     }
 }
 
+// Rounds [t0, t1) in jump mode with W = WK known at compile time: the deltas W rounds back
+// come from a register window of the last WK + 4 deltas instead of the shared-memory ring
+// (no ring stores, no slot addresses), and the level W rounds back is a fixed bit of the level
+// history.  Same alignment as run_rounds; x has been started.
+template <int WK, bool kCount, class Emit>
+__device__ __forceinline__ void run_rounds_w(const uint32_t *tr, uint64_t t0, uint64_t t1, Replay<false> &x,
+                                             const DevPolicy *Pg, const ClosedThr *Cg, const DevModel &M,
+                                             Emit emit) {
+    const DevPolicy P = *Pg;
+    const uint32_t nr = (uint32_t)(t1 - t0);
+    const uint32_t warm = t0 < (uint64_t)WK ? (uint32_t)(WK - t0) : 0u;   // rounds before the FIFO holds W + 1
+    // w[i]: the delta of round t - WK + i, t the first round of the group of four in hand
+    uint32_t w[WK + 4];
+#pragma unroll
+    for (int i = 0; i < WK; i++) w[i] = t0 + i >= (uint64_t)WK ? __ldg(tr + t0 + i - WK) : 0u;
+    // a group of four rounds; kEdge: the trace's first rounds (FIFO filling) or the last,
+    // partial group (rounds past t1 are left out; the packed layout pads every trace to a
+    // multiple of 32 deltas, so the 16-byte load stays inside it)
+    auto group = [&](uint32_t j, auto edge) {
+        constexpr bool kEdge = decltype(edge)::value;
+        const uint4 v = __ldg(reinterpret_cast<const uint4 *>(tr + t0 + j));
+        w[WK] = v.x;
+        w[WK + 1] = v.y;
+        w[WK + 2] = v.z;
+        w[WK + 3] = v.w;
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            if (kEdge && j + k >= nr) break;
+            const uint32_t lb = (uint32_t)(x.s.lvh >> (WK - 1)) & 1u;
+            x.template step<kCount, kEdge>(w[WK + k], w[k], lb, j + (uint32_t)k, t0, warm, P, Pg, Cg, M, emit);
+        }
+#pragma unroll
+        for (int i = 0; i < WK; i++) w[i] = w[i + 4];
+    };
+    uint32_t j = 0;
+#pragma unroll 1
+    for (; j < nr && j < warm; j += 4u) group(j, std::true_type{});
+#pragma unroll 1
+    for (; j + 4u <= nr; j += 4u) group(j, std::false_type{});
+    if (j < nr) group(j, std::true_type{});
+    if (kCount) {
+        x.flush(M);
+        x.finish(M);
+    }
+}
+
 // Rounds [t0, t1) replayed twice in lockstep: x (charged, entries emitted) and y (charged,
 // no entries: it repeats an earlier replay) until their states agree, checked every 8
 // rounds -- the level, the levels of the last W rounds and all 64 flags (the carried state
@@ -481,7 +529,9 @@ __device__ __forceinline__ CAcc acc_add_diff(const CAcc &x, const ClosedSlot &r,
 // Pass 1: the first replay of every segment.  Pass 2: a second replay where pass 1 started
 // from a state other than its predecessor's end state.  Separate kernels, so that the
 // lockstep replay of pass 2 does not raise the register count of pass 1.
-template <bool kL, int kPass>
+// WK > 0 (jump mode, first pass): every policy of the call has W = WK, and the rounds run from
+// a register window (run_rounds_w) without the shared-memory ring.
+template <bool kL, int kPass, int WK = 0>
 __device__ __forceinline__ void closed_pass(const ClosedParams &p) {
     extern __shared__ uint32_t ring_s[];
     const uint64_t item = (uint64_t)blockIdx.x * kThreads + threadIdx.x;
@@ -511,15 +561,23 @@ __device__ __forceinline__ void closed_pass(const ClosedParams &p) {
             st = initial_state<kL>(p, pair);
             ok |= 2u;   // started from the true state
         }
-        prefill(tr, t0, ring);
-        if (kL) hist_to_ring(x.lr, t0, nullptr, W);
-        x.start(st, t0, *Pg, C, M);
-        run_rounds<kL, false>(tr, t0, s0, x, Pg, C, M, ring, NoEmit{});
-        // the start state goes out now (fewer live registers through the segment)
-        store_in(out, x.s);
-        if (kL) ring_to_hist(x.lr, s0, slot_hist(p, 0, item, 0), W);
-        x.start(x.s, s0, *Pg, C, M);
-        run_rounds<kL, true>(tr, s0, s1, x, Pg, C, M, ring, em);
+        if constexpr (!kL && WK > 0) {
+            x.start(st, t0, *Pg, C, M);
+            run_rounds_w<WK, false>(tr, t0, s0, x, Pg, C, M, NoEmit{});
+            store_in(out, x.s);
+            x.start(x.s, s0, *Pg, C, M);
+            run_rounds_w<WK, true>(tr, s0, s1, x, Pg, C, M, em);
+        } else {
+            prefill(tr, t0, ring);
+            if (kL) hist_to_ring(x.lr, t0, nullptr, W);
+            x.start(st, t0, *Pg, C, M);
+            run_rounds<kL, false>(tr, t0, s0, x, Pg, C, M, ring, NoEmit{});
+            // the start state goes out now (fewer live registers through the segment)
+            store_in(out, x.s);
+            if (kL) ring_to_hist(x.lr, s0, slot_hist(p, 0, item, 0), W);
+            x.start(x.s, s0, *Pg, C, M);
+            run_rounds<kL, true>(tr, s0, s1, x, Pg, C, M, ring, em);
+        }
         if (logging && x.acc.nch > p.scr_cap) ok |= 4u;   // entries lost: the log pass writes them
         store_counts(out, x.acc);
         if (kL) ring_to_hist(x.lr, s1, slot_hist(p, 0, item, 1), W);
@@ -587,9 +645,9 @@ __device__ __forceinline__ void closed_pass(const ClosedParams &p) {
         store_out(out, end, 1u | ((logging && lost) ? 4u : 0u));
     }
 }
-template <bool kL>
+template <bool kL, int WK = 0>
 __global__ void __launch_bounds__(kThreads, 5) closed_first_kernel(const ClosedParams p) {
-    closed_pass<kL, 1>(p);
+    closed_pass<kL, 1, WK>(p);
 }
 template <bool kL>
 __global__ void __launch_bounds__(kThreads) closed_second_kernel(const ClosedParams p) {
@@ -780,19 +838,44 @@ size_t smem_of(uint32_t ring, int replays, int K) {
     return (size_t)ring * kThreads * sizeof(uint32_t) + (kL ? (size_t)replays * rung_block_bytes(ring, K) : 0);
 }
 
+// window lengths with their own first-replay kernel (jump mode)
+#define MAGUS_CLOSED_WINDOWS(X) X(1) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(10) X(12) X(16)
+
+// the first-replay kernel for ClosedParams::window: its W instance (no shared memory) or the
+// any-W kernel with the delta ring (smem bytes)
+template <bool kL, int WK>
+cudaError_t launch_first_t(const ClosedParams &p, size_t smem, unsigned grid, cudaStream_t stream) {
+    const size_t sm = WK > 0 ? 0 : smem;
+    cudaError_t e = cudaFuncSetAttribute(closed_first_kernel<kL, WK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    closed_first_kernel<kL, WK><<<grid, kThreads, sm, stream>>>(p);
+    return cudaGetLastError();
+}
+template <bool kL>
+cudaError_t launch_first(const ClosedParams &p, size_t smem, unsigned grid, cudaStream_t stream) {
+    if constexpr (!kL) {
+        switch (p.window) {
+#define MAGUS_CLOSED_LAUNCH_W(w) \
+            case w: return launch_first_t<false, w>(p, smem, grid, stream);
+            MAGUS_CLOSED_WINDOWS(MAGUS_CLOSED_LAUNCH_W)
+#undef MAGUS_CLOSED_LAUNCH_W
+            default: break;
+        }
+    }
+    return launch_first_t<kL, 0>(p, smem, grid, stream);
+}
+
 template <bool kL>
 cudaError_t launch_t(const ClosedParams &p, cudaStream_t stream) {
     const size_t sm1 = smem_of<kL>(p.ring, 1, p.model.K), sm2 = smem_of<kL>(p.ring, 2, p.model.K);
     cudaError_t e;
-    if ((e = cudaFuncSetAttribute(closed_first_kernel<kL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1)) ||
-        (e = cudaFuncSetAttribute(closed_second_kernel<kL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2)) ||
+    if ((e = cudaFuncSetAttribute(closed_second_kernel<kL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2)) ||
         (e = cudaFuncSetAttribute(closed_final_kernel<kL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2)) ||
         (e = cudaFuncSetAttribute(closed_log_kernel<kL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1)))
         return e;
     if (p.n_items) {
         const uint64_t grid = (p.n_items + kThreads - 1) / kThreads;
-        closed_first_kernel<kL><<<(unsigned)grid, kThreads, sm1, stream>>>(p);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if ((e = launch_first<kL>(p, sm1, (unsigned)grid, stream)) != cudaSuccess) return e;
         closed_second_kernel<kL><<<(unsigned)grid, kThreads, sm2, stream>>>(p);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
@@ -808,13 +891,14 @@ cudaError_t launch_t(const ClosedParams &p, cudaStream_t stream) {
     return cudaSuccess;
 }
 
-template <bool kL>
+template <bool kL, int WK>
 int max_ctas_t(uint32_t ring, int K) {
     int blocks = 0;
-    const size_t smem = smem_of<kL>(ring, 1, K);
-    if (cudaFuncSetAttribute(closed_first_kernel<kL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+    const size_t smem = WK > 0 ? 0 : smem_of<kL>(ring, 1, K);
+    if (cudaFuncSetAttribute(closed_first_kernel<kL, WK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
             cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, closed_first_kernel<kL>, kThreads, smem) != cudaSuccess) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, closed_first_kernel<kL, WK>, kThreads, smem) !=
+            cudaSuccess) {
         cudaGetLastError();
         return 0;
     }
@@ -825,8 +909,25 @@ int max_ctas_t(uint32_t ring, int K) {
 
 int closed_threads_per_cta() { return kThreads; }
 
-int closed_max_ctas_per_sm(uint32_t ring, bool ladder, int n_levels) {
-    return ladder ? max_ctas_t<true>(ring, n_levels) : max_ctas_t<false>(ring, n_levels);
+int closed_window(int W) {
+    switch (W) {
+#define MAGUS_CLOSED_HAS_W(w) \
+        case w: return w;
+        MAGUS_CLOSED_WINDOWS(MAGUS_CLOSED_HAS_W)
+#undef MAGUS_CLOSED_HAS_W
+        default: return 0;
+    }
+}
+
+int closed_max_ctas_per_sm(uint32_t ring, bool ladder, int n_levels, int window) {
+    if (ladder) return max_ctas_t<true, 0>(ring, n_levels);
+    switch (window) {
+#define MAGUS_CLOSED_OCC_W(w) \
+        case w: return max_ctas_t<false, w>(ring, n_levels);
+        MAGUS_CLOSED_WINDOWS(MAGUS_CLOSED_OCC_W)
+#undef MAGUS_CLOSED_OCC_W
+        default: return max_ctas_t<false, 0>(ring, n_levels);
+    }
 }
 
 cudaError_t launch_replay_closed(const ClosedParams &p, bool ladder, cudaStream_t stream) {
