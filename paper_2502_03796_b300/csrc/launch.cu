@@ -683,8 +683,8 @@ static int launch_closed_mode(magus_replay *h, const Plan &pl, int mode, const s
     }
     uint32_t ring = 1;
     while ((int)ring < wmax) ring <<= 1;
-    // jump mode, every policy with the same W: the first-replay kernel's instance for that W
-    const int window = (!ladder && wmin == wmax) ? closed_window(wmax) : 0;
+    // every policy with the same W: the first-replay kernel's instance for that W
+    const int window = wmin == wmax ? closed_window(wmax) : 0;
     // Every thread replays one segment (plus its burn-in) one round after another, so a
     // launch lasts about (waves of threads) x (segment + burn-in rounds).  Automatic choice:
     // for each wave count w, the shortest segment whose items fit w waves of resident

@@ -363,12 +363,13 @@ __device__ __forceinline__ void run_rounds(const uint32_t *tr, uint64_t t0, uint
     }
 }
 
-// Rounds [t0, t1) in jump mode with W = WK known at compile time: the deltas W rounds back
-// come from a register window of the last WK + 4 deltas instead of the shared-memory ring
-// (no ring stores, no slot addresses), and the level W rounds back is a fixed bit of the level
-// history.  Same alignment as run_rounds; x has been started.
-template <int WK, bool kCount, class Emit>
-__device__ __forceinline__ void run_rounds_w(const uint32_t *tr, uint64_t t0, uint64_t t1, Replay<false> &x,
+// Rounds [t0, t1) with W = WK known at compile time: the deltas W rounds back come from a
+// register window of the last WK + 4 deltas instead of the shared-memory ring (no ring
+// stores, no slot addresses).  The level W rounds back: jump mode, a fixed bit of the level
+// history; one rung per decision, the rung ring as in run_rounds.  Same alignment as
+// run_rounds; x has been started.
+template <bool kL, int WK, bool kCount, class Emit>
+__device__ __forceinline__ void run_rounds_w(const uint32_t *tr, uint64_t t0, uint64_t t1, Replay<kL> &x,
                                              const DevPolicy *Pg, const ClosedThr *Cg, const DevModel &M,
                                              Emit emit) {
     const DevPolicy P = *Pg;
@@ -378,6 +379,14 @@ __device__ __forceinline__ void run_rounds_w(const uint32_t *tr, uint64_t t0, ui
     uint32_t w[WK + 4];
 #pragma unroll
     for (int i = 0; i < WK; i++) w[i] = t0 + i >= (uint64_t)WK ? __ldg(tr + t0 + i - WK) : 0u;
+    // one-rung mode: the rung of round t - W fetched a round ahead, as in run_rounds
+    uint32_t lbn = kL ? x.level_back(t0, WK) : 0u;
+    auto lb_of = [&](uint32_t jj) -> uint32_t {
+        if (!kL) return (uint32_t)(x.s.lvh >> (WK - 1)) & 1u;
+        const uint32_t lb = lbn;
+        lbn = WK == 1 ? x.s.lv : (uint32_t)x.lr.at(t0 + jj + 1u - WK);
+        return lb;
+    };
     // a group of four rounds; kEdge: the trace's first rounds (FIFO filling) or the last,
     // partial group (rounds past t1 are left out; the packed layout pads every trace to a
     // multiple of 32 deltas, so the 16-byte load stays inside it)
@@ -391,7 +400,7 @@ __device__ __forceinline__ void run_rounds_w(const uint32_t *tr, uint64_t t0, ui
 #pragma unroll
         for (int k = 0; k < 4; k++) {
             if (kEdge && j + k >= nr) break;
-            const uint32_t lb = (uint32_t)(x.s.lvh >> (WK - 1)) & 1u;
+            const uint32_t lb = lb_of(j + (uint32_t)k);
             x.template step<kCount, kEdge>(w[WK + k], w[k], lb, j + (uint32_t)k, t0, warm, P, Pg, Cg, M, emit);
         }
 #pragma unroll
@@ -529,8 +538,8 @@ __device__ __forceinline__ CAcc acc_add_diff(const CAcc &x, const ClosedSlot &r,
 // Pass 1: the first replay of every segment.  Pass 2: a second replay where pass 1 started
 // from a state other than its predecessor's end state.  Separate kernels, so that the
 // lockstep replay of pass 2 does not raise the register count of pass 1.
-// WK > 0 (jump mode, first pass): every policy of the call has W = WK, and the rounds run from
-// a register window (run_rounds_w) without the shared-memory ring.
+// WK > 0 (first pass): every policy of the call has W = WK, and the rounds run from a register
+// window of deltas (run_rounds_w) without the shared-memory delta ring.
 template <bool kL, int kPass, int WK = 0>
 __device__ __forceinline__ void closed_pass(const ClosedParams &p) {
     extern __shared__ uint32_t ring_s[];
@@ -561,12 +570,14 @@ __device__ __forceinline__ void closed_pass(const ClosedParams &p) {
             st = initial_state<kL>(p, pair);
             ok |= 2u;   // started from the true state
         }
-        if constexpr (!kL && WK > 0) {
+        if constexpr (WK > 0) {
+            if (kL) hist_to_ring(x.lr, t0, nullptr, W);
             x.start(st, t0, *Pg, C, M);
-            run_rounds_w<WK, false>(tr, t0, s0, x, Pg, C, M, NoEmit{});
+            run_rounds_w<kL, WK, false>(tr, t0, s0, x, Pg, C, M, NoEmit{});
             store_in(out, x.s);
+            if (kL) ring_to_hist(x.lr, s0, slot_hist(p, 0, item, 0), W);
             x.start(x.s, s0, *Pg, C, M);
-            run_rounds_w<WK, true>(tr, s0, s1, x, Pg, C, M, em);
+            run_rounds_w<kL, WK, true>(tr, s0, s1, x, Pg, C, M, em);
         } else {
             prefill(tr, t0, ring);
             if (kL) hist_to_ring(x.lr, t0, nullptr, W);
@@ -845,7 +856,7 @@ size_t smem_of(uint32_t ring, int replays, int K) {
 // any-W kernel with the delta ring (smem bytes)
 template <bool kL, int WK>
 cudaError_t launch_first_t(const ClosedParams &p, size_t smem, unsigned grid, cudaStream_t stream) {
-    const size_t sm = WK > 0 ? 0 : smem;
+    const size_t sm = (WK > 0 && !kL) ? 0 : smem;   // one rung per decision keeps its rung block
     cudaError_t e = cudaFuncSetAttribute(closed_first_kernel<kL, WK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     closed_first_kernel<kL, WK><<<grid, kThreads, sm, stream>>>(p);
@@ -853,16 +864,13 @@ cudaError_t launch_first_t(const ClosedParams &p, size_t smem, unsigned grid, cu
 }
 template <bool kL>
 cudaError_t launch_first(const ClosedParams &p, size_t smem, unsigned grid, cudaStream_t stream) {
-    if constexpr (!kL) {
-        switch (p.window) {
+    switch (p.window) {
 #define MAGUS_CLOSED_LAUNCH_W(w) \
-            case w: return launch_first_t<false, w>(p, smem, grid, stream);
-            MAGUS_CLOSED_WINDOWS(MAGUS_CLOSED_LAUNCH_W)
+        case w: return launch_first_t<kL, w>(p, smem, grid, stream);
+        MAGUS_CLOSED_WINDOWS(MAGUS_CLOSED_LAUNCH_W)
 #undef MAGUS_CLOSED_LAUNCH_W
-            default: break;
-        }
+        default: return launch_first_t<kL, 0>(p, smem, grid, stream);
     }
-    return launch_first_t<kL, 0>(p, smem, grid, stream);
 }
 
 template <bool kL>
@@ -894,7 +902,7 @@ cudaError_t launch_t(const ClosedParams &p, cudaStream_t stream) {
 template <bool kL, int WK>
 int max_ctas_t(uint32_t ring, int K) {
     int blocks = 0;
-    const size_t smem = WK > 0 ? 0 : smem_of<kL>(ring, 1, K);
+    const size_t smem = (WK > 0 && !kL) ? 0 : smem_of<kL>(ring, 1, K);
     if (cudaFuncSetAttribute(closed_first_kernel<kL, WK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
             cudaSuccess ||
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, closed_first_kernel<kL, WK>, kThreads, smem) !=
@@ -919,15 +927,19 @@ int closed_window(int W) {
     }
 }
 
-int closed_max_ctas_per_sm(uint32_t ring, bool ladder, int n_levels, int window) {
-    if (ladder) return max_ctas_t<true, 0>(ring, n_levels);
+template <bool kL>
+int max_ctas_w(uint32_t ring, int K, int window) {
     switch (window) {
 #define MAGUS_CLOSED_OCC_W(w) \
-        case w: return max_ctas_t<false, w>(ring, n_levels);
+        case w: return max_ctas_t<kL, w>(ring, K);
         MAGUS_CLOSED_WINDOWS(MAGUS_CLOSED_OCC_W)
 #undef MAGUS_CLOSED_OCC_W
-        default: return max_ctas_t<false, 0>(ring, n_levels);
+        default: return max_ctas_t<kL, 0>(ring, K);
     }
+}
+
+int closed_max_ctas_per_sm(uint32_t ring, bool ladder, int n_levels, int window) {
+    return ladder ? max_ctas_w<true>(ring, n_levels, window) : max_ctas_w<false>(ring, n_levels, window);
 }
 
 cudaError_t launch_replay_closed(const ClosedParams &p, bool ladder, cudaStream_t stream) {

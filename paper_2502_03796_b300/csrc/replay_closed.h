@@ -57,8 +57,8 @@ struct ClosedParams {
     const int32_t *cls;          // [n_cls] policy indices replayed here
     int32_t n_cls;
     uint32_t ring;               // deltas kept per thread (a power of two >= every W)
-    int32_t window;              // jump mode: the W every policy of the call shares where the
-                                 // first-replay kernel has an instance for it, else 0
+    int32_t window;              // the W every policy of the call shares where the first-replay
+                                 // kernel has an instance for it, else 0
     const uint64_t *ibase;       // [n_traces + 1]: first item of each trace
     uint64_t n_items;            // items: (trace, policy, segment), segments innermost
     uint32_t seg_len;            // rounds per segment (a multiple of 64)
@@ -84,7 +84,7 @@ __host__ __device__ inline bool closed_policy(const DevPolicy &d) {
 // ladder: levels 0 .. K-1 (one-rung mode), else bottom and top (jump mode).
 void derive_closed(const DevPolicy &pol, const DevModel &m, bool ladder, ClosedThr *out);
 int closed_threads_per_cta();
-// W itself where the first-replay kernel has an instance for it (jump mode), else 0
+// W itself where the first-replay kernel has an instance for it, else 0
 int closed_window(int W);
 // resident CTAs of the first-replay kernel (window: as ClosedParams::window)
 int closed_max_ctas_per_sm(uint32_t ring, bool ladder, int n_levels, int window);

@@ -80,14 +80,15 @@ def test_closed_loop_matches_oracle(rp, seg, burn):
         assert items == 0
 
 
+@pytest.mark.parametrize("step_mode", [2, 3])
 @pytest.mark.parametrize("W", [1, 2, 3, 4, 5, 8, 9, 12, 16])
-def test_closed_loop_window_instances(rp, W):
-    """Jump mode with every policy of the call at one W: the first-replay kernel runs its
-    instance for that W (1-8, 10, 12, 16; 9 takes the any-W kernel), with ragged lengths,
-    failed guesses (64-round segments, no burn-in) and the automatic segments."""
+def test_closed_loop_window_instances(rp, W, step_mode):
+    """Every policy of the call at one W: the first-replay kernel runs its instance for that W
+    (1-8, 10, 12, 16; 9 takes the any-W kernel), both step modes, with ragged lengths, failed
+    guesses (64-round segments, no burn-in) and the automatic segments."""
     ts = ragged()
     model = tracegen.default_model()
-    base = dict(tracegen.default_policy(), step_mode=2, direv_length=W)
+    base = dict(tracegen.default_policy(), step_mode=step_mode, direv_length=W)
     pols = [base, dict(base, inc_threshold=0.5 * W, dec_threshold=-0.5 * W, high_freq_threshold=0.3),
             dict(base, tune_window=33, high_freq_threshold=0.5)]
     ref = oracle_pairs(ts, pols, model)
@@ -96,7 +97,7 @@ def test_closed_loop_window_instances(rp, W):
         out = to_numpy(rp.run(to_device(ts), ts.lengths, pols, log_capacity=40_000))
         assert rp.status() == 0
         for p, r in ref.items():
-            assert_pair(out, p, r, cap=40_000, tag=f"closed W={W} seg={seg} burn={burn}")
+            assert_pair(out, p, r, cap=40_000, tag=f"closed mode={step_mode} W={W} seg={seg} burn={burn}")
 
 
 def test_closed_loop_entry_scratch_overflow(rp):
