@@ -171,3 +171,38 @@ def test_random_grouped_policies(seed):
                 assert_pair(out, p, r, cap=cap, tag=f"seed {seed} tile {tile}")
     finally:
         rp.close()
+
+
+@pytest.mark.parametrize("seed", [41, 42, 43, 44, 45, 46])
+def test_random_one_window_calls(seed):
+    """Random policies of every mode that all share one W (drawn from the lengths with kernel
+    instances and a few without), so the tile, segment, one-rung and closed-loop first-replay
+    kernels run their instance for that W: random lengths, automatic and forced closed-loop
+    segments (64 rounds, no burn-in: most guesses wrong), every pair against the oracle."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2502_03796_b300 import magus
+    rng = np.random.default_rng(seed)
+    model = tracegen.default_model()
+    K = len(model["f_ghz"])
+    W = int(rng.choice([1, 2, 3, 4, 5, 6, 7, 8, 10, 12, 16, 9, 24]))
+    lengths = rng.integers(0, 30_000, size=6).astype(np.uint64)
+    ts = tracegen.make_traces(lengths, seed=seed, mean_phase=float(rng.uniform(3, 80)))
+    pols = []
+    for _ in range(int(rng.integers(1, 5))):
+        p = random_policy(rng, K)
+        p.update(direv_length=W, pin_level=0, step_mode=int(rng.choice([0, 1, 2, 3, 2, 3])))
+        pols.append(p)
+    cap = int(rng.choice([0, 17, 40_000]))
+    ref = oracle_pairs(ts, pols, model)
+    rp = magus.Replay(model)
+    try:
+        for seg, burn in ((0, -1), (256, 64), (64, 0)):
+            rp.set_closed(seg, burn)
+            out = to_numpy(rp.run(to_device(ts) if ts.data.size else torch.zeros(4, dtype=torch.int32, device="cuda"),
+                                  ts.lengths, pols, log_capacity=cap))
+            assert rp.status() == 0
+            for p, r in ref.items():
+                assert_pair(out, p, r, cap=cap, tag=f"seed {seed} W {W} closed {seg},{burn}")
+    finally:
+        rp.close()
