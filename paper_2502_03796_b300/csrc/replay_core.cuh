@@ -370,8 +370,8 @@ __device__ __forceinline__ uint32_t count4_ge(const Count4 &c, int kmin) {
 }
 
 // Algorithm 2 for any window length: the bit-sliced form for 10 rounds, else byte counts
-// (the one-rung kernel: 1.7 % faster on 4,096 x 100,000; the segment kernel measured 3 %
-// slower with it and keeps the byte counts)
+// (the one-rung kernel: 1.7 % faster on 4,096 x 100,000; the segment kernel 3.4 % on
+// 16 x 4,000,000 once the threshold became a carry chain)
 __device__ __forceinline__ uint32_t hf_row_any(uint64_t H, uint32_t FL, int L, int kmin) {
     return L == 10 ? count4_ge(window10_counts(H, FL), kmin) : hf_row(H, FL, L, kmin);
 }

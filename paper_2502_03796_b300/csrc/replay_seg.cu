@@ -201,7 +201,7 @@ __global__ void __launch_bounds__(SEG_WARPS * 32) replay_seg_kernel(const SegPar
 #pragma unroll 1
             for (int m = 0; m < (GP == 1 ? 1 : cnt); m++) {
                 const uint32_t act = (Lm[m] & 0x100) ? 0u : FULL;
-                const uint32_t HF = core::hf_row(H, FL, Lm[m] & 0xff, Km[m]) & vmask & act;
+                const uint32_t HF = core::hf_row_any(H, FL, Lm[m] & 0xff, Km[m]) & vmask & act;
                 const uint32_t SETM = (HF | UP) & act;
                 const uint32_t SET0 = DN & ~HF & act;
                 const uint32_t EV = SETM | SET0;
