@@ -70,6 +70,9 @@ struct Shared {
     uint64_t hist[CW][2];             // flags of the 64 rounds before the chunk (by parity)
     uint32_t xs[CW][GP][TG];          // sub-block summary: has | exit<<1 | first<<2 | nch<<3
     MemberCarry carry[CW][GP][2];     // per member, double-buffered by chunk parity
+    // grouped tiles: each member's count4_ge constants for its kmin (A0..A3, and all-ones
+    // when kmin <= 0), formed once per item
+    uint32_t kmask[GP > 1 ? CW : 1][GP > 1 ? GP : 1][6];
     unsigned long long red_s0[TG * CW][GP], red_sm[TG * CW][GP], red_hash[TG * CW][GP];
     uint32_t red_n0[TG * CW][GP], red_nm[TG * CW][GP], red_hf[TG * CW][GP];
     // per warp, one-member groups only: change-log entries waiting for a full warp's worth
@@ -205,6 +208,16 @@ __global__ void __launch_bounds__(TG * CW * 32)
                 c0.level = lv ? 1u : 0u;
                 c0.pad = 0;
                 sh.carry[cw][m][0] = c0;
+                if constexpr (GP > 1) {
+                    const int km = Km[m];
+                    const uint32_t a = (km > 0 && km <= 10) ? 16u - (uint32_t)km : 0u;
+                    sh.kmask[cw][m][0] = 0u - (a & 1u);
+                    sh.kmask[cw][m][1] = 0u - ((a >> 1) & 1u);
+                    sh.kmask[cw][m][2] = 0u - ((a >> 2) & 1u);
+                    sh.kmask[cw][m][3] = 0u - ((a >> 3) & 1u);
+                    sh.kmask[cw][m][4] = km <= 0 ? FULL : 0u;
+                    sh.kmask[cw][m][5] = (Lm[m] & 0x100) ? 0u : FULL;   // controlled (not a pin)
+                }
             }
         }
         // Deltas before the first chunk (the first pair's carried history), rows -2, -1.
@@ -374,11 +387,18 @@ __global__ void __launch_bounds__(TG * CW * 32)
 #pragma unroll 1
             for (int m = 0; m < (GP == 1 ? 1 : cnt); m++) {
                 // ------------------------------------------------------------ phase B
-                const uint32_t act = (Lm[m] & 0x100) ? 0u : FULL;
+                const uint32_t act = GP > 1 ? sh.kmask[GP > 1 ? cw : 0][GP > 1 ? m : 0][5] : ((Lm[m] & 0x100) ? 0u : FULL);
                 uint32_t HFr;
                 if constexpr (GP > 1) {
-                    HFr = sliced10 ? core::count4_ge(core::Count4{hw[0], hw[1], hw[2], hw[3]}, Km[m])
-                        : shared_counts ? core::hf_from_counts(hw, Km[m]) : core::hf_row(H, FL, Lm[m] & 0xff, Km[m]);
+                    if (sliced10) {
+                        const uint32_t *km = sh.kmask[GP > 1 ? cw : 0][GP > 1 ? m : 0];
+                        uint32_t cy = hw[0] & km[0];
+                        cy = core::maj3(hw[1], cy, km[1]);
+                        cy = core::maj3(hw[2], cy, km[2]);
+                        HFr = core::maj3(hw[3], cy, km[3]) | km[4];
+                    } else {
+                        HFr = shared_counts ? core::hf_from_counts(hw, Km[m]) : core::hf_row(H, FL, Lm[m] & 0xff, Km[m]);
+                    }
                 } else {
                     // the 10-round tune window bit-sliced (measured 1.5 % faster on the batched
                     // replay than the byte-parallel counts, which serve every other length)
