@@ -72,7 +72,7 @@ struct Shared {
     MemberCarry carry[CW][GP][2];     // per member, double-buffered by chunk parity
     // grouped tiles: each member's count4_ge constants for its kmin (A0..A3, and all-ones
     // when kmin <= 0), formed once per item
-    uint32_t kmask[GP > 1 ? CW : 1][GP > 1 ? GP : 1][6];
+    uint32_t kmask[GP > 1 ? CW : 1][GP > 1 ? GP : 1][7];
     unsigned long long red_s0[TG * CW][GP], red_sm[TG * CW][GP], red_hash[TG * CW][GP];
     uint32_t red_n0[TG * CW][GP], red_nm[TG * CW][GP], red_hf[TG * CW][GP];
     // per warp, one-member groups only: change-log entries waiting for a full warp's worth
@@ -217,6 +217,7 @@ __global__ void __launch_bounds__(TG * CW * 32)
                     sh.kmask[cw][m][3] = 0u - ((a >> 3) & 1u);
                     sh.kmask[cw][m][4] = km <= 0 ? FULL : 0u;
                     sh.kmask[cw][m][5] = (Lm[m] & 0x100) ? 0u : FULL;   // controlled (not a pin)
+                    sh.kmask[cw][m][6] = (uint32_t)G.member[m];         // its policy index
                 }
             }
         }
@@ -484,7 +485,7 @@ __global__ void __launch_bounds__(TG * CW * 32)
 
                 core::row_energy<true>(sub, lane, Flev, rp, vmask, acc[m]);
                 acc[m].hf += __popc(HF);
-                const int64_t pair = pbase + G.member[m];
+                const int64_t pair = pbase + (GP > 1 ? (int)sh.kmask[GP > 1 ? cw : 0][GP > 1 ? m : 0][6] : G.member[0]);
                 // frequency-change log
                 uint32_t *const log_pair = p.log_entries ? p.log_entries + (uint64_t)pair * p.log_cap : nullptr;
                 if (__any_sync(FULL, CHG != 0)) {
